@@ -1,0 +1,153 @@
+"""Pins of the oracle's transport loop (CPU only): closed-form laws the
+stepping must reproduce, exact energy conservation, and scheduling
+independence."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_17608_gb300 import workloads as wl
+
+
+def slab_problem(thickness, material, processes, **kw):
+    base = dict(materials=[material], layer_material=[0], layer_thickness=[thickness], n_periods=1,
+                half_x=1e6, half_y=1e6, Bz=0.0, cut_track=0.01, cut_moller=1.0, cut_brems=1.0,
+                processes=processes, tally_mode=wl.TALLY_LAYERS, n_zbins=0, n_slots=1024, init_capacity=4096)
+    base.update(kw)
+    return wl.Problem(**base)
+
+
+@pytest.mark.parametrize("E", [0.1, 1.0, 10.0])
+def test_uncollided_transmission(E):
+    """Fraction of photons crossing 10 cm of water without interacting is
+    exp(-mu(E) * 10), mu from the oracle's own table lookup."""
+    w = oracle.World(slab_problem(10.0, wl.WATER, wl.PHOTON_PROCS))
+    n = 100000
+    prim = wl.make_primaries(np.full(n, E), np.zeros((n, 3)), np.tile([0, 0, 1.0], (n, 1)),
+                             np.zeros(n, np.int32), np.zeros(n, np.uint32))
+    hist, _ = w.run(prim, with_edep=False)
+    uncollided = (hist["steps"] == 1) & (hist["escaped"] == E)
+    mu = sum(w.lookup(0, c, E) for c in (oracle.COL_COMPTON, oracle.COL_PE, oracle.COL_PAIR))
+    p = math.exp(-mu * 10.0)
+    sigma = math.sqrt(p * (1 - p) / n)
+    assert abs(uncollided.mean() - p) < 4 * sigma
+
+
+def check_conservation(prob, prim, rel=1e-12):
+    w = oracle.World(prob)
+    hist, edep = w.run(prim)
+    per_primary = edep.sum(1) + hist["escaped"]
+    np.testing.assert_allclose(per_primary, prim["E"], rtol=rel)
+    for ev in np.unique(prim["event"]):
+        m = prim["event"] == ev
+        tot = edep[m].sum() + hist["escaped"][m].sum()
+        assert tot == pytest.approx(prim["E"][m].sum(), rel=rel)
+    return hist, edep
+
+
+def test_energy_conservation_water_cube():
+    hist, edep = check_conservation(wl.water_cube_problem(), wl.water_cube_primaries())
+    assert hist["steps"].sum() > 20000
+    # only pair production makes secondaries (two 511 keV photons)
+    assert np.all(hist["secondaries"] % 2 == 0)
+
+
+def test_energy_conservation_calorimeter():
+    prob, prim = wl.calorimeter_1gev(40)
+    hist, edep = check_conservation(prob, prim)
+    assert np.all(hist["secondaries"] > 0)
+
+
+def test_energy_conservation_field():
+    prob, prim = wl.calorimeter_field_10gev(6)
+    check_conservation(prob, prim)
+
+
+def test_energy_conservation_event_mix():
+    events = wl.offload_events(4)
+    prim = wl.concat_primaries(events)[:600]
+    prob = wl.calorimeter_problem(65536, Bz=4.0, max_events=4)
+    check_conservation(prob, prim)
+
+
+def test_oracle_results_do_not_depend_on_threads():
+    prob, prim = wl.calorimeter_1gev(64)
+    w = oracle.World(prob)
+    h1, e1 = w.run(prim, n_threads=1)
+    h8, e8 = w.run(prim, n_threads=8)
+    np.testing.assert_array_equal(h1, h8)
+    np.testing.assert_array_equal(e1, e8)
+
+
+def test_brems_only_mean_energy_law():
+    """Discrete 1/k brems only (no continuous loss): between emissions T is
+    constant, so the mean energy after depth x obeys
+    d<T>/dx = -(<T> - k_cut)/X0, i.e. <T(x)> = k_cut + (T0 - k_cut) e^{-x/X0}
+    (up to the tiny probability of falling below k_cut)."""
+    X0, T0, kcut = 0.56, 1000.0, 1.0
+    mat = wl.Material("Pb-like", Z=82, A=207.2, rho=11.35, ne=0.0, X0=X0, I=823e-6)
+    for x_over in (0.5, 1.0, 2.0):
+        w = oracle.World(slab_problem(x_over * X0, mat, wl.PROC_BREMS, cut_track=1e-3))
+        n = 20000
+        Ts = np.empty(n)
+        n_killed = 0
+        for i in range(n):
+            r = w.transport_track(T0, (0.0, 0.0, 0.0), (0.0, 0.0, 1.0), wl.ELECTRON, tid=i)
+            # leaves through the back face, unless a photon took (almost) all of T
+            assert r["status"] in (0, 1)
+            Ts[i] = r["E"]
+            assert r["dir"] == (0.0, 0.0, 1.0)
+            n_killed += r["status"] == 0
+        assert n_killed < 0.01 * n
+        expect = kcut + (T0 - kcut) * math.exp(-x_over)
+        assert abs(Ts.mean() - expect) < 4 * Ts.std() / math.sqrt(n) + 1e-3 * expect
+
+
+def test_csda_path_matches_range_table():
+    """Continuous loss only: the path travelled until the energy drops below the
+    tracking cut equals R(E0) - R(E_final) from the range table."""
+    prob = slab_problem(1e4, wl.LAR, wl.PROC_ELOSS, cut_track=0.1)
+    w = oracle.World(prob)
+    for E0 in (0.5, 3.0, 40.0, 900.0):
+        r = w.transport_track(E0, (0.0, 0.0, 0.0), (0.0, 0.0, 1.0), wl.ELECTRON)
+        assert r["status"] == 0
+        Ef = r["E"]
+        assert Ef < 0.1
+        R0 = w.lookup(0, oracle.COL_RANGE, E0)
+        Rf = w.lookup(0, oracle.COL_RANGE, Ef) if Ef > 1e-3 else 0.0
+        if Ef > 1e-3:
+            assert r["path"] == pytest.approx(R0 - Rf, rel=1e-9)
+        else:
+            assert R0 - w.table(0, oracle.COL_RANGE)[0] <= r["path"] <= R0 * (1 + 1e-12)
+        assert r["edep"] == pytest.approx(E0, rel=1e-13)
+        # range-limited steps shrink geometrically: 0.2 R per step above 0.1 cm
+        assert r["steps"] >= 1
+
+
+def test_escape_and_boundary_bookkeeping():
+    """A photon with all processes off crosses every layer without interacting
+    and escapes with its full energy after one step per layer."""
+    prob = wl.calorimeter_problem(processes=0)
+    w = oracle.World(prob)
+    r = w.transport_track(5.0, (1.0, 2.0, 0.0), (0.0, 0.0, 1.0), wl.GAMMA)
+    assert r["status"] == 1
+    assert r["steps"] == prob.n_layers_total
+    assert r["escaped"] == 5.0
+    assert r["path"] == pytest.approx(28.0, rel=1e-12)
+    # oblique photon leaves through a side plane
+    d = np.array([0.9, 0.0, math.sqrt(1 - 0.81)])
+    r = w.transport_track(5.0, (0.0, 0.0, 0.0), tuple(d), wl.GAMMA)
+    assert r["status"] == 1
+    assert r["pos"][0] == pytest.approx(50.0, rel=1e-12)
+
+
+def test_tally_bins_water_cube():
+    prob = wl.water_cube_problem()
+    w = oracle.World(prob)
+    prim = wl.water_cube_primaries(300)
+    hist, edep = w.run(prim)
+    assert edep.shape == (300, 100)
+    prof = edep.sum(0)
+    # 10 MeV photons along +z deposit mostly downstream of the entry face
+    assert prof[:50].sum() > prof[50:].sum() > 0
