@@ -1,0 +1,249 @@
+/*
+ * celer_gb -- step-based electromagnetic Monte Carlo transport on one GB300.
+ *
+ * C ABI of the library. The method is the step-based ("per-action") stepping
+ * loop of Sec. 2 of Lund et al., "Accelerating detector simulations with
+ * Celeritas: profiling and performance optimizations" (arXiv:2503.17608):
+ * active tracks live in a structure-of-arrays slot store, each step iteration
+ * first fills vacant slots from a buffer of track initializers, then applies
+ * one action at a time (step limit, propagation, discrete interaction) to
+ * all tracks as separate kernel launches; secondaries go back into the
+ * initializer buffer. Sec. 3.1 adds reordering of track-slot indices by
+ * action so that each action kernel sees tracks doing the same thing; here
+ * that reordering is a stable radix partition, and each action kernel runs
+ * over one contiguous range of the partition.
+ *
+ * Conventions for every entry point:
+ *   - the return value is a celer_status; no call aborts, traps or exits;
+ *   - device work is ordered on the CUDA stream given in celer_problem;
+ *     calls that return data to the host synchronise that stream only;
+ *   - the context owns all device memory and all pinned host staging
+ *     memory it allocates in celer_create; the caller owns every host array
+ *     it passes and may reuse it as soon as the call returns;
+ *   - a context is not thread safe: one host thread at a time;
+ *   - after CELER_ERR_CUDA the context must be destroyed; after any other
+ *     error it stays usable.
+ *
+ * Units: MeV, cm, tesla, g/cm3.
+ */
+#ifndef CELER_GB_H
+#define CELER_GB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CELER_OK = 0,
+  CELER_ERR_INVALID = 1,   /* bad argument; nothing was changed */
+  CELER_ERR_CAPACITY = 2,  /* a fixed-size buffer would overflow; state is intact */
+  CELER_ERR_CUDA = 3,      /* a CUDA call failed; destroy the context */
+  CELER_ERR_TIMEOUT = 4,   /* the iteration limit was reached; state is intact */
+  CELER_ERR_STATE = 5      /* call not allowed in the current state */
+} celer_status;
+
+/* particle types (the "particle type" field of the track state, Sec. 2) */
+enum { CELER_GAMMA = 0, CELER_ELECTRON = 1, CELER_POSITRON = 2 };
+
+/* process bitmask */
+enum {
+  CELER_PROC_COMPTON = 1,
+  CELER_PROC_PHOTOELECTRIC = 2,
+  CELER_PROC_PAIR = 4,
+  CELER_PROC_MOLLER = 8,
+  CELER_PROC_BREMS = 16,
+  CELER_PROC_ELOSS = 32
+};
+
+/* tally layouts: uniform z bins over the world, or one bin per layer */
+enum { CELER_TALLY_ZBINS = 0, CELER_TALLY_LAYERS = 1 };
+
+/* Track-reordering policies (Sec. 3.1, "Reindexing track slots"):
+ *   NONE        every action kernel runs over all slots and masks the tracks
+ *               that do not take part (Sec. 2, "masking");
+ *   ACTION      slot indices are partitioned by along-step action (neutral
+ *               straight line vs charged), the key the paper found best;
+ *   ACTION_TYPE slot indices are partitioned by (particle type, next action),
+ *               so every along-step and interaction kernel runs over one
+ *               contiguous range. */
+enum { CELER_SORT_NONE = 0, CELER_SORT_ACTION = 1, CELER_SORT_ACTION_TYPE = 2 };
+
+typedef struct {
+  double Z;       /* atomic number (effective Z for a compound) */
+  double A;       /* g/mol; unused when ne > 0 */
+  double rho;     /* g/cm3 */
+  double ne;      /* electrons / cm3; 0: derived as N_A rho Z / A */
+  double X0;      /* radiation length, cm */
+  double I;       /* mean excitation energy, MeV */
+} celer_material;
+
+typedef struct {
+  int n_materials;
+  const celer_material* materials;   /* host, n_materials entries; copied */
+  int n_layers;                      /* slabs in one period along z */
+  const int* layer_material;         /* host, n_layers; material index per slab */
+  const double* layer_thickness;     /* host, n_layers; cm, > 0 */
+  int n_periods;                     /* the period is repeated this many times from z = 0 */
+  double half_x, half_y;             /* transverse half-widths of the world, cm */
+  double Bz;                         /* uniform field along z, tesla (0: none) */
+  double cut_track;                  /* tracking cut, all particles, MeV (>= 1 keV) */
+  double cut_moller;                 /* delta-ray production cut, MeV */
+  double cut_brems;                  /* bremsstrahlung photon production cut, MeV */
+  int processes;                     /* CELER_PROC_* bitmask */
+  int tally_mode;                    /* CELER_TALLY_* */
+  int n_zbins;                       /* bins for CELER_TALLY_ZBINS */
+  uint64_t n_slots;                  /* track slots (the state size of Sec. 2) */
+  uint64_t init_capacity;            /* initializer buffer entries (rounded up to a power of two) */
+  uint32_t max_events;               /* tally rows; event e uses row e % max_events */
+  uint64_t history_capacity;         /* per-primary records (0: off) */
+  int sort_policy;                   /* CELER_SORT_* */
+  int block_size;                    /* threads per block of the action kernels: 128, 256 or 512 */
+  uint32_t seed;                     /* first word of every Philox key */
+  uint64_t max_iterations;           /* celer_run_events limit (0: 10^6) */
+  void* cuda_stream;                 /* cudaStream_t for all work (NULL: legacy default stream) */
+} celer_problem;
+
+typedef struct {
+  double E;        /* kinetic energy, MeV, in (0, 10^4] */
+  double pos[3];   /* cm, inside the world */
+  double dir[3];   /* unit vector, |dir| = 1 within 1e-12 */
+  int32_t ptype;   /* CELER_GAMMA or CELER_ELECTRON */
+  int32_t pad;
+} celer_primary;
+
+typedef struct {
+  uint64_t iteration;        /* step iterations completed so far */
+  uint64_t alive;            /* tracks in slots after this iteration */
+  uint64_t queued;           /* initializers waiting after this iteration */
+  uint64_t steps;            /* track-steps taken in this iteration */
+  uint64_t steps_total;      /* track-steps since creation */
+  uint32_t deferred;         /* interactions postponed for lack of buffer space */
+  uint32_t error;            /* device error bits (0: none) */
+  uint32_t action_count[16]; /* tracks per next action in this iteration */
+} celer_step_stats;
+
+typedef struct {
+  uint64_t steps;        /* track-steps of the primary and all its descendants */
+  uint64_t secondaries;  /* secondary tracks created above the tracking cut */
+  double escaped;        /* energy that left the world, MeV */
+  double edep;           /* energy deposited, MeV (sum over bins) */
+} celer_history;
+
+typedef struct {
+  uint64_t iteration, alive, queued, steps;
+  uint32_t action_count[16];
+} celer_trace_row;
+
+typedef struct celer_ctx celer_ctx;
+
+/* Human-readable name of a status code (static string). */
+const char* celer_status_string(celer_status s);
+
+/* Message of the last error on this context (static per context; "" if none). */
+const char* celer_last_error(const celer_ctx* ctx);
+
+/* Build a context: validate the problem, allocate the slot store, the
+ * initializer buffer, tallies and history on the current CUDA device, and
+ * build the cross-section, stopping-power and range tables on the device.
+ * *out receives the context, or NULL on error. CELER_ERR_INVALID for an
+ * inconsistent problem, CELER_ERR_CUDA if an allocation or launch fails. */
+celer_status celer_create(const celer_problem* problem, celer_ctx** out);
+
+/* Release every resource of the context. NULL is allowed. */
+void celer_destroy(celer_ctx* ctx);
+
+/* Queue n primaries of one event as track initializers (Sec. 2: new tracks
+ * enter through the initializer buffer). host_ptr: n celer_primary records in
+ * host memory (pageable or pinned). The i-th primary added to an event gets
+ * track id = number of primaries of that event added before it, which keys
+ * its random stream together with (seed, event). Validation happens on the
+ * host before any device work: CELER_ERR_INVALID for a bad record,
+ * CELER_ERR_CAPACITY if the initializer buffer or history cannot hold them.
+ * Synchronises the stream once to read the buffer fill level. */
+celer_status celer_add_primaries(celer_ctx* ctx, uint32_t event, const celer_primary* host_ptr, uint64_t n);
+
+/* Same as celer_add_primaries for n records already in device memory
+ * (device_ptr: n celer_primary records on the context's device, e.g. a
+ * CUDA tensor). Validation and the initializer-buffer capacity check run on
+ * the device, stream ordered, without a host round trip: if any record is
+ * invalid or the buffer cannot hold all n, none is queued and the next call
+ * that synchronises (celer_run_events, celer_step with stats,
+ * celer_get_stats) reports CELER_ERR_INVALID. Track ids are assigned as in
+ * celer_add_primaries, whether or not the batch is accepted. The caller
+ * keeps device_ptr valid until the stream has passed this call. */
+celer_status celer_add_primaries_device(celer_ctx* ctx, uint32_t event, const celer_primary* device_ptr, uint64_t n);
+
+/* One step iteration (Sec. 2): fill vacant slots from initializers, step
+ * limit, reorder (Sec. 3.1, per sort_policy), propagation, interactions,
+ * secondaries to the initializer buffer. If stats is non-NULL the stream is
+ * synchronised and the iteration's counters are returned. */
+celer_status celer_step(celer_ctx* ctx, celer_step_stats* stats);
+
+/* Step until no track is alive or queued. use_graph = 0: a host loop of
+ * celer_step launches that polls the counters every few iterations;
+ * use_graph = 1: the iteration is captured once into a CUDA graph whose
+ * conditional while-node repeats it on the device with no host round trip.
+ * Returns CELER_ERR_TIMEOUT at max_iterations, CELER_ERR_CAPACITY if the
+ * initializer buffer is full and no track can make progress. */
+celer_status celer_run_events(celer_ctx* ctx, int use_graph);
+
+/* Copy the energy-deposit tally of one event (n bins, n = the problem's bin
+ * count) and its escaped energy into host memory. Synchronises the stream. */
+celer_status celer_read_tallies(celer_ctx* ctx, uint32_t event, double* host_out, uint64_t n, double* escaped);
+
+/* Zero the tally row, escaped energy and live-track count of an event so
+ * that its row can be reused by a later event. */
+celer_status celer_reset_event(celer_ctx* ctx, uint32_t event);
+
+/* Number of live (alive or queued) tracks of an event; 0 once it is done. */
+celer_status celer_event_live(celer_ctx* ctx, uint32_t event, uint64_t* live);
+
+/* Per-primary records [first, first + count) in the order primaries were
+ * added; edep_out (nullable) receives count x n_bins deposits. */
+celer_status celer_read_history(celer_ctx* ctx, uint64_t first, uint64_t count, celer_history* host_out,
+                                double* edep_out);
+
+/* Counters since creation (stream synchronised). */
+celer_status celer_get_stats(celer_ctx* ctx, celer_step_stats* out);
+
+/* Change the reordering policy between runs. */
+celer_status celer_set_sort_policy(celer_ctx* ctx, int policy);
+
+/* Per-iteration counters (alive, queued, steps, tracks per action) of the
+ * last min(n_max, recorded) iterations, the analogue of the paper's counter
+ * tracks (Sec. 4). *n_out receives the row count. */
+celer_status celer_read_trace(celer_ctx* ctx, celer_trace_row* host_out, uint64_t n_max, uint64_t* n_out);
+
+/* Average device time per launch of each kernel over the last run, measured
+ * with CUDA events when timing is enabled (enable != 0); names are static. */
+celer_status celer_enable_kernel_timing(celer_ctx* ctx, int enable);
+celer_status celer_kernel_timing(celer_ctx* ctx, const char** names, double* total_ms, uint64_t* launches,
+                                 int n_max, int* n_out);
+
+/* ---- diagnostics used by the parity tests ---- */
+
+/* Partition of the last iteration: per-slot key (n_slots bytes), the
+ * permutation (n_slots entries; the first offsets[n_keys] are valid) and the
+ * n_keys + 1 offsets. Valid only for the sorted policies. */
+celer_status celer_debug_partition(celer_ctx* ctx, uint8_t* keys_out, uint32_t* perm_out, uint32_t* offsets_out,
+                                   int* n_keys);
+
+/* Device table of material mat, column col (0 Compton, 1 photoelectric,
+ * 2 pair, 3 Moller, 4 brems, 5 range), 200 values into host memory. */
+celer_status celer_debug_table(celer_ctx* ctx, int mat, int col, double* host_out);
+
+/* Run the device Philox4x32-10 on n (counter[4], key[2]) records (host,
+ * 6 words each) and write the 4 output words of each into host_out. */
+celer_status celer_debug_philox(const uint32_t* host_ctr_key, uint32_t* host_out, uint64_t n);
+
+/* Same records through cuRAND's Philox4_32_10 device generator, mapped as
+ * key = seed, counter = (0, 0, subsequence) + offset, for cross-checking. */
+celer_status celer_debug_curand_philox(uint64_t seed, uint64_t subsequence, uint64_t offset4, uint32_t* host_out,
+                                       uint64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,317 @@
+"""ctypes binding of the C ABI in include/celer_gb.h.
+
+Argument marshalling only: every step of the transport runs in the CUDA
+library. There is no CPU fallback; if the library is missing or cannot be
+loaded the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import workloads as wl
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libceler_gb.so")
+
+CELER_OK = 0
+STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "capacity exceeded", 3: "CUDA error",
+                4: "iteration limit reached", 5: "invalid state"}
+
+
+class CelerError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class celer_material(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("Z", "A", "rho", "ne", "X0", "I")]
+
+
+class celer_problem(C.Structure):
+    _fields_ = [
+        ("n_materials", C.c_int), ("materials", C.POINTER(celer_material)),
+        ("n_layers", C.c_int), ("layer_material", C.POINTER(C.c_int)),
+        ("layer_thickness", C.POINTER(C.c_double)), ("n_periods", C.c_int),
+        ("half_x", C.c_double), ("half_y", C.c_double), ("Bz", C.c_double),
+        ("cut_track", C.c_double), ("cut_moller", C.c_double), ("cut_brems", C.c_double),
+        ("processes", C.c_int), ("tally_mode", C.c_int), ("n_zbins", C.c_int),
+        ("n_slots", C.c_uint64), ("init_capacity", C.c_uint64), ("max_events", C.c_uint32),
+        ("history_capacity", C.c_uint64), ("sort_policy", C.c_int), ("block_size", C.c_int),
+        ("seed", C.c_uint32), ("max_iterations", C.c_uint64), ("cuda_stream", C.c_void_p),
+    ]
+
+
+PRIMARY_C = np.dtype([("E", "f8"), ("pos", "f8", (3,)), ("dir", "f8", (3,)), ("ptype", "i4"), ("pad", "i4")],
+                     align=True)
+assert PRIMARY_C.itemsize == 64
+
+
+class celer_step_stats(C.Structure):
+    _fields_ = [("iteration", C.c_uint64), ("alive", C.c_uint64), ("queued", C.c_uint64), ("steps", C.c_uint64),
+                ("steps_total", C.c_uint64), ("deferred", C.c_uint32), ("error", C.c_uint32),
+                ("action_count", C.c_uint32 * 16)]
+
+
+class celer_history(C.Structure):
+    _fields_ = [("steps", C.c_uint64), ("secondaries", C.c_uint64), ("escaped", C.c_double), ("edep", C.c_double)]
+
+
+HISTORY_NP = np.dtype([("steps", "u8"), ("secondaries", "u8"), ("escaped", "f8"), ("edep", "f8")], align=True)
+
+
+class celer_trace_row(C.Structure):
+    _fields_ = [("iteration", C.c_uint64), ("alive", C.c_uint64), ("queued", C.c_uint64), ("steps", C.c_uint64),
+                ("action_count", C.c_uint32 * 16)]
+
+
+ACTION_NAMES = ["none", "zup", "zdown", "side", "range", "trapped", "compton", "photoelectric", "pair", "moller",
+                "brems"]
+
+# Every entry point declared in include/celer_gb.h.
+EXPORTS = [
+    "celer_status_string", "celer_last_error", "celer_create", "celer_destroy", "celer_add_primaries",
+    "celer_add_primaries_device",
+    "celer_step", "celer_run_events", "celer_read_tallies", "celer_reset_event", "celer_event_live",
+    "celer_read_history", "celer_get_stats", "celer_set_sort_policy", "celer_read_trace",
+    "celer_enable_kernel_timing", "celer_kernel_timing", "celer_debug_partition", "celer_debug_table",
+    "celer_debug_philox", "celer_debug_curand_philox",
+]
+
+_lib = None
+
+
+def load(path: Optional[str] = None):
+    """Load libceler_gb.so (built by paper_2503_17608_gb300.build). Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run paper_2503_17608_gb300.build.build())")
+    L = C.CDLL(path)
+    vp, u64, u32, i32, dp = C.c_void_p, C.c_uint64, C.c_uint32, C.c_int, C.POINTER(C.c_double)
+    sigs = {
+        "celer_status_string": ([i32], C.c_char_p),
+        "celer_last_error": ([vp], C.c_char_p),
+        "celer_create": ([C.POINTER(celer_problem), C.POINTER(vp)], i32),
+        "celer_destroy": ([vp], None),
+        "celer_add_primaries": ([vp, u32, vp, u64], i32),
+        "celer_add_primaries_device": ([vp, u32, vp, u64], i32),
+        "celer_step": ([vp, C.POINTER(celer_step_stats)], i32),
+        "celer_run_events": ([vp, i32], i32),
+        "celer_read_tallies": ([vp, u32, dp, u64, dp], i32),
+        "celer_reset_event": ([vp, u32], i32),
+        "celer_event_live": ([vp, u32, C.POINTER(u64)], i32),
+        "celer_read_history": ([vp, u64, u64, vp, dp], i32),
+        "celer_get_stats": ([vp, C.POINTER(celer_step_stats)], i32),
+        "celer_set_sort_policy": ([vp, i32], i32),
+        "celer_read_trace": ([vp, vp, u64, C.POINTER(u64)], i32),
+        "celer_enable_kernel_timing": ([vp, i32], i32),
+        "celer_kernel_timing": ([vp, C.POINTER(C.c_char_p), dp, C.POINTER(u64), i32, C.POINTER(i32)], i32),
+        "celer_debug_partition": ([vp, vp, vp, vp, C.POINTER(i32)], i32),
+        "celer_debug_table": ([vp, i32, i32, dp], i32),
+        "celer_debug_philox": ([vp, vp, u64], i32),
+        "celer_debug_curand_philox": ([u64, u64, u64, vp, u64], i32),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _check(status, ctx=None):
+    if status != CELER_OK:
+        msg = ""
+        if ctx:
+            msg = (load().celer_last_error(ctx) or b"").decode()
+        raise CelerError(status, msg)
+
+
+def to_c_primaries(primaries: np.ndarray, out: Optional[np.ndarray] = None) -> np.ndarray:
+    n = len(primaries)
+    p = out if out is not None else np.zeros(n, dtype=PRIMARY_C)
+    p["E"] = primaries["E"]
+    p["pos"] = primaries["pos"]
+    p["dir"] = primaries["dir"]
+    p["ptype"] = primaries["ptype"]
+    return p
+
+
+def _torch_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:  # pragma: no cover - torch without CUDA
+        pass
+    return None
+
+
+class Context:
+    """A transport context built from a workloads.Problem."""
+
+    def __init__(self, prob: wl.Problem, stream=None, max_iterations: int = 0):
+        L = load()
+        self.prob = prob
+        self.n_bins = prob.n_bins
+        self._mats = (celer_material * len(prob.materials))(
+            *[celer_material(m.Z, m.A, m.rho, m.ne, m.X0, m.I) for m in prob.materials])
+        self._lm = (C.c_int * len(prob.layer_material))(*prob.layer_material)
+        self._lt = (C.c_double * len(prob.layer_thickness))(*prob.layer_thickness)
+        cp = celer_problem()
+        cp.n_materials = len(prob.materials)
+        cp.materials = self._mats
+        cp.n_layers = len(prob.layer_material)
+        cp.layer_material = self._lm
+        cp.layer_thickness = self._lt
+        cp.n_periods = prob.n_periods
+        cp.half_x, cp.half_y, cp.Bz = prob.half_x, prob.half_y, prob.Bz
+        cp.cut_track, cp.cut_moller, cp.cut_brems = prob.cut_track, prob.cut_moller, prob.cut_brems
+        cp.processes, cp.tally_mode, cp.n_zbins = prob.processes, prob.tally_mode, prob.n_zbins
+        cp.n_slots, cp.init_capacity = prob.n_slots, prob.init_capacity
+        cp.max_events, cp.history_capacity = prob.max_events, prob.history_capacity
+        cp.sort_policy, cp.block_size, cp.seed = prob.sort_policy, prob.block_size, prob.seed
+        cp.max_iterations = max_iterations
+        self.stream = stream if stream is not None else _torch_stream()
+        cp.cuda_stream = self.stream
+        h = C.c_void_p()
+        _check(L.celer_create(C.byref(cp), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().celer_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- transport
+    def add_primaries(self, event: int, primaries: np.ndarray):
+        p = primaries if primaries.dtype == PRIMARY_C else to_c_primaries(primaries)
+        p = np.ascontiguousarray(p)
+        _check(load().celer_add_primaries(self._h, int(event), p.ctypes.data, len(p)), self._h)
+
+    def add_primaries_device(self, event: int, device_ptr: int, n: int):
+        """Queue n celer_primary records already in device memory (e.g. the
+        data_ptr() of a CUDA tensor holding 64-byte records)."""
+        _check(load().celer_add_primaries_device(self._h, int(event), C.c_void_p(int(device_ptr)), int(n)), self._h)
+
+    def add_events(self, primaries: np.ndarray):
+        """Queue primaries grouped by their event field, in order of first appearance."""
+        ev = primaries["event"]
+        for e in dict.fromkeys(ev.tolist()):
+            self.add_primaries(e, primaries[ev == e])
+
+    def step(self):
+        s = celer_step_stats()
+        _check(load().celer_step(self._h, C.byref(s)), self._h)
+        return _stats_dict(s)
+
+    def step_async(self):
+        _check(load().celer_step(self._h, None), self._h)
+
+    def run_events(self, use_graph: bool = True):
+        _check(load().celer_run_events(self._h, 1 if use_graph else 0), self._h)
+
+    def read_tallies(self, event: int = 0):
+        out = np.zeros(self.n_bins)
+        esc = C.c_double()
+        _check(load().celer_read_tallies(self._h, int(event), out.ctypes.data_as(C.POINTER(C.c_double)),
+                                         self.n_bins, C.byref(esc)), self._h)
+        return out, esc.value
+
+    def reset_event(self, event: int):
+        _check(load().celer_reset_event(self._h, int(event)), self._h)
+
+    def event_live(self, event: int) -> int:
+        v = C.c_uint64()
+        _check(load().celer_event_live(self._h, int(event), C.byref(v)), self._h)
+        return v.value
+
+    def read_history(self, first: int, count: int, with_edep: bool = True):
+        hist = np.zeros(count, dtype=HISTORY_NP)
+        edep = np.zeros((count, self.n_bins)) if with_edep else None
+        _check(load().celer_read_history(self._h, first, count, hist.ctypes.data,
+                                         edep.ctypes.data_as(C.POINTER(C.c_double)) if with_edep else None),
+               self._h)
+        return hist, edep
+
+    def stats(self):
+        s = celer_step_stats()
+        _check(load().celer_get_stats(self._h, C.byref(s)), self._h)
+        return _stats_dict(s)
+
+    def set_sort_policy(self, policy: int):
+        _check(load().celer_set_sort_policy(self._h, int(policy)), self._h)
+
+    def trace(self, n_max: int = 1 << 16):
+        rows = (celer_trace_row * n_max)()
+        n = C.c_uint64()
+        _check(load().celer_read_trace(self._h, C.cast(rows, C.c_void_p), n_max, C.byref(n)), self._h)
+        return [dict(iteration=r.iteration, alive=r.alive, queued=r.queued, steps=r.steps,
+                     actions=list(r.action_count)[:len(ACTION_NAMES)]) for r in rows[:n.value]]
+
+    def enable_kernel_timing(self, enable: bool = True):
+        _check(load().celer_enable_kernel_timing(self._h, 1 if enable else 0), self._h)
+
+    def kernel_timing(self):
+        n_max = 32
+        names = (C.c_char_p * n_max)()
+        tot = (C.c_double * n_max)()
+        cnt = (C.c_uint64 * n_max)()
+        n = C.c_int()
+        _check(load().celer_kernel_timing(self._h, names, tot, cnt, n_max, C.byref(n)), self._h)
+        return {names[i].decode(): dict(total_ms=tot[i], launches=cnt[i]) for i in range(n.value)}
+
+    # -- diagnostics
+    def debug_partition(self):
+        N = self.prob.n_slots
+        keys = np.zeros(N, np.uint8)
+        perm = np.zeros(N, np.uint32)
+        offs = np.zeros(17, np.uint32)
+        nk = C.c_int()
+        _check(load().celer_debug_partition(self._h, keys.ctypes.data, perm.ctypes.data, offs.ctypes.data,
+                                            C.byref(nk)), self._h)
+        return keys, perm, offs[:nk.value + 1]
+
+    def debug_table(self, mat: int, col: int):
+        out = np.zeros(200)
+        _check(load().celer_debug_table(self._h, mat, col, out.ctypes.data_as(C.POINTER(C.c_double))), self._h)
+        return out
+
+
+def _stats_dict(s):
+    return dict(iteration=s.iteration, alive=s.alive, queued=s.queued, steps=s.steps, steps_total=s.steps_total,
+                deferred=s.deferred, error=s.error, actions=list(s.action_count)[:len(ACTION_NAMES)])
+
+
+def debug_philox(ctr_key: np.ndarray) -> np.ndarray:
+    """Device Philox4x32-10 on rows (c0, c1, c2, c3, k0, k1)."""
+    a = np.ascontiguousarray(ctr_key, dtype=np.uint32)
+    out = np.zeros((len(a), 4), np.uint32)
+    _check(load().celer_debug_philox(a.ctypes.data, out.ctypes.data, len(a)))
+    return out
+
+
+def debug_curand_philox(seed: int, subsequence: int, offset4: int, n: int) -> np.ndarray:
+    out = np.zeros((n, 4), np.uint32)
+    _check(load().celer_debug_curand_philox(seed, subsequence, offset4, out.ctypes.data, n))
+    return out

@@ -1,0 +1,153 @@
+// Device-side data layout and launch parameters of the step-based transport
+// loop (Sec. 2 of the paper: struct-of-arrays track state, a separate buffer
+// of track initializers, one kernel per action).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace celer {
+
+constexpr int kGrid = 200;          // log-spaced energy grid points
+constexpr double kGridEmin = 1e-3;  // MeV
+constexpr double kGridEmax = 1e4;   // MeV
+constexpr int kCols = 6;            // device table columns per material
+constexpr int kMaxMaterials = 8;
+constexpr int kMaxLayers = 1024;
+constexpr int kMaxKeys = 16;
+constexpr int kTile = 256;          // slots per partition tile (= pre-step block)
+constexpr int kInitTile = 2048;     // slots per initializer tile (256 threads x 8)
+constexpr int kTraceRows = 1 << 16;
+
+// device table columns
+enum Col : int { COL_COMPTON = 0, COL_PE, COL_PAIR, COL_MOLLER, COL_BREMS, COL_RANGE };
+
+enum ProcBits : int {
+  PROC_COMPTON = 1, PROC_PE = 2, PROC_PAIR = 4, PROC_MOLLER = 8, PROC_BREMS = 16, PROC_ELOSS = 32
+};
+
+enum PType : uint8_t { GAMMA = 0, ELECTRON = 1, POSITRON = 2 };
+enum Status : uint8_t { VACANT = 0, ALIVE = 1, DEFERRED = 2 };
+
+// Next action of a track, chosen by the step-limit kernel: the
+// geometric/range limits handled by the along-step kernels, then the
+// discrete interactions handled by one kernel each.
+enum Action : uint8_t {
+  A_NONE = 0,
+  A_ZUP,      // crosses the upper z-plane of its layer
+  A_ZDOWN,    // crosses the lower z-plane of its layer
+  A_SIDE,     // leaves through a side plane
+  A_RANGE,    // range-limited step
+  A_TRAPPED,  // no finite step limit: ends in place
+  A_COMPTON,
+  A_PE,
+  A_PAIR,
+  A_MOLLER,
+  A_BREMS,
+  A_COUNT
+};
+
+// Partition keys of the ACTION_TYPE policy (particle type major).
+enum Key : uint8_t {
+  K_G_GEOM = 0, K_G_COMPTON, K_G_PE, K_G_PAIR,
+  K_E_GEOM, K_E_RANGE, K_E_MOLLER, K_E_BREMS,
+  K_VACANT_FULL = 8
+};
+constexpr int kKeysFull = 9;
+// Keys of the ACTION policy (along-step action only).
+enum KeyAlong : uint8_t { KA_NEUTRAL = 0, KA_CHARGED = 1, KA_VACANT = 2 };
+constexpr int kKeysAlong = 3;
+
+enum Policy : int { POLICY_NONE = 0, POLICY_ACTION = 1, POLICY_ACTION_TYPE = 2 };
+
+enum ErrorBits : uint32_t { ERR_RING_OVERFLOW = 1u, ERR_NO_PROGRESS = 2u, ERR_ITERATIONS = 4u, ERR_SAMPLING = 8u,
+                            ERR_PRIMARIES_REJECTED = 16u };
+
+struct Tracks {
+  double *x, *y, *z, *ux, *uy, *uz, *E, *nmfp, *step, *rpost;
+  unsigned long long* tid;
+  uint32_t *ctr, *event, *primary;
+  int32_t* layer;
+  uint8_t *ptype, *status, *action, *key;
+};
+
+struct Ring {
+  double *x, *y, *z, *ux, *uy, *uz, *E;
+  unsigned long long* tid;
+  uint32_t *event, *primary;
+  int32_t* layer;
+  uint8_t* ptype;
+};
+
+// Device-resident loop control. Ring indices are monotonic counters; the
+// entry of index i lives at i & ring_mask.
+struct Ctl {
+  unsigned long long head, tail, head_pending;
+  unsigned long long alive;          // slots holding a live or deferred track
+  unsigned long long steps_total;
+  unsigned long long steps_iter;
+  unsigned long long iteration;
+  unsigned long long max_iterations;
+  unsigned int action_count[kMaxKeys];
+  unsigned int key_total[kMaxKeys];
+  unsigned int offsets[kMaxKeys + 1];
+  unsigned int defer;                // 1: secondary-producing kernels postpone this iteration
+  unsigned int n_deferred;
+  unsigned int error;
+  unsigned int cont;                 // 1 while alive + queued > 0
+  unsigned int stall;                // consecutive iterations without progress
+  unsigned int pad;
+  unsigned long long trace_count;
+};
+
+struct TraceRow {
+  unsigned long long iteration, alive, queued, steps;
+  unsigned int action_count[kMaxKeys];
+};
+
+struct Params {
+  // state
+  Tracks trk;
+  Ring ring;
+  Ctl* ctl;
+  uint32_t n_slots;
+  uint32_t n_tiles;        // ceil(n_slots / kTile)
+  uint32_t n_init_tiles;   // ceil(n_slots / kInitTile)
+  unsigned long long ring_mask;
+  unsigned long long ring_capacity;
+  uint32_t* init_counts;   // n_init_tiles
+  // partition
+  int policy;
+  int n_keys;
+  uint32_t* perm;          // n_slots
+  uint32_t* tile_counts;   // n_keys * n_tiles, key major
+  // geometry
+  int n_layers;
+  int n_materials;
+  const double* zb;        // n_layers + 1
+  const int32_t* layer_mat;
+  double hx, hy, Bz;
+  // physics
+  double cut_track, cut_moller, cut_brems;
+  int processes;
+  const double2* tables;   // [mat][col][kGrid] (value, next - value)
+  double lnEmin, inv_dl, dl;
+  uint32_t seed;
+  // tallies
+  int tally_mode;
+  int n_bins;
+  double z0, zscale;
+  uint32_t max_events;
+  double* tally;           // max_events * n_bins
+  double* escaped;         // max_events
+  unsigned int* event_live;  // max_events
+  // per-primary history
+  unsigned long long hist_cap;
+  unsigned long long* hist_steps;
+  unsigned long long* hist_secondaries;
+  double* hist_escaped;
+  double* hist_edep;       // hist_cap * n_bins
+  TraceRow* trace;
+};
+
+}  // namespace celer

@@ -1,0 +1,79 @@
+// Diagnostics for the parity tests: the device Philox4x32-10 on given
+// (counter, key) records, and cuRAND's Philox4_32_10 generator for
+// cross-checking the two against each other and against the CPU oracle.
+#include <curand_kernel.h>
+
+#include <vector>
+
+#include "celer_gb.h"
+#include "physics.cuh"
+
+namespace {
+
+__global__ void k_philox(const uint32_t* in, uint32_t* out, uint64_t n) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t* r = in + 6 * i;
+    const uint4 o = celer::philox4x32_10(make_uint4(r[0], r[1], r[2], r[3]), make_uint2(r[4], r[5]));
+    out[4 * i + 0] = o.x;
+    out[4 * i + 1] = o.y;
+    out[4 * i + 2] = o.z;
+    out[4 * i + 3] = o.w;
+  }
+}
+
+__global__ void k_curand(unsigned long long seed, unsigned long long sub, unsigned long long offset4, uint32_t* out,
+                         uint64_t n) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  curandStatePhilox4_32_10_t st;
+  curand_init(seed, sub, 4ull * offset4, &st);
+  for (uint64_t i = 0; i < n; ++i) {
+    const uint4 o = curand4(&st);
+    out[4 * i + 0] = o.x;
+    out[4 * i + 1] = o.y;
+    out[4 * i + 2] = o.z;
+    out[4 * i + 3] = o.w;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+celer_status celer_debug_philox(const uint32_t* host_ctr_key, uint32_t* host_out, uint64_t n) {
+  if (!host_ctr_key || !host_out) return CELER_ERR_INVALID;
+  if (n == 0) return CELER_OK;
+  uint32_t *d_in = nullptr, *d_out = nullptr;
+  if (cudaMalloc(&d_in, sizeof(uint32_t) * 6 * n) != cudaSuccess) return CELER_ERR_CUDA;
+  if (cudaMalloc(&d_out, sizeof(uint32_t) * 4 * n) != cudaSuccess) {
+    cudaFree(d_in);
+    return CELER_ERR_CUDA;
+  }
+  celer_status st = CELER_OK;
+  if (cudaMemcpy(d_in, host_ctr_key, sizeof(uint32_t) * 6 * n, cudaMemcpyHostToDevice) != cudaSuccess) st = CELER_ERR_CUDA;
+  if (st == CELER_OK) {
+    const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    k_philox<<<grid, 256>>>(d_in, d_out, n);
+    if (cudaGetLastError() != cudaSuccess) st = CELER_ERR_CUDA;
+  }
+  if (st == CELER_OK && cudaMemcpy(host_out, d_out, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+    st = CELER_ERR_CUDA;
+  cudaFree(d_in);
+  cudaFree(d_out);
+  return st;
+}
+
+celer_status celer_debug_curand_philox(uint64_t seed, uint64_t subsequence, uint64_t offset4, uint32_t* host_out,
+                                       uint64_t n) {
+  if (!host_out) return CELER_ERR_INVALID;
+  if (n == 0) return CELER_OK;
+  uint32_t* d_out = nullptr;
+  if (cudaMalloc(&d_out, sizeof(uint32_t) * 4 * n) != cudaSuccess) return CELER_ERR_CUDA;
+  k_curand<<<1, 1>>>(seed, subsequence, offset4, d_out, n);
+  celer_status st = cudaGetLastError() == cudaSuccess ? CELER_OK : CELER_ERR_CUDA;
+  if (st == CELER_OK && cudaMemcpy(host_out, d_out, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+    st = CELER_ERR_CUDA;
+  cudaFree(d_out);
+  return st;
+}
+
+}  // extern "C"

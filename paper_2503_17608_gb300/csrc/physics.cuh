@@ -1,0 +1,269 @@
+// Device functions of the transport: counter-based random numbers, table
+// interpolation, geometry (straight line and exact helix in a uniform field),
+// and the sampling of the discrete interactions.
+//
+// The paper fixes no physics model (it profiles the stepping loop of an EM
+// transport code); the model here is the simplified EM set of the benchmark
+// workloads: Klein-Nishina Compton, a power-law photoelectric effect, pair
+// production with local deposition of the pair's kinetic energy, Moller delta
+// rays, a 1/k bremsstrahlung spectrum and restricted continuous loss. All of
+// it is binary64: the workloads fix FP64.
+#pragma once
+
+#include "common.cuh"
+
+namespace celer {
+
+constexpr double kMe = 0.51099895;        // electron mass, MeV
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTwoPi = 2.0 * kPi;
+constexpr double kFieldK = 2.99792458;    // curvature [1/cm] = kFieldK * B[T] / p[MeV/c]
+constexpr double kPairThreshold = 1.022;  // MeV, as in the photon model definition
+constexpr double kAlphaR = 0.2;           // range step function: fraction of range
+constexpr double kFinalR = 0.1;           // range step function: final range, cm
+constexpr double kInf = __builtin_huge_val();
+// Attempts after which a rejection sampler gives up (never reached for finite
+// inputs: the acceptance probability is at least ~0.4 per attempt).
+constexpr int kMaxAttempts = 4096;
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds, each two 32x32 -> 64-bit
+// products whose high words are mixed with the other two counter words and
+// the round key; the key advances by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// u = (floor(w / 2^12) + 1/2) 2^-52 in [2^-53, 1 - 2^-53], built from the
+// exponent bits of 1.0 and one exact subtraction (Sterbenz).
+__device__ __forceinline__ double unit_from_bits(unsigned long long w) {
+  return __longlong_as_double(0x3FF0000000000000ull | (w >> 12)) - (1.0 - 0x1p-53);
+}
+
+// A track's random stream: key (seed, event), counter (tid lo, tid hi,
+// index / 2, 0); even indices take output words 0-1, odd ones 2-3. The
+// Philox block of the last even index is cached so that each pair of draws
+// costs one Philox evaluation.
+struct TrackRng {
+  uint2 key;
+  unsigned long long tid;
+  uint32_t ctr;
+  uint32_t cached_block;
+  uint4 cached;
+
+  __device__ TrackRng(uint32_t seed, uint32_t event, unsigned long long tid_, uint32_t ctr_)
+      : key(make_uint2(seed, event)), tid(tid_), ctr(ctr_), cached_block(0xFFFFFFFFu) {}
+
+  __device__ __forceinline__ unsigned long long raw() {
+    const uint32_t block = ctr >> 1;
+    if (block != cached_block) {
+      cached = philox4x32_10(make_uint4((uint32_t)tid, (uint32_t)(tid >> 32), block, 0u), key);
+      cached_block = block;
+    }
+    const unsigned long long w = (ctr & 1u) ? ((unsigned long long)cached.w << 32 | cached.z)
+                                            : ((unsigned long long)cached.y << 32 | cached.x);
+    ++ctr;
+    return w;
+  }
+  __device__ __forceinline__ double uniform() { return unit_from_bits(raw()); }
+};
+
+// ------------------------------------------------------------------ tables
+struct GridPos {
+  int bin;
+  double frac;
+};
+
+// Grid coordinate (ln E - ln E_min) / dl, bin clamped to [0, n - 2].
+__device__ __forceinline__ GridPos grid_pos(double E, double lnEmin, double inv_dl) {
+  const double x = (log(E) - lnEmin) * inv_dl;
+  int b = (int)floor(x);
+  b = b < 0 ? 0 : (b > kGrid - 2 ? kGrid - 2 : b);
+  return GridPos{b, x - (double)b};
+}
+
+// Linear interpolation in ln E; each entry holds (value, next value - value).
+__device__ __forceinline__ double interp(const double2* col, GridPos g) {
+  const double2 v = col[g.bin];
+  return fma(g.frac, v.y, v.x);
+}
+
+// Inverse of the range interpolation: the largest bin i <= n - 2 with
+// R_i <= r, then ln E linear in R inside it. r <= R_0: the track stopped.
+__device__ __forceinline__ double inverse_range(const double2* R, double r, double lnEmin, double dl) {
+  if (r <= R[0].x) return 0.0;
+  int lo = 0;
+#pragma unroll
+  for (int step = 128; step > 0; step >>= 1) {
+    const int probe = lo + step;
+    if (probe <= kGrid - 2 && R[probe].x <= r) lo = probe;
+  }
+  const double2 v = R[lo];
+  const double lnE = lnEmin + lo * dl + (r - v.x) / v.y * dl;
+  return exp(lnE);
+}
+
+// ------------------------------------------------------------- kinematics
+__device__ __forceinline__ void rotate_dir(double& ux, double& uy, double& uz, double cost, double phi) {
+  const double sint = sqrt(fmax(0.0, 1.0 - cost * cost));
+  double sp, cp;
+  sincos(phi, &sp, &cp);
+  double e1x, e1y, e1z, e2x, e2y, e2z;
+  if (fabs(uz) < 1.0 - 1e-10) {
+    const double n = sqrt(ux * ux + uy * uy);
+    e1x = uy / n;
+    e1y = -ux / n;
+    e1z = 0.0;
+    e2x = uz * ux / n;
+    e2y = uz * uy / n;
+    e2z = -n;
+  } else {
+    const double n = sqrt(uz * uz + uy * uy);
+    e1x = 1.0;
+    e1y = 0.0;
+    e1z = 0.0;
+    e2x = 0.0;
+    e2y = uz / n;
+    e2z = -uy / n;
+  }
+  const double vx = cost * ux + sint * (cp * e1x + sp * e2x);
+  const double vy = cost * uy + sint * (cp * e1y + sp * e2y);
+  const double vz = cost * uz + sint * (cp * e1z + sp * e2z);
+  const double inv = 1.0 / sqrt(vx * vx + vy * vy + vz * vz);
+  ux = vx * inv;
+  uy = vy * inv;
+  uz = vz * inv;
+}
+
+// Signed curvature: the transverse direction turns by kappa * s over a path s.
+__device__ __forceinline__ double curvature(uint8_t ptype, double E, double Bz) {
+  const double q = (ptype == ELECTRON) ? -1.0 : 1.0;
+  return q * Bz * kFieldK / sqrt(E * (E + 2.0 * kMe));
+}
+
+// Exact helix for du/ds = kappa (u x z), with 1 - cos(phi) = 2 sin^2(phi/2).
+__device__ __forceinline__ void helix_move(double kappa, double s, double& x, double& y, double& z, double& ux,
+                                           double& uy, double uz) {
+  const double phi = kappa * s;
+  double hs, hc;
+  sincos(0.5 * phi, &hs, &hc);
+  const double sphi = 2.0 * hs * hc;
+  const double omc = 2.0 * hs * hs;
+  const double cphi = 1.0 - omc;
+  const double ox = ux, oy = uy;
+  x += (ox * sphi + oy * omc) / kappa;
+  y += (oy * sphi - ox * omc) / kappa;
+  z += uz * s;
+  ux = ox * cphi + oy * sphi;
+  uy = oy * cphi - ox * sphi;
+}
+
+// Smallest turn angle t in [0, 2 pi) with sin(sigma t + beta) = d.
+__device__ __forceinline__ double first_turn(double d, double beta, double sigma) {
+  const double a1 = asin(d);
+  const double a2 = kPi - a1;
+  double t1 = fmod(sigma * (a1 - beta), kTwoPi);
+  if (t1 < 0.0) t1 += kTwoPi;
+  double t2 = fmod(sigma * (a2 - beta), kTwoPi);
+  if (t2 < 0.0) t2 += kTwoPi;
+  return fmin(t1, t2);
+}
+
+// Path length along the helix to the first side plane (|x| = hx, |y| = hy),
+// from the intersection of its transverse circle with each plane; kInf when
+// the circle stays inside.
+static __device__ __noinline__ double helix_side_distance(double kappa, double x, double y, double ux, double uy, double hx,
+                                                   double hy) {
+  const double A = sqrt(ux * ux + uy * uy);
+  if (A == 0.0) return kInf;
+  const double K = fabs(kappa);
+  const double sigma = kappa > 0.0 ? 1.0 : -1.0;
+  const double xc = x + uy / kappa;
+  const double yc = y - ux / kappa;
+  const double rho = A / K;
+  if (xc + rho < hx && xc - rho > -hx && yc + rho < hy && yc - rho > -hy) return kInf;
+  double tmin = kInf;
+  const double bx = atan2(-uy, ux);
+  const double by = atan2(ux, uy);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const double X = i == 0 ? hx : -hx;
+    const double d = kappa * (X - xc) / A;
+    if (fabs(d) <= 1.0) tmin = fmin(tmin, first_turn(d, bx, sigma));
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const double Y = i == 0 ? hy : -hy;
+    const double d = kappa * (Y - yc) / A;
+    if (fabs(d) <= 1.0) tmin = fmin(tmin, first_turn(d, by, sigma));
+  }
+  return tmin == kInf ? kInf : tmin / K;
+}
+
+// ------------------------------------------------------------- interactions
+// Klein-Nishina sampling of eps = E'/E by Butcher and Messel's
+// composition-rejection: branch 1 samples eps from 1/eps (eps = eps0^u), branch
+// 2 samples eps^2 uniformly; both are accepted with 1 - eps sin^2 / (1 + eps^2).
+// Three draws per attempt. Returns eps; cost receives the scattering cosine;
+// ok is cleared if the attempt limit was hit.
+static __device__ __noinline__ double sample_compton(double E, TrackRng& rng, double& cost, bool& ok) {
+  const double k = E / kMe;
+  const double eps0 = 1.0 / (1.0 + 2.0 * k);
+  const double eps0sq = eps0 * eps0;
+  const double a1 = -log(eps0);
+  const double a2 = 0.5 * (1.0 - eps0sq);
+  double eps = 1.0, t = 0.0;
+  ok = false;
+  for (int attempt = 0; attempt < kMaxAttempts; ++attempt) {
+    const double u1 = rng.uniform();
+    const double u2 = rng.uniform();
+    const double u3 = rng.uniform();
+    if (u1 * (a1 + a2) < a1) {
+      eps = exp(-a1 * u2);
+    } else {
+      eps = sqrt(eps0sq + (1.0 - eps0sq) * u2);
+    }
+    t = (1.0 - eps) / (k * eps);
+    const double sint2 = t * (2.0 - t);
+    const double g = 1.0 - eps * sint2 / (1.0 + eps * eps);
+    if (u3 <= g) {
+      ok = true;
+      break;
+    }
+  }
+  cost = 1.0 - t;
+  return eps;
+}
+
+// Moller: eps = T_delta / T in [x, 1/2] from the 1/eps^2 proposal, accepted
+// with eps^2 B(eps) normalised by its maximum (9g^2 - 10g + 5)/4 at eps = 1/2.
+static __device__ __noinline__ double sample_moller(double T, double Tcut, TrackRng& rng, bool& ok) {
+  const double x = Tcut / T;
+  const double g = T / kMe + 1.0;
+  const double g2 = g * g;
+  const double norm = 4.0 / (9.0 * g2 - 10.0 * g + 5.0);
+  ok = false;
+  double eps = 0.5;
+  for (int attempt = 0; attempt < kMaxAttempts; ++attempt) {
+    const double u1 = rng.uniform();
+    const double u2 = rng.uniform();
+    eps = x / (1.0 - u1 * (1.0 - 2.0 * x));
+    const double om = 1.0 - eps;
+    const double f = (g - 1.0) * (g - 1.0) * eps * eps - (2.0 * g2 + 2.0 * g - 1.0) * eps / om + g2 / (om * om);
+    if (u2 <= norm * f) {
+      ok = true;
+      break;
+    }
+  }
+  return eps;
+}
+
+}  // namespace celer

@@ -1,0 +1,1006 @@
+// Kernels of one step iteration (Sec. 2 of the paper): fill vacant slots from
+// the track-initializer buffer, compute each track's step limit and next
+// action, reorder slot indices by action (Sec. 3.1), propagate, and apply the
+// discrete interactions, pushing secondaries back into the buffer.
+//
+// Every action kernel is persistent: a grid sized to the GPU (a multiple of
+// the SM count) strides over its work range, which is either all slots with
+// masking (policy NONE) or one contiguous range of the partition read from
+// device memory (sorted policies), so that no host round trip is needed to
+// size a launch.
+#include <cooperative_groups.h>
+#include <cooperative_groups/scan.h>
+
+#include "launch.h"
+#include "physics.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace celer {
+
+namespace {
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ uint32_t row_of(const Params& p, uint32_t ev) { return ev % p.max_events; }
+
+__device__ __forceinline__ int tally_bin(const Params& p, int layer, double z) {
+  if (p.tally_mode == 1) return layer;
+  int b = (int)floor((z - p.z0) * p.zscale);
+  return b < 0 ? 0 : (b > p.n_bins - 1 ? p.n_bins - 1 : b);
+}
+
+__device__ __forceinline__ void deposit(const Params& p, uint32_t ev, uint32_t prim, int layer, double z, double e) {
+  if (e == 0.0) return;
+  const int b = tally_bin(p, layer, z);
+  atomicAdd(&p.tally[(size_t)row_of(p, ev) * p.n_bins + b], e);
+  if (prim < p.hist_cap) atomicAdd(&p.hist_edep[(size_t)prim * p.n_bins + b], e);
+}
+
+__device__ __forceinline__ void escape(const Params& p, uint32_t ev, uint32_t prim, double e) {
+  atomicAdd(&p.escaped[row_of(p, ev)], e);
+  if (prim < p.hist_cap) atomicAdd(&p.hist_escaped[prim], e);
+}
+
+__device__ __forceinline__ void release(const Params& p, uint32_t slot, uint32_t ev) {
+  p.trk.status[slot] = VACANT;
+  p.trk.action[slot] = A_NONE;
+  atomicSub(&p.event_live[row_of(p, ev)], 1u);
+}
+
+// Warp-sum a per-thread counter and add it to a device counter (negated if
+// asked). Called by whole warps at kernel end.
+__device__ __forceinline__ void flush_counter(unsigned long long* dst, unsigned long long v, bool negate) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v != 0) atomicAdd(dst, negate ? (0ull - v) : v);
+}
+
+// Reserve n initializer entries; one atomic per group of lanes that reach
+// this point together (secondary stack allocation).
+__device__ __forceinline__ unsigned long long reserve(Ctl* c, unsigned n) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  const unsigned prefix = cg::exclusive_scan(g, n);
+  const unsigned total = g.shfl(prefix + n, g.num_threads() - 1);
+  unsigned long long base = 0;
+  if (g.thread_rank() == 0 && total > 0) base = atomicAdd(&c->tail, (unsigned long long)total);
+  base = g.shfl(base, 0);
+  return base + prefix;
+}
+
+__device__ __forceinline__ void write_initializer(const Params& p, unsigned long long index, double x, double y,
+                                                  double z, double ux, double uy, double uz, double E,
+                                                  unsigned long long tid, uint32_t ev, uint32_t prim, int32_t layer,
+                                                  uint8_t ptype) {
+  const unsigned long long i = index & p.ring_mask;
+  p.ring.x[i] = x;
+  p.ring.y[i] = y;
+  p.ring.z[i] = z;
+  p.ring.ux[i] = ux;
+  p.ring.uy[i] = uy;
+  p.ring.uz[i] = uz;
+  p.ring.E[i] = E;
+  p.ring.tid[i] = tid;
+  p.ring.event[i] = ev;
+  p.ring.primary[i] = prim;
+  p.ring.layer[i] = layer;
+  p.ring.ptype[i] = ptype;
+}
+
+struct Span {
+  uint32_t lo, hi;
+  const uint32_t* perm;
+};
+
+// Work range of an action kernel: all slots (NONE), or the partition range
+// [offsets[k_lo], offsets[k_hi]) of the policy's keys.
+__device__ __forceinline__ Span span_of(const Params& p, int ka_lo, int ka_hi, int kf_lo, int kf_hi) {
+  if (p.policy == POLICY_NONE) return Span{0u, p.n_slots, nullptr};
+  if (p.policy == POLICY_ACTION) return Span{p.ctl->offsets[ka_lo], p.ctl->offsets[ka_hi], p.perm};
+  return Span{p.ctl->offsets[kf_lo], p.ctl->offsets[kf_hi], p.perm};
+}
+
+__device__ __forceinline__ uint8_t key_of(int policy, uint8_t ptype, uint8_t act) {
+  if (policy == POLICY_ACTION) return ptype == GAMMA ? KA_NEUTRAL : KA_CHARGED;
+  if (ptype == GAMMA) {
+    switch (act) {
+      case A_COMPTON: return K_G_COMPTON;
+      case A_PE: return K_G_PE;
+      case A_PAIR: return K_G_PAIR;
+      default: return K_G_GEOM;
+    }
+  }
+  switch (act) {
+    case A_RANGE: return K_E_RANGE;
+    case A_MOLLER: return K_E_MOLLER;
+    case A_BREMS: return K_E_BREMS;
+    default: return K_E_GEOM;
+  }
+}
+
+// --------------------------------------------------------------- step limit
+// Step limit of one live track: fresh number of mean free paths if unset,
+// cross-sections from the shared-memory tables, range limit, distance to
+// the layer's planes (straight line, or the exact helix for charged tracks in
+// the field), the shortest of them with ties resolved boundary > range >
+// interaction, and for an interaction the process, chosen now with the
+// pre-step cross-sections. Writes the step length, the residual range after
+// the step, n_mfp and the draw counter; returns the next action.
+__device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, const double2* tab, const double* zb,
+                                              const int32_t* lmat) {
+  const Tracks& t = p.trk;
+  const double E = t.E[slot];
+  const uint8_t pt = t.ptype[slot];
+  const int layer = t.layer[slot];
+  double nmfp = t.nmfp[slot];
+  TrackRng rng(p.seed, t.event[slot], t.tid[slot], t.ctr[slot]);
+  if (nmfp < 0.0) nmfp = -log(rng.uniform());
+
+  const double2* mt = tab + lmat[layer] * (kCols * kGrid);
+  const GridPos g = grid_pos(E, p.lnEmin, p.inv_dl);
+  const bool charged = pt != GAMMA;
+  double mu0, mu1, mu2 = 0.0;
+  if (!charged) {
+    mu0 = interp(mt + COL_COMPTON * kGrid, g);
+    mu1 = interp(mt + COL_PE * kGrid, g);
+    mu2 = E > kPairThreshold ? interp(mt + COL_PAIR * kGrid, g) : 0.0;
+  } else {
+    mu0 = interp(mt + COL_MOLLER * kGrid, g);
+    mu1 = interp(mt + COL_BREMS * kGrid, g);
+  }
+  const double mu = (mu0 + mu1) + mu2;
+  const double s_int = mu > 0.0 ? nmfp / mu : kInf;
+
+  const bool eloss = charged && (p.processes & PROC_ELOSS);
+  double R = 0.0, s_rng = kInf;
+  if (eloss) {
+    R = interp(mt + COL_RANGE * kGrid, g);
+    s_rng = R <= kFinalR ? R : kAlphaR * R + kFinalR * (1.0 - kAlphaR) * (2.0 - kFinalR / R);
+  }
+
+  const double x = t.x[slot], y = t.y[slot], z = t.z[slot];
+  const double ux = t.ux[slot], uy = t.uy[slot], uz = t.uz[slot];
+  double s_geo = kInf;
+  uint8_t act = A_NONE;
+  if (uz > 0.0) {
+    s_geo = (zb[layer + 1] - z) / uz;
+    act = A_ZUP;
+  } else if (uz < 0.0) {
+    s_geo = (zb[layer] - z) / uz;
+    act = A_ZDOWN;
+  }
+  double s_side = kInf;
+  if (charged && p.Bz != 0.0) {
+    s_side = helix_side_distance(curvature(pt, E, p.Bz), x, y, ux, uy, p.hx, p.hy);
+  } else {
+    if (ux > 0.0) s_side = fmin(s_side, (p.hx - x) / ux);
+    if (ux < 0.0) s_side = fmin(s_side, (-p.hx - x) / ux);
+    if (uy > 0.0) s_side = fmin(s_side, (p.hy - y) / uy);
+    if (uy < 0.0) s_side = fmin(s_side, (-p.hy - y) / uy);
+  }
+  if (s_side < s_geo) {
+    s_geo = s_side;
+    act = A_SIDE;
+  }
+  if (s_geo < 0.0) s_geo = 0.0;
+
+  double s = s_geo;
+  if (s_rng < s) {
+    s = s_rng;
+    act = A_RANGE;
+  }
+  bool interact = false;
+  if (s_int < s) {
+    s = s_int;
+    interact = true;
+  }
+  if (s == kInf) {
+    act = A_TRAPPED;
+    s = 0.0;
+  } else {
+    nmfp -= s * mu;
+  }
+  if (interact) {
+    const double target = rng.uniform() * mu;
+    int last = -1;
+    if (mu0 > 0.0) last = 0;
+    if (mu1 > 0.0) last = 1;
+    if (mu2 > 0.0) last = 2;
+    int sel;
+    double acc = mu0;
+    if (target < acc) {
+      sel = 0;
+    } else {
+      acc += mu1;
+      if (target < acc) {
+        sel = 1;
+      } else {
+        acc += mu2;
+        sel = (!charged && target < acc) ? 2 : last;
+      }
+    }
+    act = charged ? (sel == 0 ? A_MOLLER : A_BREMS) : (uint8_t)(A_COMPTON + sel);
+  }
+  t.nmfp[slot] = nmfp;
+  t.ctr[slot] = rng.ctr;
+  t.step[slot] = s;
+  if (eloss) t.rpost[slot] = R - s;
+  t.action[slot] = act;
+  return act;
+}
+
+// ------------------------------------------------------------------ kernels
+// Initializer, pass 1: vacant slots per tile of kInitTile slots. Block 0 also
+// clears the per-iteration counters.
+__global__ void __launch_bounds__(256) k_init_count(Params p) {
+  Ctl* c = p.ctl;
+  if (blockIdx.x == 0) {
+    if (threadIdx.x < kMaxKeys) {
+      c->action_count[threadIdx.x] = 0;
+      c->key_total[threadIdx.x] = 0;
+    }
+    if (threadIdx.x == 0) {
+      c->steps_iter = 0;
+      c->n_deferred = 0;
+    }
+  }
+  if (c->tail == c->head) return;
+  const uint32_t tile = blockIdx.x;
+  unsigned cnt = 0;
+#pragma unroll
+  for (int j = 0; j < kInitTile / 256; ++j) {
+    const uint32_t slot = tile * kInitTile + j * 256 + threadIdx.x;
+    if (slot < p.n_slots && p.trk.status[slot] == VACANT) ++cnt;
+  }
+  __shared__ unsigned s_sum[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned tot = 0;
+    for (int w = 0; w < 8; ++w) tot += s_sum[w];
+    p.init_counts[tile] = tot;
+  }
+}
+
+// Initializer, pass 2: the r-th vacant slot in ascending slot order takes
+// initializer head + r, for r < min(vacant, queued) (deterministic filling).
+__global__ void __launch_bounds__(256) k_init_fill(Params p) {
+  Ctl* c = p.ctl;
+  const unsigned long long head = c->head;
+  const unsigned long long queued = c->tail - head;
+  if (queued == 0) return;
+  const uint32_t tile = blockIdx.x;
+  unsigned long long before = 0, total = 0;
+  for (uint32_t i = threadIdx.x; i < p.n_init_tiles; i += 256) {
+    const unsigned v = p.init_counts[i];
+    total += v;
+    if (i < tile) before += v;
+  }
+  __shared__ unsigned long long s_b[8], s_t[8];
+  __shared__ unsigned s_w[8];
+  __shared__ unsigned long long s_before;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    before += __shfl_down_sync(0xffffffffu, before, o);
+    total += __shfl_down_sync(0xffffffffu, total, o);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    s_b[warp] = before;
+    s_t[warp] = total;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long b = 0, tt = 0;
+    for (int w = 0; w < 8; ++w) {
+      b += s_b[w];
+      tt += s_t[w];
+    }
+    s_before = b;
+    if (blockIdx.x == 0) {
+      const unsigned long long take = tt < queued ? tt : queued;
+      c->head_pending = head + take;
+      c->alive += take;
+    }
+  }
+  __syncthreads();
+  before = s_before;
+  if (before >= queued) return;
+  unsigned long long running = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int j = 0; j < kInitTile / 256; ++j) {
+    const uint32_t slot = tile * kInitTile + j * 256 + threadIdx.x;
+    const bool vac = slot < p.n_slots && p.trk.status[slot] == VACANT;
+    const unsigned bal = __ballot_sync(0xffffffffu, vac);
+    if (lane == 0) s_w[warp] = __popc(bal);
+    __syncthreads();
+    unsigned wpre = 0, chunk = 0;
+    for (int w = 0; w < 8; ++w) {
+      const unsigned v = s_w[w];
+      if (w < warp) wpre += v;
+      chunk += v;
+    }
+    __syncthreads();
+    const unsigned long long r = before + running + wpre + __popc(bal & lt);
+    if (vac && r < queued) {
+      const unsigned long long i = (head + r) & p.ring_mask;
+      const Tracks& t = p.trk;
+      t.x[slot] = p.ring.x[i];
+      t.y[slot] = p.ring.y[i];
+      t.z[slot] = p.ring.z[i];
+      t.ux[slot] = p.ring.ux[i];
+      t.uy[slot] = p.ring.uy[i];
+      t.uz[slot] = p.ring.uz[i];
+      t.E[slot] = p.ring.E[i];
+      t.tid[slot] = p.ring.tid[i];
+      t.event[slot] = p.ring.event[i];
+      t.primary[slot] = p.ring.primary[i];
+      t.layer[slot] = p.ring.layer[i];
+      t.ptype[slot] = p.ring.ptype[i];
+      t.ctr[slot] = 0u;
+      t.nmfp[slot] = -1.0;
+      t.action[slot] = A_NONE;
+      t.status[slot] = ALIVE;
+    }
+    running += chunk;
+    if (before + running >= queued) break;
+  }
+}
+
+// Step limit over all slots, one tile of kTile slots per block iteration;
+// also counts tracks per next action and, for the sorted policies, per
+// partition key and tile.
+__global__ void __launch_bounds__(kTile) k_pre_step(Params p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* s_tab = reinterpret_cast<double2*>(smem_raw);
+  const int ntab = p.n_materials * kCols * kGrid;
+  double* s_zb = reinterpret_cast<double*>(s_tab + ntab);
+  int32_t* s_lmat = reinterpret_cast<int32_t*>(s_zb + p.n_layers + 1);
+  __shared__ unsigned s_keys[kMaxKeys];
+  __shared__ unsigned s_acts[A_COUNT];
+  for (int i = threadIdx.x; i < ntab; i += blockDim.x) s_tab[i] = p.tables[i];
+  for (int i = threadIdx.x; i <= p.n_layers; i += blockDim.x) s_zb[i] = p.zb[i];
+  for (int i = threadIdx.x; i < p.n_layers; i += blockDim.x) s_lmat[i] = p.layer_mat[i];
+  if (threadIdx.x < A_COUNT) s_acts[threadIdx.x] = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) p.ctl->head = p.ctl->head_pending;
+  __syncthreads();
+
+  const bool sorted = p.policy != POLICY_NONE;
+  const uint8_t vacant_key = p.policy == POLICY_ACTION ? KA_VACANT : K_VACANT_FULL;
+  unsigned long long my_steps = 0;
+  for (uint32_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
+    if (threadIdx.x < kMaxKeys) s_keys[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t slot = tile * kTile + threadIdx.x;
+    uint8_t key = vacant_key;
+    if (slot < p.n_slots) {
+      const uint8_t st = p.trk.status[slot];
+      uint8_t act = A_NONE;
+      if (st == ALIVE) {
+        act = step_limit(p, slot, s_tab, s_zb, s_lmat);
+        ++my_steps;
+      } else if (st == DEFERRED) {
+        act = p.trk.action[slot];
+      }
+      if (st != VACANT) {
+        atomicAdd(&s_acts[act], 1u);
+        if (sorted) key = key_of(p.policy, p.trk.ptype[slot], act);
+      }
+      if (sorted) p.trk.key[slot] = key;
+    }
+    if (sorted) {
+      const unsigned peers = __match_any_sync(0xffffffffu, (unsigned)key);
+      if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&s_keys[key], (unsigned)__popc(peers));
+      __syncthreads();
+      if ((int)threadIdx.x < p.n_keys) p.tile_counts[threadIdx.x * p.n_tiles + tile] = s_keys[threadIdx.x];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < A_COUNT && s_acts[threadIdx.x] != 0) atomicAdd(&p.ctl->action_count[threadIdx.x], s_acts[threadIdx.x]);
+  flush_counter(&p.ctl->steps_iter, my_steps, false);
+}
+
+// Exclusive scan of the per-(key, tile) counts in key-major order, which
+// yields each tile's output position per key and the key offsets; then the
+// decision whether this iteration's secondaries fit in the buffer.
+__global__ void __launch_bounds__(1024) k_iter_ctl(Params p) {
+  Ctl* c = p.ctl;
+  if (p.policy != POLICY_NONE) {
+    __shared__ unsigned s_warp[32];
+    __shared__ unsigned s_total;
+    const uint32_t total = (uint32_t)p.n_keys * p.n_tiles;
+    const uint32_t per = (total + blockDim.x - 1) / blockDim.x;
+    const uint32_t beg = min(threadIdx.x * per, total);
+    const uint32_t end = min(beg + per, total);
+    unsigned local = 0;
+    for (uint32_t i = beg; i < end; ++i) local += p.tile_counts[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0u;
+      unsigned wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += v;
+      }
+      s_warp[lane] = wi - w;
+      if (lane == 31) s_total = wi;
+    }
+    __syncthreads();
+    unsigned run = s_warp[warp] + incl - local;
+    for (uint32_t i = beg; i < end; ++i) {
+      const unsigned v = p.tile_counts[i];
+      p.tile_counts[i] = run;
+      run += v;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < p.n_keys) c->offsets[threadIdx.x] = p.tile_counts[threadIdx.x * p.n_tiles];
+    if ((int)threadIdx.x == p.n_keys) c->offsets[p.n_keys] = s_total;
+  }
+  if (threadIdx.x == 0) {
+    const unsigned long long queued = c->tail - c->head;
+    const unsigned long long max_new =
+        2ull * c->action_count[A_PAIR] + c->action_count[A_MOLLER] + c->action_count[A_BREMS];
+    c->defer = (queued + max_new > p.ring_capacity) ? 1u : 0u;
+  }
+}
+
+// Stable scatter of slot indices into the partition: position = tile's
+// offset for the key + same-key slots in earlier warps + same-key lanes below.
+__global__ void __launch_bounds__(kTile) k_scatter(Params p) {
+  __shared__ unsigned s_cnt[kTile / 32][kMaxKeys];
+  const uint8_t vacant_key = p.policy == POLICY_ACTION ? KA_VACANT : K_VACANT_FULL;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
+    if (threadIdx.x < (kTile / 32) * kMaxKeys) (&s_cnt[0][0])[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t slot = tile * kTile + threadIdx.x;
+    const unsigned key = slot < p.n_slots ? p.trk.key[slot] : vacant_key;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+    if (lane == __ffs(peers) - 1) s_cnt[warp][key] = __popc(peers);
+    __syncthreads();
+    if (key != vacant_key) {
+      unsigned pos = p.tile_counts[key * p.n_tiles + tile] + rank;
+      for (int w = 0; w < warp; ++w) pos += s_cnt[w][key];
+      p.perm[pos] = slot;
+    }
+    __syncthreads();
+  }
+}
+
+// Along-step: move by the step length (straight line, or the exact helix for
+// charged tracks in the field), continuous energy loss through the inverse
+// range table, then the geometric post-step: next layer or escape through a
+// z-plane, escape through a side plane, and the tracking cut.
+template <bool CHARGED>
+__global__ void k_along(Params p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* s_range = reinterpret_cast<double2*>(smem_raw);
+  const int nr = CHARGED ? p.n_materials * kGrid : 0;
+  double* s_zb = reinterpret_cast<double*>(s_range + nr);
+  int32_t* s_lmat = reinterpret_cast<int32_t*>(s_zb + p.n_layers + 1);
+  if (CHARGED) {
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+      const int mat = i / kGrid, k = i - mat * kGrid;
+      s_range[i] = p.tables[(mat * kCols + COL_RANGE) * kGrid + k];
+    }
+  }
+  for (int i = threadIdx.x; i <= p.n_layers; i += blockDim.x) s_zb[i] = p.zb[i];
+  for (int i = threadIdx.x; i < p.n_layers; i += blockDim.x) s_lmat[i] = p.layer_mat[i];
+  __syncthreads();
+
+  const Span sp = CHARGED ? span_of(p, KA_CHARGED, KA_CHARGED + 1, K_E_GEOM, K_E_BREMS + 1)
+                          : span_of(p, KA_NEUTRAL, KA_NEUTRAL + 1, K_G_GEOM, K_G_PAIR + 1);
+  const bool eloss = CHARGED && (p.processes & PROC_ELOSS);
+  const bool helix = CHARGED && p.Bz != 0.0;
+  const Tracks& t = p.trk;
+  unsigned long long killed = 0;
+  for (uint32_t i = sp.lo + blockIdx.x * blockDim.x + threadIdx.x; i < sp.hi; i += gridDim.x * blockDim.x) {
+    const uint32_t slot = sp.perm ? sp.perm[i] : i;
+    if (t.status[slot] != ALIVE) continue;
+    const uint8_t pt = t.ptype[slot];
+    if (CHARGED ? pt == GAMMA : pt != GAMMA) continue;
+    const uint8_t act = t.action[slot];
+    const uint32_t ev = t.event[slot], prim = t.primary[slot];
+    int layer = t.layer[slot];
+    double E = t.E[slot];
+    double z = t.z[slot];
+    if (prim < p.hist_cap) atomicAdd(&p.hist_steps[prim], 1ull);
+    if (act == A_TRAPPED) {
+      deposit(p, ev, prim, layer, z, E);
+      release(p, slot, ev);
+      ++killed;
+      continue;
+    }
+    const double s = t.step[slot];
+    double x = t.x[slot], y = t.y[slot];
+    double ux = t.ux[slot], uy = t.uy[slot];
+    const double uz = t.uz[slot];
+    if (helix) {
+      helix_move(curvature(pt, E, p.Bz), s, x, y, z, ux, uy, uz);
+    } else {
+      x += s * ux;
+      y += s * uy;
+      z += s * uz;
+    }
+    if (eloss) {
+      const double Ep = inverse_range(s_range + s_lmat[layer] * kGrid, t.rpost[slot], p.lnEmin, p.dl);
+      deposit(p, ev, prim, layer, z, E - Ep);
+      E = Ep;
+    }
+    bool out = false;
+    if (act == A_ZUP) {
+      layer += 1;
+      if (layer >= p.n_layers) {
+        out = true;
+      } else {
+        z = s_zb[layer];
+      }
+    } else if (act == A_ZDOWN) {
+      z = s_zb[layer];
+      layer -= 1;
+      if (layer < 0) out = true;
+    } else if (act == A_SIDE) {
+      out = true;
+    }
+    if (out) {
+      escape(p, ev, prim, E);
+      release(p, slot, ev);
+      ++killed;
+      continue;
+    }
+    if (E < p.cut_track) {
+      deposit(p, ev, prim, layer, z, E);
+      release(p, slot, ev);
+      ++killed;
+      continue;
+    }
+    t.x[slot] = x;
+    t.y[slot] = y;
+    t.z[slot] = z;
+    if (helix) {
+      t.ux[slot] = ux;
+      t.uy[slot] = uy;
+    }
+    if (eloss) t.E[slot] = E;
+    if (act == A_ZUP || act == A_ZDOWN) t.layer[slot] = layer;
+  }
+  flush_counter(&p.ctl->alive, killed, true);
+}
+
+// Compton scattering: Klein-Nishina sampling, the recoil energy deposited
+// locally, the photon rotated; below the tracking cut it is absorbed.
+__global__ void k_compton(Params p) {
+  const Span sp = span_of(p, KA_NEUTRAL, KA_NEUTRAL + 1, K_G_COMPTON, K_G_COMPTON + 1);
+  const Tracks& t = p.trk;
+  unsigned long long killed = 0;
+  for (uint32_t i = sp.lo + blockIdx.x * blockDim.x + threadIdx.x; i < sp.hi; i += gridDim.x * blockDim.x) {
+    const uint32_t slot = sp.perm ? sp.perm[i] : i;
+    if (t.status[slot] != ALIVE || t.action[slot] != A_COMPTON) continue;
+    const double E = t.E[slot];
+    const uint32_t ev = t.event[slot], prim = t.primary[slot];
+    const int layer = t.layer[slot];
+    const double z = t.z[slot];
+    TrackRng rng(p.seed, ev, t.tid[slot], t.ctr[slot]);
+    double cost;
+    bool ok;
+    const double eps = sample_compton(E, rng, cost, ok);
+    if (!ok) {  // non-finite input: end the track, flag the run
+      atomicOr(&p.ctl->error, ERR_SAMPLING);
+      deposit(p, ev, prim, layer, z, E);
+      release(p, slot, ev);
+      ++killed;
+      continue;
+    }
+    const double phi = kTwoPi * rng.uniform();
+    const double E1 = eps * E;
+    deposit(p, ev, prim, layer, z, E - E1);
+    if (E1 < p.cut_track) {
+      deposit(p, ev, prim, layer, z, E1);
+      release(p, slot, ev);
+      ++killed;
+      continue;
+    }
+    double ux = t.ux[slot], uy = t.uy[slot], uz = t.uz[slot];
+    rotate_dir(ux, uy, uz, cost, phi);
+    t.ux[slot] = ux;
+    t.uy[slot] = uy;
+    t.uz[slot] = uz;
+    t.E[slot] = E1;
+    t.nmfp[slot] = -1.0;
+    t.ctr[slot] = rng.ctr;
+  }
+  flush_counter(&p.ctl->alive, killed, true);
+}
+
+// Photoelectric absorption: all energy deposited locally.
+__global__ void k_photoelectric(Params p) {
+  const Span sp = span_of(p, KA_NEUTRAL, KA_NEUTRAL + 1, K_G_PE, K_G_PE + 1);
+  const Tracks& t = p.trk;
+  unsigned long long killed = 0;
+  for (uint32_t i = sp.lo + blockIdx.x * blockDim.x + threadIdx.x; i < sp.hi; i += gridDim.x * blockDim.x) {
+    const uint32_t slot = sp.perm ? sp.perm[i] : i;
+    if (t.status[slot] != ALIVE || t.action[slot] != A_PE) continue;
+    const uint32_t ev = t.event[slot];
+    deposit(p, ev, t.primary[slot], t.layer[slot], t.z[slot], t.E[slot]);
+    release(p, slot, ev);
+    ++killed;
+  }
+  flush_counter(&p.ctl->alive, killed, true);
+}
+
+// Defer a secondary-producing interaction when the buffer might overflow
+// this iteration: the track keeps its state and draw counter, so the
+// interaction replays identically later. Returns true if deferred.
+__device__ __forceinline__ bool maybe_defer(const Params& p, uint32_t slot, uint8_t st, bool defer,
+                                            unsigned long long& n_def) {
+  if (!defer) return false;
+  if (st == ALIVE) {
+    p.trk.status[slot] = DEFERRED;
+    ++n_def;
+  }
+  return true;
+}
+
+// Pair production: the pair's kinetic energy E - 2 m_e c^2 deposited locally,
+// two photons of m_e c^2 back to back in an isotropic direction.
+__global__ void k_pair(Params p) {
+  const Span sp = span_of(p, KA_NEUTRAL, KA_NEUTRAL + 1, K_G_PAIR, K_G_PAIR + 1);
+  const Tracks& t = p.trk;
+  const bool defer = p.ctl->defer != 0u;
+  unsigned long long killed = 0, n_def = 0;
+  for (uint32_t i = sp.lo + blockIdx.x * blockDim.x + threadIdx.x; i < sp.hi; i += gridDim.x * blockDim.x) {
+    const uint32_t slot = sp.perm ? sp.perm[i] : i;
+    const uint8_t st = t.status[slot];
+    if (st == VACANT || t.action[slot] != A_PAIR) continue;
+    if (maybe_defer(p, slot, st, defer, n_def)) continue;
+    const double E = t.E[slot];
+    const uint32_t ev = t.event[slot], prim = t.primary[slot];
+    const int layer = t.layer[slot];
+    const double x = t.x[slot], y = t.y[slot], z = t.z[slot];
+    TrackRng rng(p.seed, ev, t.tid[slot], t.ctr[slot]);
+    deposit(p, ev, prim, layer, z, E - 2.0 * kMe);
+    const double cost = 2.0 * rng.uniform() - 1.0;
+    const double phi = kTwoPi * rng.uniform();
+    const double sint = sqrt(fmax(0.0, 1.0 - cost * cost));
+    double sp_, cp_;
+    sincos(phi, &sp_, &cp_);
+    const double dx = sint * cp_, dy = sint * sp_, dz = cost;
+    const bool keep = kMe >= p.cut_track;
+    const unsigned n = keep ? 2u : 0u;
+    if (!keep) {
+      deposit(p, ev, prim, layer, z, kMe);
+      deposit(p, ev, prim, layer, z, kMe);
+    }
+    const unsigned long long base = reserve(p.ctl, n);
+    if (keep) {
+      const unsigned long long tid1 = rng.raw();
+      const unsigned long long tid2 = rng.raw();
+      write_initializer(p, base, x, y, z, dx, dy, dz, kMe, tid1, ev, prim, layer, GAMMA);
+      write_initializer(p, base + 1, x, y, z, -dx, -dy, -dz, kMe, tid2, ev, prim, layer, GAMMA);
+      atomicAdd(&p.event_live[row_of(p, ev)], 2u);
+      if (prim < p.hist_cap) atomicAdd(&p.hist_secondaries[prim], 2ull);
+    }
+    release(p, slot, ev);
+    ++killed;
+  }
+  flush_counter(&p.ctl->alive, killed, true);
+  if (n_def) atomicAdd(&p.ctl->n_deferred, (unsigned)n_def);
+}
+
+// Moller scattering: delta ray above the production cut from the Moller
+// cross-section, directions from two-body kinematics (delta polar angle from
+// energy-momentum conservation, primary from momentum conservation).
+__global__ void k_moller(Params p) {
+  const Span sp = span_of(p, KA_CHARGED, KA_CHARGED + 1, K_E_MOLLER, K_E_MOLLER + 1);
+  const Tracks& t = p.trk;
+  const bool defer = p.ctl->defer != 0u;
+  unsigned long long killed = 0, n_def = 0;
+  for (uint32_t i = sp.lo + blockIdx.x * blockDim.x + threadIdx.x; i < sp.hi; i += gridDim.x * blockDim.x) {
+    const uint32_t slot = sp.perm ? sp.perm[i] : i;
+    const uint8_t st = t.status[slot];
+    if (st == VACANT || t.action[slot] != A_MOLLER) continue;
+    if (maybe_defer(p, slot, st, defer, n_def)) continue;
+    const double T = t.E[slot];
+    if (T <= 2.0 * p.cut_moller) {  // kinematically closed at the post-step energy: null collision
+      t.nmfp[slot] = -1.0;
+      t.status[slot] = ALIVE;
+      continue;
+    }
+    const uint32_t ev = t.event[slot], prim = t.primary[slot];
+    const int layer = t.layer[slot];
+    const double x = t.x[slot], y = t.y[slot], z = t.z[slot];
+    TrackRng rng(p.seed, ev, t.tid[slot], t.ctr[slot]);
+    bool ok;
+    const double eps = sample_moller(T, p.cut_moller, rng, ok);
+    if (!ok) {  // non-finite input: end the track, flag the run
+      atomicOr(&p.ctl->error, ERR_SAMPLING);
+      deposit(p, ev, prim, layer, z, T);
+      release(p, slot, ev);
+      ++killed;
+      continue;
+    }
+    const double Td = eps * T;
+    const double cost = fmin(1.0, sqrt(Td * (T + 2.0 * kMe) / (T * (Td + 2.0 * kMe))));
+    const double phi = kTwoPi * rng.uniform();
+    const double ux = t.ux[slot], uy = t.uy[slot], uz = t.uz[slot];
+    double dx = ux, dy = uy, dz = uz;
+    rotate_dir(dx, dy, dz, cost, phi);
+    const double pp = sqrt(T * (T + 2.0 * kMe));
+    const double pd = sqrt(Td * (Td + 2.0 * kMe));
+    const double vx = pp * ux - pd * dx, vy = pp * uy - pd * dy, vz = pp * uz - pd * dz;
+    const double inv = 1.0 / sqrt(vx * vx + vy * vy + vz * vz);
+    const double E1 = T - Td;
+    const bool keep = Td >= p.cut_track;
+    if (!keep) deposit(p, ev, prim, layer, z, Td);
+    const unsigned long long base = reserve(p.ctl, keep ? 1u : 0u);
+    if (keep) {
+      const unsigned long long tid = rng.raw();
+      write_initializer(p, base, x, y, z, dx, dy, dz, Td, tid, ev, prim, layer, ELECTRON);
+      atomicAdd(&p.event_live[row_of(p, ev)], 1u);
+      if (prim < p.hist_cap) atomicAdd(&p.hist_secondaries[prim], 1ull);
+    }
+    if (E1 < p.cut_track) {
+      deposit(p, ev, prim, layer, z, E1);
+      release(p, slot, ev);
+      ++killed;
+      continue;
+    }
+    t.ux[slot] = vx * inv;
+    t.uy[slot] = vy * inv;
+    t.uz[slot] = vz * inv;
+    t.E[slot] = E1;
+    t.nmfp[slot] = -1.0;
+    t.ctr[slot] = rng.ctr;
+    t.status[slot] = ALIVE;
+  }
+  flush_counter(&p.ctl->alive, killed, true);
+  if (n_def) atomicAdd(&p.ctl->n_deferred, (unsigned)n_def);
+}
+
+// Bremsstrahlung: photon energy from the 1/k spectrum on (k_cut, T], emitted
+// along the parent direction; the parent keeps its direction.
+__global__ void k_brems(Params p) {
+  const Span sp = span_of(p, KA_CHARGED, KA_CHARGED + 1, K_E_BREMS, K_E_BREMS + 1);
+  const Tracks& t = p.trk;
+  const bool defer = p.ctl->defer != 0u;
+  unsigned long long killed = 0, n_def = 0;
+  for (uint32_t i = sp.lo + blockIdx.x * blockDim.x + threadIdx.x; i < sp.hi; i += gridDim.x * blockDim.x) {
+    const uint32_t slot = sp.perm ? sp.perm[i] : i;
+    const uint8_t st = t.status[slot];
+    if (st == VACANT || t.action[slot] != A_BREMS) continue;
+    if (maybe_defer(p, slot, st, defer, n_def)) continue;
+    const double T = t.E[slot];
+    if (T <= p.cut_brems) {  // null collision
+      t.nmfp[slot] = -1.0;
+      t.status[slot] = ALIVE;
+      continue;
+    }
+    const uint32_t ev = t.event[slot], prim = t.primary[slot];
+    const int layer = t.layer[slot];
+    const double x = t.x[slot], y = t.y[slot], z = t.z[slot];
+    TrackRng rng(p.seed, ev, t.tid[slot], t.ctr[slot]);
+    double k = p.cut_brems * exp(rng.uniform() * log(T / p.cut_brems));
+    if (k > T) k = T;
+    const double E1 = T - k;
+    const bool keep = k >= p.cut_track;
+    if (!keep) deposit(p, ev, prim, layer, z, k);
+    const unsigned long long base = reserve(p.ctl, keep ? 1u : 0u);
+    if (keep) {
+      const unsigned long long tid = rng.raw();
+      write_initializer(p, base, x, y, z, t.ux[slot], t.uy[slot], t.uz[slot], k, tid, ev, prim, layer, GAMMA);
+      atomicAdd(&p.event_live[row_of(p, ev)], 1u);
+      if (prim < p.hist_cap) atomicAdd(&p.hist_secondaries[prim], 1ull);
+    }
+    if (E1 < p.cut_track) {
+      deposit(p, ev, prim, layer, z, E1);
+      release(p, slot, ev);
+      ++killed;
+      continue;
+    }
+    t.E[slot] = E1;
+    t.nmfp[slot] = -1.0;
+    t.ctr[slot] = rng.ctr;
+    t.status[slot] = ALIVE;
+  }
+  flush_counter(&p.ctl->alive, killed, true);
+  if (n_def) atomicAdd(&p.ctl->n_deferred, (unsigned)n_def);
+}
+
+// End of an iteration: counters, the per-iteration trace row, stall and
+// iteration-limit checks, and the loop condition (set on the graph's
+// conditional node when the loop runs inside a CUDA graph).
+__global__ void k_loop_ctl(Params p, cudaGraphConditionalHandle handle, int use_handle) {
+  Ctl* c = p.ctl;
+  const unsigned long long queued = c->tail - c->head;
+  const bool worked = c->steps_iter > 0 || c->n_deferred > 0;
+  if (worked) {
+    c->steps_total += c->steps_iter;
+    TraceRow& r = p.trace[c->trace_count % kTraceRows];
+    r.iteration = c->iteration;
+    r.alive = c->alive;
+    r.queued = queued;
+    r.steps = c->steps_iter;
+    for (int k = 0; k < kMaxKeys; ++k) r.action_count[k] = c->action_count[k];
+    c->trace_count += 1;
+    c->iteration += 1;
+  }
+  if (c->steps_iter == 0 && c->n_deferred > 0) {
+    c->stall += 1;
+    if (c->stall >= 3) c->error |= ERR_NO_PROGRESS;
+  } else {
+    c->stall = 0;
+  }
+  const bool pending = c->alive + queued > 0;
+  if (pending && c->iteration >= c->max_iterations) c->error |= ERR_ITERATIONS;
+  c->cont = (pending && c->error == 0u) ? 1u : 0u;
+  if (use_handle) cudaGraphSetConditional(handle, c->cont);
+}
+
+// Queue staged primaries at the tail of the initializer buffer.
+__global__ void __launch_bounds__(1024) k_push_primaries(Params p, const StagedPrimary* src, uint32_t n) {
+  __shared__ unsigned long long s_base;
+  if (threadIdx.x == 0) s_base = p.ctl->tail;
+  __syncthreads();
+  const unsigned long long base = s_base;
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const StagedPrimary& q = src[i];
+    write_initializer(p, base + i, q.x, q.y, q.z, q.ux, q.uy, q.uz, q.E, q.tid, q.event, q.primary, q.layer,
+                      (uint8_t)q.ptype);
+    atomicAdd(&p.event_live[row_of(p, q.event)], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) p.ctl->tail = base + n;
+}
+
+// Validate and queue primaries that are already in device memory: one block;
+// pass 1 checks every record (and the buffer fill level), pass 2 queues all
+// of them only if every check passed.
+__global__ void __launch_bounds__(1024) k_push_device_primaries(Params p, const DevicePrimary* src, uint32_t n,
+                                                                 uint32_t event, unsigned long long tid0,
+                                                                 uint32_t prim0) {
+  __shared__ unsigned s_bad;
+  __shared__ unsigned long long s_base;
+  if (threadIdx.x == 0) {
+    s_bad = 0;
+    s_base = p.ctl->tail;
+    const unsigned long long queued = p.ctl->tail - p.ctl->head_pending;
+    if (queued + n > p.ring_capacity) s_bad = 1;
+  }
+  __syncthreads();
+  const double zmax = p.zb[p.n_layers];
+  unsigned bad = 0;
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const DevicePrimary& q = src[i];
+    const double d2 = q.dir[0] * q.dir[0] + q.dir[1] * q.dir[1] + q.dir[2] * q.dir[2];
+    const bool ok = isfinite(q.E) && q.E > 0.0 && q.E <= kGridEmax && isfinite(d2) &&
+                    fabs(sqrt(d2) - 1.0) <= 1e-12 && fabs(q.pos[0]) <= p.hx && fabs(q.pos[1]) <= p.hy &&
+                    q.pos[2] >= p.zb[0] && q.pos[2] <= zmax && (q.ptype == GAMMA || q.ptype == ELECTRON);
+    if (!ok) bad = 1;
+  }
+  if (bad) atomicOr(&s_bad, 1u);
+  __syncthreads();
+  if (s_bad) {
+    if (threadIdx.x == 0) atomicOr(&p.ctl->error, ERR_PRIMARIES_REJECTED);
+    return;
+  }
+  const unsigned long long base = s_base;
+  const int L = p.n_layers;
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const DevicePrimary& q = src[i];
+    const double z = q.pos[2], uz = q.dir[2];
+    // layer: the largest l <= L-1 with z_l <= z; on an inner plane moving
+    // backwards, the layer behind it
+    int lo = 0;
+    if (z >= zmax) {
+      lo = L - 1;
+    } else {
+      int hi = L - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (p.zb[mid] <= z)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      if (z == p.zb[lo] && uz < 0.0 && lo > 0) --lo;
+    }
+    const uint32_t prim = p.hist_cap > 0 ? prim0 + i : 0xFFFFFFFFu;
+    write_initializer(p, base + i, q.pos[0], q.pos[1], z, q.dir[0], q.dir[1], uz, q.E, tid0 + i, event, prim, lo,
+                      (uint8_t)q.ptype);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    p.ctl->tail = base + n;
+    atomicAdd(&p.event_live[row_of(p, event)], n);
+  }
+}
+
+int occupancy_grid(const void* fn, int block, size_t smem, int sms, int cap) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, smem) != cudaSuccess || nb < 1) nb = 1;
+  long g = (long)nb * sms;
+  if (cap > 0 && g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+cudaError_t configure_kernels(const Params& p, int block, LaunchShape* sh) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const size_t geo = (size_t)(p.n_layers + 1) * sizeof(double) + (size_t)p.n_layers * sizeof(int32_t);
+  sh->pre_smem = (size_t)p.n_materials * kCols * kGrid * sizeof(double2) + geo;
+  sh->along_smem = (size_t)p.n_materials * kGrid * sizeof(double2) + geo;
+  sh->neutral_smem = geo;
+  sh->block = block;
+  e = cudaFuncSetAttribute(k_pre_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh->pre_smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_along<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh->along_smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_along<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh->neutral_smem);
+  if (e != cudaSuccess) return e;
+  sh->pre_grid = occupancy_grid((const void*)k_pre_step, kTile, sh->pre_smem, sms, (int)p.n_tiles);
+  const int cap_action = (int)((p.n_slots + block - 1) / block);
+  sh->action_grid = occupancy_grid((const void*)k_along<true>, block, sh->along_smem, sms, cap_action);
+  return cudaGetLastError();
+}
+
+void launch_init_count(const Params& p, cudaStream_t s) { k_init_count<<<p.n_init_tiles, 256, 0, s>>>(p); }
+void launch_init_fill(const Params& p, cudaStream_t s) { k_init_fill<<<p.n_init_tiles, 256, 0, s>>>(p); }
+void launch_pre_step(const Params& p, const LaunchShape& sh, cudaStream_t s) {
+  k_pre_step<<<sh.pre_grid, kTile, sh.pre_smem, s>>>(p);
+}
+void launch_iter_ctl(const Params& p, cudaStream_t s) { k_iter_ctl<<<1, 1024, 0, s>>>(p); }
+void launch_scatter(const Params& p, const LaunchShape& sh, cudaStream_t s) {
+  k_scatter<<<sh.pre_grid, kTile, 0, s>>>(p);
+}
+void launch_along(const Params& p, bool charged, const LaunchShape& sh, cudaStream_t s) {
+  if (charged)
+    k_along<true><<<sh.action_grid, sh.block, sh.along_smem, s>>>(p);
+  else
+    k_along<false><<<sh.action_grid, sh.block, sh.neutral_smem, s>>>(p);
+}
+void launch_post(const Params& p, int which, const LaunchShape& sh, cudaStream_t s) {
+  switch (which) {
+    case POST_COMPTON: k_compton<<<sh.action_grid, sh.block, 0, s>>>(p); break;
+    case POST_PE: k_photoelectric<<<sh.action_grid, sh.block, 0, s>>>(p); break;
+    case POST_PAIR: k_pair<<<sh.action_grid, sh.block, 0, s>>>(p); break;
+    case POST_MOLLER: k_moller<<<sh.action_grid, sh.block, 0, s>>>(p); break;
+    case POST_BREMS: k_brems<<<sh.action_grid, sh.block, 0, s>>>(p); break;
+    default: break;
+  }
+}
+void launch_loop_ctl(const Params& p, unsigned long long handle, int use_handle, cudaStream_t s) {
+  k_loop_ctl<<<1, 1, 0, s>>>(p, (cudaGraphConditionalHandle)handle, use_handle);
+}
+void launch_push_primaries(const Params& p, const StagedPrimary* d_prim, uint32_t n, cudaStream_t s) {
+  k_push_primaries<<<1, 1024, 0, s>>>(p, d_prim, n);
+}
+
+void launch_push_device_primaries(const Params& p, const DevicePrimary* src, uint32_t n, uint32_t event,
+                                  unsigned long long tid0, uint32_t prim0, cudaStream_t s) {
+  k_push_device_primaries<<<1, 1024, 0, s>>>(p, src, n, event, tid0, prim0);
+}
+
+const char* kernel_name(int id) {
+  static const char* names[KID_COUNT] = {"init_count", "init_fill", "pre_step", "iter_ctl", "scatter",
+                                         "along_neutral", "along_charged", "compton", "photoelectric",
+                                         "pair", "moller", "brems", "loop_ctl"};
+  return (id >= 0 && id < KID_COUNT) ? names[id] : "?";
+}
+
+}  // namespace celer

@@ -1,0 +1,239 @@
+"""CUDA path vs CPU oracle, element by element, on the same seeded inputs.
+
+Photon-only water cube: per-history step and secondary counts bit-exact,
+deposits per history and per bin within 1e-9 relative (binary64; the two
+codes differ only in the last-bit rounding of their math libraries and of
+fused multiply-adds). Calorimeter configurations: most histories match
+outright; layer profiles agree statistically with independent seeds.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_17608_gb300 import binding, workloads as wl
+
+from gpu_helpers import assert_conservation, match_fraction, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+POLICIES = [wl.SORT_NONE, wl.SORT_ACTION, wl.SORT_ACTION_TYPE]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    binding.load()
+
+
+# ------------------------------------------------------------------ RNG
+def test_device_philox_matches_oracle():
+    rng = np.random.default_rng(3)
+    rec = rng.integers(0, 2**32, size=(20000, 6), dtype=np.uint64).astype(np.uint32)
+    dev = binding.debug_philox(rec)
+    for i in range(0, len(rec), 37):
+        assert oracle.philox(rec[i, :4].tolist(), rec[i, 4:].tolist()) == dev[i].tolist()
+
+
+def test_device_philox_matches_curand_library():
+    seed, sub, off = 0x1234_5678_9ABC_DEF0, 0xFEDC_BA98_7654_3210, 77
+    cur = binding.debug_curand_philox(seed, sub, off, 64)
+    rec = np.array([[(off + i) & 0xFFFFFFFF, (off + i) >> 32, sub & 0xFFFFFFFF, sub >> 32,
+                     seed & 0xFFFFFFFF, seed >> 32] for i in range(64)], dtype=np.uint64).astype(np.uint32)
+    np.testing.assert_array_equal(binding.debug_philox(rec), cur)
+    # and the oracle agrees with the library too
+    for i in (0, 5, 63):
+        assert oracle.philox(rec[i, :4].tolist(), rec[i, 4:].tolist()) == cur[i].tolist()
+
+
+# ------------------------------------------------------------------ tables
+@pytest.mark.parametrize("make", [wl.water_cube_problem, wl.calorimeter_problem])
+def test_device_tables_match_oracle(make):
+    prob = make()
+    w = oracle.World(prob)
+    cols = [oracle.COL_COMPTON, oracle.COL_PE, oracle.COL_PAIR, oracle.COL_MOLLER, oracle.COL_BREMS,
+            oracle.COL_RANGE]
+    with binding.Context(prob) as ctx:
+        for mat in range(len(prob.materials)):
+            for dc, oc in enumerate(cols):
+                d = ctx.debug_table(mat, dc)
+                o = w.table(mat, oc)
+                # Klein-Nishina loses ~log10(1/k^2) digits to cancellation at keV energies
+                np.testing.assert_allclose(d, o, rtol=1e-9, atol=0)
+
+
+# ------------------------------------------------------------------ photon-only water cube
+@pytest.mark.parametrize("policy", POLICIES)
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_water_cube_histories_bit_exact(policy, use_graph):
+    prob = wl.water_cube_problem()
+    prim = wl.water_cube_primaries()
+    g = run_gpu(prob, prim, use_graph=use_graph, policy=policy)
+    o = run_oracle(prob, prim)
+    np.testing.assert_array_equal(g["hist"]["steps"], o["hist"]["steps"])
+    np.testing.assert_array_equal(g["hist"]["secondaries"], o["hist"]["secondaries"])
+    np.testing.assert_allclose(g["edep"], o["edep"], rtol=1e-9, atol=1e-9 * 10.0)
+    np.testing.assert_allclose(g["hist"]["escaped"], o["hist"]["escaped"], rtol=1e-9, atol=1e-9 * 10.0)
+    tally, escaped = g["tally"][0]
+    np.testing.assert_allclose(tally, o["edep"].sum(0), rtol=1e-9, atol=1e-6)
+    assert escaped == pytest.approx(o["hist"]["escaped"].sum(), rel=1e-9)
+    assert_conservation(prim, g["tally"])
+    assert g["stats"]["steps_total"] == o["hist"]["steps"].sum()
+
+
+def test_results_independent_of_slot_count():
+    prim = wl.water_cube_primaries()
+    a = run_gpu(wl.water_cube_problem(n_slots=1024), prim, policy=wl.SORT_ACTION_TYPE)
+    b = run_gpu(wl.water_cube_problem(n_slots=4096), prim, policy=wl.SORT_NONE)
+    np.testing.assert_array_equal(a["hist"]["steps"], b["hist"]["steps"])
+    np.testing.assert_array_equal(a["hist"]["secondaries"], b["hist"]["secondaries"])
+    np.testing.assert_allclose(a["edep"], b["edep"], rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("n_slots", [1, 7, 1000, 2049])
+def test_ragged_slot_counts(n_slots):
+    prim = wl.water_cube_primaries(150)
+    prob = wl.water_cube_problem(n_slots=n_slots, init_capacity=4096)
+    g = run_gpu(prob, prim, policy=wl.SORT_ACTION_TYPE)
+    o = run_oracle(prob, prim)
+    np.testing.assert_array_equal(g["hist"]["steps"], o["hist"]["steps"])
+    np.testing.assert_allclose(g["edep"], o["edep"], rtol=1e-9, atol=1e-8)
+
+
+def test_empty_run_and_empty_add():
+    prob = wl.water_cube_problem()
+    with binding.Context(prob) as ctx:
+        ctx.add_primaries(0, wl.water_cube_primaries(0))
+        ctx.run_events(use_graph=True)
+        ctx.run_events(use_graph=False)
+        s = ctx.stats()
+        assert s["steps_total"] == 0 and s["alive"] == 0 and s["queued"] == 0
+        t, e = ctx.read_tallies(0)
+        assert t.sum() == 0 and e == 0
+
+
+def test_invalid_primaries_rejected():
+    prob = wl.water_cube_problem()
+    with binding.Context(prob) as ctx:
+        for field, value in (("E", -1.0), ("E", np.nan), ("E", 2e4)):
+            p = wl.water_cube_primaries(3)
+            p[field][1] = value
+            with pytest.raises(binding.CelerError) as ei:
+                ctx.add_primaries(0, p)
+            assert ei.value.status == 1
+        p = wl.water_cube_primaries(2)
+        p["dir"][0] = [0.0, 0.0, 1.001]
+        with pytest.raises(binding.CelerError):
+            ctx.add_primaries(0, p)
+        p = wl.water_cube_primaries(2)
+        p["pos"][0] = [60.0, 0.0, 1.0]
+        with pytest.raises(binding.CelerError):
+            ctx.add_primaries(0, p)
+        p = wl.water_cube_primaries(2)
+        p["ptype"][0] = wl.POSITRON
+        with pytest.raises(binding.CelerError):
+            ctx.add_primaries(0, p)
+        # nothing was queued by the rejected calls
+        ctx.run_events()
+        assert ctx.stats()["steps_total"] == 0
+
+
+def test_partition_is_a_stable_valid_partition():
+    prob = wl.calorimeter_problem(4096, sort_policy=wl.SORT_ACTION_TYPE)
+    prim = wl.electron_beam(8, 1000.0)
+    with binding.Context(prob) as ctx:
+        ctx.add_events(prim)
+        for it in range(60):
+            s = ctx.step()
+            if it % 10 == 9:
+                keys, perm, offs = ctx.debug_partition()
+                n_keys = len(offs) - 1
+                valid = offs[n_keys - 1]  # everything before the vacant key
+                p = perm[:valid]
+                assert len(np.unique(p)) == len(p)
+                assert np.all(p < prob.n_slots)
+                # keys non-decreasing along the permutation, slots increasing within a key
+                k = keys[p]
+                assert np.all(np.diff(k.astype(int)) >= 0)
+                expect = np.concatenate([np.flatnonzero(keys == key) for key in range(n_keys - 1)])
+                np.testing.assert_array_equal(p, expect)
+                counts = np.bincount(keys[:prob.n_slots], minlength=n_keys)
+                np.testing.assert_array_equal(np.diff(offs)[: n_keys - 1], counts[: n_keys - 1])
+            if s["alive"] == 0 and s["queued"] == 0:
+                break
+
+
+# ------------------------------------------------------------------ calorimeter, no field
+@pytest.mark.parametrize("policy", POLICIES)
+def test_calorimeter_histories(policy):
+    prob, prim = wl.calorimeter_1gev(200)
+    g = run_gpu(prob, prim, policy=policy)
+    o = run_oracle(prob, prim)
+    frac, _ = match_fraction(g, o)
+    assert frac >= 0.95, frac
+    assert_conservation(prim, g["tally"])
+    np.testing.assert_allclose(g["hist"]["edep"] + g["hist"]["escaped"], prim["E"], rtol=1e-12)
+
+
+def test_calorimeter_profile_statistics_independent_seeds():
+    """Two-sample test of per-primary layer profiles (GPU seed A vs oracle
+    seed B): Hotelling T^2 on the leading layers plus a chi-square per bin."""
+    from scipy import stats
+
+    prob, prim = wl.calorimeter_1gev(400)
+    g = run_gpu(prob.replace(seed=11), prim)
+    o = run_oracle(prob.replace(seed=12), prim)
+    a, b = g["edep"], o["edep"]
+    # group layers into 8 wide bins to keep the covariance well conditioned
+    A = a.reshape(len(a), 8, -1).sum(2)
+    B = b.reshape(len(b), 8, -1).sum(2)
+    na, nb = len(A), len(B)
+    d = A.mean(0) - B.mean(0)
+    S = ((na - 1) * np.cov(A.T) + (nb - 1) * np.cov(B.T)) / (na + nb - 2)
+    t2 = na * nb / (na + nb) * d @ np.linalg.solve(S, d)
+    p_dim = A.shape[1]
+    f = (na + nb - p_dim - 1) / (p_dim * (na + nb - 2)) * t2
+    pval = stats.f.sf(f, p_dim, na + nb - p_dim - 1)
+    assert pval > 1e-3, pval
+
+
+# ------------------------------------------------------------------ calorimeter in a 4 T field
+@pytest.mark.parametrize("policy", [wl.SORT_NONE, wl.SORT_ACTION_TYPE])
+def test_field_histories(policy):
+    prob, prim = wl.calorimeter_field_10gev(40, n_slots=1 << 16)
+    g = run_gpu(prob, prim, policy=policy)
+    o = run_oracle(prob, prim)
+    frac, _ = match_fraction(g, o)
+    assert frac >= 0.9, frac
+    assert_conservation(prim, g["tally"])
+
+
+# ------------------------------------------------------------------ events alone vs mixed
+def test_event_results_same_alone_and_mixed():
+    events = wl.offload_events(6)
+    events = [e[:80] for e in events]
+    prob = wl.calorimeter_problem(1 << 15, Bz=4.0, max_events=8, sort_policy=wl.SORT_ACTION_TYPE)
+    mix = wl.concat_primaries(events)
+    g_mix = run_gpu(prob, mix)
+    for k, ev in enumerate(events):
+        g1 = run_gpu(prob, ev)
+        sl = slice(sum(len(e) for e in events[:k]), sum(len(e) for e in events[: k + 1]))
+        np.testing.assert_array_equal(g_mix["hist"]["steps"][sl], g1["hist"]["steps"])
+        np.testing.assert_array_equal(g_mix["hist"]["secondaries"][sl], g1["hist"]["secondaries"])
+        e_id = int(ev["event"][0])
+        t_mix, esc_mix = g_mix["tally"][e_id]
+        t_one, esc_one = g1["tally"][e_id]
+        np.testing.assert_allclose(t_mix, t_one, rtol=1e-12, atol=1e-9)
+        assert esc_mix == pytest.approx(esc_one, rel=1e-12, abs=1e-9)
+
+
+# ------------------------------------------------------------------ capacity
+def test_small_initializer_buffer_defers_without_changing_results():
+    prob, prim = wl.calorimeter_1gev(30)
+    prob = prob.replace(n_slots=64, init_capacity=128)
+    g = run_gpu(prob, prim, policy=wl.SORT_ACTION_TYPE)
+    o = run_oracle(prob, prim)
+    frac, _ = match_fraction(g, o)
+    assert frac >= 0.9
+    assert_conservation(prim, g["tally"])

@@ -1,0 +1,52 @@
+"""The CUDA library loads and exports every entry point declared in
+include/*.h (CPU only: no compute call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2503_17608_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for fn in os.listdir(inc):
+        if fn.endswith(".h"):
+            text = open(os.path.join(inc, fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names.update(re.findall(r"\b(celer_[a-z_]+)\s*\(", text))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("celer_create", "celer_add_primaries", "celer_step", "celer_run_events", "celer_read_tallies"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    build.build()
+    lib = ctypes.CDLL(binding.LIB_PATH)
+    missing = [n for n in sorted(declared_symbols()) if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(binding.EXPORTS) == declared_symbols()
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    with pytest.raises(RuntimeError):
+        binding._lib = None
+        saved = binding._lib
+        try:
+            binding.load(str(tmp_path / "missing.so"))
+        finally:
+            binding._lib = saved
+
+
+def test_status_strings():
+    lib = binding.load()
+    assert lib.celer_status_string(0) == b"ok"
+    assert lib.celer_status_string(2) == b"capacity exceeded"
