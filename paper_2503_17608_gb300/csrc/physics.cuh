@@ -25,6 +25,9 @@ constexpr double kInf = __builtin_huge_val();
 // Attempts after which a rejection sampler gives up (never reached for finite
 // inputs: the acceptance probability is at least ~0.4 per attempt).
 constexpr int kMaxAttempts = 4096;
+// Compare-and-swap rounds a group of lanes may spend claiming buffer entries
+// (each failed round means another group succeeded).
+constexpr int kMaxCasAttempts = 1 << 16;
 
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds, each two 32x32 -> 64-bit

@@ -55,18 +55,6 @@ __device__ __forceinline__ void flush_counter(unsigned long long* dst, unsigned 
   if ((threadIdx.x & 31) == 0 && v != 0) atomicAdd(dst, negate ? (0ull - v) : v);
 }
 
-// Reserve n initializer entries; one atomic per group of lanes that reach
-// this point together (secondary stack allocation).
-__device__ __forceinline__ unsigned long long reserve(Ctl* c, unsigned n) {
-  cg::coalesced_group g = cg::coalesced_threads();
-  const unsigned prefix = cg::exclusive_scan(g, n);
-  const unsigned total = g.shfl(prefix + n, g.num_threads() - 1);
-  unsigned long long base = 0;
-  if (g.thread_rank() == 0 && total > 0) base = atomicAdd(&c->tail, (unsigned long long)total);
-  base = g.shfl(base, 0);
-  return base + prefix;
-}
-
 __device__ __forceinline__ void write_initializer(const Params& p, unsigned long long index, double x, double y,
                                                   double z, double ux, double uy, double uz, double E,
                                                   unsigned long long tid, uint32_t ev, uint32_t prim, int32_t layer,
@@ -639,17 +627,58 @@ __global__ void k_photoelectric(Params p) {
   flush_counter(&p.ctl->alive, killed, true);
 }
 
-// Defer a secondary-producing interaction when the buffer might overflow
-// this iteration: the track keeps its state and draw counter, so the
-// interaction replays identically later. Returns true if deferred.
-__device__ __forceinline__ bool maybe_defer(const Params& p, uint32_t slot, uint8_t st, bool defer,
-                                            unsigned long long& n_def) {
-  if (!defer) return false;
+// Secondary-producing interactions reserve their initializer entries before
+// any side effect. When the iteration's worst case fits in the free part of
+// the buffer ("tight" is false) a group of lanes takes its entries with one
+// atomic add on the tail. Otherwise the group claims, by compare-and-swap,
+// the longest prefix of its lanes that still fits; the other lanes defer:
+// the track keeps its state and draw counter, so the interaction replays
+// identically in a later iteration.
+__device__ __forceinline__ bool reserve_entries(const Params& p, unsigned n, bool tight, unsigned long long& base) {
+  Ctl* c = p.ctl;
+  cg::coalesced_group g = cg::coalesced_threads();
+  const unsigned prefix = cg::exclusive_scan(g, n);
+  const unsigned end = prefix + n;
+  const unsigned total = g.shfl(end, g.num_threads() - 1);
+  if (total == 0) {
+    base = 0;
+    return true;
+  }
+  if (!tight) {
+    unsigned long long old = 0;
+    if (g.thread_rank() == 0) old = atomicAdd(&c->tail, (unsigned long long)total);
+    base = g.shfl(old, 0) + prefix;
+    return true;
+  }
+  const unsigned long long head = c->head;
+  for (int attempt = 0; attempt < kMaxCasAttempts; ++attempt) {
+    unsigned long long cur = 0;
+    if (g.thread_rank() == 0) cur = *reinterpret_cast<volatile unsigned long long*>(&c->tail);
+    cur = g.shfl(cur, 0);
+    const unsigned long long used = cur - head;
+    const unsigned long long room = used < p.ring_capacity ? p.ring_capacity - used : 0ull;
+    const unsigned fits_mask = g.ballot((unsigned long long)end <= room);
+    const int last = fits_mask ? 31 - __clz(fits_mask) : -1;
+    unsigned take = g.shfl(end, last >= 0 ? last : 0);
+    if (last < 0) take = 0;
+    if (take == 0) break;
+    unsigned long long got = 0;
+    if (g.thread_rank() == 0) got = atomicCAS(&c->tail, cur, cur + take);
+    got = g.shfl(got, 0);
+    if (got == cur) {
+      base = cur + prefix;
+      return n == 0 || end <= take;
+    }
+  }
+  base = 0;
+  return n == 0;
+}
+
+__device__ __forceinline__ void defer_track(const Params& p, uint32_t slot, uint8_t st, unsigned long long& n_def) {
   if (st == ALIVE) {
     p.trk.status[slot] = DEFERRED;
     ++n_def;
   }
-  return true;
 }
 
 // Pair production: the pair's kinetic energy E - 2 m_e c^2 deposited locally,
@@ -657,13 +686,18 @@ __device__ __forceinline__ bool maybe_defer(const Params& p, uint32_t slot, uint
 __global__ void k_pair(Params p) {
   const Span sp = span_of(p, KA_NEUTRAL, KA_NEUTRAL + 1, K_G_PAIR, K_G_PAIR + 1);
   const Tracks& t = p.trk;
-  const bool defer = p.ctl->defer != 0u;
+  const bool tight = p.ctl->defer != 0u;
   unsigned long long killed = 0, n_def = 0;
   for (uint32_t i = sp.lo + blockIdx.x * blockDim.x + threadIdx.x; i < sp.hi; i += gridDim.x * blockDim.x) {
     const uint32_t slot = sp.perm ? sp.perm[i] : i;
     const uint8_t st = t.status[slot];
     if (st == VACANT || t.action[slot] != A_PAIR) continue;
-    if (maybe_defer(p, slot, st, defer, n_def)) continue;
+    const bool keep = kMe >= p.cut_track;
+    unsigned long long base;
+    if (!reserve_entries(p, keep ? 2u : 0u, tight, base)) {
+      defer_track(p, slot, st, n_def);
+      continue;
+    }
     const double E = t.E[slot];
     const uint32_t ev = t.event[slot], prim = t.primary[slot];
     const int layer = t.layer[slot];
@@ -676,13 +710,6 @@ __global__ void k_pair(Params p) {
     double sp_, cp_;
     sincos(phi, &sp_, &cp_);
     const double dx = sint * cp_, dy = sint * sp_, dz = cost;
-    const bool keep = kMe >= p.cut_track;
-    const unsigned n = keep ? 2u : 0u;
-    if (!keep) {
-      deposit(p, ev, prim, layer, z, kMe);
-      deposit(p, ev, prim, layer, z, kMe);
-    }
-    const unsigned long long base = reserve(p.ctl, n);
     if (keep) {
       const unsigned long long tid1 = rng.raw();
       const unsigned long long tid2 = rng.raw();
@@ -690,6 +717,9 @@ __global__ void k_pair(Params p) {
       write_initializer(p, base + 1, x, y, z, -dx, -dy, -dz, kMe, tid2, ev, prim, layer, GAMMA);
       atomicAdd(&p.event_live[row_of(p, ev)], 2u);
       if (prim < p.hist_cap) atomicAdd(&p.hist_secondaries[prim], 2ull);
+    } else {
+      deposit(p, ev, prim, layer, z, kMe);
+      deposit(p, ev, prim, layer, z, kMe);
     }
     release(p, slot, ev);
     ++killed;
@@ -704,13 +734,12 @@ __global__ void k_pair(Params p) {
 __global__ void k_moller(Params p) {
   const Span sp = span_of(p, KA_CHARGED, KA_CHARGED + 1, K_E_MOLLER, K_E_MOLLER + 1);
   const Tracks& t = p.trk;
-  const bool defer = p.ctl->defer != 0u;
+  const bool tight = p.ctl->defer != 0u;
   unsigned long long killed = 0, n_def = 0;
   for (uint32_t i = sp.lo + blockIdx.x * blockDim.x + threadIdx.x; i < sp.hi; i += gridDim.x * blockDim.x) {
     const uint32_t slot = sp.perm ? sp.perm[i] : i;
     const uint8_t st = t.status[slot];
     if (st == VACANT || t.action[slot] != A_MOLLER) continue;
-    if (maybe_defer(p, slot, st, defer, n_def)) continue;
     const double T = t.E[slot];
     if (T <= 2.0 * p.cut_moller) {  // kinematically closed at the post-step energy: null collision
       t.nmfp[slot] = -1.0;
@@ -718,11 +747,18 @@ __global__ void k_moller(Params p) {
       continue;
     }
     const uint32_t ev = t.event[slot], prim = t.primary[slot];
-    const int layer = t.layer[slot];
-    const double x = t.x[slot], y = t.y[slot], z = t.z[slot];
     TrackRng rng(p.seed, ev, t.tid[slot], t.ctr[slot]);
     bool ok;
     const double eps = sample_moller(T, p.cut_moller, rng, ok);
+    const double Td = eps * T;
+    const bool keep = ok && Td >= p.cut_track;
+    unsigned long long base;
+    if (!reserve_entries(p, keep ? 1u : 0u, tight, base)) {
+      defer_track(p, slot, st, n_def);
+      continue;
+    }
+    const int layer = t.layer[slot];
+    const double x = t.x[slot], y = t.y[slot], z = t.z[slot];
     if (!ok) {  // non-finite input: end the track, flag the run
       atomicOr(&p.ctl->error, ERR_SAMPLING);
       deposit(p, ev, prim, layer, z, T);
@@ -730,7 +766,6 @@ __global__ void k_moller(Params p) {
       ++killed;
       continue;
     }
-    const double Td = eps * T;
     const double cost = fmin(1.0, sqrt(Td * (T + 2.0 * kMe) / (T * (Td + 2.0 * kMe))));
     const double phi = kTwoPi * rng.uniform();
     const double ux = t.ux[slot], uy = t.uy[slot], uz = t.uz[slot];
@@ -741,14 +776,13 @@ __global__ void k_moller(Params p) {
     const double vx = pp * ux - pd * dx, vy = pp * uy - pd * dy, vz = pp * uz - pd * dz;
     const double inv = 1.0 / sqrt(vx * vx + vy * vy + vz * vz);
     const double E1 = T - Td;
-    const bool keep = Td >= p.cut_track;
-    if (!keep) deposit(p, ev, prim, layer, z, Td);
-    const unsigned long long base = reserve(p.ctl, keep ? 1u : 0u);
     if (keep) {
       const unsigned long long tid = rng.raw();
       write_initializer(p, base, x, y, z, dx, dy, dz, Td, tid, ev, prim, layer, ELECTRON);
       atomicAdd(&p.event_live[row_of(p, ev)], 1u);
       if (prim < p.hist_cap) atomicAdd(&p.hist_secondaries[prim], 1ull);
+    } else {
+      deposit(p, ev, prim, layer, z, Td);
     }
     if (E1 < p.cut_track) {
       deposit(p, ev, prim, layer, z, E1);
@@ -773,13 +807,12 @@ __global__ void k_moller(Params p) {
 __global__ void k_brems(Params p) {
   const Span sp = span_of(p, KA_CHARGED, KA_CHARGED + 1, K_E_BREMS, K_E_BREMS + 1);
   const Tracks& t = p.trk;
-  const bool defer = p.ctl->defer != 0u;
+  const bool tight = p.ctl->defer != 0u;
   unsigned long long killed = 0, n_def = 0;
   for (uint32_t i = sp.lo + blockIdx.x * blockDim.x + threadIdx.x; i < sp.hi; i += gridDim.x * blockDim.x) {
     const uint32_t slot = sp.perm ? sp.perm[i] : i;
     const uint8_t st = t.status[slot];
     if (st == VACANT || t.action[slot] != A_BREMS) continue;
-    if (maybe_defer(p, slot, st, defer, n_def)) continue;
     const double T = t.E[slot];
     if (T <= p.cut_brems) {  // null collision
       t.nmfp[slot] = -1.0;
@@ -787,20 +820,25 @@ __global__ void k_brems(Params p) {
       continue;
     }
     const uint32_t ev = t.event[slot], prim = t.primary[slot];
-    const int layer = t.layer[slot];
-    const double x = t.x[slot], y = t.y[slot], z = t.z[slot];
     TrackRng rng(p.seed, ev, t.tid[slot], t.ctr[slot]);
     double k = p.cut_brems * exp(rng.uniform() * log(T / p.cut_brems));
     if (k > T) k = T;
-    const double E1 = T - k;
     const bool keep = k >= p.cut_track;
-    if (!keep) deposit(p, ev, prim, layer, z, k);
-    const unsigned long long base = reserve(p.ctl, keep ? 1u : 0u);
+    unsigned long long base;
+    if (!reserve_entries(p, keep ? 1u : 0u, tight, base)) {
+      defer_track(p, slot, st, n_def);
+      continue;
+    }
+    const int layer = t.layer[slot];
+    const double x = t.x[slot], y = t.y[slot], z = t.z[slot];
+    const double E1 = T - k;
     if (keep) {
       const unsigned long long tid = rng.raw();
       write_initializer(p, base, x, y, z, t.ux[slot], t.uy[slot], t.uz[slot], k, tid, ev, prim, layer, GAMMA);
       atomicAdd(&p.event_live[row_of(p, ev)], 1u);
       if (prim < p.hist_cap) atomicAdd(&p.hist_secondaries[prim], 1ull);
+    } else {
+      deposit(p, ev, prim, layer, z, k);
     }
     if (E1 < p.cut_track) {
       deposit(p, ev, prim, layer, z, E1);
@@ -835,13 +873,16 @@ __global__ void k_loop_ctl(Params p, cudaGraphConditionalHandle handle, int use_
     c->trace_count += 1;
     c->iteration += 1;
   }
-  if (c->steps_iter == 0 && c->n_deferred > 0) {
+  const bool pending = c->alive + queued > 0;
+  // No track stepped although work is pending: every live track waits for
+  // buffer space. One such iteration can still place deferred secondaries;
+  // three in a row cannot make progress any more.
+  if (c->steps_iter == 0 && pending) {
     c->stall += 1;
     if (c->stall >= 3) c->error |= ERR_NO_PROGRESS;
   } else {
     c->stall = 0;
   }
-  const bool pending = c->alive + queued > 0;
   if (pending && c->iteration >= c->max_iterations) c->error |= ERR_ITERATIONS;
   c->cont = (pending && c->error == 0u) ? 1u : 0u;
   if (use_handle) cudaGraphSetConditional(handle, c->cont);

@@ -230,10 +230,28 @@ def test_event_results_same_alone_and_mixed():
 
 # ------------------------------------------------------------------ capacity
 def test_small_initializer_buffer_defers_without_changing_results():
-    prob, prim = wl.calorimeter_1gev(30)
-    prob = prob.replace(n_slots=64, init_capacity=128)
+    """A buffer far smaller than the shower forces interactions to wait for
+    space; deferred interactions replay with the same random numbers, so every
+    history is unchanged."""
+    prob, prim = wl.calorimeter_1gev(20)
+    prob = prob.replace(n_slots=256, init_capacity=64)
     g = run_gpu(prob, prim, policy=wl.SORT_ACTION_TYPE)
     o = run_oracle(prob, prim)
     frac, _ = match_fraction(g, o)
     assert frac >= 0.9
     assert_conservation(prim, g["tally"])
+
+
+def test_full_buffer_reports_capacity_and_stays_usable():
+    """One slot and a one-entry buffer: the electron's second secondary can
+    never be placed, so the run stops with CELER_ERR_CAPACITY instead of
+    spinning."""
+    prob = wl.calorimeter_problem(1, init_capacity=1, history_capacity=1)
+    prim = wl.electron_beam(1, 1000.0)
+    with binding.Context(prob, max_iterations=100000) as ctx:
+        ctx.add_events(prim)
+        with pytest.raises(binding.CelerError) as ei:
+            ctx.run_events(use_graph=True)
+        assert ei.value.status == 2
+        s = ctx.stats()
+        assert s["alive"] == 1 and s["queued"] == 1
