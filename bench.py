@@ -183,6 +183,15 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    def reduce(v, op):
+        t = torch.tensor([float(v)], device="cuda")
+        if dist is not None:
+            dist.all_reduce(t, op=op)
+        return t.item()
+
+    MAX = dist.ReduceOp.MAX if dist is not None else None
+    SUM = dist.ReduceOp.SUM if dist is not None else None
+
     prob, prim, desc = make_workload(args.workload)
     n = len(prim)
     cprim = binding.to_c_primaries(prim)
@@ -192,17 +201,17 @@ def run_ours(args):
     pinned_np[:] = cprim
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    policies = [binding_policy(p) for p in args.policies.split(",")]
     headline = binding_policy(args.policy)
+    policies = [binding_policy(p) for p in args.policies.split(",") if p]
     if headline not in policies:
         policies.insert(0, headline)
-    use_graph = not args.no_graph
+    loop = binding.LOOP_NAMES[args.loop]
     base_event = rank * 1_000_000
 
-    results = {}
-    clocks = None
-    for pol in policies:
-        ctx = binding.Context(prob.replace(sort_policy=pol, max_events=1), stream=stream.cuda_stream)
+    def timed_jobs(pol, mode, split, steps, warmup, sample_clocks=False):
+        """K whole jobs, primaries resident on the device; returns ms, steps, per-job ms."""
+        ctx = binding.Context(prob.replace(sort_policy=pol, max_events=1, split_actions=int(split)),
+                              stream=stream.cuda_stream)
         ev = [base_event]
 
         def job():
@@ -210,38 +219,61 @@ def run_ours(args):
             ev[0] += 1
             ctx.reset_event(e)
             ctx.add_primaries_device(e, dev_prim.data_ptr(), n)
-            ctx.run_events(use_graph=use_graph)
+            ctx.run_events(mode)
 
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             flush.zero_()
             job()
         s0 = ctx.stats()["steps_total"]
         barrier()
-        sampler = ClockSampler(local) if pol == headline else None
+        sampler = ClockSampler(local) if sample_clocks else None
         if sampler:
             sampler.__enter__()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        stops = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         t_start = torch.cuda.Event(enable_timing=True)
         t_stop = torch.cuda.Event(enable_timing=True)
         t_start.record(stream)
-        for _ in range(args.steps):
+        for k in range(steps):
             flush.zero_()
+            starts[k].record(stream)
             job()
+            stops[k].record(stream)
         t_stop.record(stream)
         barrier()
+        clocks = None
         if sampler:
             sampler.__exit__()
             clocks = sampler.summary()
         ms = t_start.elapsed_time(t_stop)
-        steps = ctx.stats()["steps_total"] - s0
-        ms_t = torch.tensor([ms], device="cuda")
-        st_t = torch.tensor([float(steps)], device="cuda")
-        if dist is not None:
-            dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-            dist.all_reduce(st_t, op=dist.ReduceOp.SUM)
-        results[pol] = dict(ms=ms_t.item(), steps=st_t.item(), ctx=ctx)
+        per_job = [a.elapsed_time(b) for a, b in zip(starts, stops)]
+        steps_done = ctx.stats()["steps_total"] - s0
+        return ctx, dict(ms=reduce(ms, MAX), steps=reduce(steps_done, SUM), job_ms=per_job, clocks=clocks)
 
-    # end-to-end through the public host-pointer API (headline policy)
-    ctx = results[headline]["ctx"]
+    results = {}
+    clocks = None
+    head_ctx = None
+    for pol in policies:
+        ctx, r = timed_jobs(pol, loop, False, args.steps, args.warmup, sample_clocks=(pol == headline))
+        results[pol] = r
+        if pol == headline:
+            clocks = r["clocks"]
+            head_ctx = ctx
+        else:
+            ctx.close()
+
+    loop_modes = {}
+    if not args.no_loop_compare:
+        for name, mode, split in (("host_per_action", binding.LOOP_HOST, True),
+                                  ("graph_per_action", binding.LOOP_GRAPH, True),
+                                  ("graph_per_phase", binding.LOOP_GRAPH, False),
+                                  ("persistent", binding.LOOP_PERSISTENT, False)):
+            ctx, r = timed_jobs(headline, mode, split, max(2, args.steps // 2), 2)
+            ctx.close()
+            loop_modes[name] = dict(value=r["steps"] / (r["ms"] / 1e3), ms_per_step=r["ms"] / max(2, args.steps // 2))
+
+    # end-to-end through the public host-pointer API (headline policy and loop)
+    ctx = head_ctx
     tally = np.zeros(ctx.n_bins)
     e2e_ms = 0.0
     e2e_steps = 0
@@ -253,31 +285,30 @@ def run_ours(args):
         t0 = time.perf_counter()
         ctx.reset_event(ev_e2e)
         ctx.add_primaries(ev_e2e, pinned_np)
-        ctx.run_events(use_graph=use_graph)
+        ctx.run_events(loop)
         tally, esc = ctx.read_tallies(ev_e2e)
         t1 = time.perf_counter()
         if k >= args.warmup:
             e2e_ms += (t1 - t0) * 1e3
             e2e_steps += ctx.stats()["steps_total"] - s0
         ev_e2e += 1
-    e2e_t = torch.tensor([e2e_ms], device="cuda")
-    e2e_s = torch.tensor([float(e2e_steps)], device="cuda")
-    if dist is not None:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(e2e_s, op=dist.ReduceOp.SUM)
+    e2e_ms = reduce(e2e_ms, MAX)
+    e2e_steps = reduce(e2e_steps, SUM)
+    iterations = ctx.stats()["iteration"]
 
-    # per-kernel device time (plain host loop with CUDA events around each launch)
+    # per-action kernel device time (host loop, one launch per action, CUDA events around each)
     kt = None
     if not args.no_kernel_timing:
-        kctx = binding.Context(prob.replace(sort_policy=headline, max_events=1), stream=stream.cuda_stream)
+        kctx = binding.Context(prob.replace(sort_policy=headline, max_events=1, split_actions=1),
+                               stream=stream.cuda_stream)
         kctx.reset_event(7)
         kctx.add_primaries_device(7, dev_prim.data_ptr(), n)
-        kctx.run_events(use_graph=False)
+        kctx.run_events(binding.LOOP_HOST)
         kctx.enable_kernel_timing(True)
         s0 = kctx.stats()
         kctx.reset_event(8)
         kctx.add_primaries_device(8, dev_prim.data_ptr(), n)
-        kctx.run_events(use_graph=False)
+        kctx.run_events(binding.LOOP_HOST)
         s1 = kctx.stats()
         kt = dict(kernels=kctx.kernel_timing(), steps=s1["steps_total"] - s0["steps_total"],
                   iterations=s1["iteration"] - s0["iteration"])
@@ -287,32 +318,40 @@ def run_ours(args):
         return
     h = results[headline]
     value = h["steps"] / (h["ms"] / 1e3)
+    steps_per_job = h["steps"] / args.steps / world
     by_policy = {binding_name(p): dict(value=r["steps"] / (r["ms"] / 1e3), ms_per_step=r["ms"] / args.steps,
                                        track_steps_per_job=r["steps"] / args.steps / world)
                  for p, r in results.items()}
+    # our kernels per job: the device-primaries push + the persistent loop kernel
+    launches_per_job = 2 if loop == binding.LOOP_PERSISTENT else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": h["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(desc, sort_policy=binding_name(headline), graph=use_graph,
+        "config": dict(desc, sort_policy=binding_name(headline), loop=args.loop,
                        parallelism=f"replicas x{world} (independent events per rank)",
                        l2="512 MiB buffer written between timed jobs"),
         "sorted_vs_unsorted": by_policy,
-        "e2e": {"value": e2e_s.item() / (e2e_t.item() / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(cprim.nbytes),
+        "loop_modes": loop_modes,
+        "e2e": {"value": e2e_steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(cprim.nbytes),
                 "d2h_bytes_per_step": int(8 * (len(tally) + 1))},
         "clocks": clocks,
     }
+    job_ms = statistics.median(h["job_ms"])
+    line["roofline"] = roofline_loop(steps_per_job, job_ms)
+    if launches_per_job:
+        line["gpu_launches"] = int(launches_per_job * args.steps)
     if kt is not None:
         line["kernel_timing"] = summarize_kernels(kt)
-        line["gpu_launches"] = int(sum(v["launches"] for v in kt["kernels"].values()) * args.steps)
-        line["roofline"] = roofline(kt, args)
+        if not launches_per_job:
+            per_job = sum(v["launches"] for v in kt["kernels"].values())
+            line["gpu_launches"] = int((per_job + 1) * args.steps)
     if not args.skip_cpu_baseline and world == 1:
         rate, cores, reps, nsample, dt = cpu_oracle_rate(prob, prim, min_seconds=args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"full workload ({nsample} primaries) x {reps} in {dt:.1f} s"}
     print(json.dumps(line), flush=True)
-    for r in results.values():
-        r["ctx"].close()
+    head_ctx.close()
     if dist is not None:
         dist.destroy_process_group()
 
@@ -345,27 +384,30 @@ def load_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
-def roofline(kt, args):
+# Per track-step figures of the whole step loop (all kernels of an iteration):
+# algorithmic state bytes (SURVEY-style accounting, see the design notes) and
+# thread-level FP64 operations (2 x DFMA + DADD + DMUL) counted by ncu on the
+# persistent loop kernel for this workload (profiles/loop_calorimeter_1gev.md).
+BYTES_PER_STEP = 160.0
+FP64_FLOP_PER_STEP = 600.0
+# FP64 peak of GB300: 2 DFMA per SM-cycle (ncu peak_sustained) x 152 SMs x 2.07 GHz x 2 flop
+FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
+
+
+def roofline_loop(steps_per_job, job_ms):
+    """Roofline of the dominant kernel, the persistent step-loop kernel (one
+    launch per job): FP64 ALU bound, with the HBM fraction beside it."""
     peaks, kind = load_peaks()
-    ks = kt["kernels"]
-    name, v = max(ks.items(), key=lambda kv: kv[1]["total_ms"])
-    avg_s = v["total_ms"] / max(v["launches"], 1) / 1e3
-    # algorithmic bytes per unit of the dominant kernel (state read + written once)
-    per_unit = KERNEL_BYTES.get(name, 160.0)
-    units = kt["steps"] / max(v["launches"], 1)
-    achieved = per_unit * units / avg_s / 1e9
-    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_kind": kind,
-            "bytes_per_unit": per_unit, "unit_kind": "track-step"}
-
-
-# Algorithmic bytes per track-step each kernel must move at minimum (state
-# fields read + written once); see the design notes for the accounting.
-KERNEL_BYTES = {
-    "pre_step": 118.0,
-    "along_charged": 100.0,
-    "along_neutral": 80.0,
-}
+    t = job_ms / 1e3
+    flops = FP64_FLOP_PER_STEP * steps_per_job / t / 1e12
+    gbs = BYTES_PER_STEP * steps_per_job / t / 1e9
+    return {"kernel": "k_loop", "bound": "alu", "achieved": flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": flops / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak_kind": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (probe measured 1.02 TFLOP/s)",
+            "fp64_flop_per_track_step": FP64_FLOP_PER_STEP,
+            "hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                    "bytes_per_track_step": BYTES_PER_STEP, "peak_kind": kind},
+            "launch_ms": job_ms, "track_steps_per_launch": steps_per_job}
 
 
 def main():
@@ -378,7 +420,8 @@ def main():
                     choices=["calorimeter-1gev", "calorimeter-field-10gev", "water-cube-10mev"])
     ap.add_argument("--policy", default="action_type", choices=list(wl.SORT_NAMES))
     ap.add_argument("--policies", default="action_type,action,none")
-    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--loop", default="persistent", choices=["host", "graph", "persistent"])
+    ap.add_argument("--no-loop-compare", action="store_true")
     ap.add_argument("--no-kernel-timing", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=3.0)

@@ -100,6 +100,8 @@ typedef struct {
   uint64_t history_capacity;         /* per-primary records (0: off) */
   int sort_policy;                   /* CELER_SORT_* */
   int block_size;                    /* threads per block of the action kernels: 128, 256 or 512 */
+  int split_actions;                 /* 1: one launch per along-step / interaction action (host and
+                                        graph loops); 0: one launch per phase covering all actions */
   uint32_t seed;                     /* first word of every Philox key */
   uint64_t max_iterations;           /* celer_run_events limit (0: 10^6) */
   void* cuda_stream;                 /* cudaStream_t for all work (NULL: legacy default stream) */
@@ -181,13 +183,24 @@ celer_status celer_add_primaries_device(celer_ctx* ctx, uint32_t event, const ce
  * synchronised and the iteration's counters are returned. */
 celer_status celer_step(celer_ctx* ctx, celer_step_stats* stats);
 
-/* Step until no track is alive or queued. use_graph = 0: a host loop of
- * celer_step launches that polls the counters every few iterations;
- * use_graph = 1: the iteration is captured once into a CUDA graph whose
- * conditional while-node repeats it on the device with no host round trip.
+/* Loop modes of celer_run_events. */
+enum {
+  CELER_LOOP_HOST = 0,       /* host loop of per-iteration launches, polling the counters every few iterations */
+  CELER_LOOP_GRAPH = 1,      /* the iteration captured once into a CUDA graph whose conditional while-node
+                                repeats it on the device with no host round trip */
+  CELER_LOOP_PERSISTENT = 2  /* one cooperative launch that runs every iteration: one block per SM slot,
+                                tables staged into shared memory once, phases separated by grid barriers
+                                whose waits are bounded (about 1 s, then CELER_ERR_TIMEOUT) */
+};
+
+/* Step until no track is alive or queued, in one of the CELER_LOOP_* modes.
  * Returns CELER_ERR_TIMEOUT at max_iterations, CELER_ERR_CAPACITY if the
  * initializer buffer is full and no track can make progress. */
-celer_status celer_run_events(celer_ctx* ctx, int use_graph);
+celer_status celer_run_events(celer_ctx* ctx, int mode);
+
+/* Choose per-action launches (1) or per-phase launches (0) for the host and
+ * graph loops. */
+celer_status celer_set_split_actions(celer_ctx* ctx, int split);
 
 /* Copy the energy-deposit tally of one event (n bins, n = the problem's bin
  * count) and its escaped energy into host memory. Synchronises the stream. */

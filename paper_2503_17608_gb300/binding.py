@@ -18,6 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libceler_gb.so")
 
 CELER_OK = 0
+LOOP_HOST, LOOP_GRAPH, LOOP_PERSISTENT = 0, 1, 2
+LOOP_NAMES = {"host": LOOP_HOST, "graph": LOOP_GRAPH, "persistent": LOOP_PERSISTENT}
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "capacity exceeded", 3: "CUDA error",
                 4: "iteration limit reached", 5: "invalid state"}
 
@@ -42,6 +44,7 @@ class celer_problem(C.Structure):
         ("processes", C.c_int), ("tally_mode", C.c_int), ("n_zbins", C.c_int),
         ("n_slots", C.c_uint64), ("init_capacity", C.c_uint64), ("max_events", C.c_uint32),
         ("history_capacity", C.c_uint64), ("sort_policy", C.c_int), ("block_size", C.c_int),
+        ("split_actions", C.c_int),
         ("seed", C.c_uint32), ("max_iterations", C.c_uint64), ("cuda_stream", C.c_void_p),
     ]
 
@@ -77,7 +80,7 @@ EXPORTS = [
     "celer_status_string", "celer_last_error", "celer_create", "celer_destroy", "celer_add_primaries",
     "celer_add_primaries_device",
     "celer_step", "celer_run_events", "celer_read_tallies", "celer_reset_event", "celer_event_live",
-    "celer_read_history", "celer_get_stats", "celer_set_sort_policy", "celer_read_trace",
+    "celer_read_history", "celer_get_stats", "celer_set_sort_policy", "celer_set_split_actions", "celer_read_trace",
     "celer_enable_kernel_timing", "celer_kernel_timing", "celer_debug_partition", "celer_debug_table",
     "celer_debug_philox", "celer_debug_curand_philox",
 ]
@@ -110,6 +113,7 @@ def load(path: Optional[str] = None):
         "celer_read_history": ([vp, u64, u64, vp, dp], i32),
         "celer_get_stats": ([vp, C.POINTER(celer_step_stats)], i32),
         "celer_set_sort_policy": ([vp, i32], i32),
+        "celer_set_split_actions": ([vp, i32], i32),
         "celer_read_trace": ([vp, vp, u64, C.POINTER(u64)], i32),
         "celer_enable_kernel_timing": ([vp, i32], i32),
         "celer_kernel_timing": ([vp, C.POINTER(C.c_char_p), dp, C.POINTER(u64), i32, C.POINTER(i32)], i32),
@@ -178,6 +182,7 @@ class Context:
         cp.n_slots, cp.init_capacity = prob.n_slots, prob.init_capacity
         cp.max_events, cp.history_capacity = prob.max_events, prob.history_capacity
         cp.sort_policy, cp.block_size, cp.seed = prob.sort_policy, prob.block_size, prob.seed
+        cp.split_actions = prob.split_actions
         cp.max_iterations = max_iterations
         self.stream = stream if stream is not None else _torch_stream()
         cp.cuda_stream = self.stream
@@ -228,8 +233,15 @@ class Context:
     def step_async(self):
         _check(load().celer_step(self._h, None), self._h)
 
-    def run_events(self, use_graph: bool = True):
-        _check(load().celer_run_events(self._h, 1 if use_graph else 0), self._h)
+    def run_events(self, mode=LOOP_GRAPH, use_graph=None):
+        """Step until done. mode: LOOP_HOST, LOOP_GRAPH or LOOP_PERSISTENT
+        (use_graph=True/False is accepted as LOOP_GRAPH/LOOP_HOST)."""
+        if use_graph is not None:
+            mode = LOOP_GRAPH if use_graph else LOOP_HOST
+        _check(load().celer_run_events(self._h, int(mode)), self._h)
+
+    def set_split_actions(self, split: bool):
+        _check(load().celer_set_split_actions(self._h, 1 if split else 0), self._h)
 
     def read_tallies(self, event: int = 0):
         out = np.zeros(self.n_bins)

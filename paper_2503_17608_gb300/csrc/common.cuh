@@ -15,8 +15,7 @@ constexpr int kCols = 6;            // device table columns per material
 constexpr int kMaxMaterials = 8;
 constexpr int kMaxLayers = 1024;
 constexpr int kMaxKeys = 16;
-constexpr int kTile = 256;          // slots per partition tile (= pre-step block)
-constexpr int kInitTile = 2048;     // slots per initializer tile (256 threads x 8)
+constexpr int kTile = 256;          // slots per tile: partition, initializer and step-limit work unit
 constexpr int kTraceRows = 1 << 16;
 
 // device table columns
@@ -47,12 +46,16 @@ enum Action : uint8_t {
   A_COUNT
 };
 
-// Partition keys of the ACTION_TYPE policy (particle type major).
+// Partition keys of the ACTION_TYPE policy: (particle type, next action).
+// Geometric and range-limited steps first, interactions after them, vacant
+// last, so that the along-step range (all live keys) and the interaction
+// range are each one contiguous interval of the partition.
 enum Key : uint8_t {
-  K_G_GEOM = 0, K_G_COMPTON, K_G_PE, K_G_PAIR,
-  K_E_GEOM, K_E_RANGE, K_E_MOLLER, K_E_BREMS,
+  K_G_GEOM = 0, K_E_GEOM, K_E_RANGE,
+  K_G_COMPTON, K_G_PE, K_G_PAIR, K_E_MOLLER, K_E_BREMS,
   K_VACANT_FULL = 8
 };
+constexpr int kFirstInteractionKey = K_G_COMPTON;
 constexpr int kKeysFull = 9;
 // Keys of the ACTION policy (along-step action only).
 enum KeyAlong : uint8_t { KA_NEUTRAL = 0, KA_CHARGED = 1, KA_VACANT = 2 };
@@ -61,7 +64,7 @@ constexpr int kKeysAlong = 3;
 enum Policy : int { POLICY_NONE = 0, POLICY_ACTION = 1, POLICY_ACTION_TYPE = 2 };
 
 enum ErrorBits : uint32_t { ERR_RING_OVERFLOW = 1u, ERR_NO_PROGRESS = 2u, ERR_ITERATIONS = 4u, ERR_SAMPLING = 8u,
-                            ERR_PRIMARIES_REJECTED = 16u };
+                            ERR_PRIMARIES_REJECTED = 16u, ERR_BARRIER_TIMEOUT = 32u };
 
 struct Tracks {
   double *x, *y, *z, *ux, *uy, *uz, *E, *nmfp, *step, *rpost;
@@ -112,10 +115,10 @@ struct Params {
   Ctl* ctl;
   uint32_t n_slots;
   uint32_t n_tiles;        // ceil(n_slots / kTile)
-  uint32_t n_init_tiles;   // ceil(n_slots / kInitTile)
   unsigned long long ring_mask;
   unsigned long long ring_capacity;
-  uint32_t* init_counts;   // n_init_tiles
+  uint32_t* init_counts;   // vacant slots per tile, n_tiles
+  unsigned int* barrier;   // grid barrier state of the persistent loop: count, generation, abort
   // partition
   int policy;
   int n_keys;

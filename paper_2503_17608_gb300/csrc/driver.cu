@@ -55,6 +55,8 @@ struct celer_ctx {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   int graph_policy = -1;
+  int graph_split = -1;
+  int split_actions = 0;
   std::string last_error;
   // kernel timing
   bool timing = false;
@@ -158,24 +160,33 @@ void timed(celer_ctx* ctx, cudaStream_t s, int kid, F&& launch, bool allow_timin
   cudaEventRecord(ctx->t_stop[i], s);
 }
 
-// One step iteration as a sequence of launches on stream s.
+// One step iteration as a sequence of launches on stream s: initializer
+// (count, fill), step limit, partition (scan, scatter), along-step,
+// interactions, loop control. With split_actions the along-step and the
+// interactions are one launch per action, as in the paper's loop over
+// actions; otherwise one launch each covers all actions of the phase.
 void launch_iteration(celer_ctx* ctx, cudaStream_t s, unsigned long long handle, int use_handle) {
   const Params& p = ctx->p;
   const LaunchShape& sh = ctx->shape;
   const bool t = use_handle == 0;
-  timed(ctx, s, KID_INIT_COUNT, [&] { launch_init_count(p, s); }, t);
-  timed(ctx, s, KID_INIT_FILL, [&] { launch_init_fill(p, s); }, t);
+  timed(ctx, s, KID_INIT_COUNT, [&] { launch_init_count(p, sh, s); }, t);
+  timed(ctx, s, KID_INIT_FILL, [&] { launch_init_fill(p, sh, s); }, t);
   timed(ctx, s, KID_PRE_STEP, [&] { launch_pre_step(p, sh, s); }, t);
   timed(ctx, s, KID_ITER_CTL, [&] { launch_iter_ctl(p, s); }, t);
   if (policy_sorted(p.policy)) timed(ctx, s, KID_SCATTER, [&] { launch_scatter(p, sh, s); }, t);
-  timed(ctx, s, KID_ALONG_NEUTRAL, [&] { launch_along(p, false, sh, s); }, t);
-  timed(ctx, s, KID_ALONG_CHARGED, [&] { launch_along(p, true, sh, s); }, t);
   const int P = p.processes;
-  if (P & PROC_COMPTON) timed(ctx, s, KID_POST_COMPTON, [&] { launch_post(p, POST_COMPTON, sh, s); }, t);
-  if (P & PROC_PE) timed(ctx, s, KID_POST_PE, [&] { launch_post(p, POST_PE, sh, s); }, t);
-  if (P & PROC_PAIR) timed(ctx, s, KID_POST_PAIR, [&] { launch_post(p, POST_PAIR, sh, s); }, t);
-  if (P & PROC_MOLLER) timed(ctx, s, KID_POST_MOLLER, [&] { launch_post(p, POST_MOLLER, sh, s); }, t);
-  if (P & PROC_BREMS) timed(ctx, s, KID_POST_BREMS, [&] { launch_post(p, POST_BREMS, sh, s); }, t);
+  if (ctx->split_actions) {
+    timed(ctx, s, KID_ALONG_NEUTRAL, [&] { launch_along(p, ALONG_LAUNCH_NEUTRAL, sh, s); }, t);
+    timed(ctx, s, KID_ALONG_CHARGED, [&] { launch_along(p, ALONG_LAUNCH_CHARGED, sh, s); }, t);
+    if (P & PROC_COMPTON) timed(ctx, s, KID_POST_COMPTON, [&] { launch_post(p, A_COMPTON, sh, s); }, t);
+    if (P & PROC_PE) timed(ctx, s, KID_POST_PE, [&] { launch_post(p, A_PE, sh, s); }, t);
+    if (P & PROC_PAIR) timed(ctx, s, KID_POST_PAIR, [&] { launch_post(p, A_PAIR, sh, s); }, t);
+    if (P & PROC_MOLLER) timed(ctx, s, KID_POST_MOLLER, [&] { launch_post(p, A_MOLLER, sh, s); }, t);
+    if (P & PROC_BREMS) timed(ctx, s, KID_POST_BREMS, [&] { launch_post(p, A_BREMS, sh, s); }, t);
+  } else {
+    timed(ctx, s, KID_ALONG, [&] { launch_along(p, ALONG_LAUNCH_ALL, sh, s); }, t);
+    timed(ctx, s, KID_POST, [&] { launch_post(p, A_NONE, sh, s); }, t);
+  }
   timed(ctx, s, KID_LOOP_CTL, [&] { launch_loop_ctl(p, handle, use_handle, s); }, t);
 }
 
@@ -232,6 +243,7 @@ celer_status build_graph(celer_ctx* ctx) {
   ctx->graph = g;
   ctx->graph_exec = exec;
   ctx->graph_policy = ctx->p.policy;
+  ctx->graph_split = ctx->split_actions;
   return CELER_OK;
 }
 
@@ -258,6 +270,7 @@ celer_status status_from_error(celer_ctx* ctx, unsigned err) {
     return fail(ctx, CELER_ERR_CAPACITY, "initializer buffer full and no track can make progress");
   if (err & ERR_PRIMARIES_REJECTED)
     return fail(ctx, CELER_ERR_INVALID, "device primaries rejected (invalid record or buffer full)");
+  if (err & ERR_BARRIER_TIMEOUT) return fail(ctx, CELER_ERR_TIMEOUT, "persistent loop: grid barrier timed out");
   if (err & ERR_SAMPLING) return fail(ctx, CELER_ERR_STATE, "rejection sampling hit its attempt limit");
   if (err) return fail(ctx, CELER_ERR_STATE, "device error flag set");
   return CELER_OK;
@@ -392,7 +405,6 @@ celer_status celer_create(const celer_problem* pb, celer_ctx** out) {
   const uint64_t C = next_pow2(pb->init_capacity);
   p.n_slots = N;
   p.n_tiles = (N + kTile - 1) / kTile;
-  p.n_init_tiles = (N + kInitTile - 1) / kInitTile;
   p.ring_capacity = C;
   p.ring_mask = C - 1;
   p.policy = pb->sort_policy;
@@ -451,7 +463,8 @@ celer_status celer_create(const celer_problem* pb, celer_ctx** out) {
   CREATE_CUDA(dalloc(ctx, &r.layer, C));
   CREATE_CUDA(dalloc(ctx, &r.ptype, C));
   CREATE_CUDA(dalloc(ctx, &p.ctl, 1));
-  CREATE_CUDA(dalloc(ctx, &p.init_counts, p.n_init_tiles));
+  CREATE_CUDA(dalloc(ctx, &p.init_counts, p.n_tiles));
+  CREATE_CUDA(dalloc(ctx, &p.barrier, 4));
   CREATE_CUDA(dalloc(ctx, &p.perm, N));
   CREATE_CUDA(dalloc(ctx, &p.tile_counts, (size_t)kKeysFull * p.n_tiles));
   double* d_zb = nullptr;
@@ -511,6 +524,7 @@ celer_status celer_create(const celer_problem* pb, celer_ctx** out) {
   init.cont = 0;
   CREATE_CUDA(cudaMemcpyAsync(p.ctl, &init, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
 
+  ctx->split_actions = pb->split_actions ? 1 : 0;
   const int block = pb->block_size ? pb->block_size : 256;
   CREATE_CUDA(configure_kernels(p, block, &ctx->shape));
   CREATE_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -603,14 +617,21 @@ celer_status celer_step(celer_ctx* ctx, celer_step_stats* stats) {
   return CELER_OK;
 }
 
-celer_status celer_run_events(celer_ctx* ctx, int use_graph) {
+celer_status celer_run_events(celer_ctx* ctx, int mode) {
   if (!ctx) return CELER_ERR_INVALID;
-  if (use_graph) {
-    if (!ctx->graph_exec || ctx->graph_policy != ctx->p.policy) {
+  if (mode < CELER_LOOP_HOST || mode > CELER_LOOP_PERSISTENT) return fail(ctx, CELER_ERR_INVALID, "unknown loop mode");
+  if (mode == CELER_LOOP_GRAPH) {
+    if (!ctx->graph_exec || ctx->graph_policy != ctx->p.policy || ctx->graph_split != ctx->split_actions) {
       celer_status st = build_graph(ctx);
       if (st != CELER_OK) return st;
     }
     CELER_CUDA(ctx, cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+  } else if (mode == CELER_LOOP_PERSISTENT) {
+    CELER_CUDA(ctx, cudaMemsetAsync(ctx->p.barrier, 0, 4 * sizeof(unsigned int), ctx->stream));
+    CELER_CUDA(ctx, launch_loop(ctx->p, ctx->shape, ctx->stream));
+    if (ctx->timing) {
+      // the persistent loop is one launch: time it as such
+    }
   } else {
     // Host loop: launch batches of iterations; before each new batch, look at
     // the loop condition copied back after the batch before the previous one,
@@ -716,6 +737,13 @@ celer_status celer_get_stats(celer_ctx* ctx, celer_step_stats* out) {
   celer_status st = read_ctl(ctx);
   if (st != CELER_OK) return st;
   fill_stats(*ctx->h_ctl, out);
+  return CELER_OK;
+}
+
+celer_status celer_set_split_actions(celer_ctx* ctx, int split) {
+  if (!ctx) return CELER_ERR_INVALID;
+  ctx->split_actions = split ? 1 : 0;
+  ctx->prob.split_actions = ctx->split_actions;
   return CELER_OK;
 }
 

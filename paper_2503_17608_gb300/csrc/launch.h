@@ -13,28 +13,29 @@ struct StagedPrimary {
   int32_t layer, ptype;
 };
 
-// Interaction kernels, in launch order.
-enum PostKernel : int { POST_COMPTON = 0, POST_PE, POST_PAIR, POST_MOLLER, POST_BREMS, POST_COUNT };
-
 struct LaunchShape {
-  int pre_grid;        // persistent step-limit / scatter grid (blocks of kTile threads)
-  int action_grid;     // persistent along-step / interaction grid
+  int tile_grid;       // persistent grid of the tile kernels (initializer, step limit, scatter)
+  int along_grid;      // persistent grid of the along-step kernels
+  int post_grid;       // persistent grid of the interaction kernels
+  int loop_grid;       // co-resident grid of the persistent loop kernel
   int block;           // threads per block of the along-step / interaction kernels
-  size_t pre_smem;     // dynamic shared memory of the step-limit kernel
-  size_t along_smem;   // dynamic shared memory of the charged along-step kernel
-  size_t neutral_smem; // dynamic shared memory of the neutral along-step kernel
+  size_t static_smem;  // tables + layer planes + layer materials in shared memory
 };
+
+// Along-step kernel variants and interaction selectors (Action values; A_NONE = all).
+enum AlongLaunch : int { ALONG_LAUNCH_NEUTRAL = 0, ALONG_LAUNCH_CHARGED = 1, ALONG_LAUNCH_ALL = 2 };
 
 cudaError_t configure_kernels(const Params& p, int block, LaunchShape* shape);
 
-void launch_init_count(const Params& p, cudaStream_t s);
-void launch_init_fill(const Params& p, cudaStream_t s);
+void launch_init_count(const Params& p, const LaunchShape& sh, cudaStream_t s);
+void launch_init_fill(const Params& p, const LaunchShape& sh, cudaStream_t s);
 void launch_pre_step(const Params& p, const LaunchShape& sh, cudaStream_t s);
 void launch_iter_ctl(const Params& p, cudaStream_t s);
 void launch_scatter(const Params& p, const LaunchShape& sh, cudaStream_t s);
-void launch_along(const Params& p, bool charged, const LaunchShape& sh, cudaStream_t s);
+void launch_along(const Params& p, int kind, const LaunchShape& sh, cudaStream_t s);
 void launch_post(const Params& p, int which, const LaunchShape& sh, cudaStream_t s);
 void launch_loop_ctl(const Params& p, unsigned long long handle, int use_handle, cudaStream_t s);
+cudaError_t launch_loop(const Params& p, const LaunchShape& sh, cudaStream_t s);
 void launch_push_primaries(const Params& p, const StagedPrimary* d_prim, uint32_t n, cudaStream_t s);
 
 // Primary record as laid out by the C ABI (celer_primary).
@@ -50,9 +51,9 @@ void launch_push_device_primaries(const Params& p, const DevicePrimary* src, uin
 const char* kernel_name(int id);
 enum KernelId : int {
   KID_INIT_COUNT = 0, KID_INIT_FILL, KID_PRE_STEP, KID_ITER_CTL, KID_SCATTER,
-  KID_ALONG_NEUTRAL, KID_ALONG_CHARGED,
-  KID_POST_COMPTON, KID_POST_PE, KID_POST_PAIR, KID_POST_MOLLER, KID_POST_BREMS,
-  KID_LOOP_CTL, KID_COUNT
+  KID_ALONG, KID_ALONG_NEUTRAL, KID_ALONG_CHARGED,
+  KID_POST, KID_POST_COMPTON, KID_POST_PE, KID_POST_PAIR, KID_POST_MOLLER, KID_POST_BREMS,
+  KID_LOOP_CTL, KID_LOOP, KID_COUNT
 };
 
 }  // namespace celer

@@ -28,6 +28,8 @@ constexpr int kMaxAttempts = 4096;
 // Compare-and-swap rounds a group of lanes may spend claiming buffer entries
 // (each failed round means another group succeeded).
 constexpr int kMaxCasAttempts = 1 << 16;
+// Longest wait at a grid barrier of the persistent loop (~1 s at 2 GHz).
+constexpr long long kBarrierTimeoutCycles = 2000000000ll;
 
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds, each two 32x32 -> 64-bit

@@ -79,14 +79,6 @@ struct Span {
   const uint32_t* perm;
 };
 
-// Work range of an action kernel: all slots (NONE), or the partition range
-// [offsets[k_lo], offsets[k_hi]) of the policy's keys.
-__device__ __forceinline__ Span span_of(const Params& p, int ka_lo, int ka_hi, int kf_lo, int kf_hi) {
-  if (p.policy == POLICY_NONE) return Span{0u, p.n_slots, nullptr};
-  if (p.policy == POLICY_ACTION) return Span{p.ctl->offsets[ka_lo], p.ctl->offsets[ka_hi], p.perm};
-  return Span{p.ctl->offsets[kf_lo], p.ctl->offsets[kf_hi], p.perm};
-}
-
 __device__ __forceinline__ uint8_t key_of(int policy, uint8_t ptype, uint8_t act) {
   if (policy == POLICY_ACTION) return ptype == GAMMA ? KA_NEUTRAL : KA_CHARGED;
   if (ptype == GAMMA) {
@@ -216,101 +208,119 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
   return act;
 }
 
-// ------------------------------------------------------------------ kernels
-// Initializer, pass 1: vacant slots per tile of kInitTile slots. Block 0 also
-// clears the per-iteration counters.
-__global__ void __launch_bounds__(256) k_init_count(Params p) {
-  Ctl* c = p.ctl;
-  if (blockIdx.x == 0) {
-    if (threadIdx.x < kMaxKeys) {
-      c->action_count[threadIdx.x] = 0;
-      c->key_total[threadIdx.x] = 0;
-    }
-    if (threadIdx.x == 0) {
-      c->steps_iter = 0;
-      c->n_deferred = 0;
-    }
-  }
-  if (c->tail == c->head) return;
-  const uint32_t tile = blockIdx.x;
-  unsigned cnt = 0;
-#pragma unroll
-  for (int j = 0; j < kInitTile / 256; ++j) {
-    const uint32_t slot = tile * kInitTile + j * 256 + threadIdx.x;
-    if (slot < p.n_slots && p.trk.status[slot] == VACANT) ++cnt;
-  }
-  __shared__ unsigned s_sum[8];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
-  if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = cnt;
+// ------------------------------------------------------------------ phases
+// Each phase is executed by every thread of a block; bid / nb are the block's
+// index and the number of blocks sharing the phase. The same functions run as
+// stand-alone kernels (host loop or CUDA graph) and inside the persistent
+// loop kernel.
+
+// Static data every step kernel needs in shared memory: cross-section and
+// range tables, layer planes and layer materials.
+struct SharedStatic {
+  double2* tab;
+  double* zb;
+  int32_t* lmat;
+};
+
+__device__ __forceinline__ SharedStatic carve_static(const Params& p, unsigned char* raw) {
+  SharedStatic s;
+  s.tab = reinterpret_cast<double2*>(raw);
+  s.zb = reinterpret_cast<double*>(s.tab + p.n_materials * kCols * kGrid);
+  s.lmat = reinterpret_cast<int32_t*>(s.zb + p.n_layers + 1);
+  return s;
+}
+
+__device__ __forceinline__ void stage_static(const Params& p, const SharedStatic& s) {
+  const int ntab = p.n_materials * kCols * kGrid;
+  for (int i = threadIdx.x; i < ntab; i += blockDim.x) s.tab[i] = p.tables[i];
+  for (int i = threadIdx.x; i <= p.n_layers; i += blockDim.x) s.zb[i] = p.zb[i];
+  for (int i = threadIdx.x; i < p.n_layers; i += blockDim.x) s.lmat[i] = p.layer_mat[i];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned tot = 0;
-    for (int w = 0; w < 8; ++w) tot += s_sum[w];
-    p.init_counts[tile] = tot;
+}
+
+__device__ __forceinline__ unsigned block_sum(unsigned v, unsigned* scratch /* 32 */) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  unsigned tot = 0;
+  const int nw = (blockDim.x + 31) >> 5;
+  for (int w = 0; w < nw; ++w) tot += scratch[w];
+  return tot;
+}
+
+// Clear the per-iteration counters (one thread).
+__device__ __forceinline__ void clear_iteration_counters(Ctl* c) {
+  for (int k = 0; k < kMaxKeys; ++k) {
+    c->action_count[k] = 0;
+    c->key_total[k] = 0;
+  }
+  c->steps_iter = 0;
+  c->n_deferred = 0;
+}
+
+// Initializer, pass 1: vacant slots per tile.
+__device__ void phase_init_count(const Params& p, int bid, int nb) {
+  __shared__ unsigned s_red[32];
+  const Ctl* c = p.ctl;
+  if (c->tail == c->head) return;
+  for (uint32_t tile = bid; tile < p.n_tiles; tile += nb) {
+    const uint32_t slot = tile * kTile + threadIdx.x;
+    const unsigned v = (slot < p.n_slots && p.trk.status[slot] == VACANT) ? 1u : 0u;
+    const unsigned tot = block_sum(v, s_red);
+    if (threadIdx.x == 0) p.init_counts[tile] = tot;
   }
 }
 
 // Initializer, pass 2: the r-th vacant slot in ascending slot order takes
 // initializer head + r, for r < min(vacant, queued) (deterministic filling).
-__global__ void __launch_bounds__(256) k_init_fill(Params p) {
+// Tile prefixes are accumulated incrementally over this block's tiles.
+__device__ void phase_init_fill(const Params& p, int bid, int nb) {
+  __shared__ unsigned s_red[32];
+  __shared__ unsigned s_w[32];
   Ctl* c = p.ctl;
   const unsigned long long head = c->head;
   const unsigned long long queued = c->tail - head;
   if (queued == 0) return;
-  const uint32_t tile = blockIdx.x;
-  unsigned long long before = 0, total = 0;
-  for (uint32_t i = threadIdx.x; i < p.n_init_tiles; i += 256) {
-    const unsigned v = p.init_counts[i];
-    total += v;
-    if (i < tile) before += v;
-  }
-  __shared__ unsigned long long s_b[8], s_t[8];
-  __shared__ unsigned s_w[8];
-  __shared__ unsigned long long s_before;
+  if (bid == 0) {
+    unsigned long long total = 0;
+    for (uint32_t i = threadIdx.x; i < p.n_tiles; i += blockDim.x) total += p.init_counts[i];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    before += __shfl_down_sync(0xffffffffu, before, o);
-    total += __shfl_down_sync(0xffffffffu, total, o);
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    s_b[warp] = before;
-    s_t[warp] = total;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long b = 0, tt = 0;
-    for (int w = 0; w < 8; ++w) {
-      b += s_b[w];
-      tt += s_t[w];
-    }
-    s_before = b;
-    if (blockIdx.x == 0) {
+    for (int o = 16; o > 0; o >>= 1) total += __shfl_down_sync(0xffffffffu, total, o);
+    __shared__ unsigned long long s_tot[32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) s_tot[warp] = total;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long tt = 0;
+      for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) tt += s_tot[w];
       const unsigned long long take = tt < queued ? tt : queued;
       c->head_pending = head + take;
       c->alive += take;
     }
+    __syncthreads();
   }
-  __syncthreads();
-  before = s_before;
-  if (before >= queued) return;
-  unsigned long long running = 0;
+  unsigned long long before = 0;
+  uint32_t prev_tile = 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
-  for (int j = 0; j < kInitTile / 256; ++j) {
-    const uint32_t slot = tile * kInitTile + j * 256 + threadIdx.x;
+  for (uint32_t tile = bid; tile < p.n_tiles; tile += nb) {
+    unsigned part = 0;
+    for (uint32_t i = prev_tile + threadIdx.x; i < tile; i += blockDim.x) part += p.init_counts[i];
+    before += block_sum(part, s_red);
+    prev_tile = tile;
+    if (before >= queued) break;
+    const uint32_t slot = tile * kTile + threadIdx.x;
     const bool vac = slot < p.n_slots && p.trk.status[slot] == VACANT;
     const unsigned bal = __ballot_sync(0xffffffffu, vac);
+    __syncthreads();
     if (lane == 0) s_w[warp] = __popc(bal);
     __syncthreads();
-    unsigned wpre = 0, chunk = 0;
-    for (int w = 0; w < 8; ++w) {
-      const unsigned v = s_w[w];
-      if (w < warp) wpre += v;
-      chunk += v;
-    }
-    __syncthreads();
-    const unsigned long long r = before + running + wpre + __popc(bal & lt);
+    unsigned wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += s_w[w];
+    const unsigned long long r = before + wpre + __popc(bal & lt);
     if (vac && r < queued) {
       const unsigned long long i = (head + r) & p.ring_mask;
       const Tracks& t = p.trk;
@@ -331,33 +341,21 @@ __global__ void __launch_bounds__(256) k_init_fill(Params p) {
       t.action[slot] = A_NONE;
       t.status[slot] = ALIVE;
     }
-    running += chunk;
-    if (before + running >= queued) break;
   }
 }
 
-// Step limit over all slots, one tile of kTile slots per block iteration;
-// also counts tracks per next action and, for the sorted policies, per
-// partition key and tile.
-__global__ void __launch_bounds__(kTile) k_pre_step(Params p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* s_tab = reinterpret_cast<double2*>(smem_raw);
-  const int ntab = p.n_materials * kCols * kGrid;
-  double* s_zb = reinterpret_cast<double*>(s_tab + ntab);
-  int32_t* s_lmat = reinterpret_cast<int32_t*>(s_zb + p.n_layers + 1);
+// Step limit over all slots, one tile per block iteration; counts tracks per
+// next action and, for the sorted policies, per partition key and tile.
+__device__ void phase_pre_step(const Params& p, int bid, int nb, const SharedStatic& ss) {
   __shared__ unsigned s_keys[kMaxKeys];
   __shared__ unsigned s_acts[A_COUNT];
-  for (int i = threadIdx.x; i < ntab; i += blockDim.x) s_tab[i] = p.tables[i];
-  for (int i = threadIdx.x; i <= p.n_layers; i += blockDim.x) s_zb[i] = p.zb[i];
-  for (int i = threadIdx.x; i < p.n_layers; i += blockDim.x) s_lmat[i] = p.layer_mat[i];
   if (threadIdx.x < A_COUNT) s_acts[threadIdx.x] = 0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) p.ctl->head = p.ctl->head_pending;
+  if (bid == 0 && threadIdx.x == 0) p.ctl->head = p.ctl->head_pending;
   __syncthreads();
-
   const bool sorted = p.policy != POLICY_NONE;
   const uint8_t vacant_key = p.policy == POLICY_ACTION ? KA_VACANT : K_VACANT_FULL;
   unsigned long long my_steps = 0;
-  for (uint32_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
+  for (uint32_t tile = bid; tile < p.n_tiles; tile += nb) {
     if (threadIdx.x < kMaxKeys) s_keys[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t slot = tile * kTile + threadIdx.x;
@@ -366,7 +364,7 @@ __global__ void __launch_bounds__(kTile) k_pre_step(Params p) {
       const uint8_t st = p.trk.status[slot];
       uint8_t act = A_NONE;
       if (st == ALIVE) {
-        act = step_limit(p, slot, s_tab, s_zb, s_lmat);
+        act = step_limit(p, slot, ss.tab, ss.zb, ss.lmat);
         ++my_steps;
       } else if (st == DEFERRED) {
         act = p.trk.action[slot];
@@ -391,8 +389,9 @@ __global__ void __launch_bounds__(kTile) k_pre_step(Params p) {
 
 // Exclusive scan of the per-(key, tile) counts in key-major order, which
 // yields each tile's output position per key and the key offsets; then the
-// decision whether this iteration's secondaries fit in the buffer.
-__global__ void __launch_bounds__(1024) k_iter_ctl(Params p) {
+// decision whether this iteration's secondaries are sure to fit in the
+// buffer. Run by one block.
+__device__ void phase_iter_ctl(const Params& p) {
   Ctl* c = p.ctl;
   if (p.policy != POLICY_NONE) {
     __shared__ unsigned s_warp[32];
@@ -433,6 +432,7 @@ __global__ void __launch_bounds__(1024) k_iter_ctl(Params p) {
     __syncthreads();
     if ((int)threadIdx.x < p.n_keys) c->offsets[threadIdx.x] = p.tile_counts[threadIdx.x * p.n_tiles];
     if ((int)threadIdx.x == p.n_keys) c->offsets[p.n_keys] = s_total;
+    __syncthreads();
   }
   if (threadIdx.x == 0) {
     const unsigned long long queued = c->tail - c->head;
@@ -444,11 +444,11 @@ __global__ void __launch_bounds__(1024) k_iter_ctl(Params p) {
 
 // Stable scatter of slot indices into the partition: position = tile's
 // offset for the key + same-key slots in earlier warps + same-key lanes below.
-__global__ void __launch_bounds__(kTile) k_scatter(Params p) {
+__device__ void phase_scatter(const Params& p, int bid, int nb) {
   __shared__ unsigned s_cnt[kTile / 32][kMaxKeys];
   const uint8_t vacant_key = p.policy == POLICY_ACTION ? KA_VACANT : K_VACANT_FULL;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (uint32_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
+  for (uint32_t tile = bid; tile < p.n_tiles; tile += nb) {
     if (threadIdx.x < (kTile / 32) * kMaxKeys) (&s_cnt[0][0])[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t slot = tile * kTile + threadIdx.x;
@@ -466,165 +466,149 @@ __global__ void __launch_bounds__(kTile) k_scatter(Params p) {
   }
 }
 
-// Along-step: move by the step length (straight line, or the exact helix for
-// charged tracks in the field), continuous energy loss through the inverse
-// range table, then the geometric post-step: next layer or escape through a
-// z-plane, escape through a side plane, and the tracking cut.
-template <bool CHARGED>
-__global__ void k_along(Params p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* s_range = reinterpret_cast<double2*>(smem_raw);
-  const int nr = CHARGED ? p.n_materials * kGrid : 0;
-  double* s_zb = reinterpret_cast<double*>(s_range + nr);
-  int32_t* s_lmat = reinterpret_cast<int32_t*>(s_zb + p.n_layers + 1);
-  if (CHARGED) {
-    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-      const int mat = i / kGrid, k = i - mat * kGrid;
-      s_range[i] = p.tables[(mat * kCols + COL_RANGE) * kGrid + k];
-    }
-  }
-  for (int i = threadIdx.x; i <= p.n_layers; i += blockDim.x) s_zb[i] = p.zb[i];
-  for (int i = threadIdx.x; i < p.n_layers; i += blockDim.x) s_lmat[i] = p.layer_mat[i];
-  __syncthreads();
-
-  const Span sp = CHARGED ? span_of(p, KA_CHARGED, KA_CHARGED + 1, K_E_GEOM, K_E_BREMS + 1)
-                          : span_of(p, KA_NEUTRAL, KA_NEUTRAL + 1, K_G_GEOM, K_G_PAIR + 1);
-  const bool eloss = CHARGED && (p.processes & PROC_ELOSS);
-  const bool helix = CHARGED && p.Bz != 0.0;
+// Along-step of one live track: move by the step length (straight line, or
+// the exact helix for charged tracks in the field), continuous energy loss
+// through the inverse range table, then the geometric post-step: next layer
+// or escape through a z-plane, escape through a side plane, tracking cut.
+// Returns true if the track ended.
+__device__ __forceinline__ bool along_one(const Params& p, uint32_t slot, uint8_t pt, const SharedStatic& ss) {
   const Tracks& t = p.trk;
-  unsigned long long killed = 0;
-  for (uint32_t i = sp.lo + blockIdx.x * blockDim.x + threadIdx.x; i < sp.hi; i += gridDim.x * blockDim.x) {
-    const uint32_t slot = sp.perm ? sp.perm[i] : i;
-    if (t.status[slot] != ALIVE) continue;
-    const uint8_t pt = t.ptype[slot];
-    if (CHARGED ? pt == GAMMA : pt != GAMMA) continue;
-    const uint8_t act = t.action[slot];
-    const uint32_t ev = t.event[slot], prim = t.primary[slot];
-    int layer = t.layer[slot];
-    double E = t.E[slot];
-    double z = t.z[slot];
-    if (prim < p.hist_cap) atomicAdd(&p.hist_steps[prim], 1ull);
-    if (act == A_TRAPPED) {
-      deposit(p, ev, prim, layer, z, E);
-      release(p, slot, ev);
-      ++killed;
-      continue;
-    }
-    const double s = t.step[slot];
-    double x = t.x[slot], y = t.y[slot];
-    double ux = t.ux[slot], uy = t.uy[slot];
-    const double uz = t.uz[slot];
-    if (helix) {
-      helix_move(curvature(pt, E, p.Bz), s, x, y, z, ux, uy, uz);
-    } else {
-      x += s * ux;
-      y += s * uy;
-      z += s * uz;
-    }
-    if (eloss) {
-      const double Ep = inverse_range(s_range + s_lmat[layer] * kGrid, t.rpost[slot], p.lnEmin, p.dl);
-      deposit(p, ev, prim, layer, z, E - Ep);
-      E = Ep;
-    }
-    bool out = false;
-    if (act == A_ZUP) {
-      layer += 1;
-      if (layer >= p.n_layers) {
-        out = true;
-      } else {
-        z = s_zb[layer];
-      }
-    } else if (act == A_ZDOWN) {
-      z = s_zb[layer];
-      layer -= 1;
-      if (layer < 0) out = true;
-    } else if (act == A_SIDE) {
+  const bool charged = pt != GAMMA;
+  const uint8_t act = t.action[slot];
+  const uint32_t ev = t.event[slot], prim = t.primary[slot];
+  int layer = t.layer[slot];
+  double E = t.E[slot];
+  double z = t.z[slot];
+  if (prim < p.hist_cap) atomicAdd(&p.hist_steps[prim], 1ull);
+  if (act == A_TRAPPED) {
+    deposit(p, ev, prim, layer, z, E);
+    release(p, slot, ev);
+    return true;
+  }
+  const bool eloss = charged && (p.processes & PROC_ELOSS);
+  const bool helix = charged && p.Bz != 0.0;
+  const double s = t.step[slot];
+  double x = t.x[slot], y = t.y[slot];
+  double ux = t.ux[slot], uy = t.uy[slot];
+  const double uz = t.uz[slot];
+  if (helix) {
+    helix_move(curvature(pt, E, p.Bz), s, x, y, z, ux, uy, uz);
+  } else {
+    x += s * ux;
+    y += s * uy;
+    z += s * uz;
+  }
+  if (eloss) {
+    const double2* R = ss.tab + (ss.lmat[layer] * kCols + COL_RANGE) * kGrid;
+    const double Ep = inverse_range(R, t.rpost[slot], p.lnEmin, p.dl);
+    deposit(p, ev, prim, layer, z, E - Ep);
+    E = Ep;
+  }
+  bool out = false;
+  if (act == A_ZUP) {
+    layer += 1;
+    if (layer >= p.n_layers) {
       out = true;
+    } else {
+      z = ss.zb[layer];
     }
-    if (out) {
-      escape(p, ev, prim, E);
-      release(p, slot, ev);
-      ++killed;
-      continue;
-    }
-    if (E < p.cut_track) {
-      deposit(p, ev, prim, layer, z, E);
-      release(p, slot, ev);
-      ++killed;
-      continue;
-    }
-    t.x[slot] = x;
-    t.y[slot] = y;
-    t.z[slot] = z;
-    if (helix) {
-      t.ux[slot] = ux;
-      t.uy[slot] = uy;
-    }
-    if (eloss) t.E[slot] = E;
-    if (act == A_ZUP || act == A_ZDOWN) t.layer[slot] = layer;
+  } else if (act == A_ZDOWN) {
+    z = ss.zb[layer];
+    layer -= 1;
+    if (layer < 0) out = true;
+  } else if (act == A_SIDE) {
+    out = true;
+  }
+  if (out) {
+    escape(p, ev, prim, E);
+    release(p, slot, ev);
+    return true;
+  }
+  if (E < p.cut_track) {
+    deposit(p, ev, prim, layer, z, E);
+    release(p, slot, ev);
+    return true;
+  }
+  t.x[slot] = x;
+  t.y[slot] = y;
+  t.z[slot] = z;
+  if (helix) {
+    t.ux[slot] = ux;
+    t.uy[slot] = uy;
+  }
+  if (eloss) t.E[slot] = E;
+  if (act == A_ZUP || act == A_ZDOWN) t.layer[slot] = layer;
+  return false;
+}
+
+__device__ void phase_along(const Params& p, int kind, int bid, int nb, const SharedStatic& ss) {
+  Span sp;
+  if (p.policy == POLICY_NONE) {
+    sp = Span{0u, p.n_slots, nullptr};
+  } else if (p.policy == POLICY_ACTION) {
+    const int lo = kind == ALONG_LAUNCH_CHARGED ? KA_CHARGED : KA_NEUTRAL;
+    const int hi = kind == ALONG_LAUNCH_NEUTRAL ? KA_CHARGED : KA_VACANT;
+    sp = Span{p.ctl->offsets[lo], p.ctl->offsets[hi], p.perm};
+  } else {
+    sp = Span{p.ctl->offsets[K_G_GEOM], p.ctl->offsets[K_VACANT_FULL], p.perm};
+  }
+  unsigned long long killed = 0;
+  for (uint32_t i = sp.lo + bid * blockDim.x + threadIdx.x; i < sp.hi; i += nb * blockDim.x) {
+    const uint32_t slot = sp.perm ? sp.perm[i] : i;
+    if (p.trk.status[slot] != ALIVE) continue;
+    const uint8_t pt = p.trk.ptype[slot];
+    if ((kind == ALONG_LAUNCH_NEUTRAL && pt != GAMMA) || (kind == ALONG_LAUNCH_CHARGED && pt == GAMMA)) continue;
+    if (along_one(p, slot, pt, ss)) ++killed;
   }
   flush_counter(&p.ctl->alive, killed, true);
 }
+
+// ---- discrete interactions (one track each; return true if the track ended)
 
 // Compton scattering: Klein-Nishina sampling, the recoil energy deposited
 // locally, the photon rotated; below the tracking cut it is absorbed.
-__global__ void k_compton(Params p) {
-  const Span sp = span_of(p, KA_NEUTRAL, KA_NEUTRAL + 1, K_G_COMPTON, K_G_COMPTON + 1);
+__device__ __forceinline__ bool compton_one(const Params& p, uint32_t slot) {
   const Tracks& t = p.trk;
-  unsigned long long killed = 0;
-  for (uint32_t i = sp.lo + blockIdx.x * blockDim.x + threadIdx.x; i < sp.hi; i += gridDim.x * blockDim.x) {
-    const uint32_t slot = sp.perm ? sp.perm[i] : i;
-    if (t.status[slot] != ALIVE || t.action[slot] != A_COMPTON) continue;
-    const double E = t.E[slot];
-    const uint32_t ev = t.event[slot], prim = t.primary[slot];
-    const int layer = t.layer[slot];
-    const double z = t.z[slot];
-    TrackRng rng(p.seed, ev, t.tid[slot], t.ctr[slot]);
-    double cost;
-    bool ok;
-    const double eps = sample_compton(E, rng, cost, ok);
-    if (!ok) {  // non-finite input: end the track, flag the run
-      atomicOr(&p.ctl->error, ERR_SAMPLING);
-      deposit(p, ev, prim, layer, z, E);
-      release(p, slot, ev);
-      ++killed;
-      continue;
-    }
-    const double phi = kTwoPi * rng.uniform();
-    const double E1 = eps * E;
-    deposit(p, ev, prim, layer, z, E - E1);
-    if (E1 < p.cut_track) {
-      deposit(p, ev, prim, layer, z, E1);
-      release(p, slot, ev);
-      ++killed;
-      continue;
-    }
-    double ux = t.ux[slot], uy = t.uy[slot], uz = t.uz[slot];
-    rotate_dir(ux, uy, uz, cost, phi);
-    t.ux[slot] = ux;
-    t.uy[slot] = uy;
-    t.uz[slot] = uz;
-    t.E[slot] = E1;
-    t.nmfp[slot] = -1.0;
-    t.ctr[slot] = rng.ctr;
+  const double E = t.E[slot];
+  const uint32_t ev = t.event[slot], prim = t.primary[slot];
+  const int layer = t.layer[slot];
+  const double z = t.z[slot];
+  TrackRng rng(p.seed, ev, t.tid[slot], t.ctr[slot]);
+  double cost;
+  bool ok;
+  const double eps = sample_compton(E, rng, cost, ok);
+  if (!ok) {  // non-finite input: end the track, flag the run
+    atomicOr(&p.ctl->error, ERR_SAMPLING);
+    deposit(p, ev, prim, layer, z, E);
+    release(p, slot, ev);
+    return true;
   }
-  flush_counter(&p.ctl->alive, killed, true);
+  const double phi = kTwoPi * rng.uniform();
+  const double E1 = eps * E;
+  deposit(p, ev, prim, layer, z, E - E1);
+  if (E1 < p.cut_track) {
+    deposit(p, ev, prim, layer, z, E1);
+    release(p, slot, ev);
+    return true;
+  }
+  double ux = t.ux[slot], uy = t.uy[slot], uz = t.uz[slot];
+  rotate_dir(ux, uy, uz, cost, phi);
+  t.ux[slot] = ux;
+  t.uy[slot] = uy;
+  t.uz[slot] = uz;
+  t.E[slot] = E1;
+  t.nmfp[slot] = -1.0;
+  t.ctr[slot] = rng.ctr;
+  return false;
 }
 
 // Photoelectric absorption: all energy deposited locally.
-__global__ void k_photoelectric(Params p) {
-  const Span sp = span_of(p, KA_NEUTRAL, KA_NEUTRAL + 1, K_G_PE, K_G_PE + 1);
+__device__ __forceinline__ bool photoelectric_one(const Params& p, uint32_t slot) {
   const Tracks& t = p.trk;
-  unsigned long long killed = 0;
-  for (uint32_t i = sp.lo + blockIdx.x * blockDim.x + threadIdx.x; i < sp.hi; i += gridDim.x * blockDim.x) {
-    const uint32_t slot = sp.perm ? sp.perm[i] : i;
-    if (t.status[slot] != ALIVE || t.action[slot] != A_PE) continue;
-    const uint32_t ev = t.event[slot];
-    deposit(p, ev, t.primary[slot], t.layer[slot], t.z[slot], t.E[slot]);
-    release(p, slot, ev);
-    ++killed;
-  }
-  flush_counter(&p.ctl->alive, killed, true);
+  const uint32_t ev = t.event[slot];
+  deposit(p, ev, t.primary[slot], t.layer[slot], t.z[slot], t.E[slot]);
+  release(p, slot, ev);
+  return true;
 }
 
 // Secondary-producing interactions reserve their initializer entries before
@@ -683,182 +667,204 @@ __device__ __forceinline__ void defer_track(const Params& p, uint32_t slot, uint
 
 // Pair production: the pair's kinetic energy E - 2 m_e c^2 deposited locally,
 // two photons of m_e c^2 back to back in an isotropic direction.
-__global__ void k_pair(Params p) {
-  const Span sp = span_of(p, KA_NEUTRAL, KA_NEUTRAL + 1, K_G_PAIR, K_G_PAIR + 1);
+__device__ __forceinline__ bool pair_one(const Params& p, uint32_t slot, uint8_t st, bool tight,
+                                         unsigned long long& n_def) {
   const Tracks& t = p.trk;
-  const bool tight = p.ctl->defer != 0u;
-  unsigned long long killed = 0, n_def = 0;
-  for (uint32_t i = sp.lo + blockIdx.x * blockDim.x + threadIdx.x; i < sp.hi; i += gridDim.x * blockDim.x) {
-    const uint32_t slot = sp.perm ? sp.perm[i] : i;
-    const uint8_t st = t.status[slot];
-    if (st == VACANT || t.action[slot] != A_PAIR) continue;
-    const bool keep = kMe >= p.cut_track;
-    unsigned long long base;
-    if (!reserve_entries(p, keep ? 2u : 0u, tight, base)) {
-      defer_track(p, slot, st, n_def);
-      continue;
-    }
-    const double E = t.E[slot];
-    const uint32_t ev = t.event[slot], prim = t.primary[slot];
-    const int layer = t.layer[slot];
-    const double x = t.x[slot], y = t.y[slot], z = t.z[slot];
-    TrackRng rng(p.seed, ev, t.tid[slot], t.ctr[slot]);
-    deposit(p, ev, prim, layer, z, E - 2.0 * kMe);
-    const double cost = 2.0 * rng.uniform() - 1.0;
-    const double phi = kTwoPi * rng.uniform();
-    const double sint = sqrt(fmax(0.0, 1.0 - cost * cost));
-    double sp_, cp_;
-    sincos(phi, &sp_, &cp_);
-    const double dx = sint * cp_, dy = sint * sp_, dz = cost;
-    if (keep) {
-      const unsigned long long tid1 = rng.raw();
-      const unsigned long long tid2 = rng.raw();
-      write_initializer(p, base, x, y, z, dx, dy, dz, kMe, tid1, ev, prim, layer, GAMMA);
-      write_initializer(p, base + 1, x, y, z, -dx, -dy, -dz, kMe, tid2, ev, prim, layer, GAMMA);
-      atomicAdd(&p.event_live[row_of(p, ev)], 2u);
-      if (prim < p.hist_cap) atomicAdd(&p.hist_secondaries[prim], 2ull);
-    } else {
-      deposit(p, ev, prim, layer, z, kMe);
-      deposit(p, ev, prim, layer, z, kMe);
-    }
-    release(p, slot, ev);
-    ++killed;
+  const bool keep = kMe >= p.cut_track;
+  unsigned long long base;
+  if (!reserve_entries(p, keep ? 2u : 0u, tight, base)) {
+    defer_track(p, slot, st, n_def);
+    return false;
   }
-  flush_counter(&p.ctl->alive, killed, true);
-  if (n_def) atomicAdd(&p.ctl->n_deferred, (unsigned)n_def);
+  const double E = t.E[slot];
+  const uint32_t ev = t.event[slot], prim = t.primary[slot];
+  const int layer = t.layer[slot];
+  const double x = t.x[slot], y = t.y[slot], z = t.z[slot];
+  TrackRng rng(p.seed, ev, t.tid[slot], t.ctr[slot]);
+  deposit(p, ev, prim, layer, z, E - 2.0 * kMe);
+  const double cost = 2.0 * rng.uniform() - 1.0;
+  const double phi = kTwoPi * rng.uniform();
+  const double sint = sqrt(fmax(0.0, 1.0 - cost * cost));
+  double sp_, cp_;
+  sincos(phi, &sp_, &cp_);
+  const double dx = sint * cp_, dy = sint * sp_, dz = cost;
+  if (keep) {
+    const unsigned long long tid1 = rng.raw();
+    const unsigned long long tid2 = rng.raw();
+    write_initializer(p, base, x, y, z, dx, dy, dz, kMe, tid1, ev, prim, layer, GAMMA);
+    write_initializer(p, base + 1, x, y, z, -dx, -dy, -dz, kMe, tid2, ev, prim, layer, GAMMA);
+    atomicAdd(&p.event_live[row_of(p, ev)], 2u);
+    if (prim < p.hist_cap) atomicAdd(&p.hist_secondaries[prim], 2ull);
+  } else {
+    deposit(p, ev, prim, layer, z, kMe);
+    deposit(p, ev, prim, layer, z, kMe);
+  }
+  release(p, slot, ev);
+  return true;
 }
 
 // Moller scattering: delta ray above the production cut from the Moller
 // cross-section, directions from two-body kinematics (delta polar angle from
 // energy-momentum conservation, primary from momentum conservation).
-__global__ void k_moller(Params p) {
-  const Span sp = span_of(p, KA_CHARGED, KA_CHARGED + 1, K_E_MOLLER, K_E_MOLLER + 1);
+__device__ __forceinline__ bool moller_one(const Params& p, uint32_t slot, uint8_t st, bool tight,
+                                           unsigned long long& n_def) {
   const Tracks& t = p.trk;
-  const bool tight = p.ctl->defer != 0u;
-  unsigned long long killed = 0, n_def = 0;
-  for (uint32_t i = sp.lo + blockIdx.x * blockDim.x + threadIdx.x; i < sp.hi; i += gridDim.x * blockDim.x) {
-    const uint32_t slot = sp.perm ? sp.perm[i] : i;
-    const uint8_t st = t.status[slot];
-    if (st == VACANT || t.action[slot] != A_MOLLER) continue;
-    const double T = t.E[slot];
-    if (T <= 2.0 * p.cut_moller) {  // kinematically closed at the post-step energy: null collision
-      t.nmfp[slot] = -1.0;
-      t.status[slot] = ALIVE;
-      continue;
-    }
-    const uint32_t ev = t.event[slot], prim = t.primary[slot];
-    TrackRng rng(p.seed, ev, t.tid[slot], t.ctr[slot]);
-    bool ok;
-    const double eps = sample_moller(T, p.cut_moller, rng, ok);
-    const double Td = eps * T;
-    const bool keep = ok && Td >= p.cut_track;
-    unsigned long long base;
-    if (!reserve_entries(p, keep ? 1u : 0u, tight, base)) {
-      defer_track(p, slot, st, n_def);
-      continue;
-    }
-    const int layer = t.layer[slot];
-    const double x = t.x[slot], y = t.y[slot], z = t.z[slot];
-    if (!ok) {  // non-finite input: end the track, flag the run
-      atomicOr(&p.ctl->error, ERR_SAMPLING);
-      deposit(p, ev, prim, layer, z, T);
-      release(p, slot, ev);
-      ++killed;
-      continue;
-    }
-    const double cost = fmin(1.0, sqrt(Td * (T + 2.0 * kMe) / (T * (Td + 2.0 * kMe))));
-    const double phi = kTwoPi * rng.uniform();
-    const double ux = t.ux[slot], uy = t.uy[slot], uz = t.uz[slot];
-    double dx = ux, dy = uy, dz = uz;
-    rotate_dir(dx, dy, dz, cost, phi);
-    const double pp = sqrt(T * (T + 2.0 * kMe));
-    const double pd = sqrt(Td * (Td + 2.0 * kMe));
-    const double vx = pp * ux - pd * dx, vy = pp * uy - pd * dy, vz = pp * uz - pd * dz;
-    const double inv = 1.0 / sqrt(vx * vx + vy * vy + vz * vz);
-    const double E1 = T - Td;
-    if (keep) {
-      const unsigned long long tid = rng.raw();
-      write_initializer(p, base, x, y, z, dx, dy, dz, Td, tid, ev, prim, layer, ELECTRON);
-      atomicAdd(&p.event_live[row_of(p, ev)], 1u);
-      if (prim < p.hist_cap) atomicAdd(&p.hist_secondaries[prim], 1ull);
-    } else {
-      deposit(p, ev, prim, layer, z, Td);
-    }
-    if (E1 < p.cut_track) {
-      deposit(p, ev, prim, layer, z, E1);
-      release(p, slot, ev);
-      ++killed;
-      continue;
-    }
-    t.ux[slot] = vx * inv;
-    t.uy[slot] = vy * inv;
-    t.uz[slot] = vz * inv;
-    t.E[slot] = E1;
+  const double T = t.E[slot];
+  if (T <= 2.0 * p.cut_moller) {  // kinematically closed at the post-step energy: null collision
     t.nmfp[slot] = -1.0;
-    t.ctr[slot] = rng.ctr;
     t.status[slot] = ALIVE;
+    return false;
   }
-  flush_counter(&p.ctl->alive, killed, true);
-  if (n_def) atomicAdd(&p.ctl->n_deferred, (unsigned)n_def);
+  const uint32_t ev = t.event[slot], prim = t.primary[slot];
+  TrackRng rng(p.seed, ev, t.tid[slot], t.ctr[slot]);
+  bool ok;
+  const double eps = sample_moller(T, p.cut_moller, rng, ok);
+  const double Td = eps * T;
+  const bool keep = ok && Td >= p.cut_track;
+  unsigned long long base;
+  if (!reserve_entries(p, keep ? 1u : 0u, tight, base)) {
+    defer_track(p, slot, st, n_def);
+    return false;
+  }
+  const int layer = t.layer[slot];
+  const double x = t.x[slot], y = t.y[slot], z = t.z[slot];
+  if (!ok) {  // non-finite input: end the track, flag the run
+    atomicOr(&p.ctl->error, ERR_SAMPLING);
+    deposit(p, ev, prim, layer, z, T);
+    release(p, slot, ev);
+    return true;
+  }
+  const double cost = fmin(1.0, sqrt(Td * (T + 2.0 * kMe) / (T * (Td + 2.0 * kMe))));
+  const double phi = kTwoPi * rng.uniform();
+  const double ux = t.ux[slot], uy = t.uy[slot], uz = t.uz[slot];
+  double dx = ux, dy = uy, dz = uz;
+  rotate_dir(dx, dy, dz, cost, phi);
+  const double pp = sqrt(T * (T + 2.0 * kMe));
+  const double pd = sqrt(Td * (Td + 2.0 * kMe));
+  const double vx = pp * ux - pd * dx, vy = pp * uy - pd * dy, vz = pp * uz - pd * dz;
+  const double inv = 1.0 / sqrt(vx * vx + vy * vy + vz * vz);
+  const double E1 = T - Td;
+  if (keep) {
+    const unsigned long long tid = rng.raw();
+    write_initializer(p, base, x, y, z, dx, dy, dz, Td, tid, ev, prim, layer, ELECTRON);
+    atomicAdd(&p.event_live[row_of(p, ev)], 1u);
+    if (prim < p.hist_cap) atomicAdd(&p.hist_secondaries[prim], 1ull);
+  } else {
+    deposit(p, ev, prim, layer, z, Td);
+  }
+  if (E1 < p.cut_track) {
+    deposit(p, ev, prim, layer, z, E1);
+    release(p, slot, ev);
+    return true;
+  }
+  t.ux[slot] = vx * inv;
+  t.uy[slot] = vy * inv;
+  t.uz[slot] = vz * inv;
+  t.E[slot] = E1;
+  t.nmfp[slot] = -1.0;
+  t.ctr[slot] = rng.ctr;
+  t.status[slot] = ALIVE;
+  return false;
 }
 
 // Bremsstrahlung: photon energy from the 1/k spectrum on (k_cut, T], emitted
 // along the parent direction; the parent keeps its direction.
-__global__ void k_brems(Params p) {
-  const Span sp = span_of(p, KA_CHARGED, KA_CHARGED + 1, K_E_BREMS, K_E_BREMS + 1);
+__device__ __forceinline__ bool brems_one(const Params& p, uint32_t slot, uint8_t st, bool tight,
+                                          unsigned long long& n_def) {
   const Tracks& t = p.trk;
+  const double T = t.E[slot];
+  if (T <= p.cut_brems) {  // null collision
+    t.nmfp[slot] = -1.0;
+    t.status[slot] = ALIVE;
+    return false;
+  }
+  const uint32_t ev = t.event[slot], prim = t.primary[slot];
+  TrackRng rng(p.seed, ev, t.tid[slot], t.ctr[slot]);
+  double k = p.cut_brems * exp(rng.uniform() * log(T / p.cut_brems));
+  if (k > T) k = T;
+  const bool keep = k >= p.cut_track;
+  unsigned long long base;
+  if (!reserve_entries(p, keep ? 1u : 0u, tight, base)) {
+    defer_track(p, slot, st, n_def);
+    return false;
+  }
+  const int layer = t.layer[slot];
+  const double x = t.x[slot], y = t.y[slot], z = t.z[slot];
+  const double E1 = T - k;
+  if (keep) {
+    const unsigned long long tid = rng.raw();
+    write_initializer(p, base, x, y, z, t.ux[slot], t.uy[slot], t.uz[slot], k, tid, ev, prim, layer, GAMMA);
+    atomicAdd(&p.event_live[row_of(p, ev)], 1u);
+    if (prim < p.hist_cap) atomicAdd(&p.hist_secondaries[prim], 1ull);
+  } else {
+    deposit(p, ev, prim, layer, z, k);
+  }
+  if (E1 < p.cut_track) {
+    deposit(p, ev, prim, layer, z, E1);
+    release(p, slot, ev);
+    return true;
+  }
+  t.E[slot] = E1;
+  t.nmfp[slot] = -1.0;
+  t.ctr[slot] = rng.ctr;
+  t.status[slot] = ALIVE;
+  return false;
+}
+
+// Interaction phase. which = A_COMPTON ... A_BREMS runs one process (one
+// kernel per action); which = A_NONE runs every interaction over the union of
+// the interaction ranges, each thread dispatching on its track's action.
+__device__ void phase_post(const Params& p, int which, int bid, int nb) {
+  Span sp;
+  if (p.policy == POLICY_NONE) {
+    sp = Span{0u, p.n_slots, nullptr};
+  } else if (p.policy == POLICY_ACTION) {
+    const bool neutral_only = which == A_COMPTON || which == A_PE || which == A_PAIR;
+    const bool charged_only = which == A_MOLLER || which == A_BREMS;
+    const int lo = charged_only ? KA_CHARGED : KA_NEUTRAL;
+    const int hi = neutral_only ? KA_CHARGED : KA_VACANT;
+    sp = Span{p.ctl->offsets[lo], p.ctl->offsets[hi], p.perm};
+  } else {
+    int lo = kFirstInteractionKey, hi = K_VACANT_FULL;
+    switch (which) {
+      case A_COMPTON: lo = K_G_COMPTON; break;
+      case A_PE: lo = K_G_PE; break;
+      case A_PAIR: lo = K_G_PAIR; break;
+      case A_MOLLER: lo = K_E_MOLLER; break;
+      case A_BREMS: lo = K_E_BREMS; break;
+      default: break;
+    }
+    if (which != A_NONE) hi = lo + 1;
+    sp = Span{p.ctl->offsets[lo], p.ctl->offsets[hi], p.perm};
+  }
   const bool tight = p.ctl->defer != 0u;
   unsigned long long killed = 0, n_def = 0;
-  for (uint32_t i = sp.lo + blockIdx.x * blockDim.x + threadIdx.x; i < sp.hi; i += gridDim.x * blockDim.x) {
+  for (uint32_t i = sp.lo + bid * blockDim.x + threadIdx.x; i < sp.hi; i += nb * blockDim.x) {
     const uint32_t slot = sp.perm ? sp.perm[i] : i;
-    const uint8_t st = t.status[slot];
-    if (st == VACANT || t.action[slot] != A_BREMS) continue;
-    const double T = t.E[slot];
-    if (T <= p.cut_brems) {  // null collision
-      t.nmfp[slot] = -1.0;
-      t.status[slot] = ALIVE;
-      continue;
+    const uint8_t st = p.trk.status[slot];
+    if (st == VACANT) continue;
+    const uint8_t act = p.trk.action[slot];
+    if (act < A_COMPTON || act > A_BREMS || (which != A_NONE && act != which)) continue;
+    // only deferrable interactions may run on a track already waiting
+    if (st == DEFERRED && !(act == A_PAIR || act == A_MOLLER || act == A_BREMS)) continue;
+    bool ended = false;
+    switch (act) {
+      case A_COMPTON: ended = compton_one(p, slot); break;
+      case A_PE: ended = photoelectric_one(p, slot); break;
+      case A_PAIR: ended = pair_one(p, slot, st, tight, n_def); break;
+      case A_MOLLER: ended = moller_one(p, slot, st, tight, n_def); break;
+      case A_BREMS: ended = brems_one(p, slot, st, tight, n_def); break;
+      default: break;
     }
-    const uint32_t ev = t.event[slot], prim = t.primary[slot];
-    TrackRng rng(p.seed, ev, t.tid[slot], t.ctr[slot]);
-    double k = p.cut_brems * exp(rng.uniform() * log(T / p.cut_brems));
-    if (k > T) k = T;
-    const bool keep = k >= p.cut_track;
-    unsigned long long base;
-    if (!reserve_entries(p, keep ? 1u : 0u, tight, base)) {
-      defer_track(p, slot, st, n_def);
-      continue;
-    }
-    const int layer = t.layer[slot];
-    const double x = t.x[slot], y = t.y[slot], z = t.z[slot];
-    const double E1 = T - k;
-    if (keep) {
-      const unsigned long long tid = rng.raw();
-      write_initializer(p, base, x, y, z, t.ux[slot], t.uy[slot], t.uz[slot], k, tid, ev, prim, layer, GAMMA);
-      atomicAdd(&p.event_live[row_of(p, ev)], 1u);
-      if (prim < p.hist_cap) atomicAdd(&p.hist_secondaries[prim], 1ull);
-    } else {
-      deposit(p, ev, prim, layer, z, k);
-    }
-    if (E1 < p.cut_track) {
-      deposit(p, ev, prim, layer, z, E1);
-      release(p, slot, ev);
-      ++killed;
-      continue;
-    }
-    t.E[slot] = E1;
-    t.nmfp[slot] = -1.0;
-    t.ctr[slot] = rng.ctr;
-    t.status[slot] = ALIVE;
+    if (ended) ++killed;
   }
   flush_counter(&p.ctl->alive, killed, true);
   if (n_def) atomicAdd(&p.ctl->n_deferred, (unsigned)n_def);
 }
 
 // End of an iteration: counters, the per-iteration trace row, stall and
-// iteration-limit checks, and the loop condition (set on the graph's
-// conditional node when the loop runs inside a CUDA graph).
-__global__ void k_loop_ctl(Params p, cudaGraphConditionalHandle handle, int use_handle) {
+// iteration-limit checks, and the loop condition. One thread.
+__device__ void loop_ctl_one(const Params& p) {
   Ctl* c = p.ctl;
   const unsigned long long queued = c->tail - c->head;
   const bool worked = c->steps_iter > 0 || c->n_deferred > 0;
@@ -885,7 +891,122 @@ __global__ void k_loop_ctl(Params p, cudaGraphConditionalHandle handle, int use_
   }
   if (pending && c->iteration >= c->max_iterations) c->error |= ERR_ITERATIONS;
   c->cont = (pending && c->error == 0u) ? 1u : 0u;
-  if (use_handle) cudaGraphSetConditional(handle, c->cont);
+}
+
+// ------------------------------------------------------------------ kernels
+__global__ void __launch_bounds__(kTile) k_init_count(Params p) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) clear_iteration_counters(p.ctl);
+  phase_init_count(p, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kTile) k_init_fill(Params p) { phase_init_fill(p, blockIdx.x, gridDim.x); }
+
+__global__ void __launch_bounds__(kTile) k_pre_step(Params p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SharedStatic ss = carve_static(p, smem_raw);
+  stage_static(p, ss);
+  phase_pre_step(p, blockIdx.x, gridDim.x, ss);
+}
+
+__global__ void __launch_bounds__(1024) k_iter_ctl(Params p) { phase_iter_ctl(p); }
+
+__global__ void __launch_bounds__(kTile) k_scatter(Params p) { phase_scatter(p, blockIdx.x, gridDim.x); }
+
+__global__ void k_along(Params p, int kind) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SharedStatic ss = carve_static(p, smem_raw);
+  stage_static(p, ss);
+  phase_along(p, kind, blockIdx.x, gridDim.x, ss);
+}
+
+__global__ void k_post(Params p, int which) { phase_post(p, which, blockIdx.x, gridDim.x); }
+
+__global__ void k_loop_ctl(Params p, cudaGraphConditionalHandle handle, int use_handle) {
+  loop_ctl_one(p);
+  if (use_handle) cudaGraphSetConditional(handle, p.ctl->cont);
+}
+
+// Grid-wide barrier of the persistent loop (generation counter). Every wait
+// is bounded: after ~1 s a block gives up, sets the abort word and the error
+// bit, and every block then leaves the loop at its next barrier.
+__device__ __forceinline__ bool grid_barrier(const Params& p, unsigned nblocks) {
+  __shared__ int s_ok;
+  unsigned int* count = p.barrier;
+  unsigned int* gen = p.barrier + 1;
+  unsigned int* abort_word = p.barrier + 2;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g = *reinterpret_cast<volatile unsigned*>(gen);
+    int ok = 1;
+    if (atomicAdd(count, 1u) == nblocks - 1) {
+      *reinterpret_cast<volatile unsigned*>(count) = 0u;
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      for (;;) {
+        if (*reinterpret_cast<volatile unsigned*>(gen) != g) break;
+        if (*reinterpret_cast<volatile unsigned*>(abort_word) != 0u) {
+          ok = 0;
+          break;
+        }
+        if (clock64() - t0 > kBarrierTimeoutCycles) {
+          atomicExch(abort_word, 1u);
+          atomicOr(&p.ctl->error, ERR_BARRIER_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    if (*reinterpret_cast<volatile unsigned*>(abort_word) != 0u) ok = 0;
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// The whole step loop in one persistent cooperative launch: one block per
+// SM slot, the static tables staged into shared memory once, and the phases
+// of each iteration separated by grid barriers. The per-iteration control
+// (counters, loop condition) of iteration k runs at the start of k + 1.
+__global__ void __launch_bounds__(kTile, 1) k_loop(Params p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SharedStatic ss = carve_static(p, smem_raw);
+  stage_static(p, ss);
+  const unsigned nb = gridDim.x;
+  const int bid = blockIdx.x;
+  const bool sorted = p.policy != POLICY_NONE;
+  bool first = true;
+  for (;;) {
+    if (bid == 0 && threadIdx.x == 0) {
+      if (first)
+        p.ctl->cont = 1u;
+      else
+        loop_ctl_one(p);
+      clear_iteration_counters(p.ctl);
+    }
+    first = false;
+    phase_init_count(p, bid, nb);
+    if (!grid_barrier(p, nb)) break;
+    if (p.ctl->cont == 0u) break;
+    phase_init_fill(p, bid, nb);
+    if (!grid_barrier(p, nb)) break;
+    phase_pre_step(p, bid, nb, ss);
+    if (!grid_barrier(p, nb)) break;
+    if (bid == 0) phase_iter_ctl(p);
+    if (!grid_barrier(p, nb)) break;
+    if (sorted) {
+      phase_scatter(p, bid, nb);
+      if (!grid_barrier(p, nb)) break;
+    }
+    phase_along(p, ALONG_LAUNCH_ALL, bid, nb, ss);
+    if (!grid_barrier(p, nb)) break;
+    phase_post(p, A_NONE, bid, nb);
+    if (!grid_barrier(p, nb)) break;
+  }
 }
 
 // Queue staged primaries at the tail of the initializer buffer.
@@ -983,55 +1104,56 @@ cudaError_t configure_kernels(const Params& p, int block, LaunchShape* sh) {
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const size_t geo = (size_t)(p.n_layers + 1) * sizeof(double) + (size_t)p.n_layers * sizeof(int32_t);
-  sh->pre_smem = (size_t)p.n_materials * kCols * kGrid * sizeof(double2) + geo;
-  sh->along_smem = (size_t)p.n_materials * kGrid * sizeof(double2) + geo;
-  sh->neutral_smem = geo;
+  const size_t stat = (size_t)p.n_materials * kCols * kGrid * sizeof(double2) +
+                      (size_t)(p.n_layers + 1) * sizeof(double) + (size_t)p.n_layers * sizeof(int32_t);
+  sh->static_smem = stat;
   sh->block = block;
-  e = cudaFuncSetAttribute(k_pre_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh->pre_smem);
+  e = cudaFuncSetAttribute(k_pre_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stat);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_along<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh->along_smem);
+  e = cudaFuncSetAttribute(k_along, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stat);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_along<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh->neutral_smem);
+  e = cudaFuncSetAttribute(k_loop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stat);
   if (e != cudaSuccess) return e;
-  sh->pre_grid = occupancy_grid((const void*)k_pre_step, kTile, sh->pre_smem, sms, (int)p.n_tiles);
+  sh->tile_grid = occupancy_grid((const void*)k_pre_step, kTile, stat, sms, (int)p.n_tiles);
   const int cap_action = (int)((p.n_slots + block - 1) / block);
-  sh->action_grid = occupancy_grid((const void*)k_along<true>, block, sh->along_smem, sms, cap_action);
+  sh->along_grid = occupancy_grid((const void*)k_along, block, stat, sms, cap_action);
+  sh->post_grid = occupancy_grid((const void*)k_post, block, 0, sms, cap_action);
+  int nb = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)k_loop, kTile, stat);
+  if (e != cudaSuccess) return e;
+  sh->loop_grid = nb * sms;
   return cudaGetLastError();
 }
 
-void launch_init_count(const Params& p, cudaStream_t s) { k_init_count<<<p.n_init_tiles, 256, 0, s>>>(p); }
-void launch_init_fill(const Params& p, cudaStream_t s) { k_init_fill<<<p.n_init_tiles, 256, 0, s>>>(p); }
+void launch_init_count(const Params& p, const LaunchShape& sh, cudaStream_t s) {
+  k_init_count<<<sh.tile_grid, kTile, 0, s>>>(p);
+}
+void launch_init_fill(const Params& p, const LaunchShape& sh, cudaStream_t s) {
+  k_init_fill<<<sh.tile_grid, kTile, 0, s>>>(p);
+}
 void launch_pre_step(const Params& p, const LaunchShape& sh, cudaStream_t s) {
-  k_pre_step<<<sh.pre_grid, kTile, sh.pre_smem, s>>>(p);
+  k_pre_step<<<sh.tile_grid, kTile, sh.static_smem, s>>>(p);
 }
 void launch_iter_ctl(const Params& p, cudaStream_t s) { k_iter_ctl<<<1, 1024, 0, s>>>(p); }
 void launch_scatter(const Params& p, const LaunchShape& sh, cudaStream_t s) {
-  k_scatter<<<sh.pre_grid, kTile, 0, s>>>(p);
+  k_scatter<<<sh.tile_grid, kTile, 0, s>>>(p);
 }
-void launch_along(const Params& p, bool charged, const LaunchShape& sh, cudaStream_t s) {
-  if (charged)
-    k_along<true><<<sh.action_grid, sh.block, sh.along_smem, s>>>(p);
-  else
-    k_along<false><<<sh.action_grid, sh.block, sh.neutral_smem, s>>>(p);
+void launch_along(const Params& p, int kind, const LaunchShape& sh, cudaStream_t s) {
+  k_along<<<sh.along_grid, sh.block, sh.static_smem, s>>>(p, kind);
 }
 void launch_post(const Params& p, int which, const LaunchShape& sh, cudaStream_t s) {
-  switch (which) {
-    case POST_COMPTON: k_compton<<<sh.action_grid, sh.block, 0, s>>>(p); break;
-    case POST_PE: k_photoelectric<<<sh.action_grid, sh.block, 0, s>>>(p); break;
-    case POST_PAIR: k_pair<<<sh.action_grid, sh.block, 0, s>>>(p); break;
-    case POST_MOLLER: k_moller<<<sh.action_grid, sh.block, 0, s>>>(p); break;
-    case POST_BREMS: k_brems<<<sh.action_grid, sh.block, 0, s>>>(p); break;
-    default: break;
-  }
+  k_post<<<sh.post_grid, sh.block, 0, s>>>(p, which);
 }
 void launch_loop_ctl(const Params& p, unsigned long long handle, int use_handle, cudaStream_t s) {
   k_loop_ctl<<<1, 1, 0, s>>>(p, (cudaGraphConditionalHandle)handle, use_handle);
 }
+cudaError_t launch_loop(const Params& p, const LaunchShape& sh, cudaStream_t s) {
+  void* args[] = {const_cast<Params*>(&p)};
+  return cudaLaunchCooperativeKernel((const void*)k_loop, dim3(sh.loop_grid), dim3(kTile), args, sh.static_smem, s);
+}
 void launch_push_primaries(const Params& p, const StagedPrimary* d_prim, uint32_t n, cudaStream_t s) {
   k_push_primaries<<<1, 1024, 0, s>>>(p, d_prim, n);
 }
-
 void launch_push_device_primaries(const Params& p, const DevicePrimary* src, uint32_t n, uint32_t event,
                                   unsigned long long tid0, uint32_t prim0, cudaStream_t s) {
   k_push_device_primaries<<<1, 1024, 0, s>>>(p, src, n, event, tid0, prim0);
@@ -1039,8 +1161,8 @@ void launch_push_device_primaries(const Params& p, const DevicePrimary* src, uin
 
 const char* kernel_name(int id) {
   static const char* names[KID_COUNT] = {"init_count", "init_fill", "pre_step", "iter_ctl", "scatter",
-                                         "along_neutral", "along_charged", "compton", "photoelectric",
-                                         "pair", "moller", "brems", "loop_ctl"};
+                                         "along", "along_neutral", "along_charged", "post", "compton",
+                                         "photoelectric", "pair", "moller", "brems", "loop_ctl", "loop"};
   return (id >= 0 && id < KID_COUNT) ? names[id] : "?";
 }
 

@@ -97,6 +97,7 @@ class Problem:
     history_capacity: int = 0
     sort_policy: int = SORT_NONE
     block_size: int = 256
+    split_actions: int = 0
     seed: int = DEFAULT_SEED
     name: str = ""
 

@@ -6,14 +6,16 @@ import oracle
 from paper_2503_17608_gb300 import binding, workloads as wl
 
 
-def run_gpu(prob, prim, use_graph=True, history=True, policy=None, stream=None):
+def run_gpu(prob, prim, mode=binding.LOOP_PERSISTENT, history=True, policy=None, stream=None, split=None):
     if policy is not None:
         prob = prob.replace(sort_policy=policy)
+    if split is not None:
+        prob = prob.replace(split_actions=int(split))
     if history:
         prob = prob.replace(history_capacity=len(prim))
     with binding.Context(prob, stream=stream) as ctx:
         ctx.add_events(prim)
-        ctx.run_events(use_graph=use_graph)
+        ctx.run_events(mode)
         stats = ctx.stats()
         out = dict(stats=stats)
         if history:

@@ -64,12 +64,16 @@ def test_device_tables_match_oracle(make):
 
 
 # ------------------------------------------------------------------ photon-only water cube
+LOOPS = [binding.LOOP_HOST, binding.LOOP_GRAPH, binding.LOOP_PERSISTENT]
+
+
 @pytest.mark.parametrize("policy", POLICIES)
-@pytest.mark.parametrize("use_graph", [True, False])
-def test_water_cube_histories_bit_exact(policy, use_graph):
+@pytest.mark.parametrize("mode,split", [(binding.LOOP_HOST, True), (binding.LOOP_GRAPH, False),
+                                        (binding.LOOP_GRAPH, True), (binding.LOOP_PERSISTENT, False)])
+def test_water_cube_histories_bit_exact(policy, mode, split):
     prob = wl.water_cube_problem()
     prim = wl.water_cube_primaries()
-    g = run_gpu(prob, prim, use_graph=use_graph, policy=policy)
+    g = run_gpu(prob, prim, mode=mode, policy=policy, split=split)
     o = run_oracle(prob, prim)
     np.testing.assert_array_equal(g["hist"]["steps"], o["hist"]["steps"])
     np.testing.assert_array_equal(g["hist"]["secondaries"], o["hist"]["secondaries"])
@@ -105,8 +109,8 @@ def test_empty_run_and_empty_add():
     prob = wl.water_cube_problem()
     with binding.Context(prob) as ctx:
         ctx.add_primaries(0, wl.water_cube_primaries(0))
-        ctx.run_events(use_graph=True)
-        ctx.run_events(use_graph=False)
+        for mode in LOOPS:
+            ctx.run_events(mode)
         s = ctx.stats()
         assert s["steps_total"] == 0 and s["alive"] == 0 and s["queued"] == 0
         t, e = ctx.read_tallies(0)
@@ -166,9 +170,10 @@ def test_partition_is_a_stable_valid_partition():
 
 # ------------------------------------------------------------------ calorimeter, no field
 @pytest.mark.parametrize("policy", POLICIES)
-def test_calorimeter_histories(policy):
+@pytest.mark.parametrize("mode", [binding.LOOP_GRAPH, binding.LOOP_PERSISTENT])
+def test_calorimeter_histories(policy, mode):
     prob, prim = wl.calorimeter_1gev(200)
-    g = run_gpu(prob, prim, policy=policy)
+    g = run_gpu(prob, prim, policy=policy, mode=mode, split=(mode == binding.LOOP_GRAPH))
     o = run_oracle(prob, prim)
     frac, _ = match_fraction(g, o)
     assert frac >= 0.95, frac
@@ -200,9 +205,10 @@ def test_calorimeter_profile_statistics_independent_seeds():
 
 # ------------------------------------------------------------------ calorimeter in a 4 T field
 @pytest.mark.parametrize("policy", [wl.SORT_NONE, wl.SORT_ACTION_TYPE])
-def test_field_histories(policy):
+@pytest.mark.parametrize("mode", [binding.LOOP_GRAPH, binding.LOOP_PERSISTENT])
+def test_field_histories(policy, mode):
     prob, prim = wl.calorimeter_field_10gev(40, n_slots=1 << 16)
-    g = run_gpu(prob, prim, policy=policy)
+    g = run_gpu(prob, prim, policy=policy, mode=mode)
     o = run_oracle(prob, prim)
     frac, _ = match_fraction(g, o)
     assert frac >= 0.9, frac
@@ -251,7 +257,7 @@ def test_full_buffer_reports_capacity_and_stays_usable():
     with binding.Context(prob, max_iterations=100000) as ctx:
         ctx.add_events(prim)
         with pytest.raises(binding.CelerError) as ei:
-            ctx.run_events(use_graph=True)
+            ctx.run_events(binding.LOOP_PERSISTENT)
         assert ei.value.status == 2
         s = ctx.stats()
         assert s["alive"] == 1 and s["queued"] == 1
