@@ -292,6 +292,7 @@ def run_ours(args):
             e2e_ms += (t1 - t0) * 1e3
             e2e_steps += ctx.stats()["steps_total"] - s0
         ev_e2e += 1
+    prof = ctx.loop_profile() if loop == binding.LOOP_PERSISTENT else None
     e2e_ms = reduce(e2e_ms, MAX)
     e2e_steps = reduce(e2e_steps, SUM)
     iterations = ctx.stats()["iteration"]
@@ -337,6 +338,10 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(8 * (len(tally) + 1))},
         "clocks": clocks,
     }
+    if prof is not None:
+        it = max(ctx.stats()["iteration"], 1)
+        line["loop_profile_us_per_iteration"] = {
+            name: round(c / it / 2.07e3, 3) for name, c in zip(("fill_step", "scatter", "step"), prof)}
     job_ms = statistics.median(h["job_ms"])
     line["roofline"] = roofline_loop(steps_per_job, job_ms)
     if launches_per_job:

@@ -198,6 +198,11 @@ enum {
  * initializer buffer is full and no track can make progress. */
 celer_status celer_run_events(celer_ctx* ctx, int mode);
 
+/* SM cycles the persistent loop spent in each of its phases since creation,
+ * as seen by its first block: [0] fill + step limit, [1] partition scatter,
+ * [2] along-step + interactions, [3] unused. n entries are written. */
+celer_status celer_read_loop_profile(celer_ctx* ctx, uint64_t* cycles_out, int n);
+
 /* Choose per-action launches (1) or per-phase launches (0) for the host and
  * graph loops. */
 celer_status celer_set_split_actions(celer_ctx* ctx, int split);

@@ -81,6 +81,7 @@ EXPORTS = [
     "celer_add_primaries_device",
     "celer_step", "celer_run_events", "celer_read_tallies", "celer_reset_event", "celer_event_live",
     "celer_read_history", "celer_get_stats", "celer_set_sort_policy", "celer_set_split_actions", "celer_read_trace",
+    "celer_read_loop_profile",
     "celer_enable_kernel_timing", "celer_kernel_timing", "celer_debug_partition", "celer_debug_table",
     "celer_debug_philox", "celer_debug_curand_philox",
 ]
@@ -114,6 +115,7 @@ def load(path: Optional[str] = None):
         "celer_get_stats": ([vp, C.POINTER(celer_step_stats)], i32),
         "celer_set_sort_policy": ([vp, i32], i32),
         "celer_set_split_actions": ([vp, i32], i32),
+        "celer_read_loop_profile": ([vp, C.POINTER(u64), i32], i32),
         "celer_read_trace": ([vp, vp, u64, C.POINTER(u64)], i32),
         "celer_enable_kernel_timing": ([vp, i32], i32),
         "celer_kernel_timing": ([vp, C.POINTER(C.c_char_p), dp, C.POINTER(u64), i32, C.POINTER(i32)], i32),
@@ -239,6 +241,12 @@ class Context:
         if use_graph is not None:
             mode = LOOP_GRAPH if use_graph else LOOP_HOST
         _check(load().celer_run_events(self._h, int(mode)), self._h)
+
+    def loop_profile(self):
+        """SM cycles of the persistent loop per phase: fill+step limit, scatter, step."""
+        out = (C.c_uint64 * 4)()
+        _check(load().celer_read_loop_profile(self._h, out, 4), self._h)
+        return list(out)[:3]
 
     def set_split_actions(self, split: bool):
         _check(load().celer_set_split_actions(self._h, 1 if split else 0), self._h)

@@ -64,7 +64,8 @@ constexpr int kKeysAlong = 3;
 enum Policy : int { POLICY_NONE = 0, POLICY_ACTION = 1, POLICY_ACTION_TYPE = 2 };
 
 enum ErrorBits : uint32_t { ERR_RING_OVERFLOW = 1u, ERR_NO_PROGRESS = 2u, ERR_ITERATIONS = 4u, ERR_SAMPLING = 8u,
-                            ERR_PRIMARIES_REJECTED = 16u, ERR_BARRIER_TIMEOUT = 32u };
+                            ERR_PRIMARIES_REJECTED = 16u, ERR_BARRIER_TIMEOUT = 32u,
+                            ERR_VACANCY = 64u };
 
 struct Tracks {
   double *x, *y, *z, *ux, *uy, *uz, *E, *nmfp, *step, *rpost;
@@ -99,8 +100,13 @@ struct Ctl {
   unsigned int error;
   unsigned int cont;                 // 1 while alive + queued > 0
   unsigned int stall;                // consecutive iterations without progress
+  unsigned int done_a, done_c;       // last-block tickets of the fill/step-limit and step phases
   unsigned int pad;
   unsigned long long trace_count;
+  unsigned long long last_steps_iter;          // copies of the last finished iteration's counters
+  unsigned int last_n_deferred;
+  unsigned int last_action_count[kMaxKeys];
+  unsigned long long phase_cycles[4];  // persistent loop: SM cycles spent per phase (block 0's view)
 };
 
 struct TraceRow {
@@ -117,7 +123,8 @@ struct Params {
   uint32_t n_tiles;        // ceil(n_slots / kTile)
   unsigned long long ring_mask;
   unsigned long long ring_capacity;
-  uint32_t* init_counts;   // vacant slots per tile, n_tiles
+  uint32_t* vacant;        // vacant slots per tile, n_tiles (kept current by every release)
+  uint32_t* filled;        // slots filled per tile in the current iteration, n_tiles
   unsigned int* barrier;   // grid barrier state of the persistent loop: count, generation, abort
   // partition
   int policy;

@@ -160,33 +160,33 @@ void timed(celer_ctx* ctx, cudaStream_t s, int kid, F&& launch, bool allow_timin
   cudaEventRecord(ctx->t_stop[i], s);
 }
 
-// One step iteration as a sequence of launches on stream s: initializer
-// (count, fill), step limit, partition (scan, scatter), along-step,
-// interactions, loop control. With split_actions the along-step and the
-// interactions are one launch per action, as in the paper's loop over
-// actions; otherwise one launch each covers all actions of the phase.
+// One step iteration as a sequence of launches on stream s. Phase-merged:
+// fill + step limit (+ bookkeeping), scatter, along-step + interactions (+
+// end of iteration). Per action (split_actions), as in the paper's loop over
+// actions: fill, step limit, scatter, one along-step kernel per particle kind,
+// one kernel per interaction, end of iteration.
 void launch_iteration(celer_ctx* ctx, cudaStream_t s, unsigned long long handle, int use_handle) {
   const Params& p = ctx->p;
   const LaunchShape& sh = ctx->shape;
   const bool t = use_handle == 0;
-  timed(ctx, s, KID_INIT_COUNT, [&] { launch_init_count(p, sh, s); }, t);
-  timed(ctx, s, KID_INIT_FILL, [&] { launch_init_fill(p, sh, s); }, t);
-  timed(ctx, s, KID_PRE_STEP, [&] { launch_pre_step(p, sh, s); }, t);
-  timed(ctx, s, KID_ITER_CTL, [&] { launch_iter_ctl(p, s); }, t);
-  if (policy_sorted(p.policy)) timed(ctx, s, KID_SCATTER, [&] { launch_scatter(p, sh, s); }, t);
-  const int P = p.processes;
-  if (ctx->split_actions) {
-    timed(ctx, s, KID_ALONG_NEUTRAL, [&] { launch_along(p, ALONG_LAUNCH_NEUTRAL, sh, s); }, t);
-    timed(ctx, s, KID_ALONG_CHARGED, [&] { launch_along(p, ALONG_LAUNCH_CHARGED, sh, s); }, t);
-    if (P & PROC_COMPTON) timed(ctx, s, KID_POST_COMPTON, [&] { launch_post(p, A_COMPTON, sh, s); }, t);
-    if (P & PROC_PE) timed(ctx, s, KID_POST_PE, [&] { launch_post(p, A_PE, sh, s); }, t);
-    if (P & PROC_PAIR) timed(ctx, s, KID_POST_PAIR, [&] { launch_post(p, A_PAIR, sh, s); }, t);
-    if (P & PROC_MOLLER) timed(ctx, s, KID_POST_MOLLER, [&] { launch_post(p, A_MOLLER, sh, s); }, t);
-    if (P & PROC_BREMS) timed(ctx, s, KID_POST_BREMS, [&] { launch_post(p, A_BREMS, sh, s); }, t);
-  } else {
-    timed(ctx, s, KID_ALONG, [&] { launch_along(p, ALONG_LAUNCH_ALL, sh, s); }, t);
-    timed(ctx, s, KID_POST, [&] { launch_post(p, A_NONE, sh, s); }, t);
+  const bool sorted = policy_sorted(p.policy);
+  if (!ctx->split_actions) {
+    timed(ctx, s, KID_FILL_STEP, [&] { launch_fill_step(p, sh, s); }, t);
+    if (sorted) timed(ctx, s, KID_SCATTER, [&] { launch_scatter(p, sh, s); }, t);
+    timed(ctx, s, KID_STEP, [&] { launch_step(p, sh, handle, use_handle, s); }, t);
+    return;
   }
+  timed(ctx, s, KID_FILL, [&] { launch_fill(p, sh, s); }, t);
+  timed(ctx, s, KID_PRE_STEP, [&] { launch_pre_step(p, sh, s); }, t);
+  if (sorted) timed(ctx, s, KID_SCATTER, [&] { launch_scatter(p, sh, s); }, t);
+  timed(ctx, s, KID_ALONG_NEUTRAL, [&] { launch_along(p, 0, sh, s); }, t);
+  timed(ctx, s, KID_ALONG_CHARGED, [&] { launch_along(p, 1, sh, s); }, t);
+  const int P = p.processes;
+  if (P & PROC_COMPTON) timed(ctx, s, KID_POST_COMPTON, [&] { launch_post(p, A_COMPTON, sh, s); }, t);
+  if (P & PROC_PE) timed(ctx, s, KID_POST_PE, [&] { launch_post(p, A_PE, sh, s); }, t);
+  if (P & PROC_PAIR) timed(ctx, s, KID_POST_PAIR, [&] { launch_post(p, A_PAIR, sh, s); }, t);
+  if (P & PROC_MOLLER) timed(ctx, s, KID_POST_MOLLER, [&] { launch_post(p, A_MOLLER, sh, s); }, t);
+  if (P & PROC_BREMS) timed(ctx, s, KID_POST_BREMS, [&] { launch_post(p, A_BREMS, sh, s); }, t);
   timed(ctx, s, KID_LOOP_CTL, [&] { launch_loop_ctl(p, handle, use_handle, s); }, t);
 }
 
@@ -257,11 +257,11 @@ void fill_stats(const Ctl& c, celer_step_stats* s) {
   s->iteration = c.iteration;
   s->alive = c.alive;
   s->queued = c.tail - c.head;
-  s->steps = c.steps_iter;
+  s->steps = c.last_steps_iter;
   s->steps_total = c.steps_total;
-  s->deferred = c.n_deferred;
+  s->deferred = c.last_n_deferred;
   s->error = c.error;
-  for (int k = 0; k < 16; ++k) s->action_count[k] = k < kMaxKeys ? c.action_count[k] : 0;
+  for (int k = 0; k < 16; ++k) s->action_count[k] = k < kMaxKeys ? c.last_action_count[k] : 0;
 }
 
 celer_status status_from_error(celer_ctx* ctx, unsigned err) {
@@ -271,6 +271,7 @@ celer_status status_from_error(celer_ctx* ctx, unsigned err) {
   if (err & ERR_PRIMARIES_REJECTED)
     return fail(ctx, CELER_ERR_INVALID, "device primaries rejected (invalid record or buffer full)");
   if (err & ERR_BARRIER_TIMEOUT) return fail(ctx, CELER_ERR_TIMEOUT, "persistent loop: grid barrier timed out");
+  if (err & ERR_VACANCY) return fail(ctx, CELER_ERR_STATE, "vacancy bookkeeping inconsistent");
   if (err & ERR_SAMPLING) return fail(ctx, CELER_ERR_STATE, "rejection sampling hit its attempt limit");
   if (err) return fail(ctx, CELER_ERR_STATE, "device error flag set");
   return CELER_OK;
@@ -463,8 +464,17 @@ celer_status celer_create(const celer_problem* pb, celer_ctx** out) {
   CREATE_CUDA(dalloc(ctx, &r.layer, C));
   CREATE_CUDA(dalloc(ctx, &r.ptype, C));
   CREATE_CUDA(dalloc(ctx, &p.ctl, 1));
-  CREATE_CUDA(dalloc(ctx, &p.init_counts, p.n_tiles));
+  CREATE_CUDA(dalloc(ctx, &p.vacant, p.n_tiles));
+  CREATE_CUDA(dalloc(ctx, &p.filled, p.n_tiles));
   CREATE_CUDA(dalloc(ctx, &p.barrier, 4));
+  {
+    std::vector<uint32_t> vac(p.n_tiles);
+    for (uint32_t tile = 0; tile < p.n_tiles; ++tile) {
+      const uint64_t lo = (uint64_t)tile * kTile;
+      vac[tile] = (uint32_t)((N - lo) < (uint64_t)kTile ? (N - lo) : (uint64_t)kTile);
+    }
+    CREATE_CUDA(cudaMemcpy(p.vacant, vac.data(), sizeof(uint32_t) * p.n_tiles, cudaMemcpyHostToDevice));
+  }
   CREATE_CUDA(dalloc(ctx, &p.perm, N));
   CREATE_CUDA(dalloc(ctx, &p.tile_counts, (size_t)kKeysFull * p.n_tiles));
   double* d_zb = nullptr;
@@ -620,6 +630,8 @@ celer_status celer_step(celer_ctx* ctx, celer_step_stats* stats) {
 celer_status celer_run_events(celer_ctx* ctx, int mode) {
   if (!ctx) return CELER_ERR_INVALID;
   if (mode < CELER_LOOP_HOST || mode > CELER_LOOP_PERSISTENT) return fail(ctx, CELER_ERR_INVALID, "unknown loop mode");
+  // last-block tickets start from zero (an aborted run could leave them set)
+  CELER_CUDA(ctx, cudaMemsetAsync(&ctx->p.ctl->done_a, 0, 2 * sizeof(unsigned int), ctx->stream));
   if (mode == CELER_LOOP_GRAPH) {
     if (!ctx->graph_exec || ctx->graph_policy != ctx->p.policy || ctx->graph_split != ctx->split_actions) {
       celer_status st = build_graph(ctx);
@@ -737,6 +749,14 @@ celer_status celer_get_stats(celer_ctx* ctx, celer_step_stats* out) {
   celer_status st = read_ctl(ctx);
   if (st != CELER_OK) return st;
   fill_stats(*ctx->h_ctl, out);
+  return CELER_OK;
+}
+
+celer_status celer_read_loop_profile(celer_ctx* ctx, uint64_t* cycles_out, int n) {
+  if (!ctx || !cycles_out || n < 1) return CELER_ERR_INVALID;
+  celer_status st = read_ctl(ctx);
+  if (st != CELER_OK) return st;
+  for (int k = 0; k < n; ++k) cycles_out[k] = k < 4 ? ctx->h_ctl->phase_cycles[k] : 0;
   return CELER_OK;
 }
 

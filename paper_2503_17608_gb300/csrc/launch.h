@@ -14,27 +14,28 @@ struct StagedPrimary {
 };
 
 struct LaunchShape {
-  int tile_grid;       // persistent grid of the tile kernels (initializer, step limit, scatter)
-  int along_grid;      // persistent grid of the along-step kernels
-  int post_grid;       // persistent grid of the interaction kernels
+  int tile_grid;       // persistent grid of the tile kernels (fill, step limit, scatter)
+  int step_grid;       // persistent grid of the phase-merged step kernel
+  int along_grid;      // persistent grid of the per-kind along-step kernels
+  int post_grid;       // persistent grid of the per-process interaction kernels
   int loop_grid;       // co-resident grid of the persistent loop kernel
-  int block;           // threads per block of the along-step / interaction kernels
+  int block;           // threads per block of the step / along-step / interaction kernels
   size_t static_smem;  // tables + layer planes + layer materials in shared memory
 };
 
-// Along-step kernel variants and interaction selectors (Action values; A_NONE = all).
-enum AlongLaunch : int { ALONG_LAUNCH_NEUTRAL = 0, ALONG_LAUNCH_CHARGED = 1, ALONG_LAUNCH_ALL = 2 };
-
 cudaError_t configure_kernels(const Params& p, int block, LaunchShape* shape);
 
-void launch_init_count(const Params& p, const LaunchShape& sh, cudaStream_t s);
-void launch_init_fill(const Params& p, const LaunchShape& sh, cudaStream_t s);
-void launch_pre_step(const Params& p, const LaunchShape& sh, cudaStream_t s);
-void launch_iter_ctl(const Params& p, cudaStream_t s);
+// phase-merged launches
+void launch_fill_step(const Params& p, const LaunchShape& sh, cudaStream_t s);
 void launch_scatter(const Params& p, const LaunchShape& sh, cudaStream_t s);
-void launch_along(const Params& p, int kind, const LaunchShape& sh, cudaStream_t s);
+void launch_step(const Params& p, const LaunchShape& sh, unsigned long long handle, int use_handle, cudaStream_t s);
+// per-action launches
+void launch_fill(const Params& p, const LaunchShape& sh, cudaStream_t s);
+void launch_pre_step(const Params& p, const LaunchShape& sh, cudaStream_t s);
+void launch_along(const Params& p, int charged, const LaunchShape& sh, cudaStream_t s);
 void launch_post(const Params& p, int which, const LaunchShape& sh, cudaStream_t s);
 void launch_loop_ctl(const Params& p, unsigned long long handle, int use_handle, cudaStream_t s);
+// persistent loop
 cudaError_t launch_loop(const Params& p, const LaunchShape& sh, cudaStream_t s);
 void launch_push_primaries(const Params& p, const StagedPrimary* d_prim, uint32_t n, cudaStream_t s);
 
@@ -50,10 +51,8 @@ void launch_push_device_primaries(const Params& p, const DevicePrimary* src, uin
 
 const char* kernel_name(int id);
 enum KernelId : int {
-  KID_INIT_COUNT = 0, KID_INIT_FILL, KID_PRE_STEP, KID_ITER_CTL, KID_SCATTER,
-  KID_ALONG, KID_ALONG_NEUTRAL, KID_ALONG_CHARGED,
-  KID_POST, KID_POST_COMPTON, KID_POST_PE, KID_POST_PAIR, KID_POST_MOLLER, KID_POST_BREMS,
-  KID_LOOP_CTL, KID_LOOP, KID_COUNT
+  KID_FILL_STEP = 0, KID_SCATTER, KID_STEP, KID_FILL, KID_PRE_STEP, KID_ALONG_NEUTRAL, KID_ALONG_CHARGED,
+  KID_POST_COMPTON, KID_POST_PE, KID_POST_PAIR, KID_POST_MOLLER, KID_POST_BREMS, KID_LOOP_CTL, KID_LOOP, KID_COUNT
 };
 
 }  // namespace celer

@@ -45,6 +45,7 @@ __device__ __forceinline__ void release(const Params& p, uint32_t slot, uint32_t
   p.trk.status[slot] = VACANT;
   p.trk.action[slot] = A_NONE;
   atomicSub(&p.event_live[row_of(p, ev)], 1u);
+  atomicAdd(&p.vacant[slot / kTile], 1u);
 }
 
 // Warp-sum a per-thread counter and add it to a device counter (negated if
@@ -212,7 +213,15 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
 // Each phase is executed by every thread of a block; bid / nb are the block's
 // index and the number of blocks sharing the phase. The same functions run as
 // stand-alone kernels (host loop or CUDA graph) and inside the persistent
-// loop kernel.
+// loop kernel. One iteration is three phases:
+//   A  fill vacant slots from the initializer buffer and compute the step
+//      limit (next action) of every live track, tile by tile; the last block
+//      to finish does the bookkeeping (buffer head, vacancy counts, partition
+//      offsets, whether secondaries are sure to fit);
+//   B  scatter slot indices into the partition (sorted policies only);
+//   C  along-step and, for tracks whose step ends in an interaction, the
+//      interaction, in partition order; the last block to finish ends the
+//      iteration (counters, trace, loop condition).
 
 // Static data every step kernel needs in shared memory: cross-section and
 // range tables, layer planes and layer materials.
@@ -261,148 +270,152 @@ __device__ __forceinline__ void clear_iteration_counters(Ctl* c) {
   c->n_deferred = 0;
 }
 
-// Initializer, pass 1: vacant slots per tile.
-__device__ void phase_init_count(const Params& p, int bid, int nb) {
-  __shared__ unsigned s_red[32];
-  const Ctl* c = p.ctl;
-  if (c->tail == c->head) return;
-  for (uint32_t tile = bid; tile < p.n_tiles; tile += nb) {
-    const uint32_t slot = tile * kTile + threadIdx.x;
-    const unsigned v = (slot < p.n_slots && p.trk.status[slot] == VACANT) ? 1u : 0u;
-    const unsigned tot = block_sum(v, s_red);
-    if (threadIdx.x == 0) p.init_counts[tile] = tot;
+// True in exactly one block: the last one to reach this point in the current
+// phase (the counter is reset for the next phase instance). The block that
+// returns true sees every other block's writes of the phase.
+__device__ __forceinline__ bool last_block_done(unsigned* counter, unsigned nb) {
+  __shared__ unsigned s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned ticket = atomicAdd(counter, 1u);
+    s_last = (ticket == nb - 1) ? 1u : 0u;
+    if (s_last) *reinterpret_cast<volatile unsigned*>(counter) = 0u;
+  }
+  __syncthreads();
+  const bool last = s_last != 0u;
+  if (last) __threadfence();
+  return last;
+}
+
+// Fill the vacant slots of one tile: the r-th vacant slot in ascending slot
+// order over the whole store takes initializer head + r, for r < queued
+// (deterministic filling). 'before' = vacant slots in earlier tiles.
+__device__ __forceinline__ void fill_tile(const Params& p, uint32_t tile, unsigned long long before,
+                                          unsigned long long head, unsigned long long queued, unsigned* s_w) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t slot = tile * kTile + threadIdx.x;
+  const bool vac = slot < p.n_slots && p.trk.status[slot] == VACANT;
+  const unsigned bal = __ballot_sync(0xffffffffu, vac);
+  __syncthreads();
+  if (lane == 0) s_w[warp] = __popc(bal);
+  __syncthreads();
+  unsigned wpre = 0, tot = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    if (w < warp) wpre += s_w[w];
+    tot += s_w[w];
+  }
+  const unsigned long long r = before + wpre + __popc(bal & ((1u << lane) - 1u));
+  if (vac && r < queued) {
+    const unsigned long long i = (head + r) & p.ring_mask;
+    const Tracks& t = p.trk;
+    t.x[slot] = p.ring.x[i];
+    t.y[slot] = p.ring.y[i];
+    t.z[slot] = p.ring.z[i];
+    t.ux[slot] = p.ring.ux[i];
+    t.uy[slot] = p.ring.uy[i];
+    t.uz[slot] = p.ring.uz[i];
+    t.E[slot] = p.ring.E[i];
+    t.tid[slot] = p.ring.tid[i];
+    t.event[slot] = p.ring.event[i];
+    t.primary[slot] = p.ring.primary[i];
+    t.layer[slot] = p.ring.layer[i];
+    t.ptype[slot] = p.ring.ptype[i];
+    t.ctr[slot] = 0u;
+    t.nmfp[slot] = -1.0;
+    t.action[slot] = A_NONE;
+    t.status[slot] = ALIVE;
+  }
+  if (threadIdx.x == 0) {
+    const unsigned long long left = queued > before ? queued - before : 0ull;
+    p.filled[tile] = (unsigned)(tot < left ? tot : left);
   }
 }
 
-// Initializer, pass 2: the r-th vacant slot in ascending slot order takes
-// initializer head + r, for r < min(vacant, queued) (deterministic filling).
-// Tile prefixes are accumulated incrementally over this block's tiles.
-__device__ void phase_init_fill(const Params& p, int bid, int nb) {
-  __shared__ unsigned s_red[32];
-  __shared__ unsigned s_w[32];
+// Step limit of every live slot of one tile, with counts per next action and
+// (sorted policies) per partition key of the tile.
+__device__ __forceinline__ void step_limit_tile(const Params& p, uint32_t tile, const SharedStatic& ss,
+                                                unsigned* s_keys, unsigned* s_acts, unsigned long long& my_steps) {
+  const bool sorted = p.policy != POLICY_NONE;
+  const uint8_t vacant_key = p.policy == POLICY_ACTION ? KA_VACANT : K_VACANT_FULL;
+  if (threadIdx.x < kMaxKeys) s_keys[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t slot = tile * kTile + threadIdx.x;
+  uint8_t key = vacant_key;
+  if (slot < p.n_slots) {
+    const uint8_t st = p.trk.status[slot];
+    uint8_t act = A_NONE;
+    if (st == ALIVE) {
+      act = step_limit(p, slot, ss.tab, ss.zb, ss.lmat);
+      ++my_steps;
+    } else if (st == DEFERRED) {
+      act = p.trk.action[slot];
+    }
+    if (st != VACANT) {
+      atomicAdd(&s_acts[act], 1u);
+      if (sorted) key = key_of(p.policy, p.trk.ptype[slot], act);
+    }
+    if (sorted) p.trk.key[slot] = key;
+  }
+  if (sorted) {
+    const unsigned peers = __match_any_sync(0xffffffffu, (unsigned)key);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&s_keys[key], (unsigned)__popc(peers));
+    __syncthreads();
+    if ((int)threadIdx.x < p.n_keys) p.tile_counts[threadIdx.x * p.n_tiles + tile] = s_keys[threadIdx.x];
+  }
+  __syncthreads();
+}
+
+// Bookkeeping at the end of phase A, by one block: commit the initializers
+// taken, move the fill counts into the vacancy counts, scan the per-(key,
+// tile) counts in key-major order into output positions and key offsets,
+// and decide whether this iteration's secondaries are sure to fit.
+__device__ void bookkeeping_after_fill_step(const Params& p, bool did_fill) {
+  __shared__ unsigned s_warp[32];
+  __shared__ unsigned s_total;
+  __shared__ unsigned long long s_sum[32];
   Ctl* c = p.ctl;
-  const unsigned long long head = c->head;
-  const unsigned long long queued = c->tail - head;
-  if (queued == 0) return;
-  if (bid == 0) {
-    unsigned long long total = 0;
-    for (uint32_t i = threadIdx.x; i < p.n_tiles; i += blockDim.x) total += p.init_counts[i];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (int)(blockDim.x >> 5);
+  if (did_fill) {
+    unsigned long long vac = 0, fil = 0;
+    for (uint32_t t = threadIdx.x; t < p.n_tiles; t += blockDim.x) {
+      const unsigned v = __ldcg(&p.vacant[t]);
+      const unsigned f = __ldcg(&p.filled[t]);
+      vac += v;
+      fil += f;
+      p.vacant[t] = v - f;
+      p.filled[t] = 0u;
+    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) total += __shfl_down_sync(0xffffffffu, total, o);
-    __shared__ unsigned long long s_tot[32];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) s_tot[warp] = total;
+    for (int o = 16; o > 0; o >>= 1) {
+      vac += __shfl_down_sync(0xffffffffu, vac, o);
+      fil += __shfl_down_sync(0xffffffffu, fil, o);
+    }
+    __syncthreads();
+    if (lane == 0) s_sum[warp] = (vac << 32) | fil;
     __syncthreads();
     if (threadIdx.x == 0) {
-      unsigned long long tt = 0;
-      for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) tt += s_tot[w];
-      const unsigned long long take = tt < queued ? tt : queued;
-      c->head_pending = head + take;
+      unsigned long long tv = 0, tf = 0;
+      for (int w = 0; w < nw; ++w) {
+        tv += s_sum[w] >> 32;
+        tf += s_sum[w] & 0xFFFFFFFFull;
+      }
+      const unsigned long long queued = c->tail - c->head;
+      const unsigned long long take = tv < queued ? tv : queued;
+      if (take != tf) c->error |= ERR_VACANCY;
+      c->head += take;
       c->alive += take;
     }
     __syncthreads();
   }
-  unsigned long long before = 0;
-  uint32_t prev_tile = 0;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  for (uint32_t tile = bid; tile < p.n_tiles; tile += nb) {
-    unsigned part = 0;
-    for (uint32_t i = prev_tile + threadIdx.x; i < tile; i += blockDim.x) part += p.init_counts[i];
-    before += block_sum(part, s_red);
-    prev_tile = tile;
-    if (before >= queued) break;
-    const uint32_t slot = tile * kTile + threadIdx.x;
-    const bool vac = slot < p.n_slots && p.trk.status[slot] == VACANT;
-    const unsigned bal = __ballot_sync(0xffffffffu, vac);
-    __syncthreads();
-    if (lane == 0) s_w[warp] = __popc(bal);
-    __syncthreads();
-    unsigned wpre = 0;
-    for (int w = 0; w < warp; ++w) wpre += s_w[w];
-    const unsigned long long r = before + wpre + __popc(bal & lt);
-    if (vac && r < queued) {
-      const unsigned long long i = (head + r) & p.ring_mask;
-      const Tracks& t = p.trk;
-      t.x[slot] = p.ring.x[i];
-      t.y[slot] = p.ring.y[i];
-      t.z[slot] = p.ring.z[i];
-      t.ux[slot] = p.ring.ux[i];
-      t.uy[slot] = p.ring.uy[i];
-      t.uz[slot] = p.ring.uz[i];
-      t.E[slot] = p.ring.E[i];
-      t.tid[slot] = p.ring.tid[i];
-      t.event[slot] = p.ring.event[i];
-      t.primary[slot] = p.ring.primary[i];
-      t.layer[slot] = p.ring.layer[i];
-      t.ptype[slot] = p.ring.ptype[i];
-      t.ctr[slot] = 0u;
-      t.nmfp[slot] = -1.0;
-      t.action[slot] = A_NONE;
-      t.status[slot] = ALIVE;
-    }
-  }
-}
-
-// Step limit over all slots, one tile per block iteration; counts tracks per
-// next action and, for the sorted policies, per partition key and tile.
-__device__ void phase_pre_step(const Params& p, int bid, int nb, const SharedStatic& ss) {
-  __shared__ unsigned s_keys[kMaxKeys];
-  __shared__ unsigned s_acts[A_COUNT];
-  if (threadIdx.x < A_COUNT) s_acts[threadIdx.x] = 0;
-  if (bid == 0 && threadIdx.x == 0) p.ctl->head = p.ctl->head_pending;
-  __syncthreads();
-  const bool sorted = p.policy != POLICY_NONE;
-  const uint8_t vacant_key = p.policy == POLICY_ACTION ? KA_VACANT : K_VACANT_FULL;
-  unsigned long long my_steps = 0;
-  for (uint32_t tile = bid; tile < p.n_tiles; tile += nb) {
-    if (threadIdx.x < kMaxKeys) s_keys[threadIdx.x] = 0;
-    __syncthreads();
-    const uint32_t slot = tile * kTile + threadIdx.x;
-    uint8_t key = vacant_key;
-    if (slot < p.n_slots) {
-      const uint8_t st = p.trk.status[slot];
-      uint8_t act = A_NONE;
-      if (st == ALIVE) {
-        act = step_limit(p, slot, ss.tab, ss.zb, ss.lmat);
-        ++my_steps;
-      } else if (st == DEFERRED) {
-        act = p.trk.action[slot];
-      }
-      if (st != VACANT) {
-        atomicAdd(&s_acts[act], 1u);
-        if (sorted) key = key_of(p.policy, p.trk.ptype[slot], act);
-      }
-      if (sorted) p.trk.key[slot] = key;
-    }
-    if (sorted) {
-      const unsigned peers = __match_any_sync(0xffffffffu, (unsigned)key);
-      if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&s_keys[key], (unsigned)__popc(peers));
-      __syncthreads();
-      if ((int)threadIdx.x < p.n_keys) p.tile_counts[threadIdx.x * p.n_tiles + tile] = s_keys[threadIdx.x];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x < A_COUNT && s_acts[threadIdx.x] != 0) atomicAdd(&p.ctl->action_count[threadIdx.x], s_acts[threadIdx.x]);
-  flush_counter(&p.ctl->steps_iter, my_steps, false);
-}
-
-// Exclusive scan of the per-(key, tile) counts in key-major order, which
-// yields each tile's output position per key and the key offsets; then the
-// decision whether this iteration's secondaries are sure to fit in the
-// buffer. Run by one block.
-__device__ void phase_iter_ctl(const Params& p) {
-  Ctl* c = p.ctl;
   if (p.policy != POLICY_NONE) {
-    __shared__ unsigned s_warp[32];
-    __shared__ unsigned s_total;
     const uint32_t total = (uint32_t)p.n_keys * p.n_tiles;
     const uint32_t per = (total + blockDim.x - 1) / blockDim.x;
     const uint32_t beg = min(threadIdx.x * per, total);
     const uint32_t end = min(beg + per, total);
     unsigned local = 0;
-    for (uint32_t i = beg; i < end; ++i) local += p.tile_counts[i];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t i = beg; i < end; ++i) local += __ldcg(&p.tile_counts[i]);
     unsigned incl = local;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -412,7 +425,7 @@ __device__ void phase_iter_ctl(const Params& p) {
     if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-      const unsigned w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0u;
+      const unsigned w = lane < nw ? s_warp[lane] : 0u;
       unsigned wi = w;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -425,7 +438,7 @@ __device__ void phase_iter_ctl(const Params& p) {
     __syncthreads();
     unsigned run = s_warp[warp] + incl - local;
     for (uint32_t i = beg; i < end; ++i) {
-      const unsigned v = p.tile_counts[i];
+      const unsigned v = __ldcg(&p.tile_counts[i]);
       p.tile_counts[i] = run;
       run += v;
     }
@@ -440,6 +453,39 @@ __device__ void phase_iter_ctl(const Params& p) {
         2ull * c->action_count[A_PAIR] + c->action_count[A_MOLLER] + c->action_count[A_BREMS];
     c->defer = (queued + max_new > p.ring_capacity) ? 1u : 0u;
   }
+}
+
+// Phase A (or its two halves in the per-action launch mode).
+__device__ void phase_fill_step(const Params& p, int bid, int nb, const SharedStatic& ss, bool do_fill, bool do_step,
+                                bool bookkeeping) {
+  __shared__ unsigned s_red[32];
+  __shared__ unsigned s_w[32];
+  __shared__ unsigned s_keys[kMaxKeys];
+  __shared__ unsigned s_acts[A_COUNT];
+  Ctl* c = p.ctl;
+  const unsigned long long head = c->head;
+  const unsigned long long queued = c->tail - head;
+  const bool fill = do_fill && queued > 0;
+  if (threadIdx.x < A_COUNT) s_acts[threadIdx.x] = 0;
+  __syncthreads();
+  unsigned long long before = 0, my_steps = 0;
+  uint32_t prev_tile = 0;
+  for (uint32_t tile = bid; tile < p.n_tiles; tile += nb) {
+    if (fill) {
+      unsigned part = 0;
+      for (uint32_t i = prev_tile + threadIdx.x; i < tile; i += blockDim.x) part += __ldcg(&p.vacant[i]);
+      before += block_sum(part, s_red);
+      prev_tile = tile;
+      if (before < queued) fill_tile(p, tile, before, head, queued, s_w);
+    }
+    if (do_step) step_limit_tile(p, tile, ss, s_keys, s_acts, my_steps);
+  }
+  if (do_step) {
+    if (threadIdx.x < A_COUNT && s_acts[threadIdx.x] != 0)
+      atomicAdd(&c->action_count[threadIdx.x], s_acts[threadIdx.x]);
+    flush_counter(&c->steps_iter, my_steps, false);
+  }
+  if (bookkeeping && last_block_done(&c->done_a, nb)) bookkeeping_after_fill_step(p, true);
 }
 
 // Stable scatter of slot indices into the partition: position = tile's
@@ -539,28 +585,6 @@ __device__ __forceinline__ bool along_one(const Params& p, uint32_t slot, uint8_
   if (eloss) t.E[slot] = E;
   if (act == A_ZUP || act == A_ZDOWN) t.layer[slot] = layer;
   return false;
-}
-
-__device__ void phase_along(const Params& p, int kind, int bid, int nb, const SharedStatic& ss) {
-  Span sp;
-  if (p.policy == POLICY_NONE) {
-    sp = Span{0u, p.n_slots, nullptr};
-  } else if (p.policy == POLICY_ACTION) {
-    const int lo = kind == ALONG_LAUNCH_CHARGED ? KA_CHARGED : KA_NEUTRAL;
-    const int hi = kind == ALONG_LAUNCH_NEUTRAL ? KA_CHARGED : KA_VACANT;
-    sp = Span{p.ctl->offsets[lo], p.ctl->offsets[hi], p.perm};
-  } else {
-    sp = Span{p.ctl->offsets[K_G_GEOM], p.ctl->offsets[K_VACANT_FULL], p.perm};
-  }
-  unsigned long long killed = 0;
-  for (uint32_t i = sp.lo + bid * blockDim.x + threadIdx.x; i < sp.hi; i += nb * blockDim.x) {
-    const uint32_t slot = sp.perm ? sp.perm[i] : i;
-    if (p.trk.status[slot] != ALIVE) continue;
-    const uint8_t pt = p.trk.ptype[slot];
-    if ((kind == ALONG_LAUNCH_NEUTRAL && pt != GAMMA) || (kind == ALONG_LAUNCH_CHARGED && pt == GAMMA)) continue;
-    if (along_one(p, slot, pt, ss)) ++killed;
-  }
-  flush_counter(&p.ctl->alive, killed, true);
 }
 
 // ---- discrete interactions (one track each; return true if the track ended)
@@ -811,55 +835,28 @@ __device__ __forceinline__ bool brems_one(const Params& p, uint32_t slot, uint8_
   return false;
 }
 
-// Interaction phase. which = A_COMPTON ... A_BREMS runs one process (one
-// kernel per action); which = A_NONE runs every interaction over the union of
-// the interaction ranges, each thread dispatching on its track's action.
-__device__ void phase_post(const Params& p, int which, int bid, int nb) {
-  Span sp;
-  if (p.policy == POLICY_NONE) {
-    sp = Span{0u, p.n_slots, nullptr};
-  } else if (p.policy == POLICY_ACTION) {
-    const bool neutral_only = which == A_COMPTON || which == A_PE || which == A_PAIR;
-    const bool charged_only = which == A_MOLLER || which == A_BREMS;
-    const int lo = charged_only ? KA_CHARGED : KA_NEUTRAL;
-    const int hi = neutral_only ? KA_CHARGED : KA_VACANT;
-    sp = Span{p.ctl->offsets[lo], p.ctl->offsets[hi], p.perm};
-  } else {
-    int lo = kFirstInteractionKey, hi = K_VACANT_FULL;
-    switch (which) {
-      case A_COMPTON: lo = K_G_COMPTON; break;
-      case A_PE: lo = K_G_PE; break;
-      case A_PAIR: lo = K_G_PAIR; break;
-      case A_MOLLER: lo = K_E_MOLLER; break;
-      case A_BREMS: lo = K_E_BREMS; break;
-      default: break;
-    }
-    if (which != A_NONE) hi = lo + 1;
-    sp = Span{p.ctl->offsets[lo], p.ctl->offsets[hi], p.perm};
+// Interaction of one track whose step ended in one (or whose interaction is
+// waiting for buffer space). Returns true if the track ended.
+__device__ __forceinline__ bool post_one(const Params& p, uint32_t slot, uint8_t st, uint8_t act, bool tight,
+                                         unsigned long long& n_def) {
+  switch (act) {
+    case A_COMPTON: return compton_one(p, slot);
+    case A_PE: return photoelectric_one(p, slot);
+    case A_PAIR: return pair_one(p, slot, st, tight, n_def);
+    case A_MOLLER: return moller_one(p, slot, st, tight, n_def);
+    case A_BREMS: return brems_one(p, slot, st, tight, n_def);
+    default: return false;
   }
-  const bool tight = p.ctl->defer != 0u;
-  unsigned long long killed = 0, n_def = 0;
-  for (uint32_t i = sp.lo + bid * blockDim.x + threadIdx.x; i < sp.hi; i += nb * blockDim.x) {
-    const uint32_t slot = sp.perm ? sp.perm[i] : i;
-    const uint8_t st = p.trk.status[slot];
-    if (st == VACANT) continue;
-    const uint8_t act = p.trk.action[slot];
-    if (act < A_COMPTON || act > A_BREMS || (which != A_NONE && act != which)) continue;
-    // only deferrable interactions may run on a track already waiting
-    if (st == DEFERRED && !(act == A_PAIR || act == A_MOLLER || act == A_BREMS)) continue;
-    bool ended = false;
-    switch (act) {
-      case A_COMPTON: ended = compton_one(p, slot); break;
-      case A_PE: ended = photoelectric_one(p, slot); break;
-      case A_PAIR: ended = pair_one(p, slot, st, tight, n_def); break;
-      case A_MOLLER: ended = moller_one(p, slot, st, tight, n_def); break;
-      case A_BREMS: ended = brems_one(p, slot, st, tight, n_def); break;
-      default: break;
-    }
-    if (ended) ++killed;
-  }
-  flush_counter(&p.ctl->alive, killed, true);
-  if (n_def) atomicAdd(&p.ctl->n_deferred, (unsigned)n_def);
+}
+
+__device__ __forceinline__ bool is_interaction(uint8_t act) { return act >= A_COMPTON && act <= A_BREMS; }
+
+// Work range of the step phase for the policy: all slots (masking), or the
+// partition range of the live keys.
+__device__ __forceinline__ Span live_span(const Params& p) {
+  if (p.policy == POLICY_NONE) return Span{0u, p.n_slots, nullptr};
+  const int hi = p.policy == POLICY_ACTION ? KA_VACANT : K_VACANT_FULL;
+  return Span{p.ctl->offsets[0], p.ctl->offsets[hi], p.perm};
 }
 
 // End of an iteration: counters, the per-iteration trace row, stall and
@@ -868,6 +865,9 @@ __device__ void loop_ctl_one(const Params& p) {
   Ctl* c = p.ctl;
   const unsigned long long queued = c->tail - c->head;
   const bool worked = c->steps_iter > 0 || c->n_deferred > 0;
+  c->last_steps_iter = c->steps_iter;
+  c->last_n_deferred = c->n_deferred;
+  for (int k = 0; k < kMaxKeys; ++k) c->last_action_count[k] = c->action_count[k];
   if (worked) {
     c->steps_total += c->steps_iter;
     TraceRow& r = p.trace[c->trace_count % kTraceRows];
@@ -893,36 +893,132 @@ __device__ void loop_ctl_one(const Params& p) {
   c->cont = (pending && c->error == 0u) ? 1u : 0u;
 }
 
-// ------------------------------------------------------------------ kernels
-__global__ void __launch_bounds__(kTile) k_init_count(Params p) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) clear_iteration_counters(p.ctl);
-  phase_init_count(p, blockIdx.x, gridDim.x);
+// Phase C: along-step of every live track and, where the step ends in an
+// interaction, that interaction, in partition order; deferred interactions
+// are retried. The last block ends the iteration.
+__device__ void phase_step(const Params& p, int bid, int nb, const SharedStatic& ss, bool bookkeeping,
+                           cudaGraphConditionalHandle handle, int use_handle) {
+  const Span sp = live_span(p);
+  const bool tight = p.ctl->defer != 0u;
+  const Tracks& t = p.trk;
+  unsigned long long killed = 0, n_def = 0;
+  for (uint32_t i = sp.lo + bid * blockDim.x + threadIdx.x; i < sp.hi; i += nb * blockDim.x) {
+    const uint32_t slot = sp.perm ? sp.perm[i] : i;
+    const uint8_t st = t.status[slot];
+    if (st == VACANT) continue;
+    const uint8_t act = t.action[slot];
+    if (st == ALIVE) {
+      if (along_one(p, slot, t.ptype[slot], ss)) {
+        ++killed;
+        continue;
+      }
+    }
+    if (is_interaction(act) && post_one(p, slot, st, act, tight, n_def)) ++killed;
+  }
+  flush_counter(&p.ctl->alive, killed, true);
+  if (n_def) atomicAdd(&p.ctl->n_deferred, (unsigned)n_def);
+  if (bookkeeping && last_block_done(&p.ctl->done_c, nb) && threadIdx.x == 0) {
+    loop_ctl_one(p);
+    clear_iteration_counters(p.ctl);
+    if (use_handle) cudaGraphSetConditional(handle, p.ctl->cont);
+  }
 }
 
-__global__ void __launch_bounds__(kTile) k_init_fill(Params p) { phase_init_fill(p, blockIdx.x, gridDim.x); }
+// Along-step only, for one particle kind (per-action launch mode).
+__device__ void phase_along_only(const Params& p, bool charged, int bid, int nb, const SharedStatic& ss) {
+  Span sp = live_span(p);
+  if (p.policy == POLICY_ACTION) {
+    sp.lo = p.ctl->offsets[charged ? KA_CHARGED : KA_NEUTRAL];
+    sp.hi = p.ctl->offsets[charged ? KA_VACANT : KA_CHARGED];
+  }
+  unsigned long long killed = 0;
+  for (uint32_t i = sp.lo + bid * blockDim.x + threadIdx.x; i < sp.hi; i += nb * blockDim.x) {
+    const uint32_t slot = sp.perm ? sp.perm[i] : i;
+    if (p.trk.status[slot] != ALIVE) continue;
+    const uint8_t pt = p.trk.ptype[slot];
+    if ((pt != GAMMA) != charged) continue;
+    if (along_one(p, slot, pt, ss)) ++killed;
+  }
+  flush_counter(&p.ctl->alive, killed, true);
+}
+
+// One interaction process only (per-action launch mode).
+__device__ void phase_post_only(const Params& p, uint8_t which, int bid, int nb) {
+  Span sp = live_span(p);
+  if (p.policy == POLICY_ACTION) {
+    const bool charged = which == A_MOLLER || which == A_BREMS;
+    sp.lo = p.ctl->offsets[charged ? KA_CHARGED : KA_NEUTRAL];
+    sp.hi = p.ctl->offsets[charged ? KA_VACANT : KA_CHARGED];
+  } else if (p.policy == POLICY_ACTION_TYPE) {
+    int k = K_G_COMPTON;
+    switch (which) {
+      case A_PE: k = K_G_PE; break;
+      case A_PAIR: k = K_G_PAIR; break;
+      case A_MOLLER: k = K_E_MOLLER; break;
+      case A_BREMS: k = K_E_BREMS; break;
+      default: break;
+    }
+    sp.lo = p.ctl->offsets[k];
+    sp.hi = p.ctl->offsets[k + 1];
+  }
+  const bool tight = p.ctl->defer != 0u;
+  unsigned long long killed = 0, n_def = 0;
+  for (uint32_t i = sp.lo + bid * blockDim.x + threadIdx.x; i < sp.hi; i += nb * blockDim.x) {
+    const uint32_t slot = sp.perm ? sp.perm[i] : i;
+    const uint8_t st = p.trk.status[slot];
+    if (st == VACANT || p.trk.action[slot] != which) continue;
+    if (post_one(p, slot, st, which, tight, n_def)) ++killed;
+  }
+  flush_counter(&p.ctl->alive, killed, true);
+  if (n_def) atomicAdd(&p.ctl->n_deferred, (unsigned)n_def);
+}
+
+// ------------------------------------------------------------------ kernels
+// Phase-merged launches (host loop / graph): A, B, C.
+__global__ void __launch_bounds__(kTile) k_fill_step(Params p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SharedStatic ss = carve_static(p, smem_raw);
+  stage_static(p, ss);
+  phase_fill_step(p, blockIdx.x, gridDim.x, ss, true, true, true);
+}
+
+__global__ void __launch_bounds__(kTile) k_scatter(Params p) { phase_scatter(p, blockIdx.x, gridDim.x); }
+
+__global__ void k_step(Params p, cudaGraphConditionalHandle handle, int use_handle) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SharedStatic ss = carve_static(p, smem_raw);
+  stage_static(p, ss);
+  phase_step(p, blockIdx.x, gridDim.x, ss, true, handle, use_handle);
+}
+
+// Per-action launches: fill, step limit (+ bookkeeping), scatter, one
+// along-step kernel per particle kind, one kernel per interaction, end.
+__global__ void __launch_bounds__(kTile) k_fill(Params p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SharedStatic ss = carve_static(p, smem_raw);
+  phase_fill_step(p, blockIdx.x, gridDim.x, ss, true, false, false);
+}
 
 __global__ void __launch_bounds__(kTile) k_pre_step(Params p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SharedStatic ss = carve_static(p, smem_raw);
   stage_static(p, ss);
-  phase_pre_step(p, blockIdx.x, gridDim.x, ss);
+  phase_fill_step(p, blockIdx.x, gridDim.x, ss, false, true, false);
+  if (last_block_done(&p.ctl->done_a, gridDim.x)) bookkeeping_after_fill_step(p, true);
 }
 
-__global__ void __launch_bounds__(1024) k_iter_ctl(Params p) { phase_iter_ctl(p); }
-
-__global__ void __launch_bounds__(kTile) k_scatter(Params p) { phase_scatter(p, blockIdx.x, gridDim.x); }
-
-__global__ void k_along(Params p, int kind) {
+__global__ void k_along(Params p, int charged) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SharedStatic ss = carve_static(p, smem_raw);
   stage_static(p, ss);
-  phase_along(p, kind, blockIdx.x, gridDim.x, ss);
+  phase_along_only(p, charged != 0, blockIdx.x, gridDim.x, ss);
 }
 
-__global__ void k_post(Params p, int which) { phase_post(p, which, blockIdx.x, gridDim.x); }
+__global__ void k_post(Params p, int which) { phase_post_only(p, (uint8_t)which, blockIdx.x, gridDim.x); }
 
 __global__ void k_loop_ctl(Params p, cudaGraphConditionalHandle handle, int use_handle) {
   loop_ctl_one(p);
+  clear_iteration_counters(p.ctl);
   if (use_handle) cudaGraphSetConditional(handle, p.ctl->cont);
 }
 
@@ -969,9 +1065,8 @@ __device__ __forceinline__ bool grid_barrier(const Params& p, unsigned nblocks) 
 }
 
 // The whole step loop in one persistent cooperative launch: one block per
-// SM slot, the static tables staged into shared memory once, and the phases
-// of each iteration separated by grid barriers. The per-iteration control
-// (counters, loop condition) of iteration k runs at the start of k + 1.
+// SM slot, the static tables staged into shared memory once, three grid
+// barriers per iteration (two without sorting).
 __global__ void __launch_bounds__(kTile, 1) k_loop(Params p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SharedStatic ss = carve_static(p, smem_raw);
@@ -979,33 +1074,32 @@ __global__ void __launch_bounds__(kTile, 1) k_loop(Params p) {
   const unsigned nb = gridDim.x;
   const int bid = blockIdx.x;
   const bool sorted = p.policy != POLICY_NONE;
-  bool first = true;
-  for (;;) {
+  if (bid == 0 && threadIdx.x == 0) {
+    clear_iteration_counters(p.ctl);
+    p.ctl->cont = 1u;
+  }
+  if (!grid_barrier(p, nb)) return;
+  long long t_prev = clock64();
+  auto mark = [&](int k) {
     if (bid == 0 && threadIdx.x == 0) {
-      if (first)
-        p.ctl->cont = 1u;
-      else
-        loop_ctl_one(p);
-      clear_iteration_counters(p.ctl);
+      const long long now = clock64();
+      p.ctl->phase_cycles[k] += (unsigned long long)(now - t_prev);
+      t_prev = now;
     }
-    first = false;
-    phase_init_count(p, bid, nb);
+  };
+  for (;;) {
+    if (*reinterpret_cast<volatile unsigned*>(&p.ctl->cont) == 0u) break;
+    phase_fill_step(p, bid, nb, ss, true, true, true);
     if (!grid_barrier(p, nb)) break;
-    if (p.ctl->cont == 0u) break;
-    phase_init_fill(p, bid, nb);
-    if (!grid_barrier(p, nb)) break;
-    phase_pre_step(p, bid, nb, ss);
-    if (!grid_barrier(p, nb)) break;
-    if (bid == 0) phase_iter_ctl(p);
-    if (!grid_barrier(p, nb)) break;
+    mark(0);
     if (sorted) {
       phase_scatter(p, bid, nb);
       if (!grid_barrier(p, nb)) break;
+      mark(1);
     }
-    phase_along(p, ALONG_LAUNCH_ALL, bid, nb, ss);
+    phase_step(p, bid, nb, ss, true, 0, 0);
     if (!grid_barrier(p, nb)) break;
-    phase_post(p, A_NONE, bid, nb);
-    if (!grid_barrier(p, nb)) break;
+    mark(2);
   }
 }
 
@@ -1108,38 +1202,41 @@ cudaError_t configure_kernels(const Params& p, int block, LaunchShape* sh) {
                       (size_t)(p.n_layers + 1) * sizeof(double) + (size_t)p.n_layers * sizeof(int32_t);
   sh->static_smem = stat;
   sh->block = block;
-  e = cudaFuncSetAttribute(k_pre_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stat);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_along, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stat);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_loop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stat);
-  if (e != cudaSuccess) return e;
-  sh->tile_grid = occupancy_grid((const void*)k_pre_step, kTile, stat, sms, (int)p.n_tiles);
+  const void* with_smem[] = {(const void*)k_fill_step, (const void*)k_step, (const void*)k_fill,
+                             (const void*)k_pre_step, (const void*)k_along, (const void*)k_loop};
+  for (const void* fn : with_smem) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stat);
+    if (e != cudaSuccess) return e;
+  }
+  sh->tile_grid = occupancy_grid((const void*)k_fill_step, kTile, stat, sms, (int)p.n_tiles);
   const int cap_action = (int)((p.n_slots + block - 1) / block);
+  sh->step_grid = occupancy_grid((const void*)k_step, block, stat, sms, cap_action);
   sh->along_grid = occupancy_grid((const void*)k_along, block, stat, sms, cap_action);
   sh->post_grid = occupancy_grid((const void*)k_post, block, 0, sms, cap_action);
   int nb = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)k_loop, kTile, stat);
   if (e != cudaSuccess) return e;
-  sh->loop_grid = nb * sms;
+  sh->loop_grid = (nb < 1 ? 1 : nb) * sms;
   return cudaGetLastError();
 }
 
-void launch_init_count(const Params& p, const LaunchShape& sh, cudaStream_t s) {
-  k_init_count<<<sh.tile_grid, kTile, 0, s>>>(p);
+void launch_fill_step(const Params& p, const LaunchShape& sh, cudaStream_t s) {
+  k_fill_step<<<sh.tile_grid, kTile, sh.static_smem, s>>>(p);
 }
-void launch_init_fill(const Params& p, const LaunchShape& sh, cudaStream_t s) {
-  k_init_fill<<<sh.tile_grid, kTile, 0, s>>>(p);
+void launch_scatter(const Params& p, const LaunchShape& sh, cudaStream_t s) {
+  k_scatter<<<sh.tile_grid, kTile, 0, s>>>(p);
+}
+void launch_step(const Params& p, const LaunchShape& sh, unsigned long long handle, int use_handle, cudaStream_t s) {
+  k_step<<<sh.step_grid, sh.block, sh.static_smem, s>>>(p, (cudaGraphConditionalHandle)handle, use_handle);
+}
+void launch_fill(const Params& p, const LaunchShape& sh, cudaStream_t s) {
+  k_fill<<<sh.tile_grid, kTile, sh.static_smem, s>>>(p);
 }
 void launch_pre_step(const Params& p, const LaunchShape& sh, cudaStream_t s) {
   k_pre_step<<<sh.tile_grid, kTile, sh.static_smem, s>>>(p);
 }
-void launch_iter_ctl(const Params& p, cudaStream_t s) { k_iter_ctl<<<1, 1024, 0, s>>>(p); }
-void launch_scatter(const Params& p, const LaunchShape& sh, cudaStream_t s) {
-  k_scatter<<<sh.tile_grid, kTile, 0, s>>>(p);
-}
-void launch_along(const Params& p, int kind, const LaunchShape& sh, cudaStream_t s) {
-  k_along<<<sh.along_grid, sh.block, sh.static_smem, s>>>(p, kind);
+void launch_along(const Params& p, int charged, const LaunchShape& sh, cudaStream_t s) {
+  k_along<<<sh.along_grid, sh.block, sh.static_smem, s>>>(p, charged);
 }
 void launch_post(const Params& p, int which, const LaunchShape& sh, cudaStream_t s) {
   k_post<<<sh.post_grid, sh.block, 0, s>>>(p, which);
@@ -1160,9 +1257,9 @@ void launch_push_device_primaries(const Params& p, const DevicePrimary* src, uin
 }
 
 const char* kernel_name(int id) {
-  static const char* names[KID_COUNT] = {"init_count", "init_fill", "pre_step", "iter_ctl", "scatter",
-                                         "along", "along_neutral", "along_charged", "post", "compton",
-                                         "photoelectric", "pair", "moller", "brems", "loop_ctl", "loop"};
+  static const char* names[KID_COUNT] = {"fill_step", "scatter", "step", "fill", "pre_step", "along_neutral",
+                                         "along_charged", "compton", "photoelectric", "pair", "moller", "brems",
+                                         "loop_ctl", "loop"};
   return (id >= 0 && id < KID_COUNT) ? names[id] : "?";
 }
 
