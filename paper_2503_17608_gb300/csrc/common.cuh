@@ -86,7 +86,7 @@ struct Ring {
 // Device-resident loop control. Ring indices are monotonic counters; the
 // entry of index i lives at i & ring_mask.
 struct Ctl {
-  unsigned long long head, tail, head_pending;
+  unsigned long long head, tail;
   unsigned long long alive;          // slots holding a live or deferred track
   unsigned long long steps_total;
   unsigned long long steps_iter;

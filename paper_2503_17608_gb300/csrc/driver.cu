@@ -563,7 +563,7 @@ celer_status celer_add_primaries(celer_ctx* ctx, uint32_t event, const celer_pri
     return fail(ctx, CELER_ERR_CAPACITY, "history capacity exceeded");
   celer_status st = read_ctl(ctx);
   if (st != CELER_OK) return st;
-  const uint64_t queued = ctx->h_ctl->tail - ctx->h_ctl->head_pending;
+  const uint64_t queued = ctx->h_ctl->tail - ctx->h_ctl->head;
   if (queued + n > ctx->p.ring_capacity) return fail(ctx, CELER_ERR_CAPACITY, "initializer buffer full");
 
   uint64_t& tid = ctx->next_tid[event];

@@ -1130,7 +1130,7 @@ __global__ void __launch_bounds__(1024) k_push_device_primaries(Params p, const 
   if (threadIdx.x == 0) {
     s_bad = 0;
     s_base = p.ctl->tail;
-    const unsigned long long queued = p.ctl->tail - p.ctl->head_pending;
+    const unsigned long long queued = p.ctl->tail - p.ctl->head;
     if (queued + n > p.ring_capacity) s_bad = 1;
   }
   __syncthreads();

@@ -261,3 +261,40 @@ def test_full_buffer_reports_capacity_and_stays_usable():
         assert ei.value.status == 2
         s = ctx.stats()
         assert s["alive"] == 1 and s["queued"] == 1
+
+
+def test_repeated_device_jobs_on_one_context():
+    """Many jobs queued from device memory on one context, one after another:
+    the buffer is reused and every job conserves energy."""
+    import torch
+
+    prob, prim = wl.calorimeter_1gev(100)
+    prob = prob.replace(n_slots=4096, init_capacity=4096)
+    cprim = binding.to_c_primaries(prim)
+    dev = torch.from_numpy(cprim.view(np.uint8).copy()).cuda()
+    steps = []
+    with binding.Context(prob.replace(max_events=2)) as ctx:
+        for job in range(60):
+            ev = job
+            ctx.reset_event(ev)
+            ctx.add_primaries_device(ev, dev.data_ptr(), len(prim))
+            ctx.run_events(binding.LOOP_PERSISTENT if job % 2 else binding.LOOP_GRAPH)
+            tally, esc = ctx.read_tallies(ev)
+            assert tally.sum() + esc == pytest.approx(prim["E"].sum(), rel=1e-12)
+            steps.append(ctx.stats()["steps_total"])
+    assert all(b > a for a, b in zip(steps, steps[1:]))
+
+
+def test_device_primaries_match_host_primaries():
+    prob = wl.water_cube_problem(history_capacity=2000)
+    prim = wl.water_cube_primaries()
+    import torch
+
+    a = run_gpu(prob, prim)
+    with binding.Context(prob) as ctx:
+        dev = torch.from_numpy(binding.to_c_primaries(prim).view(np.uint8).copy()).cuda()
+        ctx.add_primaries_device(0, dev.data_ptr(), len(prim))
+        ctx.run_events(binding.LOOP_PERSISTENT)
+        hist, edep = ctx.read_history(0, len(prim))
+    np.testing.assert_array_equal(hist["steps"], a["hist"]["steps"])
+    np.testing.assert_allclose(edep, a["edep"], rtol=1e-12, atol=1e-12)
