@@ -341,7 +341,7 @@ def run_ours(args):
     if prof is not None:
         it = max(ctx.stats()["iteration"], 1)
         line["loop_profile_us_per_iteration"] = {
-            name: round(c / it / 2.07e3, 3) for name, c in zip(("fill_step", "scatter", "step"), prof)}
+            part: {name: round(c / it / 2.07e3, 3) for name, c in vals.items()} for part, vals in prof.items()}
     job_ms = statistics.median(h["job_ms"])
     line["roofline"] = roofline_loop(steps_per_job, job_ms)
     if launches_per_job:

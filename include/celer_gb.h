@@ -198,9 +198,12 @@ enum {
  * initializer buffer is full and no track can make progress. */
 celer_status celer_run_events(celer_ctx* ctx, int mode);
 
-/* SM cycles the persistent loop spent in each of its phases since creation,
- * as seen by its first block: [0] fill + step limit, [1] partition scatter,
- * [2] along-step + interactions, [3] unused. n entries are written. */
+/* Profile of the persistent loop since creation, in SM cycles, n <= 10
+ * entries: [0..3] time per phase as seen by the first block, barrier wait
+ * included ([0] fill + step limit, [1] partition scatter, [2] along-step +
+ * interactions, [3] unused); [4..7] sum over iterations of the slowest
+ * block's work per phase; [8], [9] last-block bookkeeping after phases 0
+ * and 2. */
 celer_status celer_read_loop_profile(celer_ctx* ctx, uint64_t* cycles_out, int n);
 
 /* Choose per-action launches (1) or per-phase launches (0) for the host and

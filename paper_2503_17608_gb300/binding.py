@@ -243,10 +243,15 @@ class Context:
         _check(load().celer_run_events(self._h, int(mode)), self._h)
 
     def loop_profile(self):
-        """SM cycles of the persistent loop per phase: fill+step limit, scatter, step."""
-        out = (C.c_uint64 * 4)()
-        _check(load().celer_read_loop_profile(self._h, out, 4), self._h)
-        return list(out)[:3]
+        """Persistent-loop profile in SM cycles: per phase (block 0 view, with
+        barrier waits), slowest block's work per phase, bookkeeping."""
+        out = (C.c_uint64 * 10)()
+        _check(load().celer_read_loop_profile(self._h, out, 10), self._h)
+        v = list(out)
+        names = ("fill_step", "scatter", "step")
+        return dict(phase={k: v[i] for i, k in enumerate(names)},
+                    slowest_work={k: v[4 + i] for i, k in enumerate(names)},
+                    bookkeeping={"fill_step": v[8], "step": v[9]})
 
     def set_split_actions(self, split: bool):
         _check(load().celer_set_split_actions(self._h, 1 if split else 0), self._h)

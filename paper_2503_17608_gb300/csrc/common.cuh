@@ -106,7 +106,13 @@ struct Ctl {
   unsigned long long last_steps_iter;          // copies of the last finished iteration's counters
   unsigned int last_n_deferred;
   unsigned int last_action_count[kMaxKeys];
-  unsigned long long phase_cycles[4];  // persistent loop: SM cycles spent per phase (block 0's view)
+  // persistent loop profile (SM cycles): per phase as seen by block 0 (work +
+  // barrier), sum over iterations of the slowest block's work, and the
+  // last-block bookkeeping of the fill/step-limit and step phases
+  unsigned long long phase_cycles[4];
+  unsigned long long iter_max[2][4];
+  unsigned long long max_total[4];
+  unsigned long long book_total[2];
 };
 
 struct TraceRow {
@@ -125,6 +131,7 @@ struct Params {
   unsigned long long ring_capacity;
   uint32_t* vacant;        // vacant slots per tile, n_tiles (kept current by every release)
   uint32_t* filled;        // slots filled per tile in the current iteration, n_tiles
+  uint8_t* tile_live;      // 1 if the tile holds a live or waiting track after the fill
   unsigned int* barrier;   // grid barrier state of the persistent loop: count, generation, abort
   // partition
   int policy;

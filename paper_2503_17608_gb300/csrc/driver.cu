@@ -466,6 +466,7 @@ celer_status celer_create(const celer_problem* pb, celer_ctx** out) {
   CREATE_CUDA(dalloc(ctx, &p.ctl, 1));
   CREATE_CUDA(dalloc(ctx, &p.vacant, p.n_tiles));
   CREATE_CUDA(dalloc(ctx, &p.filled, p.n_tiles));
+  CREATE_CUDA(dalloc(ctx, &p.tile_live, p.n_tiles));
   CREATE_CUDA(dalloc(ctx, &p.barrier, 4));
   {
     std::vector<uint32_t> vac(p.n_tiles);
@@ -756,7 +757,11 @@ celer_status celer_read_loop_profile(celer_ctx* ctx, uint64_t* cycles_out, int n
   if (!ctx || !cycles_out || n < 1) return CELER_ERR_INVALID;
   celer_status st = read_ctl(ctx);
   if (st != CELER_OK) return st;
-  for (int k = 0; k < n; ++k) cycles_out[k] = k < 4 ? ctx->h_ctl->phase_cycles[k] : 0;
+  const Ctl& c = *ctx->h_ctl;
+  const unsigned long long all[10] = {c.phase_cycles[0], c.phase_cycles[1], c.phase_cycles[2], c.phase_cycles[3],
+                                      c.max_total[0], c.max_total[1], c.max_total[2], c.max_total[3],
+                                      c.book_total[0], c.book_total[1]};
+  for (int k = 0; k < n; ++k) cycles_out[k] = k < 10 ? all[k] : 0;
   return CELER_OK;
 }
 

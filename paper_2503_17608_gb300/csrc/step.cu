@@ -291,8 +291,8 @@ __device__ __forceinline__ bool last_block_done(unsigned* counter, unsigned nb) 
 // Fill the vacant slots of one tile: the r-th vacant slot in ascending slot
 // order over the whole store takes initializer head + r, for r < queued
 // (deterministic filling). 'before' = vacant slots in earlier tiles.
-__device__ __forceinline__ void fill_tile(const Params& p, uint32_t tile, unsigned long long before,
-                                          unsigned long long head, unsigned long long queued, unsigned* s_w) {
+__device__ __forceinline__ unsigned fill_tile(const Params& p, uint32_t tile, unsigned long long before,
+                                              unsigned long long head, unsigned long long queued, unsigned* s_w) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t slot = tile * kTile + threadIdx.x;
   const bool vac = slot < p.n_slots && p.trk.status[slot] == VACANT;
@@ -326,10 +326,10 @@ __device__ __forceinline__ void fill_tile(const Params& p, uint32_t tile, unsign
     t.action[slot] = A_NONE;
     t.status[slot] = ALIVE;
   }
-  if (threadIdx.x == 0) {
-    const unsigned long long left = queued > before ? queued - before : 0ull;
-    p.filled[tile] = (unsigned)(tot < left ? tot : left);
-  }
+  const unsigned long long left = queued > before ? queued - before : 0ull;
+  const unsigned n = (unsigned)(tot < left ? tot : left);
+  if (threadIdx.x == 0) p.filled[tile] = n;
+  return n;
 }
 
 // Step limit of every live slot of one tile, with counts per next action and
@@ -470,22 +470,41 @@ __device__ void phase_fill_step(const Params& p, int bid, int nb, const SharedSt
   __syncthreads();
   unsigned long long before = 0, my_steps = 0;
   uint32_t prev_tile = 0;
+  const bool sorted = p.policy != POLICY_NONE;
+  const int vacant_key = p.policy == POLICY_ACTION ? KA_VACANT : K_VACANT_FULL;
   for (uint32_t tile = bid; tile < p.n_tiles; tile += nb) {
+    unsigned nfill = 0;
     if (fill) {
       unsigned part = 0;
       for (uint32_t i = prev_tile + threadIdx.x; i < tile; i += blockDim.x) part += __ldcg(&p.vacant[i]);
       before += block_sum(part, s_red);
       prev_tile = tile;
-      if (before < queued) fill_tile(p, tile, before, head, queued, s_w);
+      if (before < queued) nfill = fill_tile(p, tile, before, head, queued, s_w);
+    } else if (!do_fill) {
+      nfill = __ldcg(&p.filled[tile]);  // filled by the separate fill launch
     }
-    if (do_step) step_limit_tile(p, tile, ss, s_keys, s_acts, my_steps);
+    if (!do_step) continue;
+    // a tile with no live or waiting track and no new one needs no step limit
+    const uint32_t lo = tile * kTile;
+    const unsigned tsize = (p.n_slots - lo) < (uint32_t)kTile ? (p.n_slots - lo) : (unsigned)kTile;
+    const bool live = __ldcg(&p.vacant[tile]) < tsize || nfill > 0;
+    if (threadIdx.x == 0) p.tile_live[tile] = live ? 1 : 0;
+    if (live) {
+      step_limit_tile(p, tile, ss, s_keys, s_acts, my_steps);
+    } else if (sorted && (int)threadIdx.x < p.n_keys) {
+      p.tile_counts[threadIdx.x * p.n_tiles + tile] = ((int)threadIdx.x == vacant_key) ? (unsigned)kTile : 0u;
+    }
   }
   if (do_step) {
     if (threadIdx.x < A_COUNT && s_acts[threadIdx.x] != 0)
       atomicAdd(&c->action_count[threadIdx.x], s_acts[threadIdx.x]);
     flush_counter(&c->steps_iter, my_steps, false);
   }
-  if (bookkeeping && last_block_done(&c->done_a, nb)) bookkeeping_after_fill_step(p, true);
+  if (bookkeeping && last_block_done(&c->done_a, nb)) {
+    const long long t0 = clock64();
+    bookkeeping_after_fill_step(p, true);
+    if (threadIdx.x == 0) c->book_total[0] += (unsigned long long)(clock64() - t0);
+  }
 }
 
 // Stable scatter of slot indices into the partition: position = tile's
@@ -495,6 +514,7 @@ __device__ void phase_scatter(const Params& p, int bid, int nb) {
   const uint8_t vacant_key = p.policy == POLICY_ACTION ? KA_VACANT : K_VACANT_FULL;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint32_t tile = bid; tile < p.n_tiles; tile += nb) {
+    if (!p.tile_live[tile]) continue;  // every slot vacant: nothing to place
     if (threadIdx.x < (kTile / 32) * kMaxKeys) (&s_cnt[0][0])[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t slot = tile * kTile + threadIdx.x;
@@ -918,9 +938,11 @@ __device__ void phase_step(const Params& p, int bid, int nb, const SharedStatic&
   flush_counter(&p.ctl->alive, killed, true);
   if (n_def) atomicAdd(&p.ctl->n_deferred, (unsigned)n_def);
   if (bookkeeping && last_block_done(&p.ctl->done_c, nb) && threadIdx.x == 0) {
+    const long long t0 = clock64();
     loop_ctl_one(p);
     clear_iteration_counters(p.ctl);
     if (use_handle) cudaGraphSetConditional(handle, p.ctl->cont);
+    p.ctl->book_total[1] += (unsigned long long)(clock64() - t0);
   }
 }
 
@@ -1079,27 +1101,53 @@ __global__ void __launch_bounds__(kTile, 1) k_loop(Params p) {
     p.ctl->cont = 1u;
   }
   if (!grid_barrier(p, nb)) return;
+  Ctl* c = p.ctl;
   long long t_prev = clock64();
-  auto mark = [&](int k) {
-    if (bid == 0 && threadIdx.x == 0) {
-      const long long now = clock64();
-      p.ctl->phase_cycles[k] += (unsigned long long)(now - t_prev);
-      t_prev = now;
+  unsigned parity = 0;
+  // phase k took (now - t_prev) for block 0 including the barrier wait; every
+  // block also records its own work time so the slowest one can be told apart
+  auto mark = [&](int k, long long work) {
+    if (threadIdx.x == 0) {
+      atomicMax(&c->iter_max[parity][k], (unsigned long long)work);
+      if (bid == 0) {
+        const long long now = clock64();
+        c->phase_cycles[k] += (unsigned long long)(now - t_prev);
+        t_prev = now;
+      }
     }
   };
   for (;;) {
-    if (*reinterpret_cast<volatile unsigned*>(&p.ctl->cont) == 0u) break;
-    phase_fill_step(p, bid, nb, ss, true, true, true);
-    if (!grid_barrier(p, nb)) break;
-    mark(0);
-    if (sorted) {
-      phase_scatter(p, bid, nb);
-      if (!grid_barrier(p, nb)) break;
-      mark(1);
+    if (*reinterpret_cast<volatile unsigned*>(&c->cont) == 0u) break;
+    if (bid == 0 && threadIdx.x == 0) {
+      for (int k = 0; k < 4; ++k) {
+        c->max_total[k] += c->iter_max[parity ^ 1][k];
+        c->iter_max[parity ^ 1][k] = 0;
+      }
     }
-    phase_step(p, bid, nb, ss, true, 0, 0);
+    long long t0 = clock64();
+    phase_fill_step(p, bid, nb, ss, true, true, true);
+    const long long wa = clock64() - t0;
     if (!grid_barrier(p, nb)) break;
-    mark(2);
+    mark(0, wa);
+    if (sorted) {
+      t0 = clock64();
+      phase_scatter(p, bid, nb);
+      const long long wb = clock64() - t0;
+      if (!grid_barrier(p, nb)) break;
+      mark(1, wb);
+    }
+    t0 = clock64();
+    phase_step(p, bid, nb, ss, true, 0, 0);
+    const long long wc = clock64() - t0;
+    if (!grid_barrier(p, nb)) break;
+    mark(2, wc);
+    parity ^= 1u;
+  }
+  if (bid == 0 && threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) {
+      c->max_total[k] += c->iter_max[0][k] + c->iter_max[1][k];
+      c->iter_max[0][k] = c->iter_max[1][k] = 0;
+    }
   }
 }
 
