@@ -491,8 +491,10 @@ __device__ void phase_fill_step(const Params& p, int bid, int nb, const SharedSt
     if (threadIdx.x == 0) p.tile_live[tile] = live ? 1 : 0;
     if (live) {
       step_limit_tile(p, tile, ss, s_keys, s_acts, my_steps);
-    } else if (sorted && (int)threadIdx.x < p.n_keys) {
-      p.tile_counts[threadIdx.x * p.n_tiles + tile] = ((int)threadIdx.x == vacant_key) ? (unsigned)kTile : 0u;
+    } else if (sorted) {
+      if ((int)threadIdx.x < p.n_keys)
+        p.tile_counts[threadIdx.x * p.n_tiles + tile] = ((int)threadIdx.x == vacant_key) ? (unsigned)kTile : 0u;
+      if (lo + threadIdx.x < p.n_slots) p.trk.key[lo + threadIdx.x] = (uint8_t)vacant_key;
     }
   }
   if (do_step) {
