@@ -243,6 +243,33 @@ celer_status celer_enable_kernel_timing(celer_ctx* ctx, int enable);
 celer_status celer_kernel_timing(celer_ctx* ctx, const char** names, double* total_ms, uint64_t* launches,
                                  int n_max, int* n_out);
 
+/* Stable partition of slot indices 0..n-1 by an 8-bit key, the same
+ * partition the step loop builds (slots grouped by key in increasing key
+ * order, ascending slot order within a key), as a stand-alone call that
+ * allocates no device memory. The paper has no counterpart: this exists for
+ * callers that cannot allocate device memory themselves, such as code that
+ * runs while another framework's caching allocator owns the GPU memory, or a
+ * host loop that cannot pay for cudaMalloc/cudaFree (cudaFree synchronises
+ * the whole device).
+ *
+ * d_keys: n keys in device memory; keys not below n_keys are ignored.
+ * d_perm: device output; the slots of every key except skip_key (-1: none)
+ * in partition order. d_offsets: device output of n_keys + 1 entries, the
+ * first position of each key and n_keys' total at the end (the counts
+ * include skip_key's slots, which occupy the last positions if skip_key is
+ * the largest key). Work is queued on cuda_stream (a cudaStream_t; NULL: the
+ * legacy default stream); the call does not synchronise.
+ *
+ * Working memory is one fixed array inside the library (256 KiB per device
+ * that loads it, held until the process exits): n <= 2^20, n_keys <= 16,
+ * otherwise CELER_ERR_INVALID. Every call on a device shares that array, so
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller. The first call on each device
+ * looks up the array's device address with that device current; make that
+ * first call before any stream capture. */
+celer_status celer_partition_keys_noalloc(const uint8_t* d_keys, uint64_t n, int n_keys, int skip_key, uint32_t* d_perm,
+                                          uint32_t* d_offsets, void* cuda_stream);
+
 /* ---- diagnostics used by the parity tests ---- */
 
 /* Partition of the last iteration: per-slot key (n_slots bytes), the

@@ -83,7 +83,7 @@ EXPORTS = [
     "celer_read_history", "celer_get_stats", "celer_set_sort_policy", "celer_set_split_actions", "celer_read_trace",
     "celer_read_loop_profile",
     "celer_enable_kernel_timing", "celer_kernel_timing", "celer_debug_partition", "celer_debug_table",
-    "celer_debug_philox", "celer_debug_curand_philox",
+    "celer_debug_philox", "celer_debug_curand_philox", "celer_partition_keys_noalloc",
 ]
 
 _lib = None
@@ -123,6 +123,7 @@ def load(path: Optional[str] = None):
         "celer_debug_table": ([vp, i32, i32, dp], i32),
         "celer_debug_philox": ([vp, vp, u64], i32),
         "celer_debug_curand_philox": ([u64, u64, u64, vp, u64], i32),
+        "celer_partition_keys_noalloc": ([vp, u64, i32, i32, vp, vp, vp], i32),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(L, name)
@@ -326,6 +327,15 @@ class Context:
 def _stats_dict(s):
     return dict(iteration=s.iteration, alive=s.alive, queued=s.queued, steps=s.steps, steps_total=s.steps_total,
                 deferred=s.deferred, error=s.error, actions=list(s.action_count)[:len(ACTION_NAMES)])
+
+
+def partition_keys_noalloc(d_keys: int, n: int, n_keys: int, skip_key: int, d_perm: int, d_offsets: int,
+                           stream=None):
+    """Stable partition of 0..n-1 by key into device buffers, using only the
+    library's fixed working array (no device allocation). Pointers are device
+    addresses (e.g. tensor.data_ptr())."""
+    _check(load().celer_partition_keys_noalloc(C.c_void_p(d_keys), n, n_keys, skip_key, C.c_void_p(d_perm),
+                                               C.c_void_p(d_offsets), C.c_void_p(stream) if stream else None))
 
 
 def debug_philox(ctr_key: np.ndarray) -> np.ndarray:
