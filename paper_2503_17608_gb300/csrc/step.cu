@@ -873,6 +873,20 @@ __device__ __forceinline__ bool post_one(const Params& p, uint32_t slot, uint8_t
 
 __device__ __forceinline__ bool is_interaction(uint8_t act) { return act >= A_COMPTON && act <= A_BREMS; }
 
+// Warp-interleaved walk over [lo, hi): 32-element chunk g goes to block
+// g % nb, so consecutive chunks land on different SMs. With few live tracks
+// this spreads the FP64 work over all SMs instead of stacking warps on the
+// few SMs that own the first chunks (an FP64 warp instruction occupies its
+// sub-partition's pipe for the same time whatever its active lanes).
+struct ChunkWalk {
+  uint32_t lo, hi, step, g;
+  __device__ ChunkWalk(uint32_t lo_, uint32_t hi_, int bid, int nb)
+      : lo(lo_), hi(hi_), step((uint32_t)nb * (blockDim.x >> 5)), g((uint32_t)bid + (threadIdx.x >> 5) * (uint32_t)nb) {}
+  __device__ __forceinline__ bool more() const { return (unsigned long long)lo + 32ull * g < hi; }
+  __device__ __forceinline__ uint32_t index() const { return lo + 32u * g + (threadIdx.x & 31); }
+  __device__ __forceinline__ void next() { g += step; }
+};
+
 // Work range of the step phase for the policy: all slots (masking), or the
 // partition range of the live keys.
 __device__ __forceinline__ Span live_span(const Params& p) {
@@ -924,7 +938,9 @@ __device__ void phase_step(const Params& p, int bid, int nb, const SharedStatic&
   const bool tight = p.ctl->defer != 0u;
   const Tracks& t = p.trk;
   unsigned long long killed = 0, n_def = 0;
-  for (uint32_t i = sp.lo + bid * blockDim.x + threadIdx.x; i < sp.hi; i += nb * blockDim.x) {
+  for (ChunkWalk w(sp.lo, sp.hi, bid, nb); w.more(); w.next()) {
+    const uint32_t i = w.index();
+    if (i >= sp.hi) continue;
     const uint32_t slot = sp.perm ? sp.perm[i] : i;
     const uint8_t st = t.status[slot];
     if (st == VACANT) continue;
@@ -956,7 +972,9 @@ __device__ void phase_along_only(const Params& p, bool charged, int bid, int nb,
     sp.hi = p.ctl->offsets[charged ? KA_VACANT : KA_CHARGED];
   }
   unsigned long long killed = 0;
-  for (uint32_t i = sp.lo + bid * blockDim.x + threadIdx.x; i < sp.hi; i += nb * blockDim.x) {
+  for (ChunkWalk w(sp.lo, sp.hi, bid, nb); w.more(); w.next()) {
+    const uint32_t i = w.index();
+    if (i >= sp.hi) continue;
     const uint32_t slot = sp.perm ? sp.perm[i] : i;
     if (p.trk.status[slot] != ALIVE) continue;
     const uint8_t pt = p.trk.ptype[slot];
@@ -987,7 +1005,9 @@ __device__ void phase_post_only(const Params& p, uint8_t which, int bid, int nb)
   }
   const bool tight = p.ctl->defer != 0u;
   unsigned long long killed = 0, n_def = 0;
-  for (uint32_t i = sp.lo + bid * blockDim.x + threadIdx.x; i < sp.hi; i += nb * blockDim.x) {
+  for (ChunkWalk w(sp.lo, sp.hi, bid, nb); w.more(); w.next()) {
+    const uint32_t i = w.index();
+    if (i >= sp.hi) continue;
     const uint32_t slot = sp.perm ? sp.perm[i] : i;
     const uint8_t st = p.trk.status[slot];
     if (st == VACANT || p.trk.action[slot] != which) continue;
