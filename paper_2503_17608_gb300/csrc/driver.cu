@@ -464,17 +464,25 @@ celer_status celer_create(const celer_problem* pb, celer_ctx** out) {
   CREATE_CUDA(dalloc(ctx, &r.layer, C));
   CREATE_CUDA(dalloc(ctx, &r.ptype, C));
   CREATE_CUDA(dalloc(ctx, &p.ctl, 1));
-  CREATE_CUDA(dalloc(ctx, &p.vacant, p.n_tiles));
-  CREATE_CUDA(dalloc(ctx, &p.filled, p.n_tiles));
+  p.n_chunks = (N + 31) / 32;
+  CREATE_CUDA(dalloc(ctx, &p.vacant, p.n_chunks));
+  CREATE_CUDA(dalloc(ctx, &p.filled, p.n_chunks));
+  CREATE_CUDA(dalloc(ctx, &p.vprefix, p.n_chunks));
   CREATE_CUDA(dalloc(ctx, &p.tile_live, p.n_tiles));
   CREATE_CUDA(dalloc(ctx, &p.barrier, 4));
   {
-    std::vector<uint32_t> vac(p.n_tiles);
-    for (uint32_t tile = 0; tile < p.n_tiles; ++tile) {
-      const uint64_t lo = (uint64_t)tile * kTile;
-      vac[tile] = (uint32_t)((N - lo) < (uint64_t)kTile ? (N - lo) : (uint64_t)kTile);
+    // every slot starts vacant
+    std::vector<uint32_t> vac(p.n_chunks);
+    std::vector<unsigned long long> pre(p.n_chunks);
+    unsigned long long run = 0;
+    for (uint32_t g = 0; g < p.n_chunks; ++g) {
+      const uint64_t lo = (uint64_t)g * 32;
+      vac[g] = (uint32_t)((N - lo) < 32ull ? (N - lo) : 32ull);
+      pre[g] = run;
+      run += vac[g];
     }
-    CREATE_CUDA(cudaMemcpy(p.vacant, vac.data(), sizeof(uint32_t) * p.n_tiles, cudaMemcpyHostToDevice));
+    CREATE_CUDA(cudaMemcpy(p.vacant, vac.data(), sizeof(uint32_t) * p.n_chunks, cudaMemcpyHostToDevice));
+    CREATE_CUDA(cudaMemcpy(p.vprefix, pre.data(), sizeof(unsigned long long) * p.n_chunks, cudaMemcpyHostToDevice));
   }
   CREATE_CUDA(dalloc(ctx, &p.perm, N));
   CREATE_CUDA(dalloc(ctx, &p.tile_counts, (size_t)kKeysFull * p.n_tiles));
@@ -532,6 +540,7 @@ celer_status celer_create(const celer_problem* pb, celer_ctx** out) {
   // control block
   Ctl init{};
   init.max_iterations = pb->max_iterations ? pb->max_iterations : 1000000ull;
+  init.total_vacant = N;
   init.cont = 0;
   CREATE_CUDA(cudaMemcpyAsync(p.ctl, &init, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
 

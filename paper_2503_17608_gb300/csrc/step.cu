@@ -45,7 +45,7 @@ __device__ __forceinline__ void release(const Params& p, uint32_t slot, uint32_t
   p.trk.status[slot] = VACANT;
   p.trk.action[slot] = A_NONE;
   atomicSub(&p.event_live[row_of(p, ev)], 1u);
-  atomicAdd(&p.vacant[slot / kTile], 1u);
+  atomicAdd(&p.vacant[slot >> 5], 1u);
 }
 
 // Warp-sum a per-thread counter and add it to a device counter (negated if
@@ -247,18 +247,6 @@ __device__ __forceinline__ void stage_static(const Params& p, const SharedStatic
   __syncthreads();
 }
 
-__device__ __forceinline__ unsigned block_sum(unsigned v, unsigned* scratch /* 32 */) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) scratch[warp] = v;
-  __syncthreads();
-  unsigned tot = 0;
-  const int nw = (blockDim.x + 31) >> 5;
-  for (int w = 0; w < nw; ++w) tot += scratch[w];
-  return tot;
-}
 
 // Clear the per-iteration counters (one thread).
 __device__ __forceinline__ void clear_iteration_counters(Ctl* c) {
@@ -288,81 +276,140 @@ __device__ __forceinline__ bool last_block_done(unsigned* counter, unsigned nb) 
   return last;
 }
 
-// Fill the vacant slots of one tile: the r-th vacant slot in ascending slot
-// order over the whole store takes initializer head + r, for r < queued
-// (deterministic filling). 'before' = vacant slots in earlier tiles.
-__device__ __forceinline__ unsigned fill_tile(const Params& p, uint32_t tile, unsigned long long before,
-                                              unsigned long long head, unsigned long long queued, unsigned* s_w) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t slot = tile * kTile + threadIdx.x;
-  const bool vac = slot < p.n_slots && p.trk.status[slot] == VACANT;
-  const unsigned bal = __ballot_sync(0xffffffffu, vac);
-  __syncthreads();
-  if (lane == 0) s_w[warp] = __popc(bal);
-  __syncthreads();
-  unsigned wpre = 0, tot = 0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-    if (w < warp) wpre += s_w[w];
-    tot += s_w[w];
-  }
-  const unsigned long long r = before + wpre + __popc(bal & ((1u << lane) - 1u));
-  if (vac && r < queued) {
-    const unsigned long long i = (head + r) & p.ring_mask;
-    const Tracks& t = p.trk;
-    t.x[slot] = p.ring.x[i];
-    t.y[slot] = p.ring.y[i];
-    t.z[slot] = p.ring.z[i];
-    t.ux[slot] = p.ring.ux[i];
-    t.uy[slot] = p.ring.uy[i];
-    t.uz[slot] = p.ring.uz[i];
-    t.E[slot] = p.ring.E[i];
-    t.tid[slot] = p.ring.tid[i];
-    t.event[slot] = p.ring.event[i];
-    t.primary[slot] = p.ring.primary[i];
-    t.layer[slot] = p.ring.layer[i];
-    t.ptype[slot] = p.ring.ptype[i];
-    t.ctr[slot] = 0u;
-    t.nmfp[slot] = -1.0;
-    t.action[slot] = A_NONE;
-    t.status[slot] = ALIVE;
-  }
-  const unsigned long long left = queued > before ? queued - before : 0ull;
-  const unsigned n = (unsigned)(tot < left ? tot : left);
-  if (threadIdx.x == 0) p.filled[tile] = n;
-  return n;
-}
+// Warp-interleaved walk over [lo, hi): 32-element chunk g goes to block
+// g % nb, so consecutive chunks land on different SMs. With few live tracks
+// this spreads the FP64 work over all SMs instead of stacking warps on the
+// few SMs that own the first chunks (an FP64 warp instruction occupies its
+// sub-partition's pipe for the same time whatever its active lanes).
+struct ChunkWalk {
+  uint32_t lo, hi, step, g;
+  __device__ ChunkWalk(uint32_t lo_, uint32_t hi_, int bid, int nb)
+      : lo(lo_), hi(hi_), step((uint32_t)nb * (blockDim.x >> 5)), g((uint32_t)bid + (threadIdx.x >> 5) * (uint32_t)nb) {}
+  __device__ __forceinline__ bool more() const { return (unsigned long long)lo + 32ull * g < hi; }
+  __device__ __forceinline__ uint32_t index() const { return lo + 32u * g + (threadIdx.x & 31); }
+  __device__ __forceinline__ void next() { g += step; }
+};
 
-// Step limit of every live slot of one tile, with counts per next action and
-// (sorted policies) per partition key of the tile.
-__device__ __forceinline__ void step_limit_tile(const Params& p, uint32_t tile, const SharedStatic& ss,
-                                                unsigned* s_keys, unsigned* s_acts, unsigned long long& my_steps) {
+// ---- phase A: initializer fill + step limit, on 32-slot warp-tiles
+// A warp owns a 32-slot chunk: it fills the chunk's vacant slots from the
+// initializer buffer (the r-th vacant slot in ascending slot order over the
+// whole store takes initializer head + r, for r < queued: deterministic
+// filling; vprefix[g] = vacant slots before chunk g, scanned at the end of
+// the previous iteration), then computes the step limit of every live slot
+// of the chunk and adds the chunk's key counts to its 256-slot tile. Chunks
+// are dealt to warps interleaved over the blocks, so a handful of live
+// chunks is spread over as many SMs.
+__device__ __forceinline__ void fill_and_limit_chunk(const Params& p, uint32_t g, const SharedStatic& ss, bool fill,
+                                                     bool do_step, unsigned long long head,
+                                                     unsigned long long queued, unsigned* s_acts,
+                                                     unsigned long long& my_steps) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t slot = g * 32u + lane;
+  const bool real = slot < p.n_slots;
+  unsigned nfill = 0;
+  if (fill) {
+    const unsigned long long before = __ldcg(&p.vprefix[g]);
+    if (before < queued) {
+      const bool vac = real && p.trk.status[slot] == VACANT;
+      const unsigned bal = __ballot_sync(0xffffffffu, vac);
+      const unsigned long long r = before + __popc(bal & ((1u << lane) - 1u));
+      if (vac && r < queued) {
+        const unsigned long long i = (head + r) & p.ring_mask;
+        const Tracks& t = p.trk;
+        t.x[slot] = p.ring.x[i];
+        t.y[slot] = p.ring.y[i];
+        t.z[slot] = p.ring.z[i];
+        t.ux[slot] = p.ring.ux[i];
+        t.uy[slot] = p.ring.uy[i];
+        t.uz[slot] = p.ring.uz[i];
+        t.E[slot] = p.ring.E[i];
+        t.tid[slot] = p.ring.tid[i];
+        t.event[slot] = p.ring.event[i];
+        t.primary[slot] = p.ring.primary[i];
+        t.layer[slot] = p.ring.layer[i];
+        t.ptype[slot] = p.ring.ptype[i];
+        t.ctr[slot] = 0u;
+        t.nmfp[slot] = -1.0;
+        t.action[slot] = A_NONE;
+        t.status[slot] = ALIVE;
+      }
+      const unsigned long long left = queued - before;
+      nfill = (unsigned)((unsigned long long)__popc(bal) < left ? __popc(bal) : left);
+    }
+    if (lane == 0) p.filled[g] = nfill;
+  } else if (do_step) {
+    nfill = __ldcg(&p.filled[g]);  // set by a separate fill launch
+  }
+  if (!do_step) return;
   const bool sorted = p.policy != POLICY_NONE;
   const uint8_t vacant_key = p.policy == POLICY_ACTION ? KA_VACANT : K_VACANT_FULL;
-  if (threadIdx.x < kMaxKeys) s_keys[threadIdx.x] = 0;
-  __syncthreads();
-  const uint32_t slot = tile * kTile + threadIdx.x;
+  const uint32_t tile = g >> 3;
+  const unsigned csize = (p.n_slots - g * 32u) < 32u ? (p.n_slots - g * 32u) : 32u;
+  const bool live = __ldcg(&p.vacant[g]) < csize || nfill > 0;  // warp-uniform
   uint8_t key = vacant_key;
-  if (slot < p.n_slots) {
-    const uint8_t st = p.trk.status[slot];
-    uint8_t act = A_NONE;
-    if (st == ALIVE) {
-      act = step_limit(p, slot, ss.tab, ss.zb, ss.lmat);
-      ++my_steps;
-    } else if (st == DEFERRED) {
-      act = p.trk.action[slot];
+  if (live) {
+    if (real) {
+      const uint8_t st = p.trk.status[slot];
+      uint8_t act = A_NONE;
+      if (st == ALIVE) {
+        act = step_limit(p, slot, ss.tab, ss.zb, ss.lmat);
+        ++my_steps;
+      } else if (st == DEFERRED) {
+        act = p.trk.action[slot];
+      }
+      if (st != VACANT) {
+        atomicAdd(&s_acts[act], 1u);
+        if (sorted) key = key_of(p.policy, p.trk.ptype[slot], act);
+      }
     }
-    if (st != VACANT) {
-      atomicAdd(&s_acts[act], 1u);
-      if (sorted) key = key_of(p.policy, p.trk.ptype[slot], act);
-    }
-    if (sorted) p.trk.key[slot] = key;
+    if (sorted && lane == 0) p.tile_live[tile] = 1;
   }
   if (sorted) {
-    const unsigned peers = __match_any_sync(0xffffffffu, (unsigned)key);
-    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&s_keys[key], (unsigned)__popc(peers));
-    __syncthreads();
-    if ((int)threadIdx.x < p.n_keys) p.tile_counts[threadIdx.x * p.n_tiles + tile] = s_keys[threadIdx.x];
+    if (real) p.trk.key[slot] = key;
+    const unsigned k = real ? (unsigned)key : 0xFFFFFFFFu;
+    const unsigned peers = __match_any_sync(0xffffffffu, k);
+    if (real && lane == __ffs(peers) - 1) atomicAdd(&p.tile_counts[key * p.n_tiles + tile], (unsigned)__popc(peers));
   }
+}
+
+// Exclusive scan of the per-chunk vacancy counts into vprefix and their
+// total, by one block (end of an iteration, when every release is counted).
+__device__ void scan_vacancy(const Params& p) {
+  __shared__ unsigned long long s_warp[32];
+  __shared__ unsigned long long s_total;
+  const uint32_t total = p.n_chunks;
+  const uint32_t per = (total + blockDim.x - 1) / blockDim.x;
+  const uint32_t beg = min(threadIdx.x * per, total);
+  const uint32_t end = min(beg + per, total);
+  unsigned long long local = 0;
+  for (uint32_t i = beg; i < end; ++i) local += __ldcg(&p.vacant[i]);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned long long w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0ull;
+    unsigned long long wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long v = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += v;
+    }
+    s_warp[lane] = wi - w;
+    if (lane == 31) s_total = wi;
+  }
+  __syncthreads();
+  unsigned long long run = s_warp[warp] + incl - local;
+  for (uint32_t i = beg; i < end; ++i) {
+    p.vprefix[i] = run;
+    run += __ldcg(&p.vacant[i]);
+  }
+  if (threadIdx.x == 0) p.ctl->total_vacant = s_total;
   __syncthreads();
 }
 
@@ -378,34 +425,30 @@ __device__ void bookkeeping_after_fill_step(const Params& p, bool did_fill) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = (int)(blockDim.x >> 5);
   if (did_fill) {
-    unsigned long long vac = 0, fil = 0;
-    for (uint32_t t = threadIdx.x; t < p.n_tiles; t += blockDim.x) {
-      const unsigned v = __ldcg(&p.vacant[t]);
-      const unsigned f = __ldcg(&p.filled[t]);
-      vac += v;
-      fil += f;
-      p.vacant[t] = v - f;
-      p.filled[t] = 0u;
+    unsigned long long fil = 0;
+    for (uint32_t g = threadIdx.x; g < p.n_chunks; g += blockDim.x) {
+      const unsigned f = __ldcg(&p.filled[g]);
+      if (f) {
+        fil += f;
+        p.vacant[g] = __ldcg(&p.vacant[g]) - f;
+        p.filled[g] = 0u;
+      }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      vac += __shfl_down_sync(0xffffffffu, vac, o);
-      fil += __shfl_down_sync(0xffffffffu, fil, o);
-    }
+    for (int o = 16; o > 0; o >>= 1) fil += __shfl_down_sync(0xffffffffu, fil, o);
     __syncthreads();
-    if (lane == 0) s_sum[warp] = (vac << 32) | fil;
+    if (lane == 0) s_sum[warp] = fil;
     __syncthreads();
     if (threadIdx.x == 0) {
-      unsigned long long tv = 0, tf = 0;
-      for (int w = 0; w < nw; ++w) {
-        tv += s_sum[w] >> 32;
-        tf += s_sum[w] & 0xFFFFFFFFull;
-      }
+      unsigned long long tf = 0;
+      for (int w = 0; w < nw; ++w) tf += s_sum[w];
       const unsigned long long queued = c->tail - c->head;
+      const unsigned long long tv = c->total_vacant;
       const unsigned long long take = tv < queued ? tv : queued;
       if (take != tf) c->error |= ERR_VACANCY;
       c->head += take;
       c->alive += take;
+      c->total_vacant = tv - take;
     }
     __syncthreads();
   }
@@ -458,9 +501,6 @@ __device__ void bookkeeping_after_fill_step(const Params& p, bool did_fill) {
 // Phase A (or its two halves in the per-action launch mode).
 __device__ void phase_fill_step(const Params& p, int bid, int nb, const SharedStatic& ss, bool do_fill, bool do_step,
                                 bool bookkeeping) {
-  __shared__ unsigned s_red[32];
-  __shared__ unsigned s_w[32];
-  __shared__ unsigned s_keys[kMaxKeys];
   __shared__ unsigned s_acts[A_COUNT];
   Ctl* c = p.ctl;
   const unsigned long long head = c->head;
@@ -468,35 +508,13 @@ __device__ void phase_fill_step(const Params& p, int bid, int nb, const SharedSt
   const bool fill = do_fill && queued > 0;
   if (threadIdx.x < A_COUNT) s_acts[threadIdx.x] = 0;
   __syncthreads();
-  unsigned long long before = 0, my_steps = 0;
-  uint32_t prev_tile = 0;
-  const bool sorted = p.policy != POLICY_NONE;
-  const int vacant_key = p.policy == POLICY_ACTION ? KA_VACANT : K_VACANT_FULL;
-  for (uint32_t tile = bid; tile < p.n_tiles; tile += nb) {
-    unsigned nfill = 0;
-    if (fill) {
-      unsigned part = 0;
-      for (uint32_t i = prev_tile + threadIdx.x; i < tile; i += blockDim.x) part += __ldcg(&p.vacant[i]);
-      before += block_sum(part, s_red);
-      prev_tile = tile;
-      if (before < queued) nfill = fill_tile(p, tile, before, head, queued, s_w);
-    } else if (!do_fill) {
-      nfill = __ldcg(&p.filled[tile]);  // filled by the separate fill launch
-    }
-    if (!do_step) continue;
-    // a tile with no live or waiting track and no new one needs no step limit
-    const uint32_t lo = tile * kTile;
-    const unsigned tsize = (p.n_slots - lo) < (uint32_t)kTile ? (p.n_slots - lo) : (unsigned)kTile;
-    const bool live = __ldcg(&p.vacant[tile]) < tsize || nfill > 0;
-    if (threadIdx.x == 0) p.tile_live[tile] = live ? 1 : 0;
-    if (live) {
-      step_limit_tile(p, tile, ss, s_keys, s_acts, my_steps);
-    } else if (sorted) {
-      if ((int)threadIdx.x < p.n_keys)
-        p.tile_counts[threadIdx.x * p.n_tiles + tile] = ((int)threadIdx.x == vacant_key) ? (unsigned)kTile : 0u;
-      if (lo + threadIdx.x < p.n_slots) p.trk.key[lo + threadIdx.x] = (uint8_t)vacant_key;
+  unsigned long long my_steps = 0;
+  if (fill || do_step) {
+    for (ChunkWalk w(0, p.n_chunks * 32u, bid, nb); w.more(); w.next()) {
+      fill_and_limit_chunk(p, w.g, ss, fill, do_step, head, queued, s_acts, my_steps);
     }
   }
+  __syncthreads();
   if (do_step) {
     if (threadIdx.x < A_COUNT && s_acts[threadIdx.x] != 0)
       atomicAdd(&c->action_count[threadIdx.x], s_acts[threadIdx.x]);
@@ -517,6 +535,8 @@ __device__ void phase_scatter(const Params& p, int bid, int nb) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint32_t tile = bid; tile < p.n_tiles; tile += nb) {
     if (!p.tile_live[tile]) continue;  // every slot vacant: nothing to place
+    __syncthreads();
+    if (threadIdx.x == 0) p.tile_live[tile] = 0;
     if (threadIdx.x < (kTile / 32) * kMaxKeys) (&s_cnt[0][0])[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t slot = tile * kTile + threadIdx.x;
@@ -873,19 +893,6 @@ __device__ __forceinline__ bool post_one(const Params& p, uint32_t slot, uint8_t
 
 __device__ __forceinline__ bool is_interaction(uint8_t act) { return act >= A_COMPTON && act <= A_BREMS; }
 
-// Warp-interleaved walk over [lo, hi): 32-element chunk g goes to block
-// g % nb, so consecutive chunks land on different SMs. With few live tracks
-// this spreads the FP64 work over all SMs instead of stacking warps on the
-// few SMs that own the first chunks (an FP64 warp instruction occupies its
-// sub-partition's pipe for the same time whatever its active lanes).
-struct ChunkWalk {
-  uint32_t lo, hi, step, g;
-  __device__ ChunkWalk(uint32_t lo_, uint32_t hi_, int bid, int nb)
-      : lo(lo_), hi(hi_), step((uint32_t)nb * (blockDim.x >> 5)), g((uint32_t)bid + (threadIdx.x >> 5) * (uint32_t)nb) {}
-  __device__ __forceinline__ bool more() const { return (unsigned long long)lo + 32ull * g < hi; }
-  __device__ __forceinline__ uint32_t index() const { return lo + 32u * g + (threadIdx.x & 31); }
-  __device__ __forceinline__ void next() { g += step; }
-};
 
 // Work range of the step phase for the policy: all slots (masking), or the
 // partition range of the live keys.
@@ -955,12 +962,19 @@ __device__ void phase_step(const Params& p, int bid, int nb, const SharedStatic&
   }
   flush_counter(&p.ctl->alive, killed, true);
   if (n_def) atomicAdd(&p.ctl->n_deferred, (unsigned)n_def);
-  if (bookkeeping && last_block_done(&p.ctl->done_c, nb) && threadIdx.x == 0) {
+  if (p.policy != POLICY_NONE) {  // key counts start from zero in the next phase A
+    const uint32_t nc = (uint32_t)p.n_keys * p.n_tiles;
+    for (uint32_t i = bid * blockDim.x + threadIdx.x; i < nc; i += nb * blockDim.x) p.tile_counts[i] = 0u;
+  }
+  if (bookkeeping && last_block_done(&p.ctl->done_c, nb)) {
     const long long t0 = clock64();
-    loop_ctl_one(p);
-    clear_iteration_counters(p.ctl);
-    if (use_handle) cudaGraphSetConditional(handle, p.ctl->cont);
-    p.ctl->book_total[1] += (unsigned long long)(clock64() - t0);
+    scan_vacancy(p);
+    if (threadIdx.x == 0) {
+      loop_ctl_one(p);
+      clear_iteration_counters(p.ctl);
+      if (use_handle) cudaGraphSetConditional(handle, p.ctl->cont);
+      p.ctl->book_total[1] += (unsigned long long)(clock64() - t0);
+    }
   }
 }
 
@@ -1060,10 +1074,17 @@ __global__ void k_along(Params p, int charged) {
 
 __global__ void k_post(Params p, int which) { phase_post_only(p, (uint8_t)which, blockIdx.x, gridDim.x); }
 
-__global__ void k_loop_ctl(Params p, cudaGraphConditionalHandle handle, int use_handle) {
-  loop_ctl_one(p);
-  clear_iteration_counters(p.ctl);
-  if (use_handle) cudaGraphSetConditional(handle, p.ctl->cont);
+__global__ void __launch_bounds__(kTile) k_loop_ctl(Params p, cudaGraphConditionalHandle handle, int use_handle) {
+  if (p.policy != POLICY_NONE) {
+    const uint32_t nc = (uint32_t)p.n_keys * p.n_tiles;
+    for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) p.tile_counts[i] = 0u;
+  }
+  scan_vacancy(p);
+  if (threadIdx.x == 0) {
+    loop_ctl_one(p);
+    clear_iteration_counters(p.ctl);
+    if (use_handle) cudaGraphSetConditional(handle, p.ctl->cont);
+  }
 }
 
 // Grid-wide barrier of the persistent loop (generation counter). Every wait
@@ -1312,7 +1333,7 @@ void launch_post(const Params& p, int which, const LaunchShape& sh, cudaStream_t
   k_post<<<sh.post_grid, sh.block, 0, s>>>(p, which);
 }
 void launch_loop_ctl(const Params& p, unsigned long long handle, int use_handle, cudaStream_t s) {
-  k_loop_ctl<<<1, 1, 0, s>>>(p, (cudaGraphConditionalHandle)handle, use_handle);
+  k_loop_ctl<<<1, kTile, 0, s>>>(p, (cudaGraphConditionalHandle)handle, use_handle);
 }
 cudaError_t launch_loop(const Params& p, const LaunchShape& sh, cudaStream_t s) {
   void* args[] = {const_cast<Params*>(&p)};
