@@ -206,6 +206,12 @@ celer_status celer_run_events(celer_ctx* ctx, int mode);
  * and 2. */
 celer_status celer_read_loop_profile(celer_ctx* ctx, uint64_t* cycles_out, int n);
 
+/* As celer_run_events, but stop after at most `budget` more step iterations
+ * (0: no limit); *done (nullable) receives the iterations run. A serving
+ * loop uses this to return to the host between chunks of iterations, to
+ * admit new events and collect finished ones while tracks stay resident. */
+celer_status celer_run_iterations(celer_ctx* ctx, int mode, uint64_t budget, uint64_t* done);
+
 /* Choose per-action launches (1) or per-phase launches (0) for the host and
  * graph loops. */
 celer_status celer_set_split_actions(celer_ctx* ctx, int split);
@@ -225,6 +231,9 @@ celer_status celer_event_live(celer_ctx* ctx, uint32_t event, uint64_t* live);
  * added; edep_out (nullable) receives count x n_bins deposits. */
 celer_status celer_read_history(celer_ctx* ctx, uint64_t first, uint64_t count, celer_history* host_out,
                                 double* edep_out);
+
+/* The problem the context was created with (pointer fields set to NULL). */
+celer_status celer_get_problem(const celer_ctx* ctx, celer_problem* out);
 
 /* Counters since creation (stream synchronised). */
 celer_status celer_get_stats(celer_ctx* ctx, celer_step_stats* out);
@@ -269,6 +278,75 @@ celer_status celer_kernel_timing(celer_ctx* ctx, const char** names, double* tot
  * first call before any stream capture. */
 celer_status celer_partition_keys_noalloc(const uint8_t* d_keys, uint64_t n, int n_keys, int skip_key, uint32_t* d_perm,
                                           uint32_t* d_offsets, void* cuda_stream);
+
+/* Live-track counts (alive or queued) of `count` consecutive tally rows
+ * starting at first_row, into host memory. Synchronises the stream. */
+celer_status celer_read_event_live(celer_ctx* ctx, uint32_t first_row, uint32_t count, uint32_t* host_out);
+
+/* ---- serving: continuous batching of arriving events ---- */
+
+typedef struct {
+  double arrival_s;                 /* arrival time, seconds after the start of celer_serve */
+  uint32_t event;                   /* event id (uses tally row event % max_events) */
+  uint32_t pad;
+  const celer_primary* primaries;   /* host */
+  uint64_t n;
+} celer_request;
+
+typedef struct {
+  double arrival_s;                 /* copied from the request */
+  double admit_s;                   /* when its primaries were queued (-1: never) */
+  double done_s;                    /* when its last track ended (-1: never) */
+  double edep, escaped;             /* event totals, MeV */
+} celer_request_result;
+
+typedef struct {
+  int mode;                         /* CELER_LOOP_* used for each chunk of iterations */
+  uint64_t chunk_iterations;        /* iterations between host checks (0: 16) */
+  double footprint_per_primary;     /* tracks reserved per primary at admission (0: 40) */
+  uint32_t max_in_flight;           /* events on the device at once (0: no limit; 1: one at a time) */
+  double stop_admitting_s;          /* requests arriving later are not served (0: serve all) */
+  double* tallies_out;              /* nullable: n_requests x n_bins deposits, host */
+} celer_serve_options;
+
+typedef struct {
+  double wall_s;                    /* from the start to the last completion */
+  uint64_t track_steps;             /* track-steps taken during the call */
+  uint64_t admitted, completed, chunks;
+} celer_serve_summary;
+
+/* Serve requests as they arrive (continuous batching, Sec. 5.1 "events mixed
+ * in a single track array"): at each check the host admits, in arrival
+ * order, every request that has arrived and whose expected footprint
+ * (footprint_per_primary x primaries tracks) fits in the free part of the
+ * slot store plus initializer buffer (slots + buffer entries, minus the
+ * footprints of the events in flight) and whose tally row is free; then it
+ * runs a chunk of step iterations with the tracks of all admitted events in
+ * one slot array, and collects every event whose live-track count reached
+ * zero (tallies copied to the host, row freed). Requests must be in
+ * nondecreasing arrival order. Wall-clock times are measured on the host. */
+celer_status celer_serve(celer_ctx* ctx, const celer_request* requests, uint64_t n, const celer_serve_options* options,
+                         celer_request_result* results, celer_serve_summary* summary);
+
+/* ---- autotuning of the launch configuration ---- */
+
+typedef struct {
+  uint64_t n_slots;
+  int block_size, sort_policy, mode;
+  double track_steps_per_s;         /* measured on the sample (0: the trial failed) */
+  double ms;
+} celer_tune_trial;
+
+/* Try every combination of the given slot counts, block sizes, sort
+ * policies and loop modes on a sample of primaries (grouped by their event
+ * ids, events[i] for primaries[i]): a fresh context per combination, one
+ * warm-up run, one timed run (CUDA events around celer_run_events). trials
+ * (nullable, max_trials entries) receives every trial; best the fastest.
+ * The base problem supplies everything else. */
+celer_status celer_autotune(const celer_problem* base, const celer_primary* primaries, const uint32_t* events,
+                            uint64_t n, const uint64_t* slot_counts, int n_slot_counts, const int* block_sizes,
+                            int n_block_sizes, const int* policies, int n_policies, const int* modes, int n_modes,
+                            celer_tune_trial* trials, int max_trials, int* n_trials, celer_tune_trial* best);
 
 /* ---- diagnostics used by the parity tests ---- */
 

@@ -72,6 +72,34 @@ class celer_trace_row(C.Structure):
                 ("action_count", C.c_uint32 * 16)]
 
 
+class celer_request(C.Structure):
+    _fields_ = [("arrival_s", C.c_double), ("event", C.c_uint32), ("pad", C.c_uint32),
+                ("primaries", C.c_void_p), ("n", C.c_uint64)]
+
+
+class celer_request_result(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("arrival_s", "admit_s", "done_s", "edep", "escaped")]
+
+
+REQUEST_RESULT_NP = np.dtype([(k, "f8") for k in ("arrival_s", "admit_s", "done_s", "edep", "escaped")])
+
+
+class celer_serve_options(C.Structure):
+    _fields_ = [("mode", C.c_int), ("chunk_iterations", C.c_uint64), ("footprint_per_primary", C.c_double),
+                ("max_in_flight", C.c_uint32), ("stop_admitting_s", C.c_double),
+                ("tallies_out", C.POINTER(C.c_double))]
+
+
+class celer_serve_summary(C.Structure):
+    _fields_ = [("wall_s", C.c_double), ("track_steps", C.c_uint64), ("admitted", C.c_uint64),
+                ("completed", C.c_uint64), ("chunks", C.c_uint64)]
+
+
+class celer_tune_trial(C.Structure):
+    _fields_ = [("n_slots", C.c_uint64), ("block_size", C.c_int), ("sort_policy", C.c_int), ("mode", C.c_int),
+                ("track_steps_per_s", C.c_double), ("ms", C.c_double)]
+
+
 ACTION_NAMES = ["none", "zup", "zdown", "side", "range", "trapped", "compton", "photoelectric", "pair", "moller",
                 "brems"]
 
@@ -84,6 +112,7 @@ EXPORTS = [
     "celer_read_loop_profile",
     "celer_enable_kernel_timing", "celer_kernel_timing", "celer_debug_partition", "celer_debug_table",
     "celer_debug_philox", "celer_debug_curand_philox", "celer_partition_keys_noalloc",
+    "celer_run_iterations", "celer_read_event_live", "celer_serve", "celer_autotune", "celer_get_problem",
 ]
 
 _lib = None
@@ -124,6 +153,12 @@ def load(path: Optional[str] = None):
         "celer_debug_philox": ([vp, vp, u64], i32),
         "celer_debug_curand_philox": ([u64, u64, u64, vp, u64], i32),
         "celer_partition_keys_noalloc": ([vp, u64, i32, i32, vp, vp, vp], i32),
+        "celer_run_iterations": ([vp, i32, u64, C.POINTER(u64)], i32),
+        "celer_read_event_live": ([vp, u32, u32, vp], i32),
+        "celer_serve": ([vp, vp, u64, C.POINTER(celer_serve_options), vp, C.POINTER(celer_serve_summary)], i32),
+        "celer_autotune": ([C.POINTER(celer_problem), vp, vp, u64, vp, i32, vp, i32, vp, i32, vp, i32, vp, i32,
+                            C.POINTER(i32), C.POINTER(celer_tune_trial)], i32),
+        "celer_get_problem": ([vp, C.POINTER(celer_problem)], i32),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(L, name)
@@ -161,13 +196,10 @@ def _torch_stream():
     return None
 
 
-class Context:
-    """A transport context built from a workloads.Problem."""
+class ProblemStruct:
+    """A celer_problem filled from a workloads.Problem; keeps its arrays alive."""
 
     def __init__(self, prob: wl.Problem, stream=None, max_iterations: int = 0):
-        L = load()
-        self.prob = prob
-        self.n_bins = prob.n_bins
         self._mats = (celer_material * len(prob.materials))(
             *[celer_material(m.Z, m.A, m.rho, m.ne, m.X0, m.I) for m in prob.materials])
         self._lm = (C.c_int * len(prob.layer_material))(*prob.layer_material)
@@ -187,8 +219,20 @@ class Context:
         cp.sort_policy, cp.block_size, cp.seed = prob.sort_policy, prob.block_size, prob.seed
         cp.split_actions = prob.split_actions
         cp.max_iterations = max_iterations
+        cp.cuda_stream = stream
+        self.c = cp
+
+
+class Context:
+    """A transport context built from a workloads.Problem."""
+
+    def __init__(self, prob: wl.Problem, stream=None, max_iterations: int = 0):
+        L = load()
+        self.prob = prob
+        self.n_bins = prob.n_bins
         self.stream = stream if stream is not None else _torch_stream()
-        cp.cuda_stream = self.stream
+        self._ps = ProblemStruct(prob, self.stream, max_iterations)
+        cp = self._ps.c
         h = C.c_void_p()
         _check(L.celer_create(C.byref(cp), C.byref(h)))
         self._h = h
@@ -253,6 +297,42 @@ class Context:
         return dict(phase={k: v[i] for i, k in enumerate(names)},
                     slowest_work={k: v[4 + i] for i, k in enumerate(names)},
                     bookkeeping={"fill_step": v[8], "step": v[9]})
+
+    def run_iterations(self, mode=LOOP_PERSISTENT, budget: int = 0) -> int:
+        done = C.c_uint64()
+        _check(load().celer_run_iterations(self._h, int(mode), int(budget), C.byref(done)), self._h)
+        return done.value
+
+    def event_live_rows(self, first: int = 0, count: int = None):
+        count = self.prob.max_events - first if count is None else count
+        out = np.zeros(count, np.uint32)
+        _check(load().celer_read_event_live(self._h, first, count, out.ctypes.data), self._h)
+        return out
+
+    def serve(self, requests, mode=LOOP_PERSISTENT, chunk_iterations=16, footprint_per_primary=40.0,
+              max_in_flight=0, stop_admitting_s=0.0, with_tallies=False):
+        """Continuous batching. requests: list of (arrival_s, event_id, primaries)
+        in arrival order. Returns (results ndarray, summary dict, tallies or None)."""
+        n = len(requests)
+        keep = [np.ascontiguousarray(to_c_primaries(p)) for _, _, p in requests]
+        reqs = (celer_request * max(n, 1))()
+        for i, ((t, ev, _), arr) in enumerate(zip(requests, keep)):
+            reqs[i].arrival_s = float(t)
+            reqs[i].event = int(ev)
+            reqs[i].primaries = arr.ctypes.data
+            reqs[i].n = len(arr)
+        res = np.zeros(max(n, 1), dtype=REQUEST_RESULT_NP)
+        tallies = np.zeros((max(n, 1), self.n_bins)) if with_tallies else None
+        opt = celer_serve_options()
+        opt.mode, opt.chunk_iterations, opt.footprint_per_primary = int(mode), chunk_iterations, footprint_per_primary
+        opt.max_in_flight, opt.stop_admitting_s = max_in_flight, stop_admitting_s
+        opt.tallies_out = tallies.ctypes.data_as(C.POINTER(C.c_double)) if with_tallies else None
+        summ = celer_serve_summary()
+        _check(load().celer_serve(self._h, C.cast(reqs, C.c_void_p), n, C.byref(opt), res.ctypes.data,
+                                  C.byref(summ)), self._h)
+        summary = dict(wall_s=summ.wall_s, track_steps=summ.track_steps, admitted=summ.admitted,
+                       completed=summ.completed, chunks=summ.chunks)
+        return res[:n], summary, (tallies[:n] if with_tallies else None)
 
     def set_split_actions(self, split: bool):
         _check(load().celer_set_split_actions(self._h, 1 if split else 0), self._h)
@@ -336,6 +416,29 @@ def partition_keys_noalloc(d_keys: int, n: int, n_keys: int, skip_key: int, d_pe
     addresses (e.g. tensor.data_ptr())."""
     _check(load().celer_partition_keys_noalloc(C.c_void_p(d_keys), n, n_keys, skip_key, C.c_void_p(d_perm),
                                                C.c_void_p(d_offsets), C.c_void_p(stream) if stream else None))
+
+
+def autotune(prob: wl.Problem, primaries: np.ndarray, slot_counts, block_sizes, policies, modes, stream=None):
+    """Measure every combination on the sample; returns (best, trials) as dicts."""
+    ps = ProblemStruct(prob, stream if stream is not None else _torch_stream())
+    cprim = np.ascontiguousarray(to_c_primaries(primaries))
+    events = np.ascontiguousarray(primaries["event"].astype(np.uint32))
+    sc = (C.c_uint64 * len(slot_counts))(*slot_counts)
+    bs = (C.c_int * len(block_sizes))(*block_sizes)
+    po = (C.c_int * len(policies))(*policies)
+    mo = (C.c_int * len(modes))(*modes)
+    n_max = len(slot_counts) * len(block_sizes) * len(policies) * len(modes)
+    trials = (celer_tune_trial * n_max)()
+    n_out = C.c_int()
+    best = celer_tune_trial()
+    _check(load().celer_autotune(C.byref(ps.c), cprim.ctypes.data, events.ctypes.data, len(cprim), sc, len(sc), bs,
+                                 len(bs), po, len(po), mo, len(mo), trials, n_max, C.byref(n_out), C.byref(best)))
+
+    def d(t):
+        return dict(n_slots=t.n_slots, block_size=t.block_size, sort_policy=t.sort_policy, mode=t.mode,
+                    track_steps_per_s=t.track_steps_per_s, ms=t.ms)
+
+    return d(best), [d(trials[i]) for i in range(n_out.value)]
 
 
 def debug_philox(ctr_key: np.ndarray) -> np.ndarray:

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libceler_gb.so")
-SOURCES = ["step.cu", "tables.cu", "driver.cu", "debug.cu", "noalloc.cu"]
+SOURCES = ["step.cu", "tables.cu", "driver.cu", "debug.cu", "noalloc.cu", "serve.cu"]
 HEADERS = ["common.cuh", "physics.cuh", "launch.h", "tables.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -92,6 +92,8 @@ struct Ctl {
   unsigned long long steps_iter;
   unsigned long long iteration;
   unsigned long long max_iterations;
+  unsigned long long budget_end;     // the current run stops when iteration reaches this
+  unsigned long long run_start;      // iteration count when the current run began
   unsigned int action_count[kMaxKeys];
   unsigned int key_total[kMaxKeys];
   unsigned int offsets[kMaxKeys + 1];

@@ -541,6 +541,7 @@ celer_status celer_create(const celer_problem* pb, celer_ctx** out) {
   Ctl init{};
   init.max_iterations = pb->max_iterations ? pb->max_iterations : 1000000ull;
   init.total_vacant = N;
+  init.budget_end = ~0ull;
   init.cont = 0;
   CREATE_CUDA(cudaMemcpyAsync(p.ctl, &init, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
 
@@ -637,11 +638,15 @@ celer_status celer_step(celer_ctx* ctx, celer_step_stats* stats) {
   return CELER_OK;
 }
 
-celer_status celer_run_events(celer_ctx* ctx, int mode) {
+celer_status celer_run_events(celer_ctx* ctx, int mode) { return celer_run_iterations(ctx, mode, 0, nullptr); }
+
+celer_status celer_run_iterations(celer_ctx* ctx, int mode, uint64_t budget, uint64_t* done) {
   if (!ctx) return CELER_ERR_INVALID;
   if (mode < CELER_LOOP_HOST || mode > CELER_LOOP_PERSISTENT) return fail(ctx, CELER_ERR_INVALID, "unknown loop mode");
-  // last-block tickets start from zero (an aborted run could leave them set)
-  CELER_CUDA(ctx, cudaMemsetAsync(&ctx->p.ctl->done_a, 0, 2 * sizeof(unsigned int), ctx->stream));
+  // iteration budget of this run; last-block tickets start from zero (an
+  // aborted run could leave them set)
+  launch_begin_run(ctx->p, budget, ctx->stream);
+  CELER_CUDA(ctx, cudaGetLastError());
   if (mode == CELER_LOOP_GRAPH) {
     if (!ctx->graph_exec || ctx->graph_policy != ctx->p.policy || ctx->graph_split != ctx->split_actions) {
       celer_status st = build_graph(ctx);
@@ -678,6 +683,7 @@ celer_status celer_run_events(celer_ctx* ctx, int mode) {
   }
   celer_status st = read_ctl(ctx);
   if (st != CELER_OK) return st;
+  if (done) *done = ctx->h_ctl->iteration - ctx->h_ctl->run_start;
   if (ctx->timing) timing_resolve(ctx);
   return status_from_error(ctx, ctx->h_ctl->error);
 }
@@ -718,6 +724,16 @@ celer_status celer_event_live(celer_ctx* ctx, uint32_t event, uint64_t* live) {
   return CELER_OK;
 }
 
+celer_status celer_read_event_live(celer_ctx* ctx, uint32_t first_row, uint32_t count, uint32_t* host_out) {
+  if (!ctx || !host_out) return CELER_ERR_INVALID;
+  if ((uint64_t)first_row + count > ctx->p.max_events) return fail(ctx, CELER_ERR_INVALID, "row range out of bounds");
+  if (count == 0) return CELER_OK;
+  CELER_CUDA(ctx, cudaMemcpyAsync(host_out, ctx->p.event_live + first_row, sizeof(uint32_t) * count,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  CELER_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return CELER_OK;
+}
+
 celer_status celer_read_history(celer_ctx* ctx, uint64_t first, uint64_t count, celer_history* out, double* edep_out) {
   if (!ctx || (!out && !edep_out)) return CELER_ERR_INVALID;
   if (first + count > ctx->p.hist_cap) return fail(ctx, CELER_ERR_INVALID, "history range out of bounds");
@@ -751,6 +767,13 @@ celer_status celer_read_history(celer_ctx* ctx, uint64_t first, uint64_t count, 
     }
     done += m;
   }
+  return CELER_OK;
+}
+
+celer_status celer_get_problem(const celer_ctx* ctx, celer_problem* out) {
+  if (!ctx || !out) return CELER_ERR_INVALID;
+  *out = ctx->prob;
+  out->sort_policy = ctx->p.policy;
   return CELER_OK;
 }
 

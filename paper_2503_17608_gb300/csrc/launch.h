@@ -35,6 +35,8 @@ void launch_pre_step(const Params& p, const LaunchShape& sh, cudaStream_t s);
 void launch_along(const Params& p, int charged, const LaunchShape& sh, cudaStream_t s);
 void launch_post(const Params& p, int which, const LaunchShape& sh, cudaStream_t s);
 void launch_loop_ctl(const Params& p, unsigned long long handle, int use_handle, cudaStream_t s);
+// start of a run (iteration budget, last-block tickets)
+void launch_begin_run(const Params& p, unsigned long long budget, cudaStream_t s);
 // persistent loop
 cudaError_t launch_loop(const Params& p, const LaunchShape& sh, cudaStream_t s);
 void launch_push_primaries(const Params& p, const StagedPrimary* d_prim, uint32_t n, cudaStream_t s);

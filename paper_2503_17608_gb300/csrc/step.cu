@@ -933,7 +933,7 @@ __device__ void loop_ctl_one(const Params& p) {
     c->stall = 0;
   }
   if (pending && c->iteration >= c->max_iterations) c->error |= ERR_ITERATIONS;
-  c->cont = (pending && c->error == 0u) ? 1u : 0u;
+  c->cont = (pending && c->error == 0u && c->iteration < c->budget_end) ? 1u : 0u;
 }
 
 // Phase C: along-step of every live track and, where the step ends in an
@@ -1085,6 +1085,14 @@ __global__ void __launch_bounds__(kTile) k_loop_ctl(Params p, cudaGraphCondition
     clear_iteration_counters(p.ctl);
     if (use_handle) cudaGraphSetConditional(handle, p.ctl->cont);
   }
+}
+
+// Start a run: the loop stops after `budget` more iterations (0: no limit).
+__global__ void k_begin_run(Ctl* c, unsigned long long budget) {
+  c->run_start = c->iteration;
+  c->budget_end = budget ? c->iteration + budget : ~0ull;
+  c->done_a = 0u;
+  c->done_c = 0u;
 }
 
 // Grid-wide barrier of the persistent loop (generation counter). Every wait
@@ -1334,6 +1342,9 @@ void launch_post(const Params& p, int which, const LaunchShape& sh, cudaStream_t
 }
 void launch_loop_ctl(const Params& p, unsigned long long handle, int use_handle, cudaStream_t s) {
   k_loop_ctl<<<1, kTile, 0, s>>>(p, (cudaGraphConditionalHandle)handle, use_handle);
+}
+void launch_begin_run(const Params& p, unsigned long long budget, cudaStream_t s) {
+  k_begin_run<<<1, 1, 0, s>>>(p.ctl, budget);
 }
 cudaError_t launch_loop(const Params& p, const LaunchShape& sh, cudaStream_t s) {
   void* args[] = {const_cast<Params*>(&p)};

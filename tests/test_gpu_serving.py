@@ -1,0 +1,80 @@
+"""Continuous batching (serving) and the autotuner, through the C ABI.
+
+An event's results must not depend on which other events share the slot
+store with it: its random streams depend only on (seed, event, track id,
+draw index), so integer counts are identical and deposits differ only by the
+order of floating-point atomic additions (1e-12 relative)."""
+import numpy as np
+import pytest
+
+from paper_2503_17608_gb300 import binding, workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    binding.load()
+
+
+def small_events(n_events=12, cap=60):
+    return [e[:cap] for e in wl.offload_events(n_events)]
+
+
+@pytest.mark.parametrize("mode", [binding.LOOP_PERSISTENT, binding.LOOP_GRAPH])
+def test_served_events_match_alone(mode):
+    events = small_events()
+    prob = wl.calorimeter_problem(1 << 14, Bz=4.0, max_events=64, sort_policy=wl.SORT_ACTION_TYPE)
+    # arrivals close together so that events overlap on the device
+    reqs = [(0.002 * i, int(e["event"][0]), e) for i, e in enumerate(events)]
+    with binding.Context(prob) as ctx:
+        res, summ, tallies = ctx.serve(reqs, mode=mode, chunk_iterations=4, with_tallies=True)
+    assert summ["completed"] == len(events) and summ["admitted"] == len(events)
+    assert np.all(res["done_s"] >= res["admit_s"]) and np.all(res["admit_s"] >= res["arrival_s"] - 1e-9)
+    for k, e in enumerate(events):
+        assert res["edep"][k] + res["escaped"][k] == pytest.approx(e["E"].sum(), rel=1e-12)
+        with binding.Context(prob) as ctx:
+            ctx.add_events(e)
+            ctx.run_events(mode)
+            t1, esc1 = ctx.read_tallies(int(e["event"][0]))
+        np.testing.assert_allclose(tallies[k], t1, rtol=1e-12, atol=1e-9)
+        assert res["escaped"][k] == pytest.approx(esc1, rel=1e-12, abs=1e-9)
+
+
+def test_one_event_at_a_time_serving():
+    events = small_events(6)
+    prob = wl.calorimeter_problem(1 << 14, Bz=4.0, max_events=8)
+    reqs = [(0.0, int(e["event"][0]), e) for e in events]
+    with binding.Context(prob) as ctx:
+        res, summ, _ = ctx.serve(reqs, max_in_flight=1)
+    order = np.argsort(res["admit_s"])
+    # each event is admitted only after the previous one finished
+    assert np.all(res["admit_s"][order][1:] >= res["done_s"][order][:-1])
+    assert summ["completed"] == len(events)
+
+
+def test_serving_reuses_tally_rows():
+    events = small_events(10, cap=20)
+    prob = wl.calorimeter_problem(1 << 13, max_events=3)
+    reqs = [(0.0005 * i, 100 + i, e) for i, e in enumerate(events)]
+    for i, e in enumerate(events):
+        e["event"][:] = 100 + i
+    with binding.Context(prob) as ctx:
+        res, summ, _ = ctx.serve(reqs)
+    assert summ["completed"] == len(events)
+    for k, e in enumerate(events):
+        assert res["edep"][k] + res["escaped"][k] == pytest.approx(e["E"].sum(), rel=1e-12)
+
+
+def test_autotuner_picks_a_measured_best():
+    events = small_events(8, cap=40)
+    prim = wl.concat_primaries(events)
+    prob = wl.calorimeter_problem(1 << 12, Bz=4.0, max_events=16)
+    best, trials = binding.autotune(prob, prim, [1 << 12, 1 << 13], [128, 256], [wl.SORT_NONE, wl.SORT_ACTION_TYPE],
+                                    [binding.LOOP_PERSISTENT])
+    assert len(trials) == 8
+    assert all(t["track_steps_per_s"] > 0 for t in trials)
+    assert best["track_steps_per_s"] == max(t["track_steps_per_s"] for t in trials)
