@@ -138,6 +138,8 @@ extern "C" celer_status celer_serve(celer_ctx* ctx, const celer_request* reqs, u
       inflight[k] = inflight.back();
       inflight.pop_back();
     }
+    // nothing left to step but events still counted live: inconsistent state
+    if (done == 0 && !inflight.empty()) return CELER_ERR_STATE;
   }
   if (summary) {
     s = celer_get_stats(ctx, &st);
