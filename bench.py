@@ -351,6 +351,8 @@ def run_ours(args):
         if not launches_per_job:
             per_job = sum(v["launches"] for v in kt["kernels"].values())
             line["gpu_launches"] = int((per_job + 1) * args.steps)
+    if not args.no_extras and world == 1:
+        line["other_workloads"] = run_extras(args, binding, stream, flush)
     if not args.skip_cpu_baseline and world == 1:
         rate, cores, reps, nsample, dt = cpu_oracle_rate(prob, prim, min_seconds=args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -359,6 +361,119 @@ def run_ours(args):
     head_ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_extras(args, binding, stream, flush):
+    """The other workloads of the benchmark suite, reported beside the headline:
+    the 4 T / 10 GeV calorimeter at 2^20 slots (three sort policies), 256
+    offload events batched in one loop (autotuned) vs 256 sequential runs, and
+    Poisson-arrival serving vs the one-event-at-a-time loop."""
+    import torch
+
+    out = {}
+    # --- 10,000 x 10 GeV e- in 4 T, 2^20 slots
+    prob2, prim2, desc2 = make_workload("calorimeter-field-10gev")
+    c2 = binding.to_c_primaries(prim2)
+    dev2 = torch.from_numpy(c2.view(np.uint8).copy()).cuda()
+    pol = {}
+    for name in ("action_type", "action", "none"):
+        ctx = binding.Context(prob2.replace(sort_policy=wl.SORT_NAMES[name], max_events=1), stream=stream.cuda_stream)
+        times, steps = [], 0
+        for rep in range(1 + args.extra_steps):
+            flush.zero_()
+            ctx.reset_event(rep)
+            s0 = ctx.stats()["steps_total"]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.add_primaries_device(rep, dev2.data_ptr(), len(c2))
+            ctx.run_events(binding.LOOP_PERSISTENT)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep >= 1:
+                times.append(e0.elapsed_time(e1))
+                steps += ctx.stats()["steps_total"] - s0
+        it = ctx.stats()["iteration"]
+        prof = ctx.loop_profile()
+        ctx.close()
+        ms = sum(times)
+        pol[name] = dict(value=steps / (ms / 1e3), ms_per_job=ms / len(times), track_steps_per_job=steps / len(times),
+                         iterations_per_job=it / (1 + args.extra_steps))
+    out["calorimeter_field_10gev"] = dict(desc2, sorted_vs_unsorted=pol)
+
+    # --- 256 offload events: autotune on a sample, then all in one loop vs one by one
+    events = wl.offload_events(256)
+    prim3 = wl.concat_primaries(events)
+    base3 = wl.calorimeter_problem(1 << 20, Bz=4.0, max_events=256)
+    sample = wl.concat_primaries(events[:24])
+    best, trials = binding.autotune(base3, sample, [1 << 18, 1 << 19, 1 << 20, 1 << 21], [128, 256, 512],
+                                    [wl.SORT_NONE, wl.SORT_ACTION, wl.SORT_ACTION_TYPE],
+                                    [binding.LOOP_PERSISTENT, binding.LOOP_GRAPH], stream=stream.cuda_stream)
+    tuned = base3.replace(n_slots=best["n_slots"], block_size=best["block_size"], sort_policy=best["sort_policy"],
+                          init_capacity=max(8 * best["n_slots"], 1 << 22))
+    mode = best["mode"]
+    ctx = binding.Context(tuned, stream=stream.cuda_stream)
+    ctx.add_events(prim3)  # warm-up pass
+    ctx.run_events(mode)
+    for e in range(256):
+        ctx.reset_event(e)
+    flush.zero_()
+    torch.cuda.synchronize()
+    s0 = ctx.stats()["steps_total"]
+    t0 = time.perf_counter()
+    ctx.add_events(prim3)
+    ctx.run_events(mode)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    steps_batch = ctx.stats()["steps_total"] - s0
+    batched_tallies = [ctx.read_tallies(e) for e in range(256)]
+    ctx.close()
+    ctx = binding.Context(tuned.replace(max_events=1), stream=stream.cuda_stream)
+    s0 = ctx.stats()["steps_total"]
+    t0 = time.perf_counter()
+    seq_tallies = []
+    for e, ev in enumerate(events):
+        ctx.reset_event(e)
+        ctx.add_primaries(e, ev)
+        ctx.run_events(mode)
+        seq_tallies.append(ctx.read_tallies(e))
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    steps_seq = ctx.stats()["steps_total"] - s0
+    ctx.close()
+    max_rel = max(float(np.max(np.abs(b[0] - q[0]) / np.maximum(np.abs(q[0]), 1e-300))) for b, q in
+                  zip(batched_tallies, seq_tallies))
+    out["offload_batched_256"] = dict(
+        events=256, primaries=int(len(prim3)), autotuned=dict(best, trials=len(trials)),
+        batched=dict(value=steps_batch / t_batch, wall_s=t_batch, track_steps=int(steps_batch),
+                     events_per_s=256 / t_batch),
+        sequential=dict(value=steps_seq / t_seq, wall_s=t_seq, track_steps=int(steps_seq), events_per_s=256 / t_seq),
+        speedup=t_seq / t_batch, max_rel_tally_diff_batched_vs_sequential=max_rel)
+
+    # --- serving: Poisson arrivals of offload events
+    rate, dur = args.serve_rate, args.serve_seconds
+    arrivals = wl.poisson_arrivals(rate, dur)
+    sev = wl.offload_events(len(arrivals), first_event=0)
+    reqs = [(float(t), i, e) for i, (t, e) in enumerate(zip(arrivals, sev))]
+    served = {}
+    sprob = tuned.replace(max_events=4096)
+    for label, kw in (("continuous_batching", dict()), ("one_event_at_a_time", dict(max_in_flight=1))):
+        ctx = binding.Context(sprob, stream=stream.cuda_stream)
+        stop = dur if label == "continuous_batching" else min(dur, args.serve_plain_seconds)
+        r_list = [r for r in reqs if r[0] <= stop]
+        res, summ, _ = ctx.serve(r_list, mode=mode, chunk_iterations=args.serve_chunk, stop_admitting_s=stop + 0.5,
+                                 **kw)
+        ctx.close()
+        done = res["done_s"] >= 0
+        lat = (res["done_s"] - res["arrival_s"])[done]
+        served[label] = dict(
+            offered_events=len(r_list), offered_rate=len(r_list) / stop, completed=int(done.sum()),
+            sustained_rate=float(done.sum() / max(summ["wall_s"], 1e-9)), wall_s=summ["wall_s"],
+            track_steps_per_s=summ["track_steps"] / max(summ["wall_s"], 1e-9),
+            latency_ms=dict(p50=float(np.percentile(lat, 50) * 1e3), p95=float(np.percentile(lat, 95) * 1e3),
+                            p99=float(np.percentile(lat, 99) * 1e3)) if len(lat) else None,
+            window_s=stop)
+    out["serving"] = dict(rate_hz=rate, duration_s=dur, mode=mode, chunk_iterations=args.serve_chunk, **served)
+    return out
 
 
 def binding_policy(name):
@@ -431,6 +546,12 @@ def main():
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=3.0)
     ap.add_argument("--reference-primaries", type=int, default=0)
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--extra-steps", type=int, default=2)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-plain-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-chunk", type=int, default=8)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -305,7 +305,8 @@ typedef struct {
   uint64_t chunk_iterations;        /* iterations between host checks (0: 16) */
   double footprint_per_primary;     /* tracks reserved per primary at admission (0: 40) */
   uint32_t max_in_flight;           /* events on the device at once (0: no limit; 1: one at a time) */
-  double stop_admitting_s;          /* requests arriving later are not served (0: serve all) */
+  double stop_admitting_s;          /* no admission after this wall-clock time (0: serve every request);
+                                       requests not admitted by then are left unserved */
   double* tallies_out;              /* nullable: n_requests x n_bins deposits, host */
 } celer_serve_options;
 

@@ -82,7 +82,7 @@ extern "C" celer_status celer_serve(celer_ctx* ctx, const celer_request* reqs, u
     // admission, in arrival order, while the head request fits
     while (next < n && reqs[next].arrival_s <= now) {
       const celer_request& q = reqs[next];
-      if (opt.stop_admitting_s > 0.0 && q.arrival_s > opt.stop_admitting_s) break;
+      if (opt.stop_admitting_s > 0.0 && now > opt.stop_admitting_s) break;
       if (opt.max_in_flight && inflight.size() >= opt.max_in_flight) break;
       const uint32_t row = (uint32_t)(q.event % max_events);
       if (row_busy[row]) break;
@@ -102,7 +102,7 @@ extern "C" celer_status celer_serve(celer_ctx* ctx, const celer_request* reqs, u
     }
     if (inflight.empty()) {
       if (next >= n) break;
-      if (opt.stop_admitting_s > 0.0 && reqs[next].arrival_s > opt.stop_admitting_s) break;
+      if (opt.stop_admitting_s > 0.0 && seconds_since(t0) > opt.stop_admitting_s) break;
       const double wait = reqs[next].arrival_s - seconds_since(t0);
       if (wait > 2e-4) std::this_thread::sleep_for(std::chrono::duration<double>(wait - 1e-4));
       continue;
