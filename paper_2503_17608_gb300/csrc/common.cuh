@@ -104,6 +104,7 @@ struct Ctl {
   unsigned int stall;                // consecutive iterations without progress
   unsigned int done_a, done_c;       // last-block tickets of the fill/step-limit and step phases
   unsigned long long total_vacant;   // vacant slots (scanned at the end of an iteration)
+  unsigned long long filled_total;   // slots filled in the current iteration
   unsigned int pad;
   unsigned long long trace_count;
   unsigned long long last_steps_iter;          // copies of the last finished iteration's counters
@@ -135,7 +136,8 @@ struct Params {
   uint32_t n_chunks;       // ceil(n_slots / 32): warp-tiles of the fill / step-limit phase
   uint32_t* vacant;        // vacant slots per chunk, n_chunks (kept current by every release)
   uint32_t* filled;        // slots filled per chunk in the current iteration, n_chunks
-  unsigned long long* vprefix;  // vacant slots before each chunk, n_chunks
+  uint32_t* tile_vacant;   // vacant slots per 256-slot tile, n_tiles
+  unsigned long long* tile_prefix;  // vacant slots before each tile, n_tiles (scanned once per iteration)
   uint8_t* tile_live;      // 1 if the tile holds a live or waiting track after the fill
   unsigned int* barrier;   // grid barrier state of the persistent loop: count, generation, abort
   // partition

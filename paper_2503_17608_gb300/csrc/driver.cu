@@ -467,22 +467,27 @@ celer_status celer_create(const celer_problem* pb, celer_ctx** out) {
   p.n_chunks = (N + 31) / 32;
   CREATE_CUDA(dalloc(ctx, &p.vacant, p.n_chunks));
   CREATE_CUDA(dalloc(ctx, &p.filled, p.n_chunks));
-  CREATE_CUDA(dalloc(ctx, &p.vprefix, p.n_chunks));
+  CREATE_CUDA(dalloc(ctx, &p.tile_vacant, p.n_tiles));
+  CREATE_CUDA(dalloc(ctx, &p.tile_prefix, p.n_tiles));
   CREATE_CUDA(dalloc(ctx, &p.tile_live, p.n_tiles));
   CREATE_CUDA(dalloc(ctx, &p.barrier, 4));
   {
     // every slot starts vacant
-    std::vector<uint32_t> vac(p.n_chunks);
-    std::vector<unsigned long long> pre(p.n_chunks);
-    unsigned long long run = 0;
+    std::vector<uint32_t> vac(p.n_chunks), tvac(p.n_tiles, 0);
+    std::vector<unsigned long long> pre(p.n_tiles);
     for (uint32_t g = 0; g < p.n_chunks; ++g) {
       const uint64_t lo = (uint64_t)g * 32;
       vac[g] = (uint32_t)((N - lo) < 32ull ? (N - lo) : 32ull);
-      pre[g] = run;
-      run += vac[g];
+      tvac[g >> 3] += vac[g];
+    }
+    unsigned long long run = 0;
+    for (uint32_t t = 0; t < p.n_tiles; ++t) {
+      pre[t] = run;
+      run += tvac[t];
     }
     CREATE_CUDA(cudaMemcpy(p.vacant, vac.data(), sizeof(uint32_t) * p.n_chunks, cudaMemcpyHostToDevice));
-    CREATE_CUDA(cudaMemcpy(p.vprefix, pre.data(), sizeof(unsigned long long) * p.n_chunks, cudaMemcpyHostToDevice));
+    CREATE_CUDA(cudaMemcpy(p.tile_vacant, tvac.data(), sizeof(uint32_t) * p.n_tiles, cudaMemcpyHostToDevice));
+    CREATE_CUDA(cudaMemcpy(p.tile_prefix, pre.data(), sizeof(unsigned long long) * p.n_tiles, cudaMemcpyHostToDevice));
   }
   CREATE_CUDA(dalloc(ctx, &p.perm, N));
   CREATE_CUDA(dalloc(ctx, &p.tile_counts, (size_t)kKeysFull * p.n_tiles));

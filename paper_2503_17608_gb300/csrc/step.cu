@@ -46,6 +46,7 @@ __device__ __forceinline__ void release(const Params& p, uint32_t slot, uint32_t
   p.trk.action[slot] = A_NONE;
   atomicSub(&p.event_live[row_of(p, ev)], 1u);
   atomicAdd(&p.vacant[slot >> 5], 1u);
+  atomicAdd(&p.tile_vacant[slot >> 8], 1u);
 }
 
 // Warp-sum a per-thread counter and add it to a device counter (negated if
@@ -308,7 +309,13 @@ __device__ __forceinline__ void fill_and_limit_chunk(const Params& p, uint32_t g
   const bool real = slot < p.n_slots;
   unsigned nfill = 0;
   if (fill) {
-    const unsigned long long before = __ldcg(&p.vprefix[g]);
+    // vacant slots before this chunk: those before its tile, plus the ones in
+    // the tile's earlier chunks (at most 7, read in parallel by the lanes)
+    const uint32_t first = (g >> 3) << 3;
+    unsigned part = (first + lane < g) ? __ldcg(&p.vacant[first + lane]) : 0u;
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    const unsigned long long before = __ldcg(&p.tile_prefix[g >> 3]) + __shfl_sync(0xffffffffu, part, 0);
     if (before < queued) {
       const bool vac = real && p.trk.status[slot] == VACANT;
       const unsigned bal = __ballot_sync(0xffffffffu, vac);
@@ -336,7 +343,10 @@ __device__ __forceinline__ void fill_and_limit_chunk(const Params& p, uint32_t g
       const unsigned long long left = queued - before;
       nfill = (unsigned)((unsigned long long)__popc(bal) < left ? __popc(bal) : left);
     }
-    if (lane == 0) p.filled[g] = nfill;
+    if (lane == 0) {
+      p.filled[g] = nfill;
+      if (nfill) atomicAdd(&p.ctl->filled_total, (unsigned long long)nfill);
+    }
   } else if (do_step) {
     nfill = __ldcg(&p.filled[g]);  // set by a separate fill launch
   }
@@ -366,23 +376,38 @@ __device__ __forceinline__ void fill_and_limit_chunk(const Params& p, uint32_t g
   }
   if (sorted) {
     if (real) p.trk.key[slot] = key;
-    const unsigned k = real ? (unsigned)key : 0xFFFFFFFFu;
+    // only live keys are counted: the vacant key is the last one, so its
+    // slots need no position
+    const unsigned k = (real && key != vacant_key) ? (unsigned)key : 0xFFFFFFFFu;
     const unsigned peers = __match_any_sync(0xffffffffu, k);
-    if (real && lane == __ffs(peers) - 1) atomicAdd(&p.tile_counts[key * p.n_tiles + tile], (unsigned)__popc(peers));
+    if (k != 0xFFFFFFFFu && lane == __ffs(peers) - 1)
+      atomicAdd(&p.tile_counts[key * p.n_tiles + tile], (unsigned)__popc(peers));
   }
 }
 
-// Exclusive scan of the per-chunk vacancy counts into vprefix and their
-// total, by one block (end of an iteration, when every release is counted).
-__device__ void scan_vacancy(const Params& p) {
+// Block-wide exclusive scan of n 32-bit counts: each thread takes a
+// contiguous segment (a multiple of four entries, read as 16-byte vectors
+// with several loads in flight), the segment sums are scanned across the
+// block, and write(i, prefix) receives the exclusive prefix of entry i.
+// Returns the total. One block; every thread must call it.
+template <class Write>
+__device__ unsigned long long block_scan_counts(const uint32_t* in, uint32_t n, Write write) {
   __shared__ unsigned long long s_warp[32];
   __shared__ unsigned long long s_total;
-  const uint32_t total = p.n_chunks;
-  const uint32_t per = (total + blockDim.x - 1) / blockDim.x;
-  const uint32_t beg = min(threadIdx.x * per, total);
-  const uint32_t end = min(beg + per, total);
+  const uint32_t per = ((n + blockDim.x - 1) / blockDim.x + 3u) & ~3u;
+  const uint32_t beg = min(threadIdx.x * per, n);
+  const uint32_t end = min(beg + per, n);
   unsigned long long local = 0;
-  for (uint32_t i = beg; i < end; ++i) local += __ldcg(&p.vacant[i]);
+  uint32_t i = beg;
+  for (; i + 16 <= end; i += 16) {
+    const uint4 a = __ldcg(reinterpret_cast<const uint4*>(in + i));
+    const uint4 b = __ldcg(reinterpret_cast<const uint4*>(in + i + 4));
+    const uint4 c = __ldcg(reinterpret_cast<const uint4*>(in + i + 8));
+    const uint4 d = __ldcg(reinterpret_cast<const uint4*>(in + i + 12));
+    local += (unsigned long long)a.x + a.y + a.z + a.w + b.x + b.y + b.z + b.w + c.x + c.y + c.z + c.w + d.x + d.y +
+             d.z + d.w;
+  }
+  for (; i < end; ++i) local += __ldcg(in + i);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned long long incl = local;
 #pragma unroll
@@ -390,6 +415,7 @@ __device__ void scan_vacancy(const Params& p) {
     const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += v;
   }
+  __syncthreads();
   if (lane == 31) s_warp[warp] = incl;
   __syncthreads();
   if (warp == 0) {
@@ -405,89 +431,63 @@ __device__ void scan_vacancy(const Params& p) {
   }
   __syncthreads();
   unsigned long long run = s_warp[warp] + incl - local;
-  for (uint32_t i = beg; i < end; ++i) {
-    p.vprefix[i] = run;
-    run += __ldcg(&p.vacant[i]);
+  i = beg;
+  for (; i + 4 <= end; i += 4) {
+    const uint4 a = __ldcg(reinterpret_cast<const uint4*>(in + i));
+    write(i, run);
+    run += a.x;
+    write(i + 1, run);
+    run += a.y;
+    write(i + 2, run);
+    run += a.z;
+    write(i + 3, run);
+    run += a.w;
   }
-  if (threadIdx.x == 0) p.ctl->total_vacant = s_total;
+  for (; i < end; ++i) {
+    const unsigned v = __ldcg(in + i);
+    write(i, run);
+    run += v;
+  }
+  const unsigned long long total = s_total;
   __syncthreads();
+  return total;
+}
+
+// Exclusive scan of the per-tile vacancy counts into tile_prefix and their
+// total, by one block (end of an iteration, when every release is counted).
+__device__ void scan_vacancy(const Params& p) {
+  unsigned long long* out = p.tile_prefix;
+  const unsigned long long total =
+      block_scan_counts(p.tile_vacant, p.n_tiles, [out](uint32_t i, unsigned long long v) { out[i] = v; });
+  if (threadIdx.x == 0) p.ctl->total_vacant = total;
 }
 
 // Bookkeeping at the end of phase A, by one block: commit the initializers
-// taken, move the fill counts into the vacancy counts, scan the per-(key,
-// tile) counts in key-major order into output positions and key offsets,
-// and decide whether this iteration's secondaries are sure to fit.
+// taken, scan the per-(key, tile) counts of the live keys in key-major order
+// into output positions and key offsets, and decide whether this
+// iteration's secondaries are sure to fit.
 __device__ void bookkeeping_after_fill_step(const Params& p, bool did_fill) {
-  __shared__ unsigned s_warp[32];
-  __shared__ unsigned s_total;
-  __shared__ unsigned long long s_sum[32];
   Ctl* c = p.ctl;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = (int)(blockDim.x >> 5);
-  if (did_fill) {
-    unsigned long long fil = 0;
-    for (uint32_t g = threadIdx.x; g < p.n_chunks; g += blockDim.x) {
-      const unsigned f = __ldcg(&p.filled[g]);
-      if (f) {
-        fil += f;
-        p.vacant[g] = __ldcg(&p.vacant[g]) - f;
-        p.filled[g] = 0u;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) fil += __shfl_down_sync(0xffffffffu, fil, o);
-    __syncthreads();
-    if (lane == 0) s_sum[warp] = fil;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned long long tf = 0;
-      for (int w = 0; w < nw; ++w) tf += s_sum[w];
-      const unsigned long long queued = c->tail - c->head;
-      const unsigned long long tv = c->total_vacant;
-      const unsigned long long take = tv < queued ? tv : queued;
-      if (take != tf) c->error |= ERR_VACANCY;
-      c->head += take;
-      c->alive += take;
-      c->total_vacant = tv - take;
-    }
-    __syncthreads();
+  if (did_fill && threadIdx.x == 0) {
+    const unsigned long long queued = c->tail - c->head;
+    const unsigned long long tv = c->total_vacant;
+    const unsigned long long take = tv < queued ? tv : queued;
+    if (take != c->filled_total) c->error |= ERR_VACANCY;
+    c->filled_total = 0;
+    c->head += take;
+    c->alive += take;
+    c->total_vacant = tv - take;
   }
   if (p.policy != POLICY_NONE) {
-    const uint32_t total = (uint32_t)p.n_keys * p.n_tiles;
-    const uint32_t per = (total + blockDim.x - 1) / blockDim.x;
-    const uint32_t beg = min(threadIdx.x * per, total);
-    const uint32_t end = min(beg + per, total);
-    unsigned local = 0;
-    for (uint32_t i = beg; i < end; ++i) local += __ldcg(&p.tile_counts[i]);
-    unsigned incl = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += v;
+    uint32_t* counts = p.tile_counts;
+    const int live_keys = p.n_keys - 1;  // the last key is the vacant one
+    const unsigned long long total = block_scan_counts(
+        counts, (uint32_t)live_keys * p.n_tiles, [counts](uint32_t i, unsigned long long v) { counts[i] = (uint32_t)v; });
+    if ((int)threadIdx.x < live_keys) c->offsets[threadIdx.x] = counts[threadIdx.x * p.n_tiles];
+    if ((int)threadIdx.x == live_keys) {
+      c->offsets[live_keys] = (unsigned)total;
+      c->offsets[p.n_keys] = p.n_slots;
     }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      const unsigned w = lane < nw ? s_warp[lane] : 0u;
-      unsigned wi = w;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned v = __shfl_up_sync(0xffffffffu, wi, o);
-        if (lane >= o) wi += v;
-      }
-      s_warp[lane] = wi - w;
-      if (lane == 31) s_total = wi;
-    }
-    __syncthreads();
-    unsigned run = s_warp[warp] + incl - local;
-    for (uint32_t i = beg; i < end; ++i) {
-      const unsigned v = __ldcg(&p.tile_counts[i]);
-      p.tile_counts[i] = run;
-      run += v;
-    }
-    __syncthreads();
-    if ((int)threadIdx.x < p.n_keys) c->offsets[threadIdx.x] = p.tile_counts[threadIdx.x * p.n_tiles];
-    if ((int)threadIdx.x == p.n_keys) c->offsets[p.n_keys] = s_total;
     __syncthreads();
   }
   if (threadIdx.x == 0) {
@@ -495,6 +495,19 @@ __device__ void bookkeeping_after_fill_step(const Params& p, bool did_fill) {
     const unsigned long long max_new =
         2ull * c->action_count[A_PAIR] + c->action_count[A_MOLLER] + c->action_count[A_BREMS];
     c->defer = (queued + max_new > p.ring_capacity) ? 1u : 0u;
+  }
+}
+
+// Move the fills of this iteration into the vacancy counts (all blocks, any
+// phase after the fill has finished everywhere).
+__device__ __forceinline__ void apply_fills(const Params& p, int bid, int nb) {
+  for (uint32_t g = bid * blockDim.x + threadIdx.x; g < p.n_chunks; g += nb * blockDim.x) {
+    const unsigned f = __ldcg(&p.filled[g]);
+    if (f) {
+      atomicSub(&p.vacant[g], f);
+      atomicSub(&p.tile_vacant[g >> 3], f);
+      p.filled[g] = 0u;
+    }
   }
 }
 
@@ -963,9 +976,10 @@ __device__ void phase_step(const Params& p, int bid, int nb, const SharedStatic&
   flush_counter(&p.ctl->alive, killed, true);
   if (n_def) atomicAdd(&p.ctl->n_deferred, (unsigned)n_def);
   if (p.policy != POLICY_NONE) {  // key counts start from zero in the next phase A
-    const uint32_t nc = (uint32_t)p.n_keys * p.n_tiles;
+    const uint32_t nc = (uint32_t)(p.n_keys - 1) * p.n_tiles;
     for (uint32_t i = bid * blockDim.x + threadIdx.x; i < nc; i += nb * blockDim.x) p.tile_counts[i] = 0u;
   }
+  apply_fills(p, bid, nb);
   if (bookkeeping && last_block_done(&p.ctl->done_c, nb)) {
     const long long t0 = clock64();
     scan_vacancy(p);
@@ -1076,9 +1090,11 @@ __global__ void k_post(Params p, int which) { phase_post_only(p, (uint8_t)which,
 
 __global__ void __launch_bounds__(kTile) k_loop_ctl(Params p, cudaGraphConditionalHandle handle, int use_handle) {
   if (p.policy != POLICY_NONE) {
-    const uint32_t nc = (uint32_t)p.n_keys * p.n_tiles;
+    const uint32_t nc = (uint32_t)(p.n_keys - 1) * p.n_tiles;
     for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) p.tile_counts[i] = 0u;
   }
+  apply_fills(p, 0, 1);
+  __syncthreads();
   scan_vacancy(p);
   if (threadIdx.x == 0) {
     loop_ctl_one(p);
