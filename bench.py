@@ -397,7 +397,10 @@ def run_extras(args, binding, stream, flush):
         ctx.close()
         ms = sum(times)
         pol[name] = dict(value=steps / (ms / 1e3), ms_per_job=ms / len(times), track_steps_per_job=steps / len(times),
-                         iterations_per_job=it / (1 + args.extra_steps))
+                         iterations_per_job=it / (1 + args.extra_steps),
+                         loop_profile_us_per_iteration={
+                             part: {k: round(v / max(it, 1) / 2.07e3, 2) for k, v in vals.items()}
+                             for part, vals in prof.items()})
     out["calorimeter_field_10gev"] = dict(desc2, sorted_vs_unsorted=pol)
 
     # --- 256 offload events: autotune on a sample, then all in one loop vs one by one

@@ -144,7 +144,8 @@ struct Params {
   int policy;
   int n_keys;
   uint32_t* perm;          // n_slots
-  uint32_t* tile_counts;   // n_keys * n_tiles, key major
+  uint32_t* tile_counts;   // live-key counts per tile, (n_keys - 1) * n_tiles, key major
+  uint32_t* tile_offsets;  // their exclusive scan: output position of each (key, tile)
   // geometry
   int n_layers;
   int n_materials;

@@ -491,6 +491,7 @@ celer_status celer_create(const celer_problem* pb, celer_ctx** out) {
   }
   CREATE_CUDA(dalloc(ctx, &p.perm, N));
   CREATE_CUDA(dalloc(ctx, &p.tile_counts, (size_t)kKeysFull * p.n_tiles));
+  CREATE_CUDA(dalloc(ctx, &p.tile_offsets, (size_t)kKeysFull * p.n_tiles));
   double* d_zb = nullptr;
   int32_t* d_lmat = nullptr;
   CREATE_CUDA(dalloc(ctx, &d_zb, L + 1));
@@ -881,9 +882,15 @@ celer_status celer_debug_partition(celer_ctx* ctx, uint8_t* keys_out, uint32_t* 
   celer_status st = read_ctl(ctx);
   if (st != CELER_OK) return st;
   const uint32_t N = ctx->p.n_slots;
+  std::vector<uint8_t> status(N);
   CELER_CUDA(ctx, cudaMemcpyAsync(keys_out, ctx->p.trk.key, N, cudaMemcpyDeviceToHost, ctx->stream));
+  CELER_CUDA(ctx, cudaMemcpyAsync(status.data(), ctx->p.trk.status, N, cudaMemcpyDeviceToHost, ctx->stream));
   CELER_CUDA(ctx, cudaMemcpyAsync(perm_out, ctx->p.perm, sizeof(uint32_t) * N, cudaMemcpyDeviceToHost, ctx->stream));
   CELER_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  // the key that takes part in the partition: vacant slots have the vacant key
+  const uint8_t vacant_key = (uint8_t)(ctx->p.n_keys - 1);
+  for (uint32_t i = 0; i < N; ++i)
+    if (status[i] == VACANT) keys_out[i] = vacant_key;
   *n_keys = ctx->p.n_keys;
   for (int k = 0; k <= ctx->p.n_keys; ++k) offsets_out[k] = ctx->h_ctl->offsets[k];
   return CELER_OK;

@@ -386,34 +386,35 @@ __device__ __forceinline__ void fill_and_limit_chunk(const Params& p, uint32_t g
 }
 
 // Block-wide exclusive scan of n 32-bit counts: each thread takes a
-// contiguous segment (a multiple of four entries, read as 16-byte vectors
-// with several loads in flight), the segment sums are scanned across the
-// block, and write(i, prefix) receives the exclusive prefix of entry i.
-// Returns the total. One block; every thread must call it.
+// contiguous segment (a multiple of 32 entries), loads it eight 16-byte
+// vectors at a time with all loads in flight, the segment sums are scanned
+// across the block, and write(i, prefix) receives the exclusive prefix of
+// entry i (written to a different array than `in`). Returns the total. One
+// block; every thread must call it.
 template <class Write>
-__device__ unsigned long long block_scan_counts(const uint32_t* in, uint32_t n, Write write) {
+__device__ unsigned long long block_scan_counts(const uint32_t* __restrict__ in, uint32_t n, Write write) {
   __shared__ unsigned long long s_warp[32];
   __shared__ unsigned long long s_total;
-  const uint32_t per = ((n + blockDim.x - 1) / blockDim.x + 3u) & ~3u;
+  const uint32_t per = ((n + blockDim.x - 1) / blockDim.x + 31u) & ~31u;
   const uint32_t beg = min(threadIdx.x * per, n);
   const uint32_t end = min(beg + per, n);
+  const uint4* v = reinterpret_cast<const uint4*>(in);
   unsigned long long local = 0;
   uint32_t i = beg;
-  for (; i + 16 <= end; i += 16) {
-    const uint4 a = __ldcg(reinterpret_cast<const uint4*>(in + i));
-    const uint4 b = __ldcg(reinterpret_cast<const uint4*>(in + i + 4));
-    const uint4 c = __ldcg(reinterpret_cast<const uint4*>(in + i + 8));
-    const uint4 d = __ldcg(reinterpret_cast<const uint4*>(in + i + 12));
-    local += (unsigned long long)a.x + a.y + a.z + a.w + b.x + b.y + b.z + b.w + c.x + c.y + c.z + c.w + d.x + d.y +
-             d.z + d.w;
+  for (; i + 32 <= end; i += 32) {
+    uint4 q[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) q[k] = __ldcg(v + (i >> 2) + k);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) local += (unsigned long long)q[k].x + q[k].y + q[k].z + q[k].w;
   }
   for (; i < end; ++i) local += __ldcg(in + i);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned long long incl = local;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += v;
+    const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
   }
   __syncthreads();
   if (lane == 31) s_warp[warp] = incl;
@@ -423,8 +424,8 @@ __device__ unsigned long long block_scan_counts(const uint32_t* in, uint32_t n, 
     unsigned long long wi = w;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long v = __shfl_up_sync(0xffffffffu, wi, o);
-      if (lane >= o) wi += v;
+      const unsigned long long t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
     }
     s_warp[lane] = wi - w;
     if (lane == 31) s_total = wi;
@@ -432,21 +433,26 @@ __device__ unsigned long long block_scan_counts(const uint32_t* in, uint32_t n, 
   __syncthreads();
   unsigned long long run = s_warp[warp] + incl - local;
   i = beg;
-  for (; i + 4 <= end; i += 4) {
-    const uint4 a = __ldcg(reinterpret_cast<const uint4*>(in + i));
-    write(i, run);
-    run += a.x;
-    write(i + 1, run);
-    run += a.y;
-    write(i + 2, run);
-    run += a.z;
-    write(i + 3, run);
-    run += a.w;
+  for (; i + 32 <= end; i += 32) {
+    uint4 q[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) q[k] = __ldcg(v + (i >> 2) + k);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      write(i + 4 * k, run);
+      run += q[k].x;
+      write(i + 4 * k + 1, run);
+      run += q[k].y;
+      write(i + 4 * k + 2, run);
+      run += q[k].z;
+      write(i + 4 * k + 3, run);
+      run += q[k].w;
+    }
   }
   for (; i < end; ++i) {
-    const unsigned v = __ldcg(in + i);
+    const unsigned t = __ldcg(in + i);
     write(i, run);
-    run += v;
+    run += t;
   }
   const unsigned long long total = s_total;
   __syncthreads();
@@ -479,11 +485,11 @@ __device__ void bookkeeping_after_fill_step(const Params& p, bool did_fill) {
     c->total_vacant = tv - take;
   }
   if (p.policy != POLICY_NONE) {
-    uint32_t* counts = p.tile_counts;
+    uint32_t* offs = p.tile_offsets;
     const int live_keys = p.n_keys - 1;  // the last key is the vacant one
     const unsigned long long total = block_scan_counts(
-        counts, (uint32_t)live_keys * p.n_tiles, [counts](uint32_t i, unsigned long long v) { counts[i] = (uint32_t)v; });
-    if ((int)threadIdx.x < live_keys) c->offsets[threadIdx.x] = counts[threadIdx.x * p.n_tiles];
+        p.tile_counts, (uint32_t)live_keys * p.n_tiles, [offs](uint32_t i, unsigned long long v) { offs[i] = (uint32_t)v; });
+    if ((int)threadIdx.x < live_keys) c->offsets[threadIdx.x] = offs[threadIdx.x * p.n_tiles];
     if ((int)threadIdx.x == live_keys) {
       c->offsets[live_keys] = (unsigned)total;
       c->offsets[p.n_keys] = p.n_slots;
@@ -523,8 +529,28 @@ __device__ void phase_fill_step(const Params& p, int bid, int nb, const SharedSt
   __syncthreads();
   unsigned long long my_steps = 0;
   if (fill || do_step) {
-    for (ChunkWalk w(0, p.n_chunks * 32u, bid, nb); w.more(); w.next()) {
-      fill_and_limit_chunk(p, w.g, ss, fill, do_step, head, queued, s_acts, my_steps);
+    // This warp's chunks are g0, g0 + step, ...: 32 at a time, each lane reads
+    // one chunk's vacancy (and its tile's prefix) so the warp visits only the
+    // chunks that hold live tracks or may receive initializers.
+    const int lane = threadIdx.x & 31;
+    const uint32_t step = (uint32_t)nb * (blockDim.x >> 5);
+    const uint32_t g0 = (uint32_t)bid + (threadIdx.x >> 5) * (uint32_t)nb;
+    for (uint32_t base = g0; base < p.n_chunks; base += 32u * step) {
+      const uint32_t g = base + lane * step;
+      bool cand = false;
+      if (g < p.n_chunks) {
+        const unsigned csize = (p.n_slots - g * 32u) < 32u ? (p.n_slots - g * 32u) : 32u;
+        const unsigned vac = __ldcg(&p.vacant[g]);
+        cand = vac < csize;
+        if (!cand && fill && vac > 0) cand = __ldcg(&p.tile_prefix[g >> 3]) < queued;
+        if (!cand && !do_fill) cand = __ldcg(&p.filled[g]) > 0;  // filled by a separate fill launch
+      }
+      unsigned mask = __ballot_sync(0xffffffffu, cand);
+      while (mask) {
+        const int j = __ffs(mask) - 1;
+        mask &= mask - 1;
+        fill_and_limit_chunk(p, base + (uint32_t)j * step, ss, fill, do_step, head, queued, s_acts, my_steps);
+      }
     }
   }
   __syncthreads();
@@ -544,26 +570,40 @@ __device__ void phase_fill_step(const Params& p, int bid, int nb, const SharedSt
 // offset for the key + same-key slots in earlier warps + same-key lanes below.
 __device__ void phase_scatter(const Params& p, int bid, int nb) {
   __shared__ unsigned s_cnt[kTile / 32][kMaxKeys];
+  __shared__ uint32_t s_live[kTile];
+  __shared__ unsigned s_nlive;
   const uint8_t vacant_key = p.policy == POLICY_ACTION ? KA_VACANT : K_VACANT_FULL;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (uint32_t tile = bid; tile < p.n_tiles; tile += nb) {
-    if (!p.tile_live[tile]) continue;  // every slot vacant: nothing to place
+  // this block's tiles are bid, bid + nb, ...: read their live flags in
+  // parallel (kTile at a time), then visit only the live ones
+  for (uint32_t base = bid; base < p.n_tiles; base += nb * kTile) {
+    if (threadIdx.x == 0) s_nlive = 0;
     __syncthreads();
-    if (threadIdx.x == 0) p.tile_live[tile] = 0;
-    if (threadIdx.x < (kTile / 32) * kMaxKeys) (&s_cnt[0][0])[threadIdx.x] = 0;
-    __syncthreads();
-    const uint32_t slot = tile * kTile + threadIdx.x;
-    const unsigned key = slot < p.n_slots ? p.trk.key[slot] : vacant_key;
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    const unsigned rank = __popc(peers & ((1u << lane) - 1u));
-    if (lane == __ffs(peers) - 1) s_cnt[warp][key] = __popc(peers);
-    __syncthreads();
-    if (key != vacant_key) {
-      unsigned pos = p.tile_counts[key * p.n_tiles + tile] + rank;
-      for (int w = 0; w < warp; ++w) pos += s_cnt[w][key];
-      p.perm[pos] = slot;
+    const uint32_t t = base + threadIdx.x * (uint32_t)nb;
+    if (t < p.n_tiles && p.tile_live[t]) {
+      s_live[atomicAdd(&s_nlive, 1u)] = t;
+      p.tile_live[t] = 0;
     }
     __syncthreads();
+    const unsigned nlive = s_nlive;
+    for (unsigned j = 0; j < nlive; ++j) {
+      const uint32_t tile = s_live[j];
+      if (threadIdx.x < (kTile / 32) * kMaxKeys) (&s_cnt[0][0])[threadIdx.x] = 0;
+      __syncthreads();
+      const uint32_t slot = tile * kTile + threadIdx.x;
+      // a vacant slot's stored key may be stale (its chunk was skipped)
+      const unsigned key = (slot < p.n_slots && p.trk.status[slot] != VACANT) ? p.trk.key[slot] : vacant_key;
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+      if (lane == __ffs(peers) - 1) s_cnt[warp][key] = __popc(peers);
+      __syncthreads();
+      if (key != vacant_key) {
+        unsigned pos = p.tile_offsets[key * p.n_tiles + tile] + rank;
+        for (int w = 0; w < warp; ++w) pos += s_cnt[w][key];
+        p.perm[pos] = slot;
+      }
+      __syncthreads();
+    }
   }
 }
 
