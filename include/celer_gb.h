@@ -352,7 +352,7 @@ celer_status celer_autotune(const celer_problem* base, const celer_primary* prim
 /* ---- diagnostics used by the parity tests ---- */
 
 /* Partition of the last iteration: per-slot key as used by the partition
- * (n_slots bytes; vacant slots carry the last, vacant key), the permutation
+ * (n_slots bytes; slots vacant at that time carry the last, vacant key), the permutation
  * (n_slots entries; the first offsets[n_keys - 1] are the live slots) and
  * the n_keys + 1 offsets. Valid only for the sorted policies. */
 celer_status celer_debug_partition(celer_ctx* ctx, uint8_t* keys_out, uint32_t* perm_out, uint32_t* offsets_out,

@@ -139,6 +139,7 @@ struct Params {
   uint32_t* tile_vacant;   // vacant slots per 256-slot tile, n_tiles
   unsigned long long* tile_prefix;  // vacant slots before each tile, n_tiles (scanned once per iteration)
   uint8_t* tile_live;      // 1 if the tile holds a live or waiting track after the fill
+  uint8_t* chunk_dirty;    // 1 if the chunk's stored keys may still name live keys (n_chunks)
   unsigned int* barrier;   // grid barrier state of the persistent loop: count, generation, abort
   // partition
   int policy;

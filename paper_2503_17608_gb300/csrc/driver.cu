@@ -470,6 +470,8 @@ celer_status celer_create(const celer_problem* pb, celer_ctx** out) {
   CREATE_CUDA(dalloc(ctx, &p.tile_vacant, p.n_tiles));
   CREATE_CUDA(dalloc(ctx, &p.tile_prefix, p.n_tiles));
   CREATE_CUDA(dalloc(ctx, &p.tile_live, p.n_tiles));
+  CREATE_CUDA(dalloc(ctx, &p.chunk_dirty, p.n_chunks));
+  CREATE_CUDA(cudaMemsetAsync(p.chunk_dirty, 1, p.n_chunks, ctx->stream));  // every key starts unset
   CREATE_CUDA(dalloc(ctx, &p.barrier, 4));
   {
     // every slot starts vacant
@@ -814,6 +816,8 @@ celer_status celer_set_sort_policy(celer_ctx* ctx, int policy) {
   if (!ctx || policy < 0 || policy > 2) return CELER_ERR_INVALID;
   ctx->p.policy = policy;
   ctx->p.n_keys = keys_of(policy);
+  // stored keys belong to the previous policy: rewrite them all at the next step
+  CELER_CUDA(ctx, cudaMemsetAsync(ctx->p.chunk_dirty, 1, ctx->p.n_chunks, ctx->stream));
   ctx->prob.sort_policy = policy;
   return CELER_OK;
 }
@@ -882,15 +886,9 @@ celer_status celer_debug_partition(celer_ctx* ctx, uint8_t* keys_out, uint32_t* 
   celer_status st = read_ctl(ctx);
   if (st != CELER_OK) return st;
   const uint32_t N = ctx->p.n_slots;
-  std::vector<uint8_t> status(N);
   CELER_CUDA(ctx, cudaMemcpyAsync(keys_out, ctx->p.trk.key, N, cudaMemcpyDeviceToHost, ctx->stream));
-  CELER_CUDA(ctx, cudaMemcpyAsync(status.data(), ctx->p.trk.status, N, cudaMemcpyDeviceToHost, ctx->stream));
   CELER_CUDA(ctx, cudaMemcpyAsync(perm_out, ctx->p.perm, sizeof(uint32_t) * N, cudaMemcpyDeviceToHost, ctx->stream));
   CELER_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  // the key that takes part in the partition: vacant slots have the vacant key
-  const uint8_t vacant_key = (uint8_t)(ctx->p.n_keys - 1);
-  for (uint32_t i = 0; i < N; ++i)
-    if (status[i] == VACANT) keys_out[i] = vacant_key;
   *n_keys = ctx->p.n_keys;
   for (int k = 0; k <= ctx->p.n_keys; ++k) offsets_out[k] = ctx->h_ctl->offsets[k];
   return CELER_OK;

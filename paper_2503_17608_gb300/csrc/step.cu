@@ -376,6 +376,7 @@ __device__ __forceinline__ void fill_and_limit_chunk(const Params& p, uint32_t g
   }
   if (sorted) {
     if (real) p.trk.key[slot] = key;
+    if (lane == 0) p.chunk_dirty[g] = live ? 1 : 0;
     // only live keys are counted: the vacant key is the last one, so its
     // slots need no position
     const unsigned k = (real && key != vacant_key) ? (unsigned)key : 0xFFFFFFFFu;
@@ -544,6 +545,7 @@ __device__ void phase_fill_step(const Params& p, int bid, int nb, const SharedSt
         cand = vac < csize;
         if (!cand && fill && vac > 0) cand = __ldcg(&p.tile_prefix[g >> 3]) < queued;
         if (!cand && !do_fill) cand = __ldcg(&p.filled[g]) > 0;  // filled by a separate fill launch
+        if (!cand && do_step && p.policy != POLICY_NONE) cand = p.chunk_dirty[g] != 0;  // keys to reset
       }
       unsigned mask = __ballot_sync(0xffffffffu, cand);
       while (mask) {
