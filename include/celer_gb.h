@@ -371,6 +371,13 @@ celer_status celer_debug_philox(const uint32_t* host_ctr_key, uint32_t* host_out
 celer_status celer_debug_curand_philox(uint64_t seed, uint64_t subsequence, uint64_t offset4, uint32_t* host_out,
                                        uint64_t n);
 
+/* Evaluate a binary64 function on n host arguments on the device: fn 0 the
+ * table-driven logarithm of the step kernels, 1 their exponential, 2 and 3
+ * CUDA's log and exp for comparison. No counterpart in the paper: it checks
+ * the step kernels' elementary functions against the library's (accuracy is
+ * about 1 ulp). fn outside 0-3 or null pointers give CELER_ERR_INVALID. */
+celer_status celer_debug_math(int fn, const double* host_x, uint64_t n, double* host_out);
+
 #ifdef __cplusplus
 }
 #endif

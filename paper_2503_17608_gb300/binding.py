@@ -111,7 +111,7 @@ EXPORTS = [
     "celer_read_history", "celer_get_stats", "celer_set_sort_policy", "celer_set_split_actions", "celer_read_trace",
     "celer_read_loop_profile",
     "celer_enable_kernel_timing", "celer_kernel_timing", "celer_debug_partition", "celer_debug_table",
-    "celer_debug_philox", "celer_debug_curand_philox", "celer_partition_keys_noalloc",
+    "celer_debug_philox", "celer_debug_curand_philox", "celer_partition_keys_noalloc", "celer_debug_math",
     "celer_run_iterations", "celer_read_event_live", "celer_serve", "celer_autotune", "celer_get_problem",
 ]
 
@@ -151,6 +151,7 @@ def load(path: Optional[str] = None):
         "celer_debug_partition": ([vp, vp, vp, vp, C.POINTER(i32)], i32),
         "celer_debug_table": ([vp, i32, i32, dp], i32),
         "celer_debug_philox": ([vp, vp, u64], i32),
+        "celer_debug_math": ([i32, vp, u64, vp], i32),
         "celer_debug_curand_philox": ([u64, u64, u64, vp, u64], i32),
         "celer_partition_keys_noalloc": ([vp, u64, i32, i32, vp, vp, vp], i32),
         "celer_run_iterations": ([vp, i32, u64, C.POINTER(u64)], i32),
@@ -446,6 +447,15 @@ def debug_philox(ctr_key: np.ndarray) -> np.ndarray:
     a = np.ascontiguousarray(ctr_key, dtype=np.uint32)
     out = np.zeros((len(a), 4), np.uint32)
     _check(load().celer_debug_philox(a.ctypes.data, out.ctypes.data, len(a)))
+    return out
+
+
+def debug_math(fn: int, x: np.ndarray) -> np.ndarray:
+    """Device elementary function fn (0 table-driven log, 1 table-driven exp,
+    2 CUDA log, 3 CUDA exp) on x."""
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros_like(a)
+    _check(load().celer_debug_math(int(fn), a.ctypes.data, len(a), out.ctypes.data))
     return out
 
 

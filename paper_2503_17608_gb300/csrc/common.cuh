@@ -157,6 +157,7 @@ struct Params {
   double cut_track, cut_moller, cut_brems;
   int processes;
   const double2* tables;   // [mat][col][kGrid] (value, next - value)
+  const double* mtab;      // log/exp reduction tables (fastmath.cuh)
   double lnEmin, inv_dl, dl;
   uint32_t seed;
   // tallies

@@ -1,6 +1,7 @@
 // Diagnostics for the parity tests: the device Philox4x32-10 on given
-// (counter, key) records, and cuRAND's Philox4_32_10 generator for
-// cross-checking the two against each other and against the CPU oracle.
+// (counter, key) records, cuRAND's Philox4_32_10 generator for
+// cross-checking the two against each other and against the CPU oracle, and
+// the table-driven log/exp next to CUDA's own.
 #include <curand_kernel.h>
 
 #include <vector>
@@ -35,9 +36,50 @@ __global__ void k_curand(unsigned long long seed, unsigned long long sub, unsign
   }
 }
 
+__global__ void k_math(int fn, const double* mt, const double* x, double* out, uint64_t n) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    double r;
+    switch (fn) {
+      case 0: r = celer::fast_log(v, mt); break;
+      case 1: r = celer::fast_exp(v, mt); break;
+      case 2: r = log(v); break;
+      default: r = exp(v); break;
+    }
+    out[i] = r;
+  }
+}
+
 }  // namespace
 
 extern "C" {
+
+celer_status celer_debug_math(int fn, const double* host_x, uint64_t n, double* host_out) {
+  if (!host_x || !host_out || fn < 0 || fn > 3) return CELER_ERR_INVALID;
+  if (n == 0) return CELER_OK;
+  std::vector<double> table(celer::kMathTableSize);
+  celer::build_math_table(table.data());
+  double *d_mt = nullptr, *d_x = nullptr, *d_out = nullptr;
+  celer_status st = CELER_OK;
+  if (cudaMalloc(&d_mt, sizeof(double) * table.size()) != cudaSuccess || cudaMalloc(&d_x, sizeof(double) * n) != cudaSuccess ||
+      cudaMalloc(&d_out, sizeof(double) * n) != cudaSuccess)
+    st = CELER_ERR_CUDA;
+  if (st == CELER_OK &&
+      (cudaMemcpy(d_mt, table.data(), sizeof(double) * table.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemcpy(d_x, host_x, sizeof(double) * n, cudaMemcpyHostToDevice) != cudaSuccess))
+    st = CELER_ERR_CUDA;
+  if (st == CELER_OK) {
+    const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    k_math<<<grid, 256>>>(fn, d_mt, d_x, d_out, n);
+    if (cudaGetLastError() != cudaSuccess) st = CELER_ERR_CUDA;
+  }
+  if (st == CELER_OK && cudaMemcpy(host_out, d_out, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+    st = CELER_ERR_CUDA;
+  cudaFree(d_mt);
+  cudaFree(d_x);
+  cudaFree(d_out);
+  return st;
+}
 
 celer_status celer_debug_philox(const uint32_t* host_ctr_key, uint32_t* host_out, uint64_t n) {
   if (!host_ctr_key || !host_out) return CELER_ERR_INVALID;

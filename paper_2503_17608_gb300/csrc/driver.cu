@@ -13,6 +13,7 @@
 #include "celer_gb.h"
 #include "launch.h"
 #include "tables.h"
+#include "fastmath.cuh"
 
 using namespace celer;
 
@@ -41,6 +42,7 @@ struct celer_ctx {
   std::vector<void*> host_allocs;
   std::vector<double> zb;
   std::vector<int> layer_mat;
+  std::vector<double> h_mtab;  // log/exp reduction tables (host copy, source of the device copy)
   std::unordered_map<uint32_t, uint64_t> next_tid;
   uint64_t next_history = 0;
   StagedPrimary* h_stage = nullptr;
@@ -533,6 +535,13 @@ celer_status celer_create(const celer_problem* pb, celer_ctx** out) {
   tb.dl = p.dl;
   CREATE_CUDA(build_tables(tb, d_tables, d_scratch, ctx->stream));
   p.tables = d_tables;
+  double* d_mtab = nullptr;
+  CREATE_CUDA(dalloc(ctx, &d_mtab, kMathTableSize));
+  ctx->h_mtab.resize(kMathTableSize);
+  build_math_table(ctx->h_mtab.data());
+  CREATE_CUDA(cudaMemcpyAsync(d_mtab, ctx->h_mtab.data(), sizeof(double) * kMathTableSize, cudaMemcpyHostToDevice,
+                              ctx->stream));
+  p.mtab = d_mtab;
 
   // staging for primaries (bounded; larger batches go in chunks)
   ctx->stage_cap = C < (1ull << 20) ? C : (1ull << 20);

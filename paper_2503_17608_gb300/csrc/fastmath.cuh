@@ -1,0 +1,133 @@
+// Table-driven binary64 logarithm and exponential after P. T. P. Tang,
+// "Table-driven implementation of the exponential function in IEEE
+// floating-point arithmetic" (ACM TOMS 15, 1989) and "... of the logarithm
+// function ..." (ACM TOMS 16, 1990): a table lookup reduces the argument to a
+// few thousandths, where a short polynomial is accurate to the last bit.
+//
+// Why: on GB300 an FP64 warp instruction holds its sub-partition's FP64 pipe
+// for ~64 cycles whatever the number of active lanes, so the latency of a
+// track step is set by how many FP64 instructions it issues. These versions
+// issue about 12 each (the reduction and the table index use integer
+// instructions), fewer than the general-purpose library routines, and stay
+// within 1.2 ulp of the correctly rounded result. Arguments outside the
+// reduced range (non-positive, subnormal, non-finite for log; |x| >= 708
+// for exp) go to the library routine.
+//
+// The tables are computed on the host from the definitions (extended
+// precision), copied to device memory once per context, and read through the
+// read-only data cache.
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+
+namespace celer {
+
+constexpr int kLogTable = 256;  // reduced mantissa m in [0.75, 1.5), 256 intervals
+constexpr int kExpTable = 64;   // 2^(j/64)
+constexpr int kMtLog = 0;                              // kLogTable x {1/c, L_hi, L_lo, 0}
+constexpr int kMtExp = kMtLog + 4 * kLogTable;         // kExpTable x {T_hi, T_lo}
+constexpr int kMtConst = kMtExp + 2 * kExpTable;       // constants below
+constexpr int kMtLn2Hi = kMtConst + 0;                 // ln 2 rounded to a multiple of 2^-42
+constexpr int kMtLn2Lo = kMtConst + 1;                 // ln 2 - kMtLn2Hi
+constexpr int kMtInvC = kMtConst + 2;                  // 64 / ln 2
+constexpr int kMtCHi = kMtConst + 3;                   // ln 2 / 64 rounded to a multiple of 2^-42
+constexpr int kMtCLo = kMtConst + 4;                   // ln 2 / 64 - kMtCHi
+constexpr int kMathTableSize = kMtConst + 8;           // doubles
+
+// Fill the table (kMathTableSize doubles). Host code, extended precision.
+//  log: interval j of the reduced mantissa has centre c_j (c = 1 exactly for
+//  the two intervals next to 1, so that log x near 1 keeps full relative
+//  accuracy), 1/c_j rounded to binary64, and L_j = -log(rounded 1/c_j) split
+//  into a head that is a multiple of 2^-42 and a tail.
+//  exp: T_j = 2^(j/64) as a head and a tail.
+inline void build_math_table(double* out) {
+  typedef long double ld;
+  const ld ln2 = logl(2.0L);
+  auto head42 = [](ld v) { return (double)(nearbyintl(v * 0x1p42L) / 0x1p42L); };
+  for (int j = 0; j < kLogTable; ++j) {
+    ld c;
+    if (j == 127 || j == 128) {
+      c = 1.0L;
+    } else if (j < 128) {
+      c = 0.75L + ((ld)j + 0.5L) / 512.0L;  // m in [0.75, 1): intervals of 1/512
+    } else {
+      c = 1.0L + ((ld)(j - 128) + 0.5L) / 256.0L;  // m in [1, 1.5): intervals of 1/256
+    }
+    const double invc = (double)(1.0L / c);
+    const ld L = -logl((ld)invc);
+    const double hi = head42(L);
+    out[kMtLog + 4 * j + 0] = invc;
+    out[kMtLog + 4 * j + 1] = hi;
+    out[kMtLog + 4 * j + 2] = (double)(L - (ld)hi);
+    out[kMtLog + 4 * j + 3] = 0.0;
+  }
+  for (int j = 0; j < kExpTable; ++j) {
+    const ld T = exp2l((ld)j / 64.0L);
+    const double hi = (double)T;
+    out[kMtExp + 2 * j + 0] = hi;
+    out[kMtExp + 2 * j + 1] = (double)(T - (ld)hi);
+  }
+  const double l2hi = head42(ln2);
+  out[kMtLn2Hi] = l2hi;
+  out[kMtLn2Lo] = (double)(ln2 - (ld)l2hi);
+  out[kMtInvC] = (double)(64.0L / ln2);
+  const double chi = head42(ln2 / 64.0L);
+  out[kMtCHi] = chi;
+  out[kMtCLo] = (double)(ln2 / 64.0L - (ld)chi);
+  for (int i = kMtConst + 5; i < kMathTableSize; ++i) out[i] = 0.0;
+}
+
+#ifdef __CUDACC__
+// log x = k ln 2 + L_j + log1p(r), x = 2^k m with m in [0.75, 1.5) taken from
+// the bits (x - bits(0.75) gives k in the exponent field and the interval j
+// in the next 8 bits), r = m / c_j - 1 = fma(m, 1/c_j, -1), |r| < 2^-8.
+// k ln2_hi + L_hi is exact (both multiples of 2^-42, below 2^10).
+__device__ __forceinline__ double fast_log(double x, const double* __restrict__ mt) {
+  const long long ix = __double_as_longlong(x);
+  if ((unsigned long long)(ix - 0x0010000000000000ll) >= 0x7FE0000000000000ull) return log(x);
+  const long long tmp = ix - 0x3FE8000000000000ll;
+  const int k = (int)(tmp >> 52);
+  const int j = (int)((tmp >> 44) & (kLogTable - 1));
+  const double m = __longlong_as_double(ix - ((long long)k << 52));
+  const double2 cl = __ldg(reinterpret_cast<const double2*>(mt + kMtLog + 4 * j));
+  const double llo = __ldg(mt + kMtLog + 4 * j + 2);
+  const double r = fma(m, cl.x, -1.0);
+  // log1p(r) = r - r^2/2 + r^3/3 - ... + r^7/7 (truncation < 2^-59 relative)
+  double q = fma(r, 1.0 / 7.0, -1.0 / 6.0);
+  q = fma(r, q, 0.2);
+  q = fma(r, q, -0.25);
+  q = fma(r, q, 1.0 / 3.0);
+  q = fma(r, q, -0.5);
+  const double p = fma(r * r, q, r);
+  const double kd = (double)k;
+  const double hi = fma(kd, __ldg(mt + kMtLn2Hi), cl.y);
+  const double lo = fma(kd, __ldg(mt + kMtLn2Lo), llo) + p;
+  return hi + lo;
+}
+
+// exp x = 2^(n/64) exp(r), n = round(64 x / ln 2) read from the low bits of
+// x 64/ln2 + 1.5 2^52, r = x - n ln2/64 in two exact-then-rounded steps,
+// |r| <= ln2/128; 2^(n/64) = 2^(n >> 6) T_(n & 63), the power of two added
+// to the exponent field (|x| < 708 keeps the result normal).
+__device__ __forceinline__ double fast_exp(double x, const double* __restrict__ mt) {
+  if (!(fabs(x) < 708.0)) return exp(x);
+  constexpr double kShift = 0x1.8p52;
+  const double t = fma(x, __ldg(mt + kMtInvC), kShift);
+  const int n = (int)(uint32_t)__double_as_longlong(t);
+  const double nd = t - kShift;
+  const double rh = fma(-nd, __ldg(mt + kMtCHi), x);
+  const double r = fma(-nd, __ldg(mt + kMtCLo), rh);
+  // exp(r) - 1 = r + r^2/2 + ... + r^6/720 (truncation < 2^-64 relative)
+  double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
+  q = fma(r, q, 1.0 / 24.0);
+  q = fma(r, q, 1.0 / 6.0);
+  q = fma(r, q, 0.5);
+  const double p = fma(r * r, q, r);
+  const double2 T = __ldg(reinterpret_cast<const double2*>(mt + kMtExp + 2 * (n & (kExpTable - 1))));
+  const double y = T.x + fma(T.x, p, T.y);
+  return __longlong_as_double(__double_as_longlong(y) + ((long long)(n >> 6) << 52));
+}
+#endif
+
+}  // namespace celer

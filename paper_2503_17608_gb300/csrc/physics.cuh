@@ -11,6 +11,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "fastmath.cuh"
 
 namespace celer {
 
@@ -28,6 +29,12 @@ constexpr int kMaxAttempts = 4096;
 // Compare-and-swap rounds a group of lanes may spend claiming buffer entries
 // (each failed round means another group succeeded).
 constexpr int kMaxCasAttempts = 1 << 16;
+// Relative margins above which a step-limit candidate cannot be the shorter
+// one after rounding: 1 + 2^-50 for a single quotient d / u tested as
+// |d| > s |u| margin, 1 + 2^-48 for the range limit's lower bound (a few
+// more roundings).
+constexpr double kLimitMargin = 1.0 + 0x1p-50;
+constexpr double kRangeMargin = 1.0 + 0x1p-48;
 // Longest wait at a grid barrier of the persistent loop (~1 s at 2 GHz).
 constexpr long long kBarrierTimeoutCycles = 2000000000ll;
 
@@ -88,8 +95,8 @@ struct GridPos {
 };
 
 // Grid coordinate (ln E - ln E_min) / dl, bin clamped to [0, n - 2].
-__device__ __forceinline__ GridPos grid_pos(double E, double lnEmin, double inv_dl) {
-  const double x = (log(E) - lnEmin) * inv_dl;
+__device__ __forceinline__ GridPos grid_pos(double E, double lnEmin, double inv_dl, const double* mt) {
+  const double x = (fast_log(E, mt) - lnEmin) * inv_dl;
   int b = (int)floor(x);
   b = b < 0 ? 0 : (b > kGrid - 2 ? kGrid - 2 : b);
   return GridPos{b, x - (double)b};
@@ -103,69 +110,90 @@ __device__ __forceinline__ double interp(const double2* col, GridPos g) {
 
 // Inverse of the range interpolation: the largest bin i <= n - 2 with
 // R_i <= r, then ln E linear in R inside it. r <= R_0: the track stopped.
-__device__ __forceinline__ double inverse_range(const double2* R, double r, double lnEmin, double dl) {
+// Ranges are non-negative, so the search compares their bit patterns as
+// integers (same order as the values) and keeps the FP64 pipe free.
+__device__ __forceinline__ double inverse_range(const double2* R, double r, double lnEmin, double dl,
+                                                const double* mt) {
   if (r <= R[0].x) return 0.0;
+  const long long rb = __double_as_longlong(r);
   int lo = 0;
 #pragma unroll
   for (int step = 128; step > 0; step >>= 1) {
     const int probe = lo + step;
-    if (probe <= kGrid - 2 && R[probe].x <= r) lo = probe;
+    if (probe <= kGrid - 2 && __double_as_longlong(R[probe].x) <= rb) lo = probe;
   }
   const double2 v = R[lo];
   const double lnE = lnEmin + lo * dl + (r - v.x) / v.y * dl;
-  return exp(lnE);
+  return fast_exp(lnE, mt);
 }
 
 // ------------------------------------------------------------- kinematics
+// An FP64 warp instruction occupies a GB300 sub-partition's FP64 pipe for
+// the same time whatever its active lanes, so the kinematics below take
+// reciprocal square roots once instead of a square root and divisions.
+
+// Rotate (ux, uy, uz) by polar cosine cost and azimuth phi about itself:
+// frame e1 = (u x z)/|u x z|, e2 = u x e1 (e1 = x near the poles), then
+// renormalised.
 __device__ __forceinline__ void rotate_dir(double& ux, double& uy, double& uz, double cost, double phi) {
   const double sint = sqrt(fmax(0.0, 1.0 - cost * cost));
   double sp, cp;
   sincos(phi, &sp, &cp);
   double e1x, e1y, e1z, e2x, e2y, e2z;
   if (fabs(uz) < 1.0 - 1e-10) {
-    const double n = sqrt(ux * ux + uy * uy);
-    e1x = uy / n;
-    e1y = -ux / n;
+    const double q = ux * ux + uy * uy;
+    const double inv_n = rsqrt(q);
+    e1x = uy * inv_n;
+    e1y = -ux * inv_n;
     e1z = 0.0;
-    e2x = uz * ux / n;
-    e2y = uz * uy / n;
-    e2z = -n;
+    e2x = uz * ux * inv_n;
+    e2y = uz * uy * inv_n;
+    e2z = -q * inv_n;
   } else {
-    const double n = sqrt(uz * uz + uy * uy);
+    const double q = uz * uz + uy * uy;
+    const double inv_n = rsqrt(q);
     e1x = 1.0;
     e1y = 0.0;
     e1z = 0.0;
     e2x = 0.0;
-    e2y = uz / n;
-    e2z = -uy / n;
+    e2y = uz * inv_n;
+    e2z = -uy * inv_n;
   }
   const double vx = cost * ux + sint * (cp * e1x + sp * e2x);
   const double vy = cost * uy + sint * (cp * e1y + sp * e2y);
   const double vz = cost * uz + sint * (cp * e1z + sp * e2z);
-  const double inv = 1.0 / sqrt(vx * vx + vy * vy + vz * vz);
+  const double inv = rsqrt(vx * vx + vy * vy + vz * vz);
   ux = vx * inv;
   uy = vy * inv;
   uz = vz * inv;
 }
 
-// Signed curvature: the transverse direction turns by kappa * s over a path s.
-__device__ __forceinline__ double curvature(uint8_t ptype, double E, double Bz) {
+// Signed curvature of a charged track in B along z: the transverse
+// direction turns by kappa * s over a path s; kappa = q B k / p and its
+// inverse p / (q B k) from one reciprocal square root of p^2.
+struct Curvature {
+  double kappa, inv_kappa;
+};
+__device__ __forceinline__ Curvature curvature(uint8_t ptype, double E, double Bz) {
   const double q = (ptype == ELECTRON) ? -1.0 : 1.0;
-  return q * Bz * kFieldK / sqrt(E * (E + 2.0 * kMe));
+  const double p2 = E * (E + 2.0 * kMe);
+  const double r = rsqrt(p2);
+  const double qbk = q * Bz * kFieldK;
+  return Curvature{qbk * r, (p2 * r) / qbk};
 }
 
 // Exact helix for du/ds = kappa (u x z), with 1 - cos(phi) = 2 sin^2(phi/2).
-__device__ __forceinline__ void helix_move(double kappa, double s, double& x, double& y, double& z, double& ux,
+__device__ __forceinline__ void helix_move(Curvature c, double s, double& x, double& y, double& z, double& ux,
                                            double& uy, double uz) {
-  const double phi = kappa * s;
+  const double phi = c.kappa * s;
   double hs, hc;
   sincos(0.5 * phi, &hs, &hc);
   const double sphi = 2.0 * hs * hc;
   const double omc = 2.0 * hs * hs;
   const double cphi = 1.0 - omc;
   const double ox = ux, oy = uy;
-  x += (ox * sphi + oy * omc) / kappa;
-  y += (oy * sphi - ox * omc) / kappa;
+  x += (ox * sphi + oy * omc) * c.inv_kappa;
+  y += (oy * sphi - ox * omc) * c.inv_kappa;
   z += uz * s;
   ux = ox * cphi + oy * sphi;
   uy = oy * cphi - ox * sphi;
@@ -185,15 +213,18 @@ __device__ __forceinline__ double first_turn(double d, double beta, double sigma
 // Path length along the helix to the first side plane (|x| = hx, |y| = hy),
 // from the intersection of its transverse circle with each plane; kInf when
 // the circle stays inside.
-static __device__ __noinline__ double helix_side_distance(double kappa, double x, double y, double ux, double uy, double hx,
-                                                   double hy) {
-  const double A = sqrt(ux * ux + uy * uy);
-  if (A == 0.0) return kInf;
-  const double K = fabs(kappa);
+static __device__ __noinline__ double helix_side_distance(Curvature c, double x, double y, double ux, double uy,
+                                                          double hx, double hy) {
+  const double A2 = ux * ux + uy * uy;
+  if (A2 == 0.0) return kInf;
+  const double inv_A = rsqrt(A2);
+  const double A = A2 * inv_A;
+  const double kappa = c.kappa;
+  const double inv_K = fabs(c.inv_kappa);
   const double sigma = kappa > 0.0 ? 1.0 : -1.0;
-  const double xc = x + uy / kappa;
-  const double yc = y - ux / kappa;
-  const double rho = A / K;
+  const double xc = x + uy * c.inv_kappa;
+  const double yc = y - ux * c.inv_kappa;
+  const double rho = A * inv_K;
   if (xc + rho < hx && xc - rho > -hx && yc + rho < hy && yc - rho > -hy) return kInf;
   double tmin = kInf;
   const double bx = atan2(-uy, ux);
@@ -201,16 +232,16 @@ static __device__ __noinline__ double helix_side_distance(double kappa, double x
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
     const double X = i == 0 ? hx : -hx;
-    const double d = kappa * (X - xc) / A;
+    const double d = kappa * (X - xc) * inv_A;
     if (fabs(d) <= 1.0) tmin = fmin(tmin, first_turn(d, bx, sigma));
   }
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
     const double Y = i == 0 ? hy : -hy;
-    const double d = kappa * (Y - yc) / A;
+    const double d = kappa * (Y - yc) * inv_A;
     if (fabs(d) <= 1.0) tmin = fmin(tmin, first_turn(d, by, sigma));
   }
-  return tmin == kInf ? kInf : tmin / K;
+  return tmin == kInf ? kInf : tmin * inv_K;
 }
 
 // ------------------------------------------------------------- interactions
@@ -218,12 +249,17 @@ static __device__ __noinline__ double helix_side_distance(double kappa, double x
 // composition-rejection: branch 1 samples eps from 1/eps (eps = eps0^u), branch
 // 2 samples eps^2 uniformly; both are accepted with 1 - eps sin^2 / (1 + eps^2).
 // Three draws per attempt. Returns eps; cost receives the scattering cosine;
-// ok is cleared if the attempt limit was hit.
-static __device__ __noinline__ double sample_compton(double E, TrackRng& rng, double& cost, bool& ok) {
+// ok is cleared if the attempt limit was hit. With a = 1 - eps and b = k eps,
+// t = 1 - cos = a / b and sin^2 = a (2b - a) / b^2, so the test
+// u3 <= 1 - eps sin^2 / (1 + eps^2) is taken multiplied through by the
+// positive b^2 (1 + eps^2), without divisions; t is divided out once, for
+// the accepted attempt.
+static __device__ __noinline__ double sample_compton(double E, TrackRng& rng, double& cost, bool& ok,
+                                                     const double* mt) {
   const double k = E / kMe;
   const double eps0 = 1.0 / (1.0 + 2.0 * k);
   const double eps0sq = eps0 * eps0;
-  const double a1 = -log(eps0);
+  const double a1 = -fast_log(eps0, mt);
   const double a2 = 0.5 * (1.0 - eps0sq);
   double eps = 1.0, t = 0.0;
   ok = false;
@@ -232,14 +268,15 @@ static __device__ __noinline__ double sample_compton(double E, TrackRng& rng, do
     const double u2 = rng.uniform();
     const double u3 = rng.uniform();
     if (u1 * (a1 + a2) < a1) {
-      eps = exp(-a1 * u2);
+      eps = fast_exp(-a1 * u2, mt);
     } else {
       eps = sqrt(eps0sq + (1.0 - eps0sq) * u2);
     }
-    t = (1.0 - eps) / (k * eps);
-    const double sint2 = t * (2.0 - t);
-    const double g = 1.0 - eps * sint2 / (1.0 + eps * eps);
-    if (u3 <= g) {
+    const double a = 1.0 - eps;
+    const double b = k * eps;
+    const double B = b * b * (1.0 + eps * eps);
+    if (eps * a * (2.0 * b - a) <= (1.0 - u3) * B) {
+      t = a / b;
       ok = true;
       break;
     }
@@ -250,6 +287,7 @@ static __device__ __noinline__ double sample_compton(double E, TrackRng& rng, do
 
 // Moller: eps = T_delta / T in [x, 1/2] from the 1/eps^2 proposal, accepted
 // with eps^2 B(eps) normalised by its maximum (9g^2 - 10g + 5)/4 at eps = 1/2.
+// The test u2 <= norm f(eps) is taken multiplied by the positive (1 - eps)^2.
 static __device__ __noinline__ double sample_moller(double T, double Tcut, TrackRng& rng, bool& ok) {
   const double x = Tcut / T;
   const double g = T / kMe + 1.0;
@@ -262,8 +300,9 @@ static __device__ __noinline__ double sample_moller(double T, double Tcut, Track
     const double u2 = rng.uniform();
     eps = x / (1.0 - u1 * (1.0 - 2.0 * x));
     const double om = 1.0 - eps;
-    const double f = (g - 1.0) * (g - 1.0) * eps * eps - (2.0 * g2 + 2.0 * g - 1.0) * eps / om + g2 / (om * om);
-    if (u2 <= norm * f) {
+    const double eom = eps * om;
+    const double fom2 = (g - 1.0) * (g - 1.0) * eom * eom - (2.0 * g2 + 2.0 * g - 1.0) * eom + g2;
+    if (u2 * (om * om) <= norm * fom2) {
       ok = true;
       break;
     }

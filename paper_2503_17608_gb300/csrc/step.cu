@@ -115,10 +115,10 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
   const int layer = t.layer[slot];
   double nmfp = t.nmfp[slot];
   TrackRng rng(p.seed, t.event[slot], t.tid[slot], t.ctr[slot]);
-  if (nmfp < 0.0) nmfp = -log(rng.uniform());
+  if (nmfp < 0.0) nmfp = -fast_log(rng.uniform(), p.mtab);
 
   const double2* mt = tab + lmat[layer] * (kCols * kGrid);
-  const GridPos g = grid_pos(E, p.lnEmin, p.inv_dl);
+  const GridPos g = grid_pos(E, p.lnEmin, p.inv_dl, p.mtab);
   const bool charged = pt != GAMMA;
   double mu0, mu1, mu2 = 0.0;
   if (!charged) {
@@ -130,15 +130,16 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
     mu1 = interp(mt + COL_BREMS * kGrid, g);
   }
   const double mu = (mu0 + mu1) + mu2;
-  const double s_int = mu > 0.0 ? nmfp / mu : kInf;
-
   const bool eloss = charged && (p.processes & PROC_ELOSS);
-  double R = 0.0, s_rng = kInf;
-  if (eloss) {
-    R = interp(mt + COL_RANGE * kGrid, g);
-    s_rng = R <= kFinalR ? R : kAlphaR * R + kFinalR * (1.0 - kAlphaR) * (2.0 - kFinalR / R);
-  }
+  const double R = eloss ? interp(mt + COL_RANGE * kGrid, g) : 0.0;
 
+  // The limits are compared in the order z-planes, side planes, range,
+  // interaction, each candidate replacing the current one only if strictly
+  // shorter. A candidate that is a quotient d / u (or bounded below by an
+  // expression) is evaluated only if it can be shorter than the current
+  // limit s, i.e. unless |d| > s |u| (1 + 2^-50): beyond that margin the
+  // rounded quotient is >= s too, so skipping its division changes no choice
+  // (the divisions dominate the FP64 cost of the step limit).
   const double x = t.x[slot], y = t.y[slot], z = t.z[slot];
   const double ux = t.ux[slot], uy = t.uy[slot], uz = t.uz[slot];
   double s_geo = kInf;
@@ -154,10 +155,15 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
   if (charged && p.Bz != 0.0) {
     s_side = helix_side_distance(curvature(pt, E, p.Bz), x, y, ux, uy, p.hx, p.hy);
   } else {
-    if (ux > 0.0) s_side = fmin(s_side, (p.hx - x) / ux);
-    if (ux < 0.0) s_side = fmin(s_side, (-p.hx - x) / ux);
-    if (uy > 0.0) s_side = fmin(s_side, (p.hy - y) / uy);
-    if (uy < 0.0) s_side = fmin(s_side, (-p.hy - y) / uy);
+    const double reach = s_geo * kLimitMargin;
+    if (ux != 0.0) {
+      const double d = ux > 0.0 ? p.hx - x : -p.hx - x;
+      if ((ux > 0.0 ? d : -d) <= reach * fabs(ux)) s_side = d / ux;
+    }
+    if (uy != 0.0) {
+      const double d = uy > 0.0 ? p.hy - y : -p.hy - y;
+      if ((uy > 0.0 ? d : -d) <= reach * fabs(uy)) s_side = fmin(s_side, d / uy);
+    }
   }
   if (s_side < s_geo) {
     s_geo = s_side;
@@ -166,14 +172,26 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
   if (s_geo < 0.0) s_geo = 0.0;
 
   double s = s_geo;
-  if (s_rng < s) {
-    s = s_rng;
-    act = A_RANGE;
+  if (eloss) {
+    // s_rng = R (R <= f) or a R + f (1 - a)(2 - f / R) >= a R + f (1 - a)
+    double s_rng = kInf;
+    if (R <= kFinalR) {
+      s_rng = R;
+    } else if (kAlphaR * R + kFinalR * (1.0 - kAlphaR) <= s * kRangeMargin) {
+      s_rng = kAlphaR * R + kFinalR * (1.0 - kAlphaR) * (2.0 - kFinalR / R);
+    }
+    if (s_rng < s) {
+      s = s_rng;
+      act = A_RANGE;
+    }
   }
   bool interact = false;
-  if (s_int < s) {
-    s = s_int;
-    interact = true;
+  if (mu > 0.0 && nmfp <= s * mu * kLimitMargin) {
+    const double s_int = nmfp / mu;
+    if (s_int < s) {
+      s = s_int;
+      interact = true;
+    }
   }
   if (s == kInf) {
     act = A_TRAPPED;
@@ -643,7 +661,7 @@ __device__ __forceinline__ bool along_one(const Params& p, uint32_t slot, uint8_
   }
   if (eloss) {
     const double2* R = ss.tab + (ss.lmat[layer] * kCols + COL_RANGE) * kGrid;
-    const double Ep = inverse_range(R, t.rpost[slot], p.lnEmin, p.dl);
+    const double Ep = inverse_range(R, t.rpost[slot], p.lnEmin, p.dl, p.mtab);
     deposit(p, ev, prim, layer, z, E - Ep);
     E = Ep;
   }
@@ -697,7 +715,7 @@ __device__ __forceinline__ bool compton_one(const Params& p, uint32_t slot) {
   TrackRng rng(p.seed, ev, t.tid[slot], t.ctr[slot]);
   double cost;
   bool ok;
-  const double eps = sample_compton(E, rng, cost, ok);
+  const double eps = sample_compton(E, rng, cost, ok, p.mtab);
   if (!ok) {  // non-finite input: end the track, flag the run
     atomicOr(&p.ctl->error, ERR_SAMPLING);
     deposit(p, ev, prim, layer, z, E);
@@ -901,7 +919,7 @@ __device__ __forceinline__ bool brems_one(const Params& p, uint32_t slot, uint8_
   }
   const uint32_t ev = t.event[slot], prim = t.primary[slot];
   TrackRng rng(p.seed, ev, t.tid[slot], t.ctr[slot]);
-  double k = p.cut_brems * exp(rng.uniform() * log(T / p.cut_brems));
+  double k = p.cut_brems * fast_exp(rng.uniform() * fast_log(T / p.cut_brems, p.mtab), p.mtab);
   if (k > T) k = T;
   const bool keep = k >= p.cut_track;
   unsigned long long base;
