@@ -353,10 +353,13 @@ celer_status celer_autotune(const celer_problem* base, const celer_primary* prim
 
 /* Partition of the last iteration: per-slot key as used by the partition
  * (n_slots bytes; slots vacant at that time carry the last, vacant key), the permutation
- * (n_slots entries; the first offsets[n_keys - 1] are the live slots) and
- * the n_keys + 1 offsets. Valid only for the sorted policies. */
+ * (n_slots entries; the first offsets[n_keys - 1] are the live slots), the
+ * n_keys + 1 offsets, and the number of blocks B that counted the keys.
+ * Within a key the slots are ordered by the block owning their 32-slot chunk
+ * (chunk c: block c mod B), then by chunk, then by slot. Valid only for the
+ * sorted policies. */
 celer_status celer_debug_partition(celer_ctx* ctx, uint8_t* keys_out, uint32_t* perm_out, uint32_t* offsets_out,
-                                   int* n_keys);
+                                   int* n_keys, int* n_blocks);
 
 /* Device table of material mat, column col (0 Compton, 1 photoelectric,
  * 2 pair, 3 Moller, 4 brems, 5 range), 200 values into host memory. */

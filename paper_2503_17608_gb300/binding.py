@@ -148,7 +148,7 @@ def load(path: Optional[str] = None):
         "celer_read_trace": ([vp, vp, u64, C.POINTER(u64)], i32),
         "celer_enable_kernel_timing": ([vp, i32], i32),
         "celer_kernel_timing": ([vp, C.POINTER(C.c_char_p), dp, C.POINTER(u64), i32, C.POINTER(i32)], i32),
-        "celer_debug_partition": ([vp, vp, vp, vp, C.POINTER(i32)], i32),
+        "celer_debug_partition": ([vp, vp, vp, vp, C.POINTER(i32), C.POINTER(i32)], i32),
         "celer_debug_table": ([vp, i32, i32, dp], i32),
         "celer_debug_philox": ([vp, vp, u64], i32),
         "celer_debug_math": ([i32, vp, u64, vp], i32),
@@ -395,8 +395,10 @@ class Context:
         perm = np.zeros(N, np.uint32)
         offs = np.zeros(17, np.uint32)
         nk = C.c_int()
+        nb = C.c_int()
         _check(load().celer_debug_partition(self._h, keys.ctypes.data, perm.ctypes.data, offs.ctypes.data,
-                                            C.byref(nk)), self._h)
+                                            C.byref(nk), C.byref(nb)), self._h)
+        self.partition_blocks = nb.value
         return keys, perm, offs[:nk.value + 1]
 
     def debug_table(self, mat: int, col: int):

@@ -105,7 +105,7 @@ struct Ctl {
   unsigned int done_a, done_c;       // last-block tickets of the fill/step-limit and step phases
   unsigned long long total_vacant;   // vacant slots (scanned at the end of an iteration)
   unsigned long long filled_total;   // slots filled in the current iteration
-  unsigned int pad;
+  unsigned int part_blocks;          // blocks that counted the last partition (chunk g: block g mod it)
   unsigned long long trace_count;
   unsigned long long last_steps_iter;          // copies of the last finished iteration's counters
   unsigned int last_n_deferred;
@@ -138,15 +138,15 @@ struct Params {
   uint32_t* filled;        // slots filled per chunk in the current iteration, n_chunks
   uint32_t* tile_vacant;   // vacant slots per 256-slot tile, n_tiles
   unsigned long long* tile_prefix;  // vacant slots before each tile, n_tiles (scanned once per iteration)
-  uint8_t* tile_live;      // 1 if the tile holds a live or waiting track after the fill
-  uint8_t* chunk_dirty;    // 1 if the chunk's stored keys may still name live keys (n_chunks)
+  uint8_t* chunk_dirty;    // 1 if the chunk's stored keys may name live keys (n_chunks); after
+                           // phase A: 1 exactly for the chunks holding live keys
   unsigned int* barrier;   // grid barrier state of the persistent loop: count, generation, abort
   // partition
   int policy;
   int n_keys;
   uint32_t* perm;          // n_slots
-  uint32_t* tile_counts;   // live-key counts per tile, (n_keys - 1) * n_tiles, key major
-  uint32_t* tile_offsets;  // their exclusive scan: output position of each (key, tile)
+  uint32_t* block_counts;  // live-key counts per counting block, (n_keys - 1) x blocks, key major
+  uint32_t* block_offsets; // their exclusive scan: each block's first position per key
   // geometry
   int n_layers;
   int n_materials;

@@ -471,7 +471,6 @@ celer_status celer_create(const celer_problem* pb, celer_ctx** out) {
   CREATE_CUDA(dalloc(ctx, &p.filled, p.n_chunks));
   CREATE_CUDA(dalloc(ctx, &p.tile_vacant, p.n_tiles));
   CREATE_CUDA(dalloc(ctx, &p.tile_prefix, p.n_tiles));
-  CREATE_CUDA(dalloc(ctx, &p.tile_live, p.n_tiles));
   CREATE_CUDA(dalloc(ctx, &p.chunk_dirty, p.n_chunks));
   CREATE_CUDA(cudaMemsetAsync(p.chunk_dirty, 1, p.n_chunks, ctx->stream));  // every key starts unset
   CREATE_CUDA(dalloc(ctx, &p.barrier, 4));
@@ -494,8 +493,11 @@ celer_status celer_create(const celer_problem* pb, celer_ctx** out) {
     CREATE_CUDA(cudaMemcpy(p.tile_prefix, pre.data(), sizeof(unsigned long long) * p.n_tiles, cudaMemcpyHostToDevice));
   }
   CREATE_CUDA(dalloc(ctx, &p.perm, N));
-  CREATE_CUDA(dalloc(ctx, &p.tile_counts, (size_t)kKeysFull * p.n_tiles));
-  CREATE_CUDA(dalloc(ctx, &p.tile_offsets, (size_t)kKeysFull * p.n_tiles));
+  // per-(key, block) partition counts: blocks of phase A, at most one per tile
+  // or the persistent grid
+  const size_t max_blocks = p.n_tiles > 4096 ? p.n_tiles : 4096;
+  CREATE_CUDA(dalloc(ctx, &p.block_counts, (size_t)kKeysFull * max_blocks));
+  CREATE_CUDA(dalloc(ctx, &p.block_offsets, (size_t)kKeysFull * max_blocks));
   double* d_zb = nullptr;
   int32_t* d_lmat = nullptr;
   CREATE_CUDA(dalloc(ctx, &d_zb, L + 1));
@@ -889,8 +891,8 @@ celer_status celer_kernel_timing(celer_ctx* ctx, const char** names, double* tot
 }
 
 celer_status celer_debug_partition(celer_ctx* ctx, uint8_t* keys_out, uint32_t* perm_out, uint32_t* offsets_out,
-                                   int* n_keys) {
-  if (!ctx || !keys_out || !perm_out || !offsets_out || !n_keys) return CELER_ERR_INVALID;
+                                   int* n_keys, int* n_blocks) {
+  if (!ctx || !keys_out || !perm_out || !offsets_out || !n_keys || !n_blocks) return CELER_ERR_INVALID;
   if (!policy_sorted(ctx->p.policy)) return fail(ctx, CELER_ERR_STATE, "no partition under policy NONE");
   celer_status st = read_ctl(ctx);
   if (st != CELER_OK) return st;
@@ -899,6 +901,7 @@ celer_status celer_debug_partition(celer_ctx* ctx, uint8_t* keys_out, uint32_t* 
   CELER_CUDA(ctx, cudaMemcpyAsync(perm_out, ctx->p.perm, sizeof(uint32_t) * N, cudaMemcpyDeviceToHost, ctx->stream));
   CELER_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   *n_keys = ctx->p.n_keys;
+  *n_blocks = (int)ctx->h_ctl->part_blocks;
   for (int k = 0; k <= ctx->p.n_keys; ++k) offsets_out[k] = ctx->h_ctl->offsets[k];
   return CELER_OK;
 }

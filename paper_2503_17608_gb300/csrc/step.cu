@@ -321,7 +321,7 @@ struct ChunkWalk {
 __device__ __forceinline__ void fill_and_limit_chunk(const Params& p, uint32_t g, const SharedStatic& ss, bool fill,
                                                      bool do_step, unsigned long long head,
                                                      unsigned long long queued, unsigned* s_acts,
-                                                     unsigned long long& my_steps) {
+                                                     unsigned* s_keys, unsigned long long& my_steps) {
   const int lane = threadIdx.x & 31;
   const uint32_t slot = g * 32u + lane;
   const bool real = slot < p.n_slots;
@@ -371,7 +371,6 @@ __device__ __forceinline__ void fill_and_limit_chunk(const Params& p, uint32_t g
   if (!do_step) return;
   const bool sorted = p.policy != POLICY_NONE;
   const uint8_t vacant_key = p.policy == POLICY_ACTION ? KA_VACANT : K_VACANT_FULL;
-  const uint32_t tile = g >> 3;
   const unsigned csize = (p.n_slots - g * 32u) < 32u ? (p.n_slots - g * 32u) : 32u;
   const bool live = __ldcg(&p.vacant[g]) < csize || nfill > 0;  // warp-uniform
   uint8_t key = vacant_key;
@@ -390,17 +389,15 @@ __device__ __forceinline__ void fill_and_limit_chunk(const Params& p, uint32_t g
         if (sorted) key = key_of(p.policy, p.trk.ptype[slot], act);
       }
     }
-    if (sorted && lane == 0) p.tile_live[tile] = 1;
   }
   if (sorted) {
     if (real) p.trk.key[slot] = key;
     if (lane == 0) p.chunk_dirty[g] = live ? 1 : 0;
-    // only live keys are counted: the vacant key is the last one, so its
-    // slots need no position
+    // only live keys are counted (per block, for the scatter): the vacant
+    // key is the last one, so its slots need no position
     const unsigned k = (real && key != vacant_key) ? (unsigned)key : 0xFFFFFFFFu;
     const unsigned peers = __match_any_sync(0xffffffffu, k);
-    if (k != 0xFFFFFFFFu && lane == __ffs(peers) - 1)
-      atomicAdd(&p.tile_counts[key * p.n_tiles + tile], (unsigned)__popc(peers));
+    if (k != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&s_keys[k], (unsigned)__popc(peers));
   }
 }
 
@@ -488,10 +485,11 @@ __device__ void scan_vacancy(const Params& p) {
 }
 
 // Bookkeeping at the end of phase A, by one block: commit the initializers
-// taken, scan the per-(key, tile) counts of the live keys in key-major order
-// into output positions and key offsets, and decide whether this
-// iteration's secondaries are sure to fit.
-__device__ void bookkeeping_after_fill_step(const Params& p, bool did_fill) {
+// taken, scan the per-(key, block) counts of the live keys (nb blocks counted
+// them) in key-major order into each block's first output position per key
+// and the key offsets, and decide whether this iteration's secondaries are
+// sure to fit.
+__device__ void bookkeeping_after_fill_step(const Params& p, bool did_fill, int nb) {
   Ctl* c = p.ctl;
   if (did_fill && threadIdx.x == 0) {
     const unsigned long long queued = c->tail - c->head;
@@ -504,11 +502,13 @@ __device__ void bookkeeping_after_fill_step(const Params& p, bool did_fill) {
     c->total_vacant = tv - take;
   }
   if (p.policy != POLICY_NONE) {
-    uint32_t* offs = p.tile_offsets;
+    uint32_t* offs = p.block_offsets;
     const int live_keys = p.n_keys - 1;  // the last key is the vacant one
     const unsigned long long total = block_scan_counts(
-        p.tile_counts, (uint32_t)live_keys * p.n_tiles, [offs](uint32_t i, unsigned long long v) { offs[i] = (uint32_t)v; });
-    if ((int)threadIdx.x < live_keys) c->offsets[threadIdx.x] = offs[threadIdx.x * p.n_tiles];
+        p.block_counts, (uint32_t)(live_keys * nb), [offs](uint32_t i, unsigned long long v) { offs[i] = (uint32_t)v; });
+    __syncthreads();
+    if ((int)threadIdx.x < live_keys) c->offsets[threadIdx.x] = offs[threadIdx.x * nb];
+    if (threadIdx.x == 0) c->part_blocks = (unsigned)nb;
     if ((int)threadIdx.x == live_keys) {
       c->offsets[live_keys] = (unsigned)total;
       c->offsets[p.n_keys] = p.n_slots;
@@ -540,11 +540,13 @@ __device__ __forceinline__ void apply_fills(const Params& p, int bid, int nb) {
 __device__ void phase_fill_step(const Params& p, int bid, int nb, const SharedStatic& ss, bool do_fill, bool do_step,
                                 bool bookkeeping) {
   __shared__ unsigned s_acts[A_COUNT];
+  __shared__ unsigned s_keys[kMaxKeys];
   Ctl* c = p.ctl;
   const unsigned long long head = c->head;
   const unsigned long long queued = c->tail - head;
   const bool fill = do_fill && queued > 0;
   if (threadIdx.x < A_COUNT) s_acts[threadIdx.x] = 0;
+  if (threadIdx.x < kMaxKeys) s_keys[threadIdx.x] = 0;
   __syncthreads();
   unsigned long long my_steps = 0;
   if (fill || do_step) {
@@ -569,7 +571,7 @@ __device__ void phase_fill_step(const Params& p, int bid, int nb, const SharedSt
       while (mask) {
         const int j = __ffs(mask) - 1;
         mask &= mask - 1;
-        fill_and_limit_chunk(p, base + (uint32_t)j * step, ss, fill, do_step, head, queued, s_acts, my_steps);
+        fill_and_limit_chunk(p, base + (uint32_t)j * step, ss, fill, do_step, head, queued, s_acts, s_keys, my_steps);
       }
     }
   }
@@ -577,50 +579,76 @@ __device__ void phase_fill_step(const Params& p, int bid, int nb, const SharedSt
   if (do_step) {
     if (threadIdx.x < A_COUNT && s_acts[threadIdx.x] != 0)
       atomicAdd(&c->action_count[threadIdx.x], s_acts[threadIdx.x]);
+    if (p.policy != POLICY_NONE && (int)threadIdx.x < p.n_keys - 1)
+      p.block_counts[threadIdx.x * nb + bid] = s_keys[threadIdx.x];
     flush_counter(&c->steps_iter, my_steps, false);
   }
   if (bookkeeping && last_block_done(&c->done_a, nb)) {
     const long long t0 = clock64();
-    bookkeeping_after_fill_step(p, true);
+    bookkeeping_after_fill_step(p, true, nb);
     if (threadIdx.x == 0) c->book_total[0] += (unsigned long long)(clock64() - t0);
   }
 }
 
-// Stable scatter of slot indices into the partition: position = tile's
-// offset for the key + same-key slots in earlier warps + same-key lanes below.
+// Scatter slot indices into the partition. Block b owns chunks b, b + nb,
+// b + 2 nb, ... (the chunks it counted in phase A). It walks those that hold
+// live keys in that order, one per warp, and places each live slot at: the
+// block's first position for the key (from the scan) + the block's same-key
+// slots placed so far (a running cursor) + same-key slots of earlier warps in
+// this round + same-key lanes below. The order within a key is thus by owning
+// block, then chunk, then lane: deterministic, and no scan over all tiles.
 __device__ void phase_scatter(const Params& p, int bid, int nb) {
   __shared__ unsigned s_cnt[kTile / 32][kMaxKeys];
+  __shared__ unsigned s_cursor[kMaxKeys];
+  __shared__ unsigned s_wlive[kTile / 32];
   __shared__ uint32_t s_live[kTile];
-  __shared__ unsigned s_nlive;
-  const uint8_t vacant_key = p.policy == POLICY_ACTION ? KA_VACANT : K_VACANT_FULL;
+  const int live_keys = p.n_keys - 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // this block's tiles are bid, bid + nb, ...: read their live flags in
-  // parallel (kTile at a time), then visit only the live ones
-  for (uint32_t base = bid; base < p.n_tiles; base += nb * kTile) {
-    if (threadIdx.x == 0) s_nlive = 0;
+  const int nwarps = (int)(blockDim.x >> 5);
+  const unsigned lt = (1u << lane) - 1u;
+  if ((int)threadIdx.x < live_keys) s_cursor[threadIdx.x] = p.block_offsets[threadIdx.x * nb + bid];
+  const uint32_t n_own = (uint32_t)bid < p.n_chunks ? (p.n_chunks - (uint32_t)bid + nb - 1) / nb : 0u;
+  for (uint32_t m0 = 0; m0 < n_own; m0 += blockDim.x) {
+    // this round's live chunks of the block, compacted in order
+    const uint32_t m = m0 + threadIdx.x;
+    const uint32_t gm = (uint32_t)bid + (uint32_t)nb * m;
+    const bool live = m < n_own && p.chunk_dirty[gm] != 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, live);
+    __syncthreads();  // the previous round is done with s_wlive and s_live
+    if (lane == 0) s_wlive[warp] = __popc(bal);
     __syncthreads();
-    const uint32_t t = base + threadIdx.x * (uint32_t)nb;
-    if (t < p.n_tiles && p.tile_live[t]) {
-      s_live[atomicAdd(&s_nlive, 1u)] = t;
-      p.tile_live[t] = 0;
+    unsigned before = 0, nlive = 0;
+    for (int w = 0; w < nwarps; ++w) {
+      const unsigned cw = s_wlive[w];
+      before += w < warp ? cw : 0u;
+      nlive += cw;
     }
+    if (live) s_live[before + __popc(bal & lt)] = gm;
     __syncthreads();
-    const unsigned nlive = s_nlive;
-    for (unsigned j = 0; j < nlive; ++j) {
-      const uint32_t tile = s_live[j];
-      if (threadIdx.x < (kTile / 32) * kMaxKeys) (&s_cnt[0][0])[threadIdx.x] = 0;
-      __syncthreads();
-      const uint32_t slot = tile * kTile + threadIdx.x;
-      // a vacant slot's stored key may be stale (its chunk was skipped)
-      const unsigned key = (slot < p.n_slots && p.trk.status[slot] != VACANT) ? p.trk.key[slot] : vacant_key;
+    for (unsigned j0 = 0; j0 < nlive; j0 += (unsigned)nwarps) {
+      const unsigned j = j0 + (unsigned)warp;
+      unsigned key = 0xFFFFFFFFu;
+      uint32_t slot = 0;
+      if (j < nlive) {
+        slot = s_live[j] * 32u + lane;
+        if (slot < p.n_slots && p.trk.status[slot] != VACANT) key = p.trk.key[slot];
+        if (key >= (unsigned)live_keys) key = 0xFFFFFFFFu;
+      }
       const unsigned peers = __match_any_sync(0xffffffffu, key);
-      const unsigned rank = __popc(peers & ((1u << lane) - 1u));
-      if (lane == __ffs(peers) - 1) s_cnt[warp][key] = __popc(peers);
+      if (lane < live_keys) s_cnt[warp][lane] = 0u;
+      __syncwarp();
+      if (key != 0xFFFFFFFFu && lane == __ffs(peers) - 1) s_cnt[warp][key] = __popc(peers);
       __syncthreads();
-      if (key != vacant_key) {
-        unsigned pos = p.tile_offsets[key * p.n_tiles + tile] + rank;
+      if (key != 0xFFFFFFFFu) {
+        unsigned pos = s_cursor[key] + __popc(peers & lt);
         for (int w = 0; w < warp; ++w) pos += s_cnt[w][key];
         p.perm[pos] = slot;
+      }
+      __syncthreads();
+      if ((int)threadIdx.x < live_keys) {
+        unsigned add = 0;
+        for (int w = 0; w < nwarps; ++w) add += s_cnt[w][threadIdx.x];
+        s_cursor[threadIdx.x] += add;
       }
       __syncthreads();
     }
@@ -1035,10 +1063,6 @@ __device__ void phase_step(const Params& p, int bid, int nb, const SharedStatic&
   }
   flush_counter(&p.ctl->alive, killed, true);
   if (n_def) atomicAdd(&p.ctl->n_deferred, (unsigned)n_def);
-  if (p.policy != POLICY_NONE) {  // key counts start from zero in the next phase A
-    const uint32_t nc = (uint32_t)(p.n_keys - 1) * p.n_tiles;
-    for (uint32_t i = bid * blockDim.x + threadIdx.x; i < nc; i += nb * blockDim.x) p.tile_counts[i] = 0u;
-  }
   apply_fills(p, bid, nb);
   if (bookkeeping && last_block_done(&p.ctl->done_c, nb)) {
     const long long t0 = clock64();
@@ -1136,7 +1160,7 @@ __global__ void __launch_bounds__(kTile) k_pre_step(Params p) {
   const SharedStatic ss = carve_static(p, smem_raw);
   stage_static(p, ss);
   phase_fill_step(p, blockIdx.x, gridDim.x, ss, false, true, false);
-  if (last_block_done(&p.ctl->done_a, gridDim.x)) bookkeeping_after_fill_step(p, true);
+  if (last_block_done(&p.ctl->done_a, gridDim.x)) bookkeeping_after_fill_step(p, true, gridDim.x);
 }
 
 __global__ void k_along(Params p, int charged) {
@@ -1149,10 +1173,6 @@ __global__ void k_along(Params p, int charged) {
 __global__ void k_post(Params p, int which) { phase_post_only(p, (uint8_t)which, blockIdx.x, gridDim.x); }
 
 __global__ void __launch_bounds__(kTile) k_loop_ctl(Params p, cudaGraphConditionalHandle handle, int use_handle) {
-  if (p.policy != POLICY_NONE) {
-    const uint32_t nc = (uint32_t)(p.n_keys - 1) * p.n_tiles;
-    for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) p.tile_counts[i] = 0u;
-  }
   apply_fills(p, 0, 1);
   __syncthreads();
   scan_vacancy(p);

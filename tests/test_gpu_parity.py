@@ -143,25 +143,37 @@ def test_invalid_primaries_rejected():
         assert ctx.stats()["steps_total"] == 0
 
 
-def test_partition_is_a_stable_valid_partition():
+@pytest.mark.parametrize("mode", [binding.LOOP_HOST, binding.LOOP_PERSISTENT])
+def test_partition_is_a_deterministic_valid_partition(mode):
     prob = wl.calorimeter_problem(4096, sort_policy=wl.SORT_ACTION_TYPE)
     prim = wl.electron_beam(8, 1000.0)
     with binding.Context(prob) as ctx:
         ctx.add_events(prim)
         for it in range(60):
-            s = ctx.step()
+            if mode == binding.LOOP_HOST:
+                s = ctx.step()
+            else:
+                ctx.run_iterations(mode, 1)
+                s = ctx.stats()
             if it % 10 == 9:
                 keys, perm, offs = ctx.debug_partition()
+                nb = ctx.partition_blocks
+                assert nb >= 1
                 n_keys = len(offs) - 1
                 valid = offs[n_keys - 1]  # everything before the vacant key
                 p = perm[:valid]
                 assert len(np.unique(p)) == len(p)
                 assert np.all(p < prob.n_slots)
-                # keys non-decreasing along the permutation, slots increasing within a key
+                # keys non-decreasing along the permutation; within a key the
+                # order is (owning block of the chunk, chunk, slot)
                 k = keys[p]
                 assert np.all(np.diff(k.astype(int)) >= 0)
-                expect = np.concatenate([np.flatnonzero(keys == key) for key in range(n_keys - 1)])
-                np.testing.assert_array_equal(p, expect)
+                expect = []
+                for key in range(n_keys - 1):
+                    sl = np.flatnonzero(keys == key)
+                    chunk = sl // 32
+                    expect.append(sl[np.lexsort((sl, chunk, chunk % nb))])
+                np.testing.assert_array_equal(p, np.concatenate(expect))
                 counts = np.bincount(keys[:prob.n_slots], minlength=n_keys)
                 np.testing.assert_array_equal(np.diff(offs)[: n_keys - 1], counts[: n_keys - 1])
             if s["alive"] == 0 and s["queued"] == 0:
