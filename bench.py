@@ -73,7 +73,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except (OSError, FileNotFoundError):
@@ -201,9 +201,10 @@ def run_ours(args):
     pinned_np[:] = cprim
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    headline = binding_policy(args.policy)
     policies = [binding_policy(p) for p in args.policies.split(",") if p]
-    if headline not in policies:
+    auto = args.policy == "auto"
+    headline = None if auto else binding_policy(args.policy)
+    if headline is not None and headline not in policies:
         policies.insert(0, headline)
     loop = binding.LOOP_NAMES[args.loop]
     base_event = rank * 1_000_000
@@ -250,17 +251,20 @@ def run_ours(args):
         steps_done = ctx.stats()["steps_total"] - s0
         return ctx, dict(ms=reduce(ms, MAX), steps=reduce(steps_done, SUM), job_ms=per_job, clocks=clocks)
 
+    # every policy is timed the same way; the headline is the one named, or
+    # with "auto" the fastest (what the autotuner would pick for this workload)
     results = {}
-    clocks = None
-    head_ctx = None
+    ctxs = {}
     for pol in policies:
-        ctx, r = timed_jobs(pol, loop, False, args.steps, args.warmup, sample_clocks=(pol == headline))
+        ctx, r = timed_jobs(pol, loop, False, args.steps, args.warmup, sample_clocks=True)
         results[pol] = r
-        if pol == headline:
-            clocks = r["clocks"]
-            head_ctx = ctx
-        else:
-            ctx.close()
+        ctxs[pol] = ctx
+    if auto:
+        headline = max(policies, key=lambda q: results[q]["steps"] / results[q]["ms"])
+    clocks = results[headline]["clocks"]
+    head_ctx = ctxs.pop(headline)
+    for ctx in ctxs.values():
+        ctx.close()
 
     loop_modes = {}
     if not args.no_loop_compare:
@@ -343,7 +347,7 @@ def run_ours(args):
         line["loop_profile_us_per_iteration"] = {
             part: {name: round(c / it / 2.07e3, 3) for name, c in vals.items()} for part, vals in prof.items()}
     job_ms = statistics.median(h["job_ms"])
-    line["roofline"] = roofline_loop(steps_per_job, job_ms)
+    line["roofline"] = roofline_loop(args.workload, steps_per_job, job_ms)
     if launches_per_job:
         line["gpu_launches"] = int(launches_per_job * args.steps)
     if kt is not None:
@@ -507,27 +511,31 @@ def load_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
-# Per track-step figures of the whole step loop (all kernels of an iteration):
-# algorithmic state bytes (SURVEY-style accounting, see the design notes) and
-# thread-level FP64 operations (2 x DFMA + DADD + DMUL) counted by ncu on the
-# persistent loop kernel for this workload (profiles/loop_calorimeter_1gev.md).
+# Per track-step figures of the whole step loop (all phases of an iteration):
+# algorithmic state bytes (state read and written back once per step, without
+# secondaries or scratch) and thread-level FP64 operations
+# (2 x DFMA + DADD + DMUL) counted by ncu on the persistent loop kernel
+# (profiles/loop_kernel_calorimeters.md); DRAM bytes per launch of that kernel
+# from the same captures, for the workloads that were captured whole.
 BYTES_PER_STEP = 160.0
-FP64_FLOP_PER_STEP = 600.0
+FP64_FLOP_PER_STEP = {"calorimeter-1gev": 124.7, "calorimeter-field-10gev": 135.1, "water-cube-10mev": 124.7}
+DRAM_BYTES_PER_LAUNCH = {"calorimeter-1gev": 900.9e3}
 # FP64 peak of GB300: 2 DFMA per SM-cycle (ncu peak_sustained) x 152 SMs x 2.07 GHz x 2 flop
 FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
 
-def roofline_loop(steps_per_job, job_ms):
+def roofline_loop(workload, steps_per_job, job_ms):
     """Roofline of the dominant kernel, the persistent step-loop kernel (one
     launch per job): FP64 ALU bound, with the HBM fraction beside it."""
     peaks, kind = load_peaks()
     t = job_ms / 1e3
-    flops = FP64_FLOP_PER_STEP * steps_per_job / t / 1e12
+    fpstep = FP64_FLOP_PER_STEP[workload]
+    flops = fpstep * steps_per_job / t / 1e12
     gbs = BYTES_PER_STEP * steps_per_job / t / 1e9
     return {"kernel": "k_loop", "bound": "alu", "achieved": flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": flops / FP64_PEAK_TFLOPS, "traffic": None,
+            "frac": flops / FP64_PEAK_TFLOPS, "traffic": DRAM_BYTES_PER_LAUNCH.get(workload),
             "peak_kind": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (probe measured 1.02 TFLOP/s)",
-            "fp64_flop_per_track_step": FP64_FLOP_PER_STEP,
+            "fp64_flop_per_track_step": fpstep,
             "hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
                     "bytes_per_track_step": BYTES_PER_STEP, "peak_kind": kind},
             "launch_ms": job_ms, "track_steps_per_launch": steps_per_job}
@@ -541,7 +549,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="calorimeter-1gev",
                     choices=["calorimeter-1gev", "calorimeter-field-10gev", "water-cube-10mev"])
-    ap.add_argument("--policy", default="action_type", choices=list(wl.SORT_NAMES))
+    ap.add_argument("--policy", default="auto", choices=["auto"] + list(wl.SORT_NAMES))
     ap.add_argument("--policies", default="action_type,action,none")
     ap.add_argument("--loop", default="persistent", choices=["host", "graph", "persistent"])
     ap.add_argument("--no-loop-compare", action="store_true")
