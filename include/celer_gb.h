@@ -375,10 +375,12 @@ celer_status celer_debug_curand_philox(uint64_t seed, uint64_t subsequence, uint
                                        uint64_t n);
 
 /* Evaluate a binary64 function on n host arguments on the device: fn 0 the
- * table-driven logarithm of the step kernels, 1 their exponential, 2 and 3
- * CUDA's log and exp for comparison. No counterpart in the paper: it checks
- * the step kernels' elementary functions against the library's (accuracy is
- * about 1 ulp). fn outside 0-3 or null pointers give CELER_ERR_INVALID. */
+ * table-driven logarithm of the step kernels, 1 their exponential, 4 and 5
+ * their sin(2 pi x) and cos(2 pi x); 2, 3, 6, 7 CUDA's log, exp,
+ * sin(2 pi x), cos(2 pi x) for comparison. No counterpart in the paper: it
+ * checks the step kernels' elementary functions against the library's
+ * (accuracy about 1 ulp). fn outside 0-7 or null pointers give
+ * CELER_ERR_INVALID. */
 celer_status celer_debug_math(int fn, const double* host_x, uint64_t n, double* host_out);
 
 #ifdef __cplusplus

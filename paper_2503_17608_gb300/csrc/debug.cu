@@ -44,7 +44,11 @@ __global__ void k_math(int fn, const double* mt, const double* x, double* out, u
       case 0: r = celer::fast_log(v, mt); break;
       case 1: r = celer::fast_exp(v, mt); break;
       case 2: r = log(v); break;
-      default: r = exp(v); break;
+      case 3: r = exp(v); break;
+      case 4: { double sn, cs; celer::fast_sincos_2pi(v, mt, &sn, &cs); r = sn; break; }
+      case 5: { double sn, cs; celer::fast_sincos_2pi(v, mt, &sn, &cs); r = cs; break; }
+      case 6: r = sin(2.0 * celer::kPi * v); break;
+      default: r = cos(2.0 * celer::kPi * v); break;
     }
     out[i] = r;
   }
@@ -55,7 +59,7 @@ __global__ void k_math(int fn, const double* mt, const double* x, double* out, u
 extern "C" {
 
 celer_status celer_debug_math(int fn, const double* host_x, uint64_t n, double* host_out) {
-  if (!host_x || !host_out || fn < 0 || fn > 3) return CELER_ERR_INVALID;
+  if (!host_x || !host_out || fn < 0 || fn > 7) return CELER_ERR_INVALID;
   if (n == 0) return CELER_OK;
   std::vector<double> table(celer::kMathTableSize);
   celer::build_math_table(table.data());

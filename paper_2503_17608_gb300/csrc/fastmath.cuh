@@ -1,8 +1,10 @@
-// Table-driven binary64 logarithm and exponential after P. T. P. Tang,
+// Table-driven binary64 logarithm, exponential and sine/cosine of 2 pi u,
+// after P. T. P. Tang,
 // "Table-driven implementation of the exponential function in IEEE
 // floating-point arithmetic" (ACM TOMS 15, 1989) and "... of the logarithm
 // function ..." (ACM TOMS 16, 1990): a table lookup reduces the argument to a
-// few thousandths, where a short polynomial is accurate to the last bit.
+// few thousandths, where a short polynomial is accurate to the last bit (the
+// sine/cosine use the same idea with the angle-addition formulas).
 //
 // Why: on GB300 an FP64 warp instruction holds its sub-partition's FP64 pipe
 // for ~64 cycles whatever the number of active lanes, so the latency of a
@@ -27,12 +29,16 @@ constexpr int kLogTable = 256;  // reduced mantissa m in [0.75, 1.5), 256 interv
 constexpr int kExpTable = 64;   // 2^(j/64)
 constexpr int kMtLog = 0;                              // kLogTable x {1/c, L_hi, L_lo, 0}
 constexpr int kMtExp = kMtLog + 4 * kLogTable;         // kExpTable x {T_hi, T_lo}
-constexpr int kMtConst = kMtExp + 2 * kExpTable;       // constants below
+constexpr int kSinTable = 256;  // sin, cos of 2 pi j / 256
+constexpr int kMtSin = kMtExp + 2 * kExpTable;         // (kSinTable + 1) x {sin, cos}
+constexpr int kMtConst = kMtSin + 2 * (kSinTable + 1); // constants below
 constexpr int kMtLn2Hi = kMtConst + 0;                 // ln 2 rounded to a multiple of 2^-42
 constexpr int kMtLn2Lo = kMtConst + 1;                 // ln 2 - kMtLn2Hi
 constexpr int kMtInvC = kMtConst + 2;                  // 64 / ln 2
 constexpr int kMtCHi = kMtConst + 3;                   // ln 2 / 64 rounded to a multiple of 2^-42
 constexpr int kMtCLo = kMtConst + 4;                   // ln 2 / 64 - kMtCHi
+constexpr int kMt2PiHi = kMtConst + 5;                 // 2 pi
+constexpr int kMt2PiLo = kMtConst + 6;                 // 2 pi - kMt2PiHi
 constexpr int kMathTableSize = kMtConst + 8;           // doubles
 
 // Fill the table (kMathTableSize doubles). Host code, extended precision.
@@ -41,6 +47,7 @@ constexpr int kMathTableSize = kMtConst + 8;           // doubles
 //  accuracy), 1/c_j rounded to binary64, and L_j = -log(rounded 1/c_j) split
 //  into a head that is a multiple of 2^-42 and a tail.
 //  exp: T_j = 2^(j/64) as a head and a tail.
+//  sin/cos: sin and cos of 2 pi j / 256, j = 0 .. 256.
 inline void build_math_table(double* out) {
   typedef long double ld;
   const ld ln2 = logl(2.0L);
@@ -75,7 +82,16 @@ inline void build_math_table(double* out) {
   const double chi = head42(ln2 / 64.0L);
   out[kMtCHi] = chi;
   out[kMtCLo] = (double)(ln2 / 64.0L - (ld)chi);
-  for (int i = kMtConst + 5; i < kMathTableSize; ++i) out[i] = 0.0;
+  const ld twopi = 8.0L * atanl(1.0L);
+  for (int j = 0; j <= kSinTable; ++j) {
+    const ld a = twopi * (ld)j / (ld)kSinTable;
+    out[kMtSin + 2 * j + 0] = (double)sinl(a);
+    out[kMtSin + 2 * j + 1] = (double)cosl(a);
+  }
+  const double tp = (double)twopi;
+  out[kMt2PiHi] = tp;
+  out[kMt2PiLo] = (double)(twopi - (ld)tp);
+  for (int i = kMt2PiLo + 1; i < kMathTableSize; ++i) out[i] = 0.0;
 }
 
 #ifdef __CUDACC__
@@ -127,6 +143,28 @@ __device__ __forceinline__ double fast_exp(double x, const double* __restrict__ 
   const double2 T = __ldg(reinterpret_cast<const double2*>(mt + kMtExp + 2 * (n & (kExpTable - 1))));
   const double y = T.x + fma(T.x, p, T.y);
   return __longlong_as_double(__double_as_longlong(y) + ((long long)(n >> 6) << 52));
+}
+// sin and cos of 2 pi u for u in [0, 1] (an azimuth from a uniform draw):
+// j = nearest multiple of 1/256, r = u - j/256 exact, |r| <= 2^-9, theta =
+// 2 pi r (|theta| < 0.0123), then the angle-addition formulas with the
+// tabulated sin, cos of 2 pi j/256 and short Taylor series for theta
+// (truncation below 2^-70). Arguments outside [0, 1] go to sincospi.
+__device__ __forceinline__ void fast_sincos_2pi(double u, const double* __restrict__ mt, double* s, double* c) {
+  if (!(u >= 0.0 && u <= 1.0)) {
+    sincospi(2.0 * u, s, c);
+    return;
+  }
+  const int j = __double2int_rn(u * (double)kSinTable);
+  const double r = u - (double)j * (1.0 / kSinTable);
+  const double th = fma(r, __ldg(mt + kMt2PiHi), r * __ldg(mt + kMt2PiLo));
+  const double t2 = th * th;
+  // sin th = th + th^3 (-1/6 + t2 (1/120 - t2/5040)); cos th - 1 = t2 (-1/2 + t2 (1/24 - t2/720))
+  const double sp = fma(t2, fma(t2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0);
+  const double sn = fma(th * t2, sp, th);
+  const double cm1 = t2 * fma(t2, fma(t2, -1.0 / 720.0, 1.0 / 24.0), -0.5);
+  const double2 sc = __ldg(reinterpret_cast<const double2*>(mt + kMtSin + 2 * j));
+  *s = sc.x + fma(sc.x, cm1, sc.y * sn);
+  *c = sc.y + fma(sc.y, cm1, -sc.x * sn);
 }
 #endif
 

@@ -132,13 +132,16 @@ __device__ __forceinline__ double inverse_range(const double2* R, double r, doub
 // the same time whatever its active lanes, so the kinematics below take
 // reciprocal square roots once instead of a square root and divisions.
 
-// Rotate (ux, uy, uz) by polar cosine cost and azimuth phi about itself:
-// frame e1 = (u x z)/|u x z|, e2 = u x e1 (e1 = x near the poles), then
-// renormalised.
-__device__ __forceinline__ void rotate_dir(double& ux, double& uy, double& uz, double cost, double phi) {
+// Rotate (ux, uy, uz) by polar cosine cost and azimuth 2 pi u_phi about
+// itself: frame e1 = (u x z)/|u x z|, e2 = u x e1 (e1 = x near the poles),
+// then renormalised. The input is a unit vector to rounding, so the result's
+// squared norm q is 1 + O(1e-16) and one Newton step from 1, 1.5 - q/2, is
+// 1/sqrt(q) to O((q - 1)^2).
+__device__ __forceinline__ void rotate_dir(double& ux, double& uy, double& uz, double cost, double u_phi,
+                                           const double* mt) {
   const double sint = sqrt(fmax(0.0, 1.0 - cost * cost));
   double sp, cp;
-  sincos(phi, &sp, &cp);
+  fast_sincos_2pi(u_phi, mt, &sp, &cp);
   double e1x, e1y, e1z, e2x, e2y, e2z;
   if (fabs(uz) < 1.0 - 1e-10) {
     const double q = ux * ux + uy * uy;
@@ -162,7 +165,7 @@ __device__ __forceinline__ void rotate_dir(double& ux, double& uy, double& uz, d
   const double vx = cost * ux + sint * (cp * e1x + sp * e2x);
   const double vy = cost * uy + sint * (cp * e1y + sp * e2y);
   const double vz = cost * uz + sint * (cp * e1z + sp * e2z);
-  const double inv = rsqrt(vx * vx + vy * vy + vz * vz);
+  const double inv = fma(-0.5, fma(vx, vx, fma(vy, vy, vz * vz)), 1.5);
   ux = vx * inv;
   uy = vy * inv;
   uz = vz * inv;

@@ -295,19 +295,33 @@ __device__ __forceinline__ bool last_block_done(unsigned* counter, unsigned nb) 
   return last;
 }
 
-// Warp-interleaved walk over [lo, hi): 32-element chunk g goes to block
-// g % nb, so consecutive chunks land on different SMs. With few live tracks
-// this spreads the FP64 work over all SMs instead of stacking warps on the
-// few SMs that own the first chunks (an FP64 warp instruction occupies its
+// Warp-interleaved walk over [lo, hi): chunk g of `width` elements (8, 16
+// or 32; lanes at and above the width idle) goes to block g % nb, so
+// consecutive chunks land on different SMs. With few live tracks this
+// spreads the FP64 work over all SMs instead of stacking warps on the few
+// SMs that own the first chunks (an FP64 warp instruction occupies its
 // sub-partition's pipe for the same time whatever its active lanes).
 struct ChunkWalk {
-  uint32_t lo, hi, step, g;
-  __device__ ChunkWalk(uint32_t lo_, uint32_t hi_, int bid, int nb)
-      : lo(lo_), hi(hi_), step((uint32_t)nb * (blockDim.x >> 5)), g((uint32_t)bid + (threadIdx.x >> 5) * (uint32_t)nb) {}
-  __device__ __forceinline__ bool more() const { return (unsigned long long)lo + 32ull * g < hi; }
-  __device__ __forceinline__ uint32_t index() const { return lo + 32u * g + (threadIdx.x & 31); }
+  uint32_t lo, hi, step, g, width;
+  __device__ ChunkWalk(uint32_t lo_, uint32_t hi_, int bid, int nb, uint32_t width_ = 32u)
+      : lo(lo_), hi(hi_), step((uint32_t)nb * (blockDim.x >> 5)), g((uint32_t)bid + (threadIdx.x >> 5) * (uint32_t)nb),
+        width(width_) {}
+  __device__ __forceinline__ bool more() const { return (unsigned long long)lo + (unsigned long long)width * g < hi; }
+  __device__ __forceinline__ uint32_t index() const {
+    const uint32_t lane = threadIdx.x & 31;
+    return lane < width ? lo + width * g + lane : hi;
+  }
   __device__ __forceinline__ void next() { g += step; }
 };
+
+// Width of the step-phase chunks for a partition range of n live tracks: as
+// few tracks per warp as keep one warp per SM sub-partition (nb blocks of
+// four), since a warp's time is set by its instruction count and the
+// slowest of its lanes (rejection loops), not by how many lanes it runs.
+__device__ __forceinline__ uint32_t spread_width(uint32_t n, int nb) {
+  const uint32_t subs = (uint32_t)nb * 4u;
+  return n <= subs * 8u ? 8u : (n <= subs * 16u ? 16u : 32u);
+}
 
 // ---- phase A: initializer fill + step limit, on 32-slot warp-tiles
 // A warp owns a 32-slot chunk: it fills the chunk's vacant slots from the
@@ -417,6 +431,17 @@ __device__ unsigned long long block_scan_counts(const uint32_t* __restrict__ in,
   const uint4* v = reinterpret_cast<const uint4*>(in);
   unsigned long long local = 0;
   uint32_t i = beg;
+  // the first 32 values stay in registers for the second pass (all of them
+  // when the segment is a single round, the common case)
+  uint4 q0[8];
+  const bool first = i + 32 <= end;
+  if (first) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) q0[k] = __ldcg(v + (i >> 2) + k);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) local += (unsigned long long)q0[k].x + q0[k].y + q0[k].z + q0[k].w;
+    i += 32;
+  }
   for (; i + 32 <= end; i += 32) {
     uint4 q[8];
 #pragma unroll
@@ -449,6 +474,20 @@ __device__ unsigned long long block_scan_counts(const uint32_t* __restrict__ in,
   __syncthreads();
   unsigned long long run = s_warp[warp] + incl - local;
   i = beg;
+  if (first) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      write(i + 4 * k, run);
+      run += q0[k].x;
+      write(i + 4 * k + 1, run);
+      run += q0[k].y;
+      write(i + 4 * k + 2, run);
+      run += q0[k].z;
+      write(i + 4 * k + 3, run);
+      run += q0[k].w;
+    }
+    i += 32;
+  }
   for (; i + 32 <= end; i += 32) {
     uint4 q[8];
 #pragma unroll
@@ -750,7 +789,7 @@ __device__ __forceinline__ bool compton_one(const Params& p, uint32_t slot) {
     release(p, slot, ev);
     return true;
   }
-  const double phi = kTwoPi * rng.uniform();
+  const double u_phi = rng.uniform();
   const double E1 = eps * E;
   deposit(p, ev, prim, layer, z, E - E1);
   if (E1 < p.cut_track) {
@@ -759,7 +798,7 @@ __device__ __forceinline__ bool compton_one(const Params& p, uint32_t slot) {
     return true;
   }
   double ux = t.ux[slot], uy = t.uy[slot], uz = t.uz[slot];
-  rotate_dir(ux, uy, uz, cost, phi);
+  rotate_dir(ux, uy, uz, cost, u_phi, p.mtab);
   t.ux[slot] = ux;
   t.uy[slot] = uy;
   t.uz[slot] = uz;
@@ -850,10 +889,10 @@ __device__ __forceinline__ bool pair_one(const Params& p, uint32_t slot, uint8_t
   TrackRng rng(p.seed, ev, t.tid[slot], t.ctr[slot]);
   deposit(p, ev, prim, layer, z, E - 2.0 * kMe);
   const double cost = 2.0 * rng.uniform() - 1.0;
-  const double phi = kTwoPi * rng.uniform();
+  const double u_phi = rng.uniform();
   const double sint = sqrt(fmax(0.0, 1.0 - cost * cost));
   double sp_, cp_;
-  sincos(phi, &sp_, &cp_);
+  fast_sincos_2pi(u_phi, p.mtab, &sp_, &cp_);
   const double dx = sint * cp_, dy = sint * sp_, dz = cost;
   if (keep) {
     const unsigned long long tid1 = rng.raw();
@@ -901,15 +940,20 @@ __device__ __forceinline__ bool moller_one(const Params& p, uint32_t slot, uint8
     release(p, slot, ev);
     return true;
   }
-  const double cost = fmin(1.0, sqrt(Td * (T + 2.0 * kMe) / (T * (Td + 2.0 * kMe))));
-  const double phi = kTwoPi * rng.uniform();
+  // momenta p^2 = T (T + 2 m) and the delta's polar cosine
+  // sqrt(Td (T + 2m) / (T (Td + 2m))) = Td (T + 2m) / (p p_delta), from two
+  // reciprocal square roots
+  const double pp2 = T * (T + 2.0 * kMe), pd2 = Td * (Td + 2.0 * kMe);
+  const double rpp = rsqrt(pp2), rpd = rsqrt(pd2);
+  const double cost = fmin(1.0, Td * (T + 2.0 * kMe) * rpp * rpd);
+  const double u_phi = rng.uniform();
   const double ux = t.ux[slot], uy = t.uy[slot], uz = t.uz[slot];
   double dx = ux, dy = uy, dz = uz;
-  rotate_dir(dx, dy, dz, cost, phi);
-  const double pp = sqrt(T * (T + 2.0 * kMe));
-  const double pd = sqrt(Td * (Td + 2.0 * kMe));
+  rotate_dir(dx, dy, dz, cost, u_phi, p.mtab);
+  const double pp = pp2 * rpp;
+  const double pd = pd2 * rpd;
   const double vx = pp * ux - pd * dx, vy = pp * uy - pd * dy, vz = pp * uz - pd * dz;
-  const double inv = 1.0 / sqrt(vx * vx + vy * vy + vz * vz);
+  const double inv = rsqrt(vx * vx + vy * vy + vz * vz);
   const double E1 = T - Td;
   if (keep) {
     const unsigned long long tid = rng.raw();
@@ -1004,37 +1048,58 @@ __device__ __forceinline__ Span live_span(const Params& p) {
 }
 
 // End of an iteration: counters, the per-iteration trace row, stall and
-// iteration-limit checks, and the loop condition. One thread.
-__device__ void loop_ctl_one(const Params& p) {
+// iteration-limit checks, the loop condition, and the per-iteration counters
+// cleared for the next one. One warp: every counter is read in one batch of
+// loads, the per-action counts one per lane.
+__device__ void loop_ctl_warp(const Params& p) {
   Ctl* c = p.ctl;
-  const unsigned long long queued = c->tail - c->head;
-  const bool worked = c->steps_iter > 0 || c->n_deferred > 0;
-  c->last_steps_iter = c->steps_iter;
-  c->last_n_deferred = c->n_deferred;
-  for (int k = 0; k < kMaxKeys; ++k) c->last_action_count[k] = c->action_count[k];
-  if (worked) {
-    c->steps_total += c->steps_iter;
-    TraceRow& r = p.trace[c->trace_count % kTraceRows];
-    r.iteration = c->iteration;
-    r.alive = c->alive;
-    r.queued = queued;
-    r.steps = c->steps_iter;
-    for (int k = 0; k < kMaxKeys; ++k) r.action_count[k] = c->action_count[k];
-    c->trace_count += 1;
-    c->iteration += 1;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long head = c->head, tail = c->tail, alive = c->alive;
+  const unsigned long long steps_iter = c->steps_iter, steps_total = c->steps_total;
+  const unsigned long long iteration = c->iteration, trace_count = c->trace_count;
+  const unsigned long long max_iterations = c->max_iterations, budget_end = c->budget_end;
+  const unsigned n_def = c->n_deferred, stall = c->stall, error = c->error;
+  const unsigned ac = lane < kMaxKeys ? c->action_count[lane] : 0u;
+  const unsigned long long queued = tail - head;
+  const bool worked = steps_iter > 0 || n_def > 0;
+  TraceRow& r = p.trace[trace_count % kTraceRows];
+  if (lane < kMaxKeys) {
+    c->last_action_count[lane] = ac;
+    if (worked) r.action_count[lane] = ac;
+    c->action_count[lane] = 0u;
+    c->key_total[lane] = 0u;
   }
-  const bool pending = c->alive + queued > 0;
-  // No track stepped although work is pending: every live track waits for
-  // buffer space. One such iteration can still place deferred secondaries;
-  // three in a row cannot make progress any more.
-  if (c->steps_iter == 0 && pending) {
-    c->stall += 1;
-    if (c->stall >= 3) c->error |= ERR_NO_PROGRESS;
-  } else {
-    c->stall = 0;
+  if (lane == 0) {
+    c->last_steps_iter = steps_iter;
+    c->last_n_deferred = n_def;
+    unsigned long long it = iteration;
+    if (worked) {
+      c->steps_total = steps_total + steps_iter;
+      r.iteration = iteration;
+      r.alive = alive;
+      r.queued = queued;
+      r.steps = steps_iter;
+      c->trace_count = trace_count + 1;
+      it = iteration + 1;
+      c->iteration = it;
+    }
+    const bool pending = alive + queued > 0;
+    // No track stepped although work is pending: every live track waits for
+    // buffer space. One such iteration can still place deferred secondaries;
+    // three in a row cannot make progress any more.
+    unsigned err = error;
+    if (steps_iter == 0 && pending) {
+      if (stall + 1 >= 3) err |= ERR_NO_PROGRESS;
+      c->stall = stall + 1;
+    } else {
+      c->stall = 0u;
+    }
+    if (pending && it >= max_iterations) err |= ERR_ITERATIONS;
+    if (err != error) c->error = err;
+    c->cont = (pending && err == 0u && it < budget_end) ? 1u : 0u;
+    c->steps_iter = 0;
+    c->n_deferred = 0;
   }
-  if (pending && c->iteration >= c->max_iterations) c->error |= ERR_ITERATIONS;
-  c->cont = (pending && c->error == 0u && c->iteration < c->budget_end) ? 1u : 0u;
 }
 
 // Phase C: along-step of every live track and, where the step ends in an
@@ -1046,7 +1111,8 @@ __device__ void phase_step(const Params& p, int bid, int nb, const SharedStatic&
   const bool tight = p.ctl->defer != 0u;
   const Tracks& t = p.trk;
   unsigned long long killed = 0, n_def = 0;
-  for (ChunkWalk w(sp.lo, sp.hi, bid, nb); w.more(); w.next()) {
+  const uint32_t width = sp.perm ? spread_width(sp.hi - sp.lo, nb) : 32u;
+  for (ChunkWalk w(sp.lo, sp.hi, bid, nb, width); w.more(); w.next()) {
     const uint32_t i = w.index();
     if (i >= sp.hi) continue;
     const uint32_t slot = sp.perm ? sp.perm[i] : i;
@@ -1067,9 +1133,8 @@ __device__ void phase_step(const Params& p, int bid, int nb, const SharedStatic&
   if (bookkeeping && last_block_done(&p.ctl->done_c, nb)) {
     const long long t0 = clock64();
     scan_vacancy(p);
+    if (threadIdx.x < 32) loop_ctl_warp(p);
     if (threadIdx.x == 0) {
-      loop_ctl_one(p);
-      clear_iteration_counters(p.ctl);
       if (use_handle) cudaGraphSetConditional(handle, p.ctl->cont);
       p.ctl->book_total[1] += (unsigned long long)(clock64() - t0);
     }
@@ -1176,11 +1241,8 @@ __global__ void __launch_bounds__(kTile) k_loop_ctl(Params p, cudaGraphCondition
   apply_fills(p, 0, 1);
   __syncthreads();
   scan_vacancy(p);
-  if (threadIdx.x == 0) {
-    loop_ctl_one(p);
-    clear_iteration_counters(p.ctl);
-    if (use_handle) cudaGraphSetConditional(handle, p.ctl->cont);
-  }
+  if (threadIdx.x < 32) loop_ctl_warp(p);
+  if (threadIdx.x == 0 && use_handle) cudaGraphSetConditional(handle, p.ctl->cont);
 }
 
 // Start a run: the loop stops after `budget` more iterations (0: no limit).

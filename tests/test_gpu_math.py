@@ -72,4 +72,30 @@ def test_fast_log_exp_round_trip():
 
 def test_invalid_function_code_is_rejected():
     with pytest.raises(Exception):
-        binding.debug_math(4, np.ones(3))
+        binding.debug_math(8, np.ones(3))
+
+
+def test_fast_sincos_2pi_absolute_error():
+    rng = np.random.default_rng(8)
+    u = np.concatenate([rng.uniform(0, 1, 400000), rng.uniform(0, 1e-6, 20000), 1.0 - rng.uniform(0, 1e-6, 20000),
+                        np.array([0.0, 0.25, 0.5, 0.75, 1.0, 2.0 ** -53, 1.0 - 2.0 ** -53])])
+    s = binding.debug_math(4, u)
+    c = binding.debug_math(5, u)
+    # reference in extended precision (2 pi u rounded in binary64 alone is
+    # off by up to 4.4e-16 near u = 1)
+    twopi = 2 * np.longdouble("3.141592653589793238462643383279502884")
+    ul = u.astype(np.longdouble)
+    ref_s = np.sin(twopi * ul)
+    ref_c = np.cos(twopi * ul)
+    assert float(np.max(np.abs(s - ref_s))) < 2.5e-16
+    assert float(np.max(np.abs(c - ref_c))) < 2.5e-16
+    # CUDA's sin(2 pi u) carries the rounding of 2 pi u
+    assert np.max(np.abs(s - binding.debug_math(6, u))) < 8e-16
+    assert np.max(np.abs(c - binding.debug_math(7, u))) < 8e-16
+    assert np.max(np.abs(s * s + c * c - 1.0)) < 4.5e-16
+
+
+def test_fast_sincos_outside_unit_interval_follows_library():
+    u = np.array([-0.25, 1.25, 3.5, -2.0])
+    np.testing.assert_allclose(binding.debug_math(4, u), np.sin(2 * np.pi * u), atol=1e-15)
+    np.testing.assert_allclose(binding.debug_math(5, u), np.cos(2 * np.pi * u), atol=1e-15)
