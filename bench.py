@@ -38,21 +38,28 @@ METRIC = "track-steps/s on 1 GB300, sorted vs unsorted; p50/p99 event latency se
 UNIT = "track-steps/s"
 
 
-def make_workload(name: str):
+def make_workload(name: str, primaries: int = 0, slots: int = 0):
+    """The named workload; primaries / slots override its sizes (smaller
+    cases of the same shape, e.g. for profiler captures)."""
     if name == "calorimeter-1gev":
-        prob, prim = wl.calorimeter_1gev(1000)
-        desc = dict(workload="Pb/LAr calorimeter, 1000 x 1 GeV e-, no field", primaries=1000, energy_MeV=1000.0,
-                    slots=prob.n_slots, layers=prob.n_layers_total, field_T=0.0)
+        n = primaries or 1000
+        prob, prim = wl.calorimeter_1gev(n)
+        desc = dict(workload=f"Pb/LAr calorimeter, {n} x 1 GeV e-, no field", primaries=n, energy_MeV=1000.0,
+                    layers=prob.n_layers_total, field_T=0.0)
     elif name == "calorimeter-field-10gev":
-        prob, prim = wl.calorimeter_field_10gev(10000)
-        desc = dict(workload="Pb/LAr calorimeter in 4 T, 10000 x 10 GeV e-", primaries=10000, energy_MeV=1e4,
-                    slots=prob.n_slots, layers=prob.n_layers_total, field_T=4.0)
+        n = primaries or 10000
+        prob, prim = wl.calorimeter_field_10gev(n)
+        desc = dict(workload=f"Pb/LAr calorimeter in 4 T, {n} x 10 GeV e-", primaries=n, energy_MeV=1e4,
+                    layers=prob.n_layers_total, field_T=4.0)
     elif name == "water-cube-10mev":
-        prob, prim = wl.water_cube_problem(), wl.water_cube_primaries()
-        desc = dict(workload="water cube, 2000 x 10 MeV photons", primaries=2000, energy_MeV=10.0,
-                    slots=prob.n_slots, layers=1, field_T=0.0)
+        n = primaries or 2000
+        prob, prim = wl.water_cube_problem(), wl.water_cube_primaries(n)
+        desc = dict(workload=f"water cube, {n} x 10 MeV photons", primaries=n, energy_MeV=10.0, layers=1, field_T=0.0)
     else:
         raise SystemExit(f"unknown workload {name}")
+    if slots:
+        prob = prob.replace(n_slots=slots)
+    desc["slots"] = prob.n_slots
     return prob, prim, desc
 
 
@@ -67,22 +74,33 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.lines = []  # (host time, csv line)
+        self.window = None
 
     def __enter__(self):
+        """Start sampling every 20 ms and wait (up to 3 s) for the first
+        sample, so that the sampler is live when the timed region starts."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.monotonic()
+            while not self.lines and time.monotonic() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.005)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def region(self, t_begin, t_end):
+        """The timed region in host time; samples inside it (plus the first
+        one after it, which covers its tail) make the summary."""
+        self.window = (t_begin, t_end)
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -95,7 +113,15 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        rows = self.lines
+        if self.window is not None:
+            b, e = self.window
+            inside = [ln for t, ln in rows if b <= t <= e]
+            after = [ln for t, ln in rows if t > e][:1]
+            rows = inside + after
+        else:
+            rows = [ln for _, ln in rows]
+        for ln in rows:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -135,7 +161,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    prob, prim, desc = make_workload(args.workload)
+    prob, prim, desc = make_workload(args.workload, args.primaries, args.slots)
     import oracle
 
     world = oracle.World(prob)
@@ -192,7 +218,7 @@ def run_ours(args):
     MAX = dist.ReduceOp.MAX if dist is not None else None
     SUM = dist.ReduceOp.SUM if dist is not None else None
 
-    prob, prim, desc = make_workload(args.workload)
+    prob, prim, desc = make_workload(args.workload, args.primaries, args.slots)
     n = len(prim)
     cprim = binding.to_c_primaries(prim)
     dev_prim = torch.from_numpy(cprim.view(np.uint8).copy()).cuda()
@@ -222,14 +248,15 @@ def run_ours(args):
             ctx.add_primaries_device(e, dev_prim.data_ptr(), n)
             ctx.run_events(mode)
 
+        sampler = ClockSampler(local) if sample_clocks else None
+        if sampler:
+            sampler.__enter__()
         for _ in range(warmup):
             flush.zero_()
             job()
         s0 = ctx.stats()["steps_total"]
         barrier()
-        sampler = ClockSampler(local) if sample_clocks else None
-        if sampler:
-            sampler.__enter__()
+        h_begin = time.monotonic()
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         stops = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         t_start = torch.cuda.Event(enable_timing=True)
@@ -242,9 +269,12 @@ def run_ours(args):
             stops[k].record(stream)
         t_stop.record(stream)
         barrier()
+        h_end = time.monotonic()
         clocks = None
         if sampler:
+            time.sleep(0.05)  # let the sample after the region arrive
             sampler.__exit__()
+            sampler.region(h_begin, h_end)
             clocks = sampler.summary()
         ms = t_start.elapsed_time(t_stop)
         per_job = [a.elapsed_time(b) for a, b in zip(starts, stops)]
@@ -256,7 +286,7 @@ def run_ours(args):
     results = {}
     ctxs = {}
     for pol in policies:
-        ctx, r = timed_jobs(pol, loop, False, args.steps, args.warmup, sample_clocks=True)
+        ctx, r = timed_jobs(pol, loop, args.split, args.steps, args.warmup, sample_clocks=True)
         results[pol] = r
         ctxs[pol] = ctx
     if auto:
@@ -327,13 +357,12 @@ def run_ours(args):
     by_policy = {binding_name(p): dict(value=r["steps"] / (r["ms"] / 1e3), ms_per_step=r["ms"] / args.steps,
                                        track_steps_per_job=r["steps"] / args.steps / world)
                  for p, r in results.items()}
-    # our kernels per job: the device-primaries push + the persistent loop kernel
-    launches_per_job = 2 if loop == binding.LOOP_PERSISTENT else None
+    launches_per_job = 3 if loop == binding.LOOP_PERSISTENT else None  # push, run start, loop kernel
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": h["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(desc, sort_policy=binding_name(headline), loop=args.loop,
+        "config": dict(desc, sort_policy=binding_name(headline), loop=args.loop + (" per-action" if args.split else ""),
                        parallelism=f"replicas x{world} (independent events per rank)",
                        l2="512 MiB buffer written between timed jobs"),
         "sorted_vs_unsorted": by_policy,
@@ -347,7 +376,8 @@ def run_ours(args):
         line["loop_profile_us_per_iteration"] = {
             part: {name: round(c / it / 2.07e3, 3) for name, c in vals.items()} for part, vals in prof.items()}
     job_ms = statistics.median(h["job_ms"])
-    line["roofline"] = roofline_loop(args.workload, steps_per_job, job_ms)
+    line["roofline"] = roofline_loop(args.workload, binding_name(headline), steps_per_job, job_ms,
+                                     full_size=not (args.primaries or args.slots))
     if launches_per_job:
         line["gpu_launches"] = int(launches_per_job * args.steps)
     if kt is not None:
@@ -518,13 +548,15 @@ def load_peaks():
 # (profiles/loop_kernel_calorimeters.md); DRAM bytes per launch of that kernel
 # from the same captures, for the workloads that were captured whole.
 BYTES_PER_STEP = 160.0
-FP64_FLOP_PER_STEP = {"calorimeter-1gev": 124.7, "calorimeter-field-10gev": 135.1, "water-cube-10mev": 124.7}
-DRAM_BYTES_PER_LAUNCH = {"calorimeter-1gev": 900.9e3}
+FP64_FLOP_PER_STEP = {"calorimeter-1gev": 122.1, "calorimeter-field-10gev": 132.2, "water-cube-10mev": 122.1}
+DRAM_BYTES_PER_LAUNCH = {("calorimeter-1gev", "none"): 778.5e3, ("calorimeter-1gev", "action_type"): 867.6e3,
+                         ("calorimeter-field-10gev", "none"): 28.74e6, ("calorimeter-field-10gev", "action"): 30.47e6,
+                         ("calorimeter-field-10gev", "action_type"): 28.28e6}
 # FP64 peak of GB300: 2 DFMA per SM-cycle (ncu peak_sustained) x 152 SMs x 2.07 GHz x 2 flop
 FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
 
-def roofline_loop(workload, steps_per_job, job_ms):
+def roofline_loop(workload, policy, steps_per_job, job_ms, full_size=True):
     """Roofline of the dominant kernel, the persistent step-loop kernel (one
     launch per job): FP64 ALU bound, with the HBM fraction beside it."""
     peaks, kind = load_peaks()
@@ -533,7 +565,7 @@ def roofline_loop(workload, steps_per_job, job_ms):
     flops = fpstep * steps_per_job / t / 1e12
     gbs = BYTES_PER_STEP * steps_per_job / t / 1e9
     return {"kernel": "k_loop", "bound": "alu", "achieved": flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": flops / FP64_PEAK_TFLOPS, "traffic": DRAM_BYTES_PER_LAUNCH.get(workload),
+            "frac": flops / FP64_PEAK_TFLOPS, "traffic": DRAM_BYTES_PER_LAUNCH.get((workload, policy)) if full_size else None,
             "peak_kind": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (probe measured 1.02 TFLOP/s)",
             "fp64_flop_per_track_step": fpstep,
             "hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
@@ -550,6 +582,9 @@ def main():
     ap.add_argument("--workload", default="calorimeter-1gev",
                     choices=["calorimeter-1gev", "calorimeter-field-10gev", "water-cube-10mev"])
     ap.add_argument("--policy", default="auto", choices=["auto"] + list(wl.SORT_NAMES))
+    ap.add_argument("--split", action="store_true", help="one kernel per action in the host or graph loop")
+    ap.add_argument("--primaries", type=int, default=0, help="override the workload's primary count")
+    ap.add_argument("--slots", type=int, default=0, help="override the workload's track-slot count")
     ap.add_argument("--policies", default="action_type,action,none")
     ap.add_argument("--loop", default="persistent", choices=["host", "graph", "persistent"])
     ap.add_argument("--no-loop-compare", action="store_true")
