@@ -399,7 +399,7 @@ def run_ours(args):
 
 def run_extras(args, binding, stream, flush):
     """The other workloads of the benchmark suite, reported beside the headline:
-    the 4 T / 10 GeV calorimeter at 2^20 slots (three sort policies), 256
+    the 4 T / 10 GeV calorimeter at 2^20 slots (all sort policies), 256
     offload events batched in one loop (autotuned) vs 256 sequential runs, and
     Poisson-arrival serving vs the one-event-at-a-time loop."""
     import torch
@@ -410,7 +410,7 @@ def run_extras(args, binding, stream, flush):
     c2 = binding.to_c_primaries(prim2)
     dev2 = torch.from_numpy(c2.view(np.uint8).copy()).cuda()
     pol = {}
-    for name in ("action_type", "action", "none"):
+    for name in ("action_type", "action", "none", "local"):
         ctx = binding.Context(prob2.replace(sort_policy=wl.SORT_NAMES[name], max_events=1), stream=stream.cuda_stream)
         times, steps = [], 0
         for rep in range(1 + args.extra_steps):
@@ -443,7 +443,7 @@ def run_extras(args, binding, stream, flush):
     base3 = wl.calorimeter_problem(1 << 20, Bz=4.0, max_events=256)
     sample = wl.concat_primaries(events[:24])
     best, trials = binding.autotune(base3, sample, [1 << 18, 1 << 19, 1 << 20, 1 << 21], [128, 256, 512],
-                                    [wl.SORT_NONE, wl.SORT_ACTION, wl.SORT_ACTION_TYPE],
+                                    [wl.SORT_NONE, wl.SORT_ACTION, wl.SORT_ACTION_TYPE, wl.SORT_LOCAL],
                                     [binding.LOOP_PERSISTENT, binding.LOOP_GRAPH], stream=stream.cuda_stream)
     tuned = base3.replace(n_slots=best["n_slots"], block_size=best["block_size"], sort_policy=best["sort_policy"],
                           init_capacity=max(8 * best["n_slots"], 1 << 22))
@@ -585,7 +585,7 @@ def main():
     ap.add_argument("--split", action="store_true", help="one kernel per action in the host or graph loop")
     ap.add_argument("--primaries", type=int, default=0, help="override the workload's primary count")
     ap.add_argument("--slots", type=int, default=0, help="override the workload's track-slot count")
-    ap.add_argument("--policies", default="action_type,action,none")
+    ap.add_argument("--policies", default="action_type,action,none,local")
     ap.add_argument("--loop", default="persistent", choices=["host", "graph", "persistent"])
     ap.add_argument("--no-loop-compare", action="store_true")
     ap.add_argument("--no-kernel-timing", action="store_true")

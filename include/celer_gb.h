@@ -67,8 +67,14 @@ enum { CELER_TALLY_ZBINS = 0, CELER_TALLY_LAYERS = 1 };
  *               straight line vs charged), the key the paper found best;
  *   ACTION_TYPE slot indices are partitioned by (particle type, next action),
  *               so every along-step and interaction kernel runs over one
- *               contiguous range. */
-enum { CELER_SORT_NONE = 0, CELER_SORT_ACTION = 1, CELER_SORT_ACTION_TYPE = 2 };
+ *               contiguous range;
+ *   LOCAL       no grid-wide partition: in the step phase each GPU block
+ *               groups its own live tracks by (particle type, next action) in
+ *               on-chip memory and gives each warp one group (no counterpart
+ *               in the paper; it keeps the divergence cut of ACTION_TYPE
+ *               without the partition's extra grid-wide pass). The per-action
+ *               launch mode runs it like NONE. */
+enum { CELER_SORT_NONE = 0, CELER_SORT_ACTION = 1, CELER_SORT_ACTION_TYPE = 2, CELER_SORT_LOCAL = 3 };
 
 typedef struct {
   double Z;       /* atomic number (effective Z for a compound) */

@@ -61,7 +61,14 @@ constexpr int kKeysFull = 9;
 enum KeyAlong : uint8_t { KA_NEUTRAL = 0, KA_CHARGED = 1, KA_VACANT = 2 };
 constexpr int kKeysAlong = 3;
 
-enum Policy : int { POLICY_NONE = 0, POLICY_ACTION = 1, POLICY_ACTION_TYPE = 2 };
+// NONE: slot order. ACTION / ACTION_TYPE: a grid-wide partition of the live
+// slots by key before the step phase. LOCAL: no grid-wide partition; each
+// block groups its own live tracks by action and particle type in shared
+// memory during the step phase.
+enum Policy : int { POLICY_NONE = 0, POLICY_ACTION = 1, POLICY_ACTION_TYPE = 2, POLICY_LOCAL = 3 };
+__host__ __device__ __forceinline__ bool global_partition(int policy) {
+  return policy == POLICY_ACTION || policy == POLICY_ACTION_TYPE;
+}
 
 enum ErrorBits : uint32_t { ERR_RING_OVERFLOW = 1u, ERR_NO_PROGRESS = 2u, ERR_ITERATIONS = 4u, ERR_SAMPLING = 8u,
                             ERR_PRIMARIES_REJECTED = 16u, ERR_BARRIER_TIMEOUT = 32u,

@@ -128,7 +128,7 @@ int layer_of(const std::vector<double>& zb, double z, double uz) {
   return lo;
 }
 
-bool policy_sorted(int policy) { return policy == POLICY_ACTION || policy == POLICY_ACTION_TYPE; }
+bool policy_sorted(int policy) { return global_partition(policy); }
 
 int keys_of(int policy) {
   return policy == POLICY_ACTION ? kKeysAlong : (policy == POLICY_ACTION_TYPE ? kKeysFull : 0);
@@ -310,7 +310,7 @@ celer_status validate_problem(const celer_problem* pb, std::string& why) {
   if (pb->n_slots < 1 || pb->n_slots > (1ull << 30)) return why = "n_slots must be in [1, 2^30]", CELER_ERR_INVALID;
   if (pb->init_capacity < 1 || pb->init_capacity > (1ull << 34)) return why = "bad init_capacity", CELER_ERR_INVALID;
   if (pb->max_events < 1) return why = "max_events must be >= 1", CELER_ERR_INVALID;
-  if (pb->sort_policy < 0 || pb->sort_policy > 2) return why = "unknown sort policy", CELER_ERR_INVALID;
+  if (pb->sort_policy < 0 || pb->sort_policy > 3) return why = "unknown sort policy", CELER_ERR_INVALID;
   if (pb->block_size != 0 && pb->block_size != 128 && pb->block_size != 256 && pb->block_size != 512)
     return why = "block_size must be 128, 256 or 512", CELER_ERR_INVALID;
   return CELER_OK;
@@ -824,7 +824,7 @@ celer_status celer_set_split_actions(celer_ctx* ctx, int split) {
 }
 
 celer_status celer_set_sort_policy(celer_ctx* ctx, int policy) {
-  if (!ctx || policy < 0 || policy > 2) return CELER_ERR_INVALID;
+  if (!ctx || policy < 0 || policy > 3) return CELER_ERR_INVALID;
   ctx->p.policy = policy;
   ctx->p.n_keys = keys_of(policy);
   // stored keys belong to the previous policy: rewrite them all at the next step
@@ -893,7 +893,7 @@ celer_status celer_kernel_timing(celer_ctx* ctx, const char** names, double* tot
 celer_status celer_debug_partition(celer_ctx* ctx, uint8_t* keys_out, uint32_t* perm_out, uint32_t* offsets_out,
                                    int* n_keys, int* n_blocks) {
   if (!ctx || !keys_out || !perm_out || !offsets_out || !n_keys || !n_blocks) return CELER_ERR_INVALID;
-  if (!policy_sorted(ctx->p.policy)) return fail(ctx, CELER_ERR_STATE, "no partition under policy NONE");
+  if (!policy_sorted(ctx->p.policy)) return fail(ctx, CELER_ERR_STATE, "no grid-wide partition under this policy");
   celer_status st = read_ctl(ctx);
   if (st != CELER_OK) return st;
   const uint32_t N = ctx->p.n_slots;

@@ -383,7 +383,7 @@ __device__ __forceinline__ void fill_and_limit_chunk(const Params& p, uint32_t g
     nfill = __ldcg(&p.filled[g]);  // set by a separate fill launch
   }
   if (!do_step) return;
-  const bool sorted = p.policy != POLICY_NONE;
+  const bool sorted = global_partition(p.policy);
   const uint8_t vacant_key = p.policy == POLICY_ACTION ? KA_VACANT : K_VACANT_FULL;
   const unsigned csize = (p.n_slots - g * 32u) < 32u ? (p.n_slots - g * 32u) : 32u;
   const bool live = __ldcg(&p.vacant[g]) < csize || nfill > 0;  // warp-uniform
@@ -540,7 +540,7 @@ __device__ void bookkeeping_after_fill_step(const Params& p, bool did_fill, int 
     c->alive += take;
     c->total_vacant = tv - take;
   }
-  if (p.policy != POLICY_NONE) {
+  if (global_partition(p.policy)) {
     uint32_t* offs = p.block_offsets;
     const int live_keys = p.n_keys - 1;  // the last key is the vacant one
     const unsigned long long total = block_scan_counts(
@@ -604,7 +604,7 @@ __device__ void phase_fill_step(const Params& p, int bid, int nb, const SharedSt
         cand = vac < csize;
         if (!cand && fill && vac > 0) cand = __ldcg(&p.tile_prefix[g >> 3]) < queued;
         if (!cand && !do_fill) cand = __ldcg(&p.filled[g]) > 0;  // filled by a separate fill launch
-        if (!cand && do_step && p.policy != POLICY_NONE) cand = p.chunk_dirty[g] != 0;  // keys to reset
+        if (!cand && do_step && global_partition(p.policy)) cand = p.chunk_dirty[g] != 0;  // keys to reset
       }
       unsigned mask = __ballot_sync(0xffffffffu, cand);
       while (mask) {
@@ -618,7 +618,7 @@ __device__ void phase_fill_step(const Params& p, int bid, int nb, const SharedSt
   if (do_step) {
     if (threadIdx.x < A_COUNT && s_acts[threadIdx.x] != 0)
       atomicAdd(&c->action_count[threadIdx.x], s_acts[threadIdx.x]);
-    if (p.policy != POLICY_NONE && (int)threadIdx.x < p.n_keys - 1)
+    if (global_partition(p.policy) && (int)threadIdx.x < p.n_keys - 1)
       p.block_counts[threadIdx.x * nb + bid] = s_keys[threadIdx.x];
     flush_counter(&c->steps_iter, my_steps, false);
   }
@@ -1042,7 +1042,7 @@ __device__ __forceinline__ bool is_interaction(uint8_t act) { return act >= A_CO
 // Work range of the step phase for the policy: all slots (masking), or the
 // partition range of the live keys.
 __device__ __forceinline__ Span live_span(const Params& p) {
-  if (p.policy == POLICY_NONE) return Span{0u, p.n_slots, nullptr};
+  if (!global_partition(p.policy)) return Span{0u, p.n_slots, nullptr};
   const int hi = p.policy == POLICY_ACTION ? KA_VACANT : K_VACANT_FULL;
   return Span{p.ctl->offsets[0], p.ctl->offsets[hi], p.perm};
 }
@@ -1102,6 +1102,144 @@ __device__ void loop_ctl_warp(const Params& p) {
   }
 }
 
+// Along-step and, if the step ends in one, the interaction of the track in
+// `slot` (phase C's body). Returns true if the track ended.
+__device__ __forceinline__ bool step_one(const Params& p, uint32_t slot, uint8_t st, const SharedStatic& ss, bool tight,
+                                         unsigned long long& n_def) {
+  const uint8_t act = p.trk.action[slot];
+  if (st == ALIVE && along_one(p, slot, p.trk.ptype[slot], ss)) return true;
+  return is_interaction(act) && post_one(p, slot, st, act, tight, n_def);
+}
+
+// Phase C under the block-local policy. Block b walks its chunks b, b + nb,
+// ... (those holding live tracks, from the vacancy counts), gathers their
+// live slots into shared memory a round of one chunk per warp at a time, and
+// once a few hundred are gathered (or its chunks are done) groups them by key
+// (action and particle type) with a counting sort. Each group is cut into
+// pieces of 8, 16 or 32 (the smallest size whose piece count fits the warps),
+// and the pieces are dealt to the warps: every warp runs one kind of
+// along-step and interaction, and few tracks spread over all warps.
+__device__ void phase_step_local(const Params& p, int bid, int nb, const SharedStatic& ss, bool tight,
+                                 unsigned long long& killed, unsigned long long& n_def) {
+  constexpr int kCap = 2 * kTile;
+  constexpr int kMaxPieces = kCap / 8 + kMaxKeys;
+  __shared__ uint32_t s_slot[kCap];
+  __shared__ uint32_t s_sorted[kCap];
+  __shared__ uint8_t s_key[kCap];
+  __shared__ uint32_t s_chunks[kTile];
+  __shared__ unsigned s_wn[kTile / 32];
+  __shared__ unsigned s_cnt[kMaxKeys], s_cur[kMaxKeys];
+  __shared__ unsigned short s_pstart[kMaxPieces];
+  __shared__ unsigned char s_plen[kMaxPieces];
+  __shared__ unsigned s_npieces;
+  const Tracks& t = p.trk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (int)(blockDim.x >> 5);
+  const unsigned lt = (1u << lane) - 1u;
+  // group the n gathered slots by key and run them, one piece per warp
+  auto flush = [&](unsigned n) {
+    if (threadIdx.x < kMaxKeys) s_cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_cnt[s_key[i]], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned piece = 32u;
+      for (unsigned pc = 8u; pc <= 32u; pc <<= 1) {  // smallest piece size whose pieces fit the warps
+        unsigned np = 0;
+        for (int k = 0; k < kMaxKeys; ++k) np += (s_cnt[k] + pc - 1) / pc;
+        if (np <= (unsigned)nwarps) {
+          piece = pc;
+          break;
+        }
+      }
+      unsigned off = 0, np = 0;
+      for (int k = 0; k < kMaxKeys; ++k) {
+        const unsigned ck = s_cnt[k];
+        s_cur[k] = off;
+        for (unsigned q = 0; q < ck; q += piece) {
+          s_pstart[np] = (unsigned short)(off + q);
+          s_plen[np] = (unsigned char)(ck - q < piece ? ck - q : piece);
+          ++np;
+        }
+        off += ck;
+      }
+      s_npieces = np;
+    }
+    __syncthreads();
+    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) s_sorted[atomicAdd(&s_cur[s_key[i]], 1u)] = s_slot[i];
+    __syncthreads();
+    const unsigned npieces = s_npieces;
+    for (unsigned q = (unsigned)warp; q < npieces; q += (unsigned)nwarps) {
+      if ((unsigned)lane >= s_plen[q]) continue;
+      const uint32_t sl = s_sorted[s_pstart[q] + lane];
+      if (step_one(p, sl, t.status[sl], ss, tight, n_def)) ++killed;
+    }
+    __syncthreads();  // the lists are reused by the next gather
+  };
+  const uint32_t n_own = (uint32_t)bid < p.n_chunks ? (p.n_chunks - (uint32_t)bid + nb - 1) / nb : 0u;
+  unsigned pending = 0;  // gathered and not yet run (block-uniform)
+  for (uint32_t c0 = 0; c0 < n_own; c0 += blockDim.x) {
+    // this batch's chunks that hold live tracks (or tracks filled this iteration)
+    const uint32_t m = c0 + threadIdx.x;
+    const uint32_t g = (uint32_t)bid + (uint32_t)nb * m;
+    bool cand = false;
+    if (m < n_own) {
+      const unsigned csize = (p.n_slots - g * 32u) < 32u ? (p.n_slots - g * 32u) : 32u;
+      cand = __ldcg(&p.vacant[g]) < csize || __ldcg(&p.filled[g]) > 0;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, cand);
+    __syncthreads();  // the previous batch is done with s_wn / s_chunks
+    if (lane == 0) s_wn[warp] = __popc(bal);
+    __syncthreads();
+    unsigned before = 0, nch = 0;
+    for (int w = 0; w < nwarps; ++w) {
+      const unsigned cw = s_wn[w];
+      before += w < warp ? cw : 0u;
+      nch += cw;
+    }
+    if (cand) s_chunks[before + __popc(bal & lt)] = g;
+    __syncthreads();
+    for (unsigned j0 = 0; j0 < nch; j0 += (unsigned)nwarps) {
+      // gather: one chunk per warp, appended after the `pending` entries
+      const unsigned j = j0 + (unsigned)warp;
+      bool live = false;
+      uint32_t slot = 0;
+      uint8_t key = 0;
+      if (j < nch) {
+        slot = s_chunks[j] * 32u + lane;
+        if (slot < p.n_slots) {
+          const uint8_t st = t.status[slot];
+          if (st != VACANT) {
+            live = true;
+            key = key_of(POLICY_ACTION_TYPE, t.ptype[slot], t.action[slot]);
+          }
+        }
+      }
+      const unsigned lb = __ballot_sync(0xffffffffu, live);
+      if (lane == 0) s_wn[warp] = __popc(lb);
+      __syncthreads();
+      unsigned wb = 0, add = 0;
+      for (int w = 0; w < nwarps; ++w) {
+        const unsigned cw = s_wn[w];
+        wb += w < warp ? cw : 0u;
+        add += cw;
+      }
+      if (live) {
+        const unsigned pos = pending + wb + __popc(lb & lt);
+        s_slot[pos] = slot;
+        s_key[pos] = key;
+      }
+      pending += add;
+      __syncthreads();
+      if (pending >= (unsigned)kTile) {
+        flush(pending);
+        pending = 0;
+      }
+    }
+  }
+  if (pending > 0) flush(pending);
+}
+
 // Phase C: along-step of every live track and, where the step ends in an
 // interaction, that interaction, in partition order; deferred interactions
 // are retried. The last block ends the iteration.
@@ -1112,7 +1250,8 @@ __device__ void phase_step(const Params& p, int bid, int nb, const SharedStatic&
   const Tracks& t = p.trk;
   unsigned long long killed = 0, n_def = 0;
   const uint32_t width = sp.perm ? spread_width(sp.hi - sp.lo, nb) : 32u;
-  for (ChunkWalk w(sp.lo, sp.hi, bid, nb, width); w.more(); w.next()) {
+  if (p.policy == POLICY_LOCAL) phase_step_local(p, bid, nb, ss, tight, killed, n_def);
+  for (ChunkWalk w(sp.lo, p.policy == POLICY_LOCAL ? sp.lo : sp.hi, bid, nb, width); w.more(); w.next()) {
     const uint32_t i = w.index();
     if (i >= sp.hi) continue;
     const uint32_t slot = sp.perm ? sp.perm[i] : i;
@@ -1304,7 +1443,7 @@ __global__ void __launch_bounds__(kTile, 1) k_loop(Params p) {
   stage_static(p, ss);
   const unsigned nb = gridDim.x;
   const int bid = blockIdx.x;
-  const bool sorted = p.policy != POLICY_NONE;
+  const bool sorted = global_partition(p.policy);
   if (bid == 0 && threadIdx.x == 0) {
     clear_iteration_counters(p.ctl);
     p.ctl->cont = 1u;

@@ -44,7 +44,8 @@ TALLY_LAYERS = 1
 SORT_NONE = 0
 SORT_ACTION = 1
 SORT_ACTION_TYPE = 2
-SORT_NAMES = {"none": SORT_NONE, "action": SORT_ACTION, "action_type": SORT_ACTION_TYPE}
+SORT_LOCAL = 3
+SORT_NAMES = {"none": SORT_NONE, "action": SORT_ACTION, "action_type": SORT_ACTION_TYPE, "local": SORT_LOCAL}
 
 DEFAULT_SEED = 20250321
 

@@ -16,7 +16,7 @@ from gpu_helpers import assert_conservation, match_fraction, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
-POLICIES = [wl.SORT_NONE, wl.SORT_ACTION, wl.SORT_ACTION_TYPE]
+POLICIES = [wl.SORT_NONE, wl.SORT_ACTION, wl.SORT_ACTION_TYPE, wl.SORT_LOCAL]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -216,7 +216,7 @@ def test_calorimeter_profile_statistics_independent_seeds():
 
 
 # ------------------------------------------------------------------ calorimeter in a 4 T field
-@pytest.mark.parametrize("policy", [wl.SORT_NONE, wl.SORT_ACTION_TYPE])
+@pytest.mark.parametrize("policy", [wl.SORT_NONE, wl.SORT_ACTION_TYPE, wl.SORT_LOCAL])
 @pytest.mark.parametrize("mode", [binding.LOOP_GRAPH, binding.LOOP_PERSISTENT])
 def test_field_histories(policy, mode):
     prob, prim = wl.calorimeter_field_10gev(40, n_slots=1 << 16)
@@ -247,13 +247,14 @@ def test_event_results_same_alone_and_mixed():
 
 
 # ------------------------------------------------------------------ capacity
-def test_small_initializer_buffer_defers_without_changing_results():
+@pytest.mark.parametrize("policy", [wl.SORT_ACTION_TYPE, wl.SORT_LOCAL])
+def test_small_initializer_buffer_defers_without_changing_results(policy):
     """A buffer far smaller than the shower forces interactions to wait for
     space; deferred interactions replay with the same random numbers, so every
     history is unchanged."""
     prob, prim = wl.calorimeter_1gev(20)
     prob = prob.replace(n_slots=256, init_capacity=64)
-    g = run_gpu(prob, prim, policy=wl.SORT_ACTION_TYPE)
+    g = run_gpu(prob, prim, policy=policy)
     o = run_oracle(prob, prim)
     frac, _ = match_fraction(g, o)
     assert frac >= 0.9
