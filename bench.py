@@ -79,7 +79,8 @@ class ClockSampler:
 
     def __enter__(self):
         """Start sampling every 20 ms and wait (up to 3 s) for the first
-        sample, so that the sampler is live when the timed region starts."""
+        three samples, so that the sampler is live and past its start-up
+        queries when the timed region starts."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -87,7 +88,7 @@ class ClockSampler:
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
             t0 = time.monotonic()
-            while not self.lines and time.monotonic() - t0 < 3.0 and self.proc.poll() is None:
+            while len(self.lines) < 3 and time.monotonic() - t0 < 3.0 and self.proc.poll() is None:
                 time.sleep(0.005)
         except (OSError, FileNotFoundError):
             self.proc = None

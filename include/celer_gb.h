@@ -389,6 +389,23 @@ celer_status celer_debug_curand_philox(uint64_t seed, uint64_t subsequence, uint
  * CELER_ERR_INVALID. */
 celer_status celer_debug_math(int fn, const double* host_x, uint64_t n, double* host_out);
 
+/* Draw one rejection sample per record on the device: which 0 the Compton
+ * (Klein-Nishina, Butcher-Messel) sampler of the step kernels, which decides
+ * each attempt in FP32 and falls back to FP64 near the acceptance boundary,
+ * 1 its plain FP64 form, 2 the step kernels' Moller sampler (same FP32
+ * filtering), 3 its plain FP64 form. Record i: energy host_E[i] MeV (photon
+ * energy, or electron kinetic energy for Moller), random stream key
+ * (seed, event), track id host_tid[i], draw counter host_ctr[i]; cut is the
+ * Moller production cut (MeV, unused for Compton). Outputs (host arrays of n):
+ * eps (E'/E, or T_delta/T), the Compton scattering cosine (0 for Moller), the
+ * draw counter after sampling and the sampler's ok flag. No counterpart in
+ * the paper: it checks that the filtered samplers give bit-identical results
+ * to the plain FP64 ones. which outside 0-3 or null pointers give
+ * CELER_ERR_INVALID. */
+celer_status celer_debug_sample(int which, uint32_t seed, uint32_t event, const double* host_E, double cut,
+                                const uint64_t* host_tid, const uint32_t* host_ctr, uint64_t n, double* eps_out,
+                                double* cost_out, uint32_t* ctr_out, uint8_t* ok_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -113,6 +113,7 @@ EXPORTS = [
     "celer_enable_kernel_timing", "celer_kernel_timing", "celer_debug_partition", "celer_debug_table",
     "celer_debug_philox", "celer_debug_curand_philox", "celer_partition_keys_noalloc", "celer_debug_math",
     "celer_run_iterations", "celer_read_event_live", "celer_serve", "celer_autotune", "celer_get_problem",
+    "celer_debug_sample",
 ]
 
 _lib = None
@@ -153,6 +154,7 @@ def load(path: Optional[str] = None):
         "celer_debug_philox": ([vp, vp, u64], i32),
         "celer_debug_math": ([i32, vp, u64, vp], i32),
         "celer_debug_curand_philox": ([u64, u64, u64, vp, u64], i32),
+        "celer_debug_sample": ([i32, u32, u32, vp, C.c_double, vp, vp, u64, vp, vp, vp, vp], i32),
         "celer_partition_keys_noalloc": ([vp, u64, i32, i32, vp, vp, vp], i32),
         "celer_run_iterations": ([vp, i32, u64, C.POINTER(u64)], i32),
         "celer_read_event_live": ([vp, u32, u32, vp], i32),
@@ -465,3 +467,21 @@ def debug_curand_philox(seed: int, subsequence: int, offset4: int, n: int) -> np
     out = np.zeros((n, 4), np.uint32)
     _check(load().celer_debug_curand_philox(seed, subsequence, offset4, out.ctypes.data, n))
     return out
+
+def debug_sample(which: int, E: np.ndarray, tid: np.ndarray, ctr: np.ndarray, seed: int = 20250321, event: int = 0,
+                 cut: float = 1.0):
+    """Device rejection samplers: which 0 filtered Compton, 1 plain FP64
+    Compton, 2 filtered Moller, 3 plain FP64 Moller. Returns eps, cos(theta)
+    (Compton), the draw counter after sampling and the ok flags."""
+    e = np.ascontiguousarray(E, dtype=np.float64)
+    t = np.ascontiguousarray(tid, dtype=np.uint64)
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    n = len(e)
+    eps = np.zeros(n)
+    cost = np.zeros(n)
+    ctr_out = np.zeros(n, np.uint32)
+    ok = np.zeros(n, np.uint8)
+    _check(load().celer_debug_sample(int(which), C.c_uint32(seed), C.c_uint32(event), e.ctypes.data, C.c_double(cut),
+                                     t.ctypes.data, c.ctypes.data, C.c_uint64(n), eps.ctypes.data, cost.ctypes.data,
+                                     ctr_out.ctypes.data, ok.ctypes.data))
+    return eps, cost, ctr_out, ok

@@ -54,6 +54,30 @@ __global__ void k_math(int fn, const double* mt, const double* x, double* out, u
   }
 }
 
+
+// One rejection sample per record: which 0 the FP32-filtered Compton sampler
+// of the step kernels, 1 its plain FP64 form, 2 the filtered Moller sampler,
+// 3 its plain FP64 form.
+__global__ void k_sample(int which, uint32_t seed, uint32_t event, const double* mt, const double* E, double cut,
+                         const uint64_t* tid, const uint32_t* ctr, double* eps_out, double* cost_out,
+                         uint32_t* ctr_out, uint8_t* ok_out, uint64_t n) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    celer::TrackRng rng(seed, event, tid[i], ctr[i]);
+    bool ok = false;
+    double eps = 0.0, cost = 0.0;
+    switch (which) {
+      case 0: eps = celer::sample_compton(E[i], rng, cost, ok, mt); break;
+      case 1: eps = celer::sample_compton_fp64(E[i], rng, cost, ok, mt); break;
+      case 2: eps = celer::sample_moller(E[i], cut, rng, ok); break;
+      default: eps = celer::sample_moller_fp64(E[i], cut, rng, ok); break;
+    }
+    eps_out[i] = eps;
+    cost_out[i] = cost;
+    ctr_out[i] = rng.ctr;
+    ok_out[i] = ok ? 1 : 0;
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -119,6 +143,51 @@ celer_status celer_debug_curand_philox(uint64_t seed, uint64_t subsequence, uint
   if (st == CELER_OK && cudaMemcpy(host_out, d_out, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost) != cudaSuccess)
     st = CELER_ERR_CUDA;
   cudaFree(d_out);
+  return st;
+}
+
+celer_status celer_debug_sample(int which, uint32_t seed, uint32_t event, const double* host_E, double cut,
+                                const uint64_t* host_tid, const uint32_t* host_ctr, uint64_t n, double* eps_out,
+                                double* cost_out, uint32_t* ctr_out, uint8_t* ok_out) {
+  if (which < 0 || which > 3 || !host_E || !host_tid || !host_ctr || !eps_out || !cost_out || !ctr_out || !ok_out)
+    return CELER_ERR_INVALID;
+  if (n == 0) return CELER_OK;
+  std::vector<double> table(celer::kMathTableSize);
+  celer::build_math_table(table.data());
+  double *d_mt = nullptr, *d_E = nullptr, *d_eps = nullptr, *d_cost = nullptr;
+  uint64_t* d_tid = nullptr;
+  uint32_t *d_ctr = nullptr, *d_ctr_out = nullptr;
+  uint8_t* d_ok = nullptr;
+  celer_status st = CELER_OK;
+  if (cudaMalloc(&d_mt, sizeof(double) * table.size()) != cudaSuccess || cudaMalloc(&d_E, sizeof(double) * n) != cudaSuccess ||
+      cudaMalloc(&d_eps, sizeof(double) * n) != cudaSuccess || cudaMalloc(&d_cost, sizeof(double) * n) != cudaSuccess ||
+      cudaMalloc(&d_tid, sizeof(uint64_t) * n) != cudaSuccess || cudaMalloc(&d_ctr, sizeof(uint32_t) * n) != cudaSuccess ||
+      cudaMalloc(&d_ctr_out, sizeof(uint32_t) * n) != cudaSuccess || cudaMalloc(&d_ok, n) != cudaSuccess)
+    st = CELER_ERR_CUDA;
+  if (st == CELER_OK &&
+      (cudaMemcpy(d_mt, table.data(), sizeof(double) * table.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemcpy(d_E, host_E, sizeof(double) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemcpy(d_tid, host_tid, sizeof(uint64_t) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemcpy(d_ctr, host_ctr, sizeof(uint32_t) * n, cudaMemcpyHostToDevice) != cudaSuccess))
+    st = CELER_ERR_CUDA;
+  if (st == CELER_OK) {
+    const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    k_sample<<<grid, 256>>>(which, seed, event, d_mt, d_E, cut, d_tid, d_ctr, d_eps, d_cost, d_ctr_out, d_ok, n);
+    if (cudaGetLastError() != cudaSuccess) st = CELER_ERR_CUDA;
+  }
+  if (st == CELER_OK && (cudaMemcpy(eps_out, d_eps, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                         cudaMemcpy(cost_out, d_cost, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                         cudaMemcpy(ctr_out, d_ctr_out, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                         cudaMemcpy(ok_out, d_ok, n, cudaMemcpyDeviceToHost) != cudaSuccess))
+    st = CELER_ERR_CUDA;
+  cudaFree(d_mt);
+  cudaFree(d_E);
+  cudaFree(d_eps);
+  cudaFree(d_cost);
+  cudaFree(d_tid);
+  cudaFree(d_ctr);
+  cudaFree(d_ctr_out);
+  cudaFree(d_ok);
   return st;
 }
 

@@ -248,6 +248,48 @@ static __device__ __noinline__ double helix_side_distance(Curvature c, double x,
 }
 
 // ------------------------------------------------------------- interactions
+// The rejection samplers below decide each attempt in FP32 and fall back to
+// FP64 only near the acceptance boundary. An FP64 warp instruction holds a
+// GB300 sub-partition's FP64 pipe for 64 cycles, an FP32 one for about two,
+// so an FP64 attempt (~40 instructions with its exp or sqrt) costs ~2,500
+// cycles and an FP32 one a few hundred. Only the accepted attempt's value is
+// computed in FP64, by the same expressions as the plain FP64 sampler, so
+// the samples are bit-identical to it:
+//  * the FP32 quantities are evaluated from cancellation-free forms
+//    (1 - eps by expm1 or an algebraic rewrite, 2b - a likewise) with
+//    relative errors below 2^-16 of the values the FP64 expressions
+//    approximate, and the FP64 expressions are within 2^-19 of them
+//    whenever 1 - eps >= 2^-30 and 2b - a >= 2^-30 (2k + 1) eps, which the
+//    filter checks;
+//  * a decision is taken in FP32 only if the two sides differ by more than
+//    kFilterMargin = 2^-12 relative, far above both error bounds, so both
+//    evaluations take the same decision; otherwise (probability ~2^-11 per
+//    attempt) the FP64 test of the plain sampler decides.
+// The filter covers k = E/m in [1e-4, 1e6] (Compton) and x = Tcut/T in
+// [1e-8, 1/2) (Moller); other inputs take the plain FP64 sampler.
+constexpr float kFilterMargin = 0x1p-12f;
+constexpr float kFilterTiny = 0x1p-30f;
+
+// n 2^-53 in FP32 for 1 <= n < 2^53, truncated to 24 bits (relative error
+// below 2^-23), by integer operations only: with the draw word w,
+// n = 2 (w >> 12) + 1 gives the draw u and 2^53 - n gives 1 - u.
+__device__ __forceinline__ float f32_scaled_2m53(unsigned long long n) {
+  const int lz = __clzll((long long)n);  // 11 .. 63
+  const unsigned m24 = (unsigned)((n << lz) >> 40);
+  return __uint_as_float(((unsigned)(137 - lz) << 23) | (m24 & 0x7FFFFFu));
+}
+__device__ __forceinline__ unsigned long long draw_numerator(unsigned long long w) { return ((w >> 12) << 1) | 1ull; }
+constexpr unsigned long long k2p53 = 1ull << 53;
+
+// A positive normal double in the FP32 exponent range, truncated to FP32
+// (relative error below 2^-23) by integer operations.
+__device__ __forceinline__ float f32_trunc(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned e = ((hi >> 20) & 0x7FFu) - 1023u + 127u;
+  return __uint_as_float((e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+
 // Klein-Nishina sampling of eps = E'/E by Butcher and Messel's
 // composition-rejection: branch 1 samples eps from 1/eps (eps = eps0^u), branch
 // 2 samples eps^2 uniformly; both are accepted with 1 - eps sin^2 / (1 + eps^2).
@@ -256,24 +298,25 @@ static __device__ __noinline__ double helix_side_distance(Curvature c, double x,
 // t = 1 - cos = a / b and sin^2 = a (2b - a) / b^2, so the test
 // u3 <= 1 - eps sin^2 / (1 + eps^2) is taken multiplied through by the
 // positive b^2 (1 + eps^2), without divisions; t is divided out once, for
-// the accepted attempt.
-static __device__ __noinline__ double sample_compton(double E, TrackRng& rng, double& cost, bool& ok,
-                                                     const double* mt) {
+// the accepted attempt. This is the plain FP64 form; sample_compton below
+// gives the same results with FP32 filtering.
+static __device__ __noinline__ double sample_compton_fp64(double E, TrackRng& rng, double& cost, bool& ok,
+                                                          const double* mt) {
   const double k = E / kMe;
   const double eps0 = 1.0 / (1.0 + 2.0 * k);
   const double eps0sq = eps0 * eps0;
   const double a1 = -fast_log(eps0, mt);
-  const double a2 = 0.5 * (1.0 - eps0sq);
+  const double w = 1.0 - eps0sq;
   double eps = 1.0, t = 0.0;
   ok = false;
   for (int attempt = 0; attempt < kMaxAttempts; ++attempt) {
     const double u1 = rng.uniform();
     const double u2 = rng.uniform();
     const double u3 = rng.uniform();
-    if (u1 * (a1 + a2) < a1) {
+    if (u1 * (a1 + 0.5 * w) < a1) {
       eps = fast_exp(-a1 * u2, mt);
     } else {
-      eps = sqrt(eps0sq + (1.0 - eps0sq) * u2);
+      eps = sqrt(fma(w, u2, eps0sq));
     }
     const double a = 1.0 - eps;
     const double b = k * eps;
@@ -288,11 +331,104 @@ static __device__ __noinline__ double sample_compton(double E, TrackRng& rng, do
   return eps;
 }
 
+// FP32-filtered Compton sampler (same draws, same results as
+// sample_compton_fp64). Per attempt, with u = u1..u3 and v = 1 - u:
+//  branch: u1 (a1 + a2) < a1;
+//  branch 1: x = a1 u2, eps = e^-x, a = -expm1(-x), 2b - a = (2k + 1) eps - 1
+//    = expm1(a1 v2) (since (2k + 1) e^-a1 = 1 up to the FP64 roundings of
+//    eps0 and a1, an absolute 2^-47.7 (2k + 1) eps);
+//  branch 2: eps = sqrt(eps0^2 + w u2), w = 1 - eps0^2, a = w v2 / (1 + eps),
+//    2b - a = (2k + 1) w u2 / (eps + eps0);
+//  accept: eps a (2b - a) <= v3 b^2 (1 + eps^2).
+// The loop keeps only the accepted attempt's draw and branch; its FP64 value
+// is computed once after the loop, where the warp has reconverged (inside
+// the loop, lanes accepting at different attempts would each run it).
+static __device__ __noinline__ double sample_compton(double E, TrackRng& rng, double& cost, bool& ok,
+                                                     const double* mt) {
+  const double k = E / kMe;
+  if (!(k >= 1e-4 && k <= 1e6)) return sample_compton_fp64(E, rng, cost, ok, mt);
+  const double eps0 = 1.0 / (1.0 + 2.0 * k);
+  const double eps0sq = eps0 * eps0;
+  const double a1 = -fast_log(eps0, mt);
+  const double w = 1.0 - eps0sq;
+  const float kf = f32_trunc(k), e0f = f32_trunc(eps0), e0sqf = f32_trunc(eps0sq), a1f = f32_trunc(a1);
+  const float wf = f32_trunc(w);
+  const float k21f = fmaf(2.0f, kf, 1.0f);
+  const float sf = fmaf(0.5f, wf, a1f);
+  unsigned long long w2_acc = 0;
+  int branch_acc = 0;
+  ok = false;
+  for (int attempt = 0; attempt < kMaxAttempts; ++attempt) {
+    const unsigned long long w1 = rng.raw(), w2 = rng.raw(), w3 = rng.raw();
+    int branch = 0;   // 1 or 2 once decided
+    int verdict = -1; // 1 accept, 0 reject, -1 undecided
+    {
+      const unsigned long long n2 = draw_numerator(w2);
+      const float u1f = f32_scaled_2m53(draw_numerator(w1));
+      const float u2f = f32_scaled_2m53(n2), v2f = f32_scaled_2m53(k2p53 - n2);
+      const float v3f = f32_scaled_2m53(k2p53 - draw_numerator(w3));
+      const float p = u1f * sf;
+      if (p < a1f * (1.0f - kFilterMargin)) {
+        branch = 1;
+      } else if (p > a1f * (1.0f + kFilterMargin)) {
+        branch = 2;
+      }
+      if (branch != 0) {
+        float ef, af, cf;
+        if (branch == 1) {
+          const float x = a1f * u2f;
+          ef = expf(-x);
+          af = -expm1f(-x);
+          cf = expm1f(a1f * v2f);
+        } else {
+          ef = sqrtf(fmaf(wf, u2f, e0sqf));
+          af = wf * v2f / (1.0f + ef);
+          cf = k21f * wf * u2f / (ef + e0f);
+        }
+        if (af >= kFilterTiny && cf >= kFilterTiny * k21f * ef) {
+          const float bf = kf * ef;
+          const float L = ef * af * cf;
+          const float R = v3f * (bf * bf) * fmaf(ef, ef, 1.0f);
+          if (L < R * (1.0f - kFilterMargin)) {
+            verdict = 1;
+          } else if (L > R * (1.0f + kFilterMargin)) {
+            verdict = 0;
+          }
+        }
+      }
+    }
+    if (verdict == 0) continue;
+    if (verdict < 0) {  // the plain FP64 attempt
+      const double u2 = unit_from_bits(w2);
+      if (branch == 0) branch = (unit_from_bits(w1) * (a1 + 0.5 * w) < a1) ? 1 : 2;
+      const double e = branch == 1 ? fast_exp(-a1 * u2, mt) : sqrt(fma(w, u2, eps0sq));
+      const double a = 1.0 - e;
+      const double b = k * e;
+      const double B = b * b * (1.0 + e * e);
+      if (!(e * a * (2.0 * b - a) <= (1.0 - unit_from_bits(w3)) * B)) continue;
+    }
+    w2_acc = w2;
+    branch_acc = branch;
+    ok = true;
+    break;
+  }
+  double eps = 1.0, t = 0.0;
+  if (ok) {
+    const double u2 = unit_from_bits(w2_acc);
+    eps = branch_acc == 1 ? fast_exp(-a1 * u2, mt) : sqrt(fma(w, u2, eps0sq));
+    t = (1.0 - eps) / (k * eps);
+  }
+  cost = 1.0 - t;
+  return eps;
+}
+
 // Moller: eps = T_delta / T in [x, 1/2] from the 1/eps^2 proposal, accepted
 // with eps^2 B(eps) normalised by its maximum (9g^2 - 10g + 5)/4 at eps = 1/2.
 // The test u2 <= norm f(eps) is taken multiplied by the positive (1 - eps)^2.
-static __device__ __noinline__ double sample_moller(double T, double Tcut, TrackRng& rng, bool& ok) {
+// Plain FP64 form; sample_moller below gives the same results.
+static __device__ __noinline__ double sample_moller_fp64(double T, double Tcut, TrackRng& rng, bool& ok) {
   const double x = Tcut / T;
+  const double y = 1.0 - 2.0 * x;
   const double g = T / kMe + 1.0;
   const double g2 = g * g;
   const double norm = 4.0 / (9.0 * g2 - 10.0 * g + 5.0);
@@ -301,7 +437,7 @@ static __device__ __noinline__ double sample_moller(double T, double Tcut, Track
   for (int attempt = 0; attempt < kMaxAttempts; ++attempt) {
     const double u1 = rng.uniform();
     const double u2 = rng.uniform();
-    eps = x / (1.0 - u1 * (1.0 - 2.0 * x));
+    eps = x / fma(-u1, y, 1.0);
     const double om = 1.0 - eps;
     const double eom = eps * om;
     const double fom2 = (g - 1.0) * (g - 1.0) * eom * eom - (2.0 * g2 + 2.0 * g - 1.0) * eom + g2;
@@ -311,6 +447,69 @@ static __device__ __noinline__ double sample_moller(double T, double Tcut, Track
     }
   }
   return eps;
+}
+
+// FP32-filtered Moller sampler (same draws, same results as
+// sample_moller_fp64). The proposal's denominator 1 - u1 (1 - 2x) is taken as
+// v1 + 2x u1 (no cancellation); the polynomial (g-1)^2 eom^2 - (2g^2 + 2g - 1)
+// eom + g^2 is at least 1/7 of the sum of its terms' magnitudes for g >= 1
+// and eom <= 1/4, and 9g^2 - 10g + 5 at least 1/6 of its terms', so their
+// FP32 relative errors stay below 2^-16; g - 1 = T/m is formed directly.
+// g, g^2 and the normalisation are needed in FP64 only for an undecided
+// attempt; the accepted attempt's eps is computed once, after the loop.
+static __device__ __noinline__ double sample_moller(double T, double Tcut, TrackRng& rng, bool& ok) {
+  const double x = Tcut / T;
+  if (!(x >= 1e-8 && x < 0.5)) return sample_moller_fp64(T, Tcut, rng, ok);
+  const double y = 1.0 - 2.0 * x;
+  const float tmf = f32_trunc(T) * (float)(1.0 / kMe);  // g - 1
+  const float gf = tmf + 1.0f;
+  const float g2f = gf * gf;
+  const float normf = 4.0f / fmaf(9.0f, g2f, fmaf(-10.0f, gf, 5.0f));
+  const float c1f = tmf * tmf;
+  const float c2f = fmaf(2.0f, g2f, fmaf(2.0f, gf, -1.0f));
+  const float xf = f32_trunc(x);
+  const float txf = 2.0f * xf;
+  double g = 0.0, g2 = 0.0, norm = 0.0;
+  bool fp64_ready = false;
+  unsigned long long w1_acc = 0;
+  ok = false;
+  for (int attempt = 0; attempt < kMaxAttempts; ++attempt) {
+    const unsigned long long w1 = rng.raw(), w2 = rng.raw();
+    int verdict = -1;
+    {
+      const unsigned long long n1 = draw_numerator(w1);
+      const float u1f = f32_scaled_2m53(n1), v1f = f32_scaled_2m53(k2p53 - n1);
+      const float u2f = f32_scaled_2m53(draw_numerator(w2));
+      const float ef = xf / fmaf(u1f, txf, v1f);
+      const float omf = 1.0f - ef;
+      const float eomf = ef * omf;
+      const float L = u2f * (omf * omf);
+      const float R = normf * (fmaf(c1f * eomf, eomf, -c2f * eomf) + g2f);
+      if (L < R * (1.0f - kFilterMargin)) {
+        verdict = 1;
+      } else if (L > R * (1.0f + kFilterMargin)) {
+        verdict = 0;
+      }
+    }
+    if (verdict == 0) continue;
+    if (verdict < 0) {  // the plain FP64 attempt
+      if (!fp64_ready) {
+        g = T / kMe + 1.0;
+        g2 = g * g;
+        norm = 4.0 / (9.0 * g2 - 10.0 * g + 5.0);
+        fp64_ready = true;
+      }
+      const double e = x / fma(-unit_from_bits(w1), y, 1.0);
+      const double om = 1.0 - e;
+      const double eom = e * om;
+      const double fom2 = (g - 1.0) * (g - 1.0) * eom * eom - (2.0 * g2 + 2.0 * g - 1.0) * eom + g2;
+      if (!(unit_from_bits(w2) * (om * om) <= norm * fom2)) continue;
+    }
+    w1_acc = w1;
+    ok = true;
+    break;
+  }
+  return ok ? x / fma(-unit_from_bits(w1_acc), y, 1.0) : 0.5;
 }
 
 }  // namespace celer
