@@ -17,6 +17,7 @@ constexpr int kMaxLayers = 1024;
 constexpr int kMaxKeys = 16;
 constexpr int kTile = 256;          // slots per tile: partition, initializer and step-limit work unit
 constexpr int kTraceRows = 1 << 16;
+constexpr int kMaxLoopBlocks = 4096;  // grid of the persistent loop and the block-local launches
 
 // device table columns
 enum Col : int { COL_COMPTON = 0, COL_PE, COL_PAIR, COL_MOLLER, COL_BREMS, COL_RANGE };
@@ -124,6 +125,13 @@ struct Ctl {
   unsigned long long iter_max[2][4];
   unsigned long long max_total[4];
   unsigned long long book_total[2];
+  // block-local policy (one pass per block and iteration): initializers the
+  // next iteration takes, its secondary-buffer verdict, the last-block ticket
+  // of the per-block vacancy scan, and the grid that scan was made for
+  unsigned long long fill_take;
+  unsigned int defer_local;
+  unsigned int done_p;
+  unsigned int local_blocks;
 };
 
 struct TraceRow {
@@ -148,6 +156,9 @@ struct Params {
   uint8_t* chunk_dirty;    // 1 if the chunk's stored keys may name live keys (n_chunks); after
                            // phase A: 1 exactly for the chunks holding live keys
   unsigned int* barrier;   // grid barrier state of the persistent loop: count, generation, abort
+  uint32_t* block_vacant;  // block-local policy: vacant slots of each block's chunks (grid of the loop)
+  uint32_t* block_quota;   // initializers each block takes in the next iteration (level filling)
+  unsigned long long* block_prefix;  // exclusive scan of the quotas: each block's first initializer
   // partition
   int policy;
   int n_keys;

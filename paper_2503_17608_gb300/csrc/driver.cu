@@ -65,6 +65,7 @@ struct celer_ctx {
   std::vector<cudaEvent_t> t_start, t_stop;
   std::vector<int> t_kid;
   int t_used = 0;
+  bool tiles_stale = false;  // the per-tile vacancy prefix predates the last block-local iterations
   double t_total_ms[KID_COUNT] = {};
   uint64_t t_launches[KID_COUNT] = {};
 };
@@ -167,11 +168,32 @@ void timed(celer_ctx* ctx, cudaStream_t s, int kid, F&& launch, bool allow_timin
 // end of iteration). Per action (split_actions), as in the paper's loop over
 // actions: fill, step limit, scatter, one along-step kernel per particle kind,
 // one kernel per interaction, end of iteration.
+// The block-local policy runs one fused launch per iteration (phase-merged
+// modes); it needs the per-block vacancy scan at the start of each run.
+bool fused_local(const celer_ctx* ctx) { return !ctx->split_actions && ctx->p.policy == POLICY_LOCAL; }
+
+// Start of a run (or a single step): the block-local iterations start from a
+// fresh per-block vacancy scan; the others, after block-local ones, from a
+// fresh per-tile scan.
+void begin_policy_run(celer_ctx* ctx) {
+  if (fused_local(ctx)) {
+    launch_local_prepare(ctx->p, ctx->shape, ctx->stream);
+    ctx->tiles_stale = true;
+  } else if (ctx->tiles_stale) {
+    launch_scan_tiles(ctx->p, ctx->stream);
+    ctx->tiles_stale = false;
+  }
+}
+
 void launch_iteration(celer_ctx* ctx, cudaStream_t s, unsigned long long handle, int use_handle) {
   const Params& p = ctx->p;
   const LaunchShape& sh = ctx->shape;
   const bool t = use_handle == 0;
   const bool sorted = policy_sorted(p.policy);
+  if (!ctx->split_actions && p.policy == POLICY_LOCAL) {
+    timed(ctx, s, KID_LOCAL, [&] { launch_local(p, sh, handle, use_handle, s); }, t);
+    return;
+  }
   if (!ctx->split_actions) {
     timed(ctx, s, KID_FILL_STEP, [&] { launch_fill_step(p, sh, s); }, t);
     if (sorted) timed(ctx, s, KID_SCATTER, [&] { launch_scatter(p, sh, s); }, t);
@@ -498,6 +520,9 @@ celer_status celer_create(const celer_problem* pb, celer_ctx** out) {
   const size_t max_blocks = p.n_tiles > 4096 ? p.n_tiles : 4096;
   CREATE_CUDA(dalloc(ctx, &p.block_counts, (size_t)kKeysFull * max_blocks));
   CREATE_CUDA(dalloc(ctx, &p.block_offsets, (size_t)kKeysFull * max_blocks));
+  CREATE_CUDA(dalloc(ctx, &p.block_vacant, (size_t)kMaxLoopBlocks));
+  CREATE_CUDA(dalloc(ctx, &p.block_quota, (size_t)kMaxLoopBlocks));
+  CREATE_CUDA(dalloc(ctx, &p.block_prefix, (size_t)kMaxLoopBlocks));
   double* d_zb = nullptr;
   int32_t* d_lmat = nullptr;
   CREATE_CUDA(dalloc(ctx, &d_zb, L + 1));
@@ -646,6 +671,7 @@ celer_status celer_add_primaries_device(celer_ctx* ctx, uint32_t event, const ce
 
 celer_status celer_step(celer_ctx* ctx, celer_step_stats* stats) {
   if (!ctx) return CELER_ERR_INVALID;
+  begin_policy_run(ctx);
   launch_iteration(ctx, ctx->stream, 0, 0);
   CELER_CUDA(ctx, cudaGetLastError());
   if (stats) {
@@ -665,6 +691,7 @@ celer_status celer_run_iterations(celer_ctx* ctx, int mode, uint64_t budget, uin
   // iteration budget of this run; last-block tickets start from zero (an
   // aborted run could leave them set)
   launch_begin_run(ctx->p, budget, ctx->stream);
+  begin_policy_run(ctx);
   CELER_CUDA(ctx, cudaGetLastError());
   if (mode == CELER_LOOP_GRAPH) {
     if (!ctx->graph_exec || ctx->graph_policy != ctx->p.policy || ctx->graph_split != ctx->split_actions) {

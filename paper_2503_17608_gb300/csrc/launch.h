@@ -29,6 +29,12 @@ cudaError_t configure_kernels(const Params& p, int block, LaunchShape* shape);
 void launch_fill_step(const Params& p, const LaunchShape& sh, cudaStream_t s);
 void launch_scatter(const Params& p, const LaunchShape& sh, cudaStream_t s);
 void launch_step(const Params& p, const LaunchShape& sh, unsigned long long handle, int use_handle, cudaStream_t s);
+// block-local policy: one launch per iteration, and the per-block vacancy
+// scan a run starts with (both on the loop's grid)
+void launch_local(const Params& p, const LaunchShape& sh, unsigned long long handle, int use_handle, cudaStream_t s);
+void launch_local_prepare(const Params& p, const LaunchShape& sh, cudaStream_t s);
+// per-tile vacancy scan for a slot-order run after block-local iterations
+void launch_scan_tiles(const Params& p, cudaStream_t s);
 // per-action launches
 void launch_fill(const Params& p, const LaunchShape& sh, cudaStream_t s);
 void launch_pre_step(const Params& p, const LaunchShape& sh, cudaStream_t s);
@@ -54,7 +60,8 @@ void launch_push_device_primaries(const Params& p, const DevicePrimary* src, uin
 const char* kernel_name(int id);
 enum KernelId : int {
   KID_FILL_STEP = 0, KID_SCATTER, KID_STEP, KID_FILL, KID_PRE_STEP, KID_ALONG_NEUTRAL, KID_ALONG_CHARGED,
-  KID_POST_COMPTON, KID_POST_PE, KID_POST_PAIR, KID_POST_MOLLER, KID_POST_BREMS, KID_LOOP_CTL, KID_LOOP, KID_COUNT
+  KID_POST_COMPTON, KID_POST_PE, KID_POST_PAIR, KID_POST_MOLLER, KID_POST_BREMS, KID_LOOP_CTL, KID_LOOP, KID_LOCAL,
+  KID_COUNT
 };
 
 }  // namespace celer

@@ -1047,14 +1047,31 @@ __device__ __forceinline__ Span live_span(const Params& p) {
   return Span{p.ctl->offsets[0], p.ctl->offsets[hi], p.perm};
 }
 
+// Plan of the block-local policy's next fill (one thread, between
+// iterations): the initializers it takes, min(vacant slots, queued), and
+// whether the secondary buffer could overflow during that iteration: every
+// track steps at most once and creates at most two secondaries, and the
+// taken entries stay counted until the iteration ends, so the buffer is
+// sure to suffice if queued + 2 (live + taken) fits its capacity.
+__device__ __forceinline__ unsigned long long plan_local_fill(const Params& p, unsigned long long head,
+                                                              unsigned long long tail, unsigned long long alive,
+                                                              unsigned long long total_vacant) {
+  Ctl* c = p.ctl;
+  const unsigned long long queued = tail - head;
+  const unsigned long long take = total_vacant < queued ? total_vacant : queued;
+  c->fill_take = take;
+  c->defer_local = (queued + 2ull * (alive + take) > p.ring_capacity) ? 1u : 0u;
+  return take;
+}
+
 // End of an iteration: counters, the per-iteration trace row, stall and
 // iteration-limit checks, the loop condition, and the per-iteration counters
 // cleared for the next one. One warp: every counter is read in one batch of
 // loads, the per-action counts one per lane.
-__device__ void loop_ctl_warp(const Params& p) {
+__device__ void loop_ctl_warp(const Params& p, unsigned long long* take_out = nullptr) {
   Ctl* c = p.ctl;
   const int lane = threadIdx.x & 31;
-  const unsigned long long head = c->head, tail = c->tail, alive = c->alive;
+  const unsigned long long head = c->head, tail = c->tail, alive = c->alive, total_vacant = c->total_vacant;
   const unsigned long long steps_iter = c->steps_iter, steps_total = c->steps_total;
   const unsigned long long iteration = c->iteration, trace_count = c->trace_count;
   const unsigned long long max_iterations = c->max_iterations, budget_end = c->budget_end;
@@ -1099,6 +1116,8 @@ __device__ void loop_ctl_warp(const Params& p) {
     c->cont = (pending && err == 0u && it < budget_end) ? 1u : 0u;
     c->steps_iter = 0;
     c->n_deferred = 0;
+    const unsigned long long take = plan_local_fill(p, head, tail, alive, total_vacant);
+    if (take_out) *take_out = take;
   }
 }
 
@@ -1111,34 +1130,193 @@ __device__ __forceinline__ bool step_one(const Params& p, uint32_t slot, uint8_t
   return is_interaction(act) && post_one(p, slot, st, act, tight, n_def);
 }
 
-// Phase C under the block-local policy. Block b walks its chunks b, b + nb,
-// ... (those holding live tracks, from the vacancy counts), gathers their
-// live slots into shared memory a round of one chunk per warp at a time, and
-// once a few hundred are gathered (or its chunks are done) groups them by key
-// (action and particle type) with a counting sort. Each group is cut into
-// pieces of 8, 16 or 32 (the smallest size whose piece count fits the warps),
-// and the pieces are dealt to the warps: every warp runs one kind of
-// along-step and interaction, and few tracks spread over all warps.
-__device__ void phase_step_local(const Params& p, int bid, int nb, const SharedStatic& ss, bool tight,
-                                 unsigned long long& killed, unsigned long long& n_def) {
+// Block-wide exclusive scan of one count per thread (blockDim.x a multiple
+// of 32, at most 32 warps); returns the thread's exclusive prefix and sets
+// total to the block's sum. Every thread must call it.
+__device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned& total) {
+  __shared__ unsigned s_w[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (int)(blockDim.x >> 5);
+  unsigned incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  __syncthreads();
+  if (lane == 31) s_w[warp] = incl;
+  __syncthreads();
+  unsigned before = 0, all = 0;
+  for (int w = 0; w < nwarps; ++w) {
+    const unsigned cw = s_w[w];
+    before += w < warp ? cw : 0u;
+    all += cw;
+  }
+  total = all;
+  return before + incl - v;
+}
+
+// Vacant slots of this block's chunks b, b + nb, ... (block-local policy),
+// summed by the whole block into block_vacant[b].
+__device__ __forceinline__ void count_block_vacancies(const Params& p, int bid, int nb) {
+  __shared__ unsigned long long s_r[32];
+  const uint32_t n_own = (uint32_t)bid < p.n_chunks ? (p.n_chunks - (uint32_t)bid + nb - 1) / nb : 0u;
+  unsigned long long own = 0;
+  for (uint32_t m = threadIdx.x; m < n_own; m += blockDim.x) own += __ldcg(&p.vacant[(uint32_t)bid + (uint32_t)nb * m]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) own += __shfl_xor_sync(0xffffffffu, own, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) s_r[threadIdx.x >> 5] = own;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long sum = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += s_r[w];
+    p.block_vacant[bid] = (uint32_t)sum;
+  }
+}
+
+// Level filling of the block-local policy's next fill, by one whole block:
+// the `take` initializers are dealt to the nb blocks as evenly as their
+// vacancies allow. With v_b the vacant slots of block b, the level L is the
+// largest with sum_b min(v_b, L) <= take; block b takes min(v_b, L), plus one
+// for the first (take - that sum) blocks, in block order, with v_b > L. The
+// quotas' exclusive scan gives each block's first initializer. Fresh tracks
+// thus spread over all SMs (a block fills its lowest vacancies, in its chunk
+// order), and the fill stays deterministic. s_v holds v_b; vmin and vmax
+// are their extremes. When every block has room for take/nb + 1 the level
+// is take/nb; otherwise one warp finds it by bisection.
+__device__ void plan_block_quotas(const Params& p, const uint32_t* s_v, int nb, unsigned vmin, unsigned vmax,
+                                  unsigned long long take) {
+  __shared__ unsigned s_level, s_extra;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long l0 = take / (unsigned)nb;
+  if (l0 + 1 <= vmin) {
+    if (threadIdx.x == 0) {
+      s_level = (unsigned)l0;
+      s_extra = (unsigned)(take - l0 * (unsigned)nb);
+    }
+  } else if (threadIdx.x < 32) {
+    unsigned lo = 0, hi = vmax;  // S(0) = 0 <= take <= S(vmax) = sum v_b
+    unsigned long long s_lo = 0;
+    while (lo < hi) {
+      const unsigned mid = lo + (hi - lo + 1) / 2;
+      unsigned long long sm = 0;
+      for (int b = lane; b < nb; b += 32) sm += min(s_v[b], mid);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
+      if (sm <= take) {
+        lo = mid;
+        s_lo = sm;
+      } else {
+        hi = mid - 1;
+      }
+    }
+    if (lane == 0) {
+      s_level = lo;
+      s_extra = (unsigned)(take > s_lo ? take - s_lo : 0ull);
+    }
+  }
+  __syncthreads();
+  const unsigned L = s_level, extra = s_extra;
+  unsigned above_before = 0;
+  unsigned long long quota_before = 0;
+  for (int b0 = 0; b0 < nb; b0 += (int)blockDim.x) {
+    const int b = b0 + (int)threadIdx.x;
+    const unsigned v = b < nb ? s_v[b] : 0u;
+    const unsigned above = v > L ? 1u : 0u;
+    unsigned round_above = 0, round_quota = 0;
+    const unsigned rank = above_before + block_exclusive_scan(above, round_above);
+    const unsigned q = b < nb ? min(v, L) + ((above && rank < extra) ? 1u : 0u) : 0u;
+    const unsigned qpre = block_exclusive_scan(q, round_quota);
+    if (b < nb) {
+      p.block_quota[b] = q;
+      p.block_prefix[b] = quota_before + qpre;
+    }
+    above_before += round_above;
+    quota_before += round_quota;
+  }
+}
+
+// Per-block vacancy counts into shared memory (whole block) with their sum
+// and extremes (one warp); block_vacant holds them (count_block_vacancies).
+__device__ __forceinline__ void load_block_vacancies(const Params& p, uint32_t* s_v, int nb, unsigned long long* sum,
+                                                     unsigned* vmin, unsigned* vmax) {
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s_v[b] = __ldcg(&p.block_vacant[b]);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    unsigned lo = 0xFFFFFFFFu, hi = 0;
+    unsigned long long sm = 0;
+    for (int b = lane; b < nb; b += 32) {
+      lo = min(lo, s_v[b]);
+      hi = max(hi, s_v[b]);
+      sm += s_v[b];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      sm += __shfl_xor_sync(0xffffffffu, sm, o);
+    }
+    if (lane == 0) {
+      *sum = sm;
+      *vmin = lo;
+      *vmax = hi;
+    }
+  }
+  __syncthreads();
+}
+
+// One whole iteration of the block-local policy, in one pass per block with
+// no grid barrier between the fill and the step. Block b owns the 32-slot
+// chunks b, b + nb, b + 2 nb, ...:
+//  * fill: the block's lowest vacant slots (its chunk order, then slot order
+//    within a chunk) take its quota of initializers, planned at the end of
+//    the previous iteration by level filling (plan_block_quotas): a
+//    deterministic fill that needs no other block's counts during the
+//    iteration and spreads fresh tracks over all SMs;
+//  * step limit of each live track of the chunk, by the warp that filled it;
+//  * the live tracks gathered into shared memory a few hundred at a time and
+//    grouped by key (action and particle type) with a counting sort; each
+//    group is cut into pieces of 8, 16 or 32 (the smallest size whose piece
+//    count fits the warps) and the pieces are dealt to the warps: every warp
+//    runs one kind of along-step and interaction, and few tracks spread over
+//    all warps;
+//  * the last block to finish commits the fill, scans the per-block and
+//    per-tile vacancy counts and ends the iteration (which plans the next
+//    fill).
+// Secondaries go to the buffer's tail while the taken entries are being read:
+// the capacity checks count from the uncommitted head.
+__device__ void phase_local(const Params& p, int bid, int nb, const SharedStatic& ss, cudaGraphConditionalHandle handle,
+                            int use_handle) {
   constexpr int kCap = 2 * kTile;
   constexpr int kMaxPieces = kCap / 8 + kMaxKeys;
   __shared__ uint32_t s_slot[kCap];
   __shared__ uint32_t s_sorted[kCap];
   __shared__ uint8_t s_key[kCap];
   __shared__ uint32_t s_chunks[kTile];
+  __shared__ uint32_t s_cpre[kTile];
   __shared__ unsigned s_wn[kTile / 32];
   __shared__ unsigned s_cnt[kMaxKeys], s_cur[kMaxKeys];
   __shared__ unsigned short s_pstart[kMaxPieces];
   __shared__ unsigned char s_plen[kMaxPieces];
   __shared__ unsigned s_npieces;
+  __shared__ unsigned s_acts[A_COUNT];
+  Ctl* c = p.ctl;
   const Tracks& t = p.trk;
+  const unsigned long long head = c->head, take = c->fill_take;
+  const bool tight = c->defer_local != 0u;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = (int)(blockDim.x >> 5);
   const unsigned lt = (1u << lane) - 1u;
+  if (bid == 0 && threadIdx.x == 0 && c->local_blocks != (unsigned)nb) atomicOr(&c->error, ERR_VACANCY);
+  if (threadIdx.x < A_COUNT) s_acts[threadIdx.x] = 0u;
+  unsigned long long killed = 0, n_def = 0, my_steps = 0, my_fill = 0;
+  const unsigned quota = p.block_quota[bid];     // initializers this block takes
+  const unsigned long long first = head + p.block_prefix[bid];
+  unsigned run = 0;  // the block's vacancies before the next batch
   // group the n gathered slots by key and run them, one piece per warp
   auto flush = [&](unsigned n) {
-    if (threadIdx.x < kMaxKeys) s_cnt[threadIdx.x] = 0u;
+    if (threadIdx.x < kMaxKeys) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     for (unsigned i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_cnt[s_key[i]], 1u);
     __syncthreads();
@@ -1179,16 +1357,21 @@ __device__ void phase_step_local(const Params& p, int bid, int nb, const SharedS
   const uint32_t n_own = (uint32_t)bid < p.n_chunks ? (p.n_chunks - (uint32_t)bid + nb - 1) / nb : 0u;
   unsigned pending = 0;  // gathered and not yet run (block-uniform)
   for (uint32_t c0 = 0; c0 < n_own; c0 += blockDim.x) {
-    // this batch's chunks that hold live tracks (or tracks filled this iteration)
+    // this batch's chunks: start-of-iteration vacancies and their exclusive
+    // scan (fill ranks); a chunk is visited if it holds live tracks or
+    // receives initializers
     const uint32_t m = c0 + threadIdx.x;
     const uint32_t g = (uint32_t)bid + (uint32_t)nb * m;
-    bool cand = false;
+    unsigned vac = 0, csize = 0;
     if (m < n_own) {
-      const unsigned csize = (p.n_slots - g * 32u) < 32u ? (p.n_slots - g * 32u) : 32u;
-      cand = __ldcg(&p.vacant[g]) < csize || __ldcg(&p.filled[g]) > 0;
+      csize = (p.n_slots - g * 32u) < 32u ? (p.n_slots - g * 32u) : 32u;
+      vac = __ldcg(&p.vacant[g]);
     }
+    unsigned batch_vac = 0;
+    const unsigned pre = block_exclusive_scan(vac, batch_vac);
+    const bool cand = m < n_own && (vac < csize || (vac > 0 && run + pre < quota));
     const unsigned bal = __ballot_sync(0xffffffffu, cand);
-    __syncthreads();  // the previous batch is done with s_wn / s_chunks
+    __syncthreads();  // the previous batch is done with s_wn / s_chunks / s_cpre
     if (lane == 0) s_wn[warp] = __popc(bal);
     __syncthreads();
     unsigned before = 0, nch = 0;
@@ -1197,21 +1380,69 @@ __device__ void phase_step_local(const Params& p, int bid, int nb, const SharedS
       before += w < warp ? cw : 0u;
       nch += cw;
     }
-    if (cand) s_chunks[before + __popc(bal & lt)] = g;
+    if (cand) {
+      s_chunks[before + __popc(bal & lt)] = g;
+      s_cpre[before + __popc(bal & lt)] = pre;
+    }
     __syncthreads();
+    const unsigned run0 = run;
+    run += batch_vac;
     for (unsigned j0 = 0; j0 < nch; j0 += (unsigned)nwarps) {
-      // gather: one chunk per warp, appended after the `pending` entries
+      // one chunk per warp: fill, step limit, key; live slots appended after
+      // the `pending` entries
       const unsigned j = j0 + (unsigned)warp;
       bool live = false;
       uint32_t slot = 0;
       uint8_t key = 0;
       if (j < nch) {
-        slot = s_chunks[j] * 32u + lane;
-        if (slot < p.n_slots) {
+        const uint32_t gc = s_chunks[j];
+        const unsigned q = run0 + s_cpre[j];
+        slot = gc * 32u + lane;
+        const bool real = slot < p.n_slots;
+        if (q < quota) {
+          const bool vac_l = real && t.status[slot] == VACANT;
+          const unsigned vb = __ballot_sync(0xffffffffu, vac_l);
+          const unsigned r = q + __popc(vb & lt);
+          if (vac_l && r < quota) {
+            const unsigned long long i = (first + r) & p.ring_mask;
+            t.x[slot] = p.ring.x[i];
+            t.y[slot] = p.ring.y[i];
+            t.z[slot] = p.ring.z[i];
+            t.ux[slot] = p.ring.ux[i];
+            t.uy[slot] = p.ring.uy[i];
+            t.uz[slot] = p.ring.uz[i];
+            t.E[slot] = p.ring.E[i];
+            t.tid[slot] = p.ring.tid[i];
+            t.event[slot] = p.ring.event[i];
+            t.primary[slot] = p.ring.primary[i];
+            t.layer[slot] = p.ring.layer[i];
+            t.ptype[slot] = p.ring.ptype[i];
+            t.ctr[slot] = 0u;
+            t.nmfp[slot] = -1.0;
+            t.action[slot] = A_NONE;
+            t.status[slot] = ALIVE;
+          }
+          const unsigned left = quota - q;
+          const unsigned nfill = (unsigned)__popc(vb) < left ? (unsigned)__popc(vb) : left;
+          if (lane == 0 && nfill) {
+            atomicSub(&p.vacant[gc], nfill);
+            atomicSub(&p.tile_vacant[gc >> 3], nfill);
+            my_fill += nfill;
+          }
+        }
+        if (real) {
           const uint8_t st = t.status[slot];
+          uint8_t act = A_NONE;
+          if (st == ALIVE) {
+            act = step_limit(p, slot, ss.tab, ss.zb, ss.lmat);
+            ++my_steps;
+          } else if (st == DEFERRED) {
+            act = t.action[slot];
+          }
           if (st != VACANT) {
+            atomicAdd(&s_acts[act], 1u);
             live = true;
-            key = key_of(POLICY_ACTION_TYPE, t.ptype[slot], t.action[slot]);
+            key = key_of(POLICY_ACTION_TYPE, t.ptype[slot], act);
           }
         }
       }
@@ -1238,7 +1469,66 @@ __device__ void phase_step_local(const Params& p, int bid, int nb, const SharedS
     }
   }
   if (pending > 0) flush(pending);
+  flush_counter(&c->alive, killed, true);
+  flush_counter(&c->steps_iter, my_steps, false);
+  flush_counter(&c->filled_total, my_fill, false);
+  if (n_def) atomicAdd(&c->n_deferred, (unsigned)n_def);
+  __syncthreads();
+  if (threadIdx.x < A_COUNT && s_acts[threadIdx.x] != 0) atomicAdd(&c->action_count[threadIdx.x], s_acts[threadIdx.x]);
+  count_block_vacancies(p, bid, nb);
+  if (last_block_done(&c->done_c, (unsigned)nb)) {
+    // commit the fill, vacancy totals from the per-block counts (the per-tile
+    // prefix is left to the next run of another policy), end the iteration,
+    // plan the next fill
+    __shared__ uint32_t s_v[kMaxLoopBlocks];
+    __shared__ unsigned long long s_sum, s_take;
+    __shared__ unsigned s_vmin, s_vmax;
+    const long long t0 = clock64();
+    if (threadIdx.x == 0) {
+      if (c->filled_total != take) c->error |= ERR_VACANCY;
+      c->filled_total = 0;
+      c->head = head + take;
+      c->alive += take;
+    }
+    load_block_vacancies(p, s_v, nb, &s_sum, &s_vmin, &s_vmax);
+    if (threadIdx.x == 0) c->total_vacant = s_sum;
+    __syncthreads();
+    if (threadIdx.x < 32) loop_ctl_warp(p, &s_take);
+    __syncthreads();
+    plan_block_quotas(p, s_v, nb, s_vmin, s_vmax, s_take);
+    if (threadIdx.x == 0) {
+      if (use_handle) cudaGraphSetConditional(handle, c->cont);
+      c->book_total[1] += (unsigned long long)(clock64() - t0);
+    }
+  }
 }
+
+// Per-block vacancy counts and the plan of the first fill (fill_take and the
+// block quotas) for the block-local policy, at the start of a run (its
+// iterations keep them current; a run of another policy, or primaries pushed
+// since, leave them to be recomputed). Same grid as the loop.
+__global__ void __launch_bounds__(kTile) k_local_prepare(Params p) {
+  count_block_vacancies(p, blockIdx.x, gridDim.x);
+  Ctl* c = p.ctl;
+  if (last_block_done(&c->done_p, gridDim.x)) {
+    __shared__ uint32_t s_v[kMaxLoopBlocks];
+    __shared__ unsigned long long s_sum, s_take;
+    __shared__ unsigned s_vmin, s_vmax;
+    load_block_vacancies(p, s_v, (int)gridDim.x, &s_sum, &s_vmin, &s_vmax);
+    if (threadIdx.x == 0) {
+      if (s_sum != c->total_vacant) c->error |= ERR_VACANCY;
+      c->local_blocks = gridDim.x;
+      s_take = plan_local_fill(p, c->head, c->tail, c->alive, s_sum);
+    }
+    __syncthreads();
+    plan_block_quotas(p, s_v, (int)gridDim.x, s_vmin, s_vmax, s_take);
+  }
+}
+
+// Per-tile vacancy prefix and total, recomputed at the start of a run of a
+// policy that fills in slot order after block-local iterations (which keep
+// the per-tile counts but not their scan). One block.
+__global__ void __launch_bounds__(kTile) k_scan_tiles(Params p) { scan_vacancy(p); }
 
 // Phase C: along-step of every live track and, where the step ends in an
 // interaction, that interaction, in partition order; deferred interactions
@@ -1250,8 +1540,7 @@ __device__ void phase_step(const Params& p, int bid, int nb, const SharedStatic&
   const Tracks& t = p.trk;
   unsigned long long killed = 0, n_def = 0;
   const uint32_t width = sp.perm ? spread_width(sp.hi - sp.lo, nb) : 32u;
-  if (p.policy == POLICY_LOCAL) phase_step_local(p, bid, nb, ss, tight, killed, n_def);
-  for (ChunkWalk w(sp.lo, p.policy == POLICY_LOCAL ? sp.lo : sp.hi, bid, nb, width); w.more(); w.next()) {
+  for (ChunkWalk w(sp.lo, sp.hi, bid, nb, width); w.more(); w.next()) {
     const uint32_t i = w.index();
     if (i >= sp.hi) continue;
     const uint32_t slot = sp.perm ? sp.perm[i] : i;
@@ -1351,6 +1640,14 @@ __global__ void k_step(Params p, cudaGraphConditionalHandle handle, int use_hand
   phase_step(p, blockIdx.x, gridDim.x, ss, true, handle, use_handle);
 }
 
+// The block-local policy: one launch per iteration (same grid as the loop).
+__global__ void __launch_bounds__(kTile) k_local(Params p, cudaGraphConditionalHandle handle, int use_handle) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SharedStatic ss = carve_static(p, smem_raw);
+  stage_static(p, ss);
+  phase_local(p, blockIdx.x, gridDim.x, ss, handle, use_handle);
+}
+
 // Per-action launches: fill, step limit (+ bookkeeping), scatter, one
 // along-step kernel per particle kind, one kernel per interaction, end.
 __global__ void __launch_bounds__(kTile) k_fill(Params p) {
@@ -1390,6 +1687,7 @@ __global__ void k_begin_run(Ctl* c, unsigned long long budget) {
   c->budget_end = budget ? c->iteration + budget : ~0ull;
   c->done_a = 0u;
   c->done_c = 0u;
+  c->done_p = 0u;
 }
 
 // Grid-wide barrier of the persistent loop (generation counter). Every wait
@@ -1499,6 +1797,48 @@ __global__ void __launch_bounds__(kTile, 1) k_loop(Params p) {
   }
 }
 
+// The persistent loop of the block-local policy: one pass per block and
+// iteration (phase_local), one grid barrier per iteration.
+__global__ void __launch_bounds__(kTile, 1) k_loop_local(Params p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SharedStatic ss = carve_static(p, smem_raw);
+  stage_static(p, ss);
+  const unsigned nb = gridDim.x;
+  const int bid = blockIdx.x;
+  Ctl* c = p.ctl;
+  if (bid == 0 && threadIdx.x == 0) {
+    clear_iteration_counters(c);
+    c->cont = 1u;
+  }
+  if (!grid_barrier(p, nb)) return;
+  long long t_prev = clock64();
+  unsigned parity = 0;
+  for (;;) {
+    if (*reinterpret_cast<volatile unsigned*>(&c->cont) == 0u) break;
+    if (bid == 0 && threadIdx.x == 0) {
+      c->max_total[2] += c->iter_max[parity ^ 1][2];
+      c->iter_max[parity ^ 1][2] = 0;
+    }
+    const long long t0 = clock64();
+    phase_local(p, bid, (int)nb, ss, 0, 0);
+    const long long work = clock64() - t0;
+    if (!grid_barrier(p, nb)) break;
+    if (threadIdx.x == 0) {
+      atomicMax(&c->iter_max[parity][2], (unsigned long long)work);
+      if (bid == 0) {
+        const long long now = clock64();
+        c->phase_cycles[2] += (unsigned long long)(now - t_prev);
+        t_prev = now;
+      }
+    }
+    parity ^= 1u;
+  }
+  if (bid == 0 && threadIdx.x == 0) {
+    c->max_total[2] += c->iter_max[0][2] + c->iter_max[1][2];
+    c->iter_max[0][2] = c->iter_max[1][2] = 0;
+  }
+}
+
 // Queue staged primaries at the tail of the initializer buffer.
 __global__ void __launch_bounds__(1024) k_push_primaries(Params p, const StagedPrimary* src, uint32_t n) {
   __shared__ unsigned long long s_base;
@@ -1512,7 +1852,10 @@ __global__ void __launch_bounds__(1024) k_push_primaries(Params p, const StagedP
     atomicAdd(&p.event_live[row_of(p, q.event)], 1u);
   }
   __syncthreads();
-  if (threadIdx.x == 0) p.ctl->tail = base + n;
+  if (threadIdx.x == 0) {
+    p.ctl->tail = base + n;
+    plan_local_fill(p, p.ctl->head, base + n, p.ctl->alive, p.ctl->total_vacant);
+  }
 }
 
 // Validate and queue primaries that are already in device memory: one block;
@@ -1575,6 +1918,7 @@ __global__ void __launch_bounds__(1024) k_push_device_primaries(Params p, const 
   if (threadIdx.x == 0) {
     p.ctl->tail = base + n;
     atomicAdd(&p.event_live[row_of(p, event)], n);
+    plan_local_fill(p, p.ctl->head, base + n, p.ctl->alive, p.ctl->total_vacant);
   }
 }
 
@@ -1599,7 +1943,8 @@ cudaError_t configure_kernels(const Params& p, int block, LaunchShape* sh) {
   sh->static_smem = stat;
   sh->block = block;
   const void* with_smem[] = {(const void*)k_fill_step, (const void*)k_step, (const void*)k_fill,
-                             (const void*)k_pre_step, (const void*)k_along, (const void*)k_loop};
+                             (const void*)k_pre_step, (const void*)k_along, (const void*)k_loop,
+                             (const void*)k_local, (const void*)k_loop_local};
   for (const void* fn : with_smem) {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stat);
     if (e != cudaSuccess) return e;
@@ -1612,7 +1957,12 @@ cudaError_t configure_kernels(const Params& p, int block, LaunchShape* sh) {
   int nb = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)k_loop, kTile, stat);
   if (e != cudaSuccess) return e;
+  int nb_local = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_local, (const void*)k_loop_local, kTile, stat);
+  if (e != cudaSuccess) return e;
+  if (nb_local < nb) nb = nb_local;  // one grid for both loops (and the block-local launches)
   sh->loop_grid = (nb < 1 ? 1 : nb) * sms;
+  if (sh->loop_grid > kMaxLoopBlocks) sh->loop_grid = kMaxLoopBlocks;  // size of the per-block arrays
   return cudaGetLastError();
 }
 
@@ -1625,6 +1975,13 @@ void launch_scatter(const Params& p, const LaunchShape& sh, cudaStream_t s) {
 void launch_step(const Params& p, const LaunchShape& sh, unsigned long long handle, int use_handle, cudaStream_t s) {
   k_step<<<sh.step_grid, sh.block, sh.static_smem, s>>>(p, (cudaGraphConditionalHandle)handle, use_handle);
 }
+void launch_local(const Params& p, const LaunchShape& sh, unsigned long long handle, int use_handle, cudaStream_t s) {
+  k_local<<<sh.loop_grid, kTile, sh.static_smem, s>>>(p, (cudaGraphConditionalHandle)handle, use_handle);
+}
+void launch_local_prepare(const Params& p, const LaunchShape& sh, cudaStream_t s) {
+  k_local_prepare<<<sh.loop_grid, kTile, 0, s>>>(p);
+}
+void launch_scan_tiles(const Params& p, cudaStream_t s) { k_scan_tiles<<<1, kTile, 0, s>>>(p); }
 void launch_fill(const Params& p, const LaunchShape& sh, cudaStream_t s) {
   k_fill<<<sh.tile_grid, kTile, sh.static_smem, s>>>(p);
 }
@@ -1645,7 +2002,8 @@ void launch_begin_run(const Params& p, unsigned long long budget, cudaStream_t s
 }
 cudaError_t launch_loop(const Params& p, const LaunchShape& sh, cudaStream_t s) {
   void* args[] = {const_cast<Params*>(&p)};
-  return cudaLaunchCooperativeKernel((const void*)k_loop, dim3(sh.loop_grid), dim3(kTile), args, sh.static_smem, s);
+  const void* fn = p.policy == POLICY_LOCAL ? (const void*)k_loop_local : (const void*)k_loop;
+  return cudaLaunchCooperativeKernel(fn, dim3(sh.loop_grid), dim3(kTile), args, sh.static_smem, s);
 }
 void launch_push_primaries(const Params& p, const StagedPrimary* d_prim, uint32_t n, cudaStream_t s) {
   k_push_primaries<<<1, 1024, 0, s>>>(p, d_prim, n);
@@ -1658,7 +2016,7 @@ void launch_push_device_primaries(const Params& p, const DevicePrimary* src, uin
 const char* kernel_name(int id) {
   static const char* names[KID_COUNT] = {"fill_step", "scatter", "step", "fill", "pre_step", "along_neutral",
                                          "along_charged", "compton", "photoelectric", "pair", "moller", "brems",
-                                         "loop_ctl", "loop"};
+                                         "loop_ctl", "loop", "local"};
   return (id >= 0 && id < KID_COUNT) ? names[id] : "?";
 }
 

@@ -261,11 +261,12 @@ def test_small_initializer_buffer_defers_without_changing_results(policy):
     assert_conservation(prim, g["tally"])
 
 
-def test_full_buffer_reports_capacity_and_stays_usable():
+@pytest.mark.parametrize("policy", [wl.SORT_ACTION_TYPE, wl.SORT_LOCAL])
+def test_full_buffer_reports_capacity_and_stays_usable(policy):
     """One slot and a one-entry buffer: the electron's second secondary can
     never be placed, so the run stops with CELER_ERR_CAPACITY instead of
     spinning."""
-    prob = wl.calorimeter_problem(1, init_capacity=1, history_capacity=1)
+    prob = wl.calorimeter_problem(1, init_capacity=1, history_capacity=1, sort_policy=policy)
     prim = wl.electron_beam(1, 1000.0)
     with binding.Context(prob, max_iterations=100000) as ctx:
         ctx.add_events(prim)
@@ -311,3 +312,37 @@ def test_device_primaries_match_host_primaries():
         hist, edep = ctx.read_history(0, len(prim))
     np.testing.assert_array_equal(hist["steps"], a["hist"]["steps"])
     np.testing.assert_allclose(edep, a["edep"], rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------------------------------ policy changes within a run
+def test_policies_switched_between_runs_and_single_steps():
+    """One context stepped in short runs that alternate the policies (the
+    block-local policy's one-pass iteration and its block-major fill between
+    the others' slot-order fills) and single celer_step calls: every water-cube
+    history still matches the oracle."""
+    prob = wl.water_cube_problem(n_slots=1024, history_capacity=2000)
+    prim = wl.water_cube_primaries()
+    order = [wl.SORT_LOCAL, wl.SORT_NONE, wl.SORT_LOCAL, wl.SORT_ACTION_TYPE, wl.SORT_ACTION]
+    modes = [binding.LOOP_PERSISTENT, binding.LOOP_GRAPH, binding.LOOP_HOST]
+    with binding.Context(prob) as ctx:
+        ctx.add_events(prim)
+        k = 0
+        while True:
+            ctx.set_sort_policy(order[k % len(order)])
+            if k % 4 == 3:
+                for _ in range(3):
+                    ctx.step()
+            else:
+                ctx.run_iterations(modes[k % len(modes)], budget=5)
+            k += 1
+            s = ctx.stats()
+            if s["alive"] == 0 and s["queued"] == 0:
+                break
+            assert k < 10000
+        hist, edep = ctx.read_history(0, len(prim))
+        tally = {0: ctx.read_tallies(0)}
+    o = run_oracle(prob, prim)
+    np.testing.assert_array_equal(hist["steps"], o["hist"]["steps"])
+    np.testing.assert_array_equal(hist["secondaries"], o["hist"]["secondaries"])
+    np.testing.assert_allclose(edep, o["edep"], rtol=1e-9, atol=1e-9 * 10.0)
+    assert_conservation(prim, tally)
