@@ -81,6 +81,12 @@ struct Span {
   const uint32_t* perm;
 };
 
+// Order in which the block-local policy deals its groups to the warps: the
+// interactions (costliest first), then the charged along-steps, then the
+// photon along-steps (unused keys last).
+__constant__ uint8_t kPieceOrder[kMaxKeys] = {K_G_COMPTON, K_E_MOLLER, K_G_PAIR, K_E_BREMS, K_E_RANGE, K_E_GEOM,
+                                              K_G_GEOM, K_G_PE, 8, 9, 10, 11, 12, 13, 14, 15};
+
 __device__ __forceinline__ uint8_t key_of(int policy, uint8_t ptype, uint8_t act) {
   if (policy == POLICY_ACTION) return ptype == GAMMA ? KA_NEUTRAL : KA_CHARGED;
   if (ptype == GAMMA) {
@@ -144,12 +150,12 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
   const double ux = t.ux[slot], uy = t.uy[slot], uz = t.uz[slot];
   double s_geo = kInf;
   uint8_t act = A_NONE;
-  if (uz > 0.0) {
-    s_geo = (zb[layer + 1] - z) / uz;
-    act = A_ZUP;
-  } else if (uz < 0.0) {
-    s_geo = (zb[layer] - z) / uz;
-    act = A_ZDOWN;
+  const long long uzb = __double_as_longlong(uz);
+  const unsigned long long uza = (unsigned long long)uzb & 0x7FFFFFFFFFFFFFFFull;
+  if (uza != 0ull && uza <= 0x7FF0000000000000ull) {  // uz nonzero, not NaN: one division whatever the sign
+    const bool up = uzb >= 0;
+    s_geo = (zb[up ? layer + 1 : layer] - z) / uz;
+    act = up ? A_ZUP : A_ZDOWN;
   }
   double s_side = kInf;
   if (charged && p.Bz != 0.0) {
@@ -1320,28 +1326,42 @@ __device__ void phase_local(const Params& p, int bid, int nb, const SharedStatic
     __syncthreads();
     for (unsigned i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_cnt[s_key[i]], 1u);
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+      // one lane per key, keys taken in the order of kPieceOrder (the
+      // interactions first: piece q runs on warp q mod nwarps, so the costly
+      // pieces get sub-partitions, and FP64 pipes, of their own)
+      const int k = lane < kMaxKeys ? (int)kPieceOrder[lane] : 0;
+      const unsigned ck = lane < kMaxKeys ? s_cnt[k] : 0u;
       unsigned piece = 32u;
       for (unsigned pc = 8u; pc <= 32u; pc <<= 1) {  // smallest piece size whose pieces fit the warps
-        unsigned np = 0;
-        for (int k = 0; k < kMaxKeys; ++k) np += (s_cnt[k] + pc - 1) / pc;
+        unsigned np = (ck + pc - 1) / pc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) np += __shfl_xor_sync(0xffffffffu, np, o);
         if (np <= (unsigned)nwarps) {
           piece = pc;
           break;
         }
       }
-      unsigned off = 0, np = 0;
-      for (int k = 0; k < kMaxKeys; ++k) {
-        const unsigned ck = s_cnt[k];
-        s_cur[k] = off;
-        for (unsigned q = 0; q < ck; q += piece) {
-          s_pstart[np] = (unsigned short)(off + q);
-          s_plen[np] = (unsigned char)(ck - q < piece ? ck - q : piece);
-          ++np;
+      const unsigned mine = (ck + piece - 1) / piece;
+      unsigned off = ck, pstart = mine;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned a = __shfl_up_sync(0xffffffffu, off, o), b = __shfl_up_sync(0xffffffffu, pstart, o);
+        if (lane >= o) {
+          off += a;
+          pstart += b;
         }
-        off += ck;
       }
-      s_npieces = np;
+      off -= ck;
+      pstart -= mine;
+      if (lane < kMaxKeys) {
+        s_cur[k] = off;
+        for (unsigned q = 0; q < mine; ++q) {
+          s_pstart[pstart + q] = (unsigned short)(off + q * piece);
+          s_plen[pstart + q] = (unsigned char)(ck - q * piece < piece ? ck - q * piece : piece);
+        }
+      }
+      if (lane == 31) s_npieces = pstart + mine;
     }
     __syncthreads();
     for (unsigned i = threadIdx.x; i < n; i += blockDim.x) s_sorted[atomicAdd(&s_cur[s_key[i]], 1u)] = s_slot[i];
