@@ -358,7 +358,9 @@ def run_ours(args):
     by_policy = {binding_name(p): dict(value=r["steps"] / (r["ms"] / 1e3), ms_per_step=r["ms"] / args.steps,
                                        track_steps_per_job=r["steps"] / args.steps / world)
                  for p, r in results.items()}
-    launches_per_job = 3 if loop == binding.LOOP_PERSISTENT else None  # push, run start, loop kernel
+    # persistent loop, per job: primaries push, run start, (block-local policy:
+    # per-block vacancy scan), loop kernel
+    launches_per_job = (4 if headline == wl.SORT_LOCAL else 3) if loop == binding.LOOP_PERSISTENT else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": h["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -546,13 +548,13 @@ def load_peaks():
 # algorithmic state bytes (state read and written back once per step, without
 # secondaries or scratch) and thread-level FP64 operations
 # (2 x DFMA + DADD + DMUL) counted by ncu on the persistent loop kernel
-# (profiles/loop_kernel_calorimeters.md); DRAM bytes per launch of that kernel
-# from the same captures, for the workloads that were captured whole.
+# (profiles/loop_local_calorimeter_1gev.md, profiles/loop_kernel_calorimeters.md);
+# DRAM bytes per launch of that kernel from the same captures, for the
+# workloads that were captured whole. Keys: (workload, policy).
 BYTES_PER_STEP = 160.0
-FP64_FLOP_PER_STEP = {"calorimeter-1gev": 122.1, "calorimeter-field-10gev": 132.2, "water-cube-10mev": 122.1}
-DRAM_BYTES_PER_LAUNCH = {("calorimeter-1gev", "none"): 778.5e3, ("calorimeter-1gev", "action_type"): 867.6e3,
-                         ("calorimeter-field-10gev", "none"): 28.74e6, ("calorimeter-field-10gev", "action"): 30.47e6,
-                         ("calorimeter-field-10gev", "action_type"): 28.28e6}
+FP64_FLOP_PER_STEP = {("calorimeter-1gev", "local"): 119.7, ("calorimeter-1gev", None): 119.7,
+                      ("calorimeter-field-10gev", None): 132.2, ("water-cube-10mev", None): 119.7}
+DRAM_BYTES_PER_LAUNCH = {("calorimeter-1gev", "local"): 1.374e6}
 # FP64 peak of GB300: 2 DFMA per SM-cycle (ncu peak_sustained) x 152 SMs x 2.07 GHz x 2 flop
 FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
@@ -562,10 +564,11 @@ def roofline_loop(workload, policy, steps_per_job, job_ms, full_size=True):
     launch per job): FP64 ALU bound, with the HBM fraction beside it."""
     peaks, kind = load_peaks()
     t = job_ms / 1e3
-    fpstep = FP64_FLOP_PER_STEP[workload]
+    fpstep = FP64_FLOP_PER_STEP.get((workload, policy), FP64_FLOP_PER_STEP[(workload, None)])
     flops = fpstep * steps_per_job / t / 1e12
     gbs = BYTES_PER_STEP * steps_per_job / t / 1e9
-    return {"kernel": "k_loop", "bound": "alu", "achieved": flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+    kernel = "k_loop_local" if policy == "local" else "k_loop"
+    return {"kernel": kernel, "bound": "alu", "achieved": flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": flops / FP64_PEAK_TFLOPS, "traffic": DRAM_BYTES_PER_LAUNCH.get((workload, policy)) if full_size else None,
             "peak_kind": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (probe measured 1.02 TFLOP/s)",
             "fp64_flop_per_track_step": fpstep,
