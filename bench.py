@@ -360,7 +360,7 @@ def run_ours(args):
                  for p, r in results.items()}
     # persistent loop, per job: primaries push, run start, (block-local policy:
     # per-block vacancy scan), loop kernel
-    launches_per_job = (4 if headline == wl.SORT_LOCAL else 3) if loop == binding.LOOP_PERSISTENT else None
+    launches_per_job = (4 if headline in (wl.SORT_LOCAL, wl.SORT_DATA) else 3) if loop == binding.LOOP_PERSISTENT else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": h["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -446,7 +446,7 @@ def run_extras(args, binding, stream, flush):
     base3 = wl.calorimeter_problem(1 << 20, Bz=4.0, max_events=256)
     sample = wl.concat_primaries(events[:24])
     best, trials = binding.autotune(base3, sample, [1 << 18, 1 << 19, 1 << 20, 1 << 21], [128, 256, 512],
-                                    [wl.SORT_NONE, wl.SORT_ACTION, wl.SORT_ACTION_TYPE, wl.SORT_LOCAL],
+                                    [wl.SORT_NONE, wl.SORT_ACTION, wl.SORT_ACTION_TYPE, wl.SORT_LOCAL, wl.SORT_DATA],
                                     [binding.LOOP_PERSISTENT, binding.LOOP_GRAPH], stream=stream.cuda_stream)
     tuned = base3.replace(n_slots=best["n_slots"], block_size=best["block_size"], sort_policy=best["sort_policy"],
                           init_capacity=max(8 * best["n_slots"], 1 << 22))
@@ -567,7 +567,7 @@ def roofline_loop(workload, policy, steps_per_job, job_ms, full_size=True):
     fpstep = FP64_FLOP_PER_STEP.get((workload, policy), FP64_FLOP_PER_STEP[(workload, None)])
     flops = fpstep * steps_per_job / t / 1e12
     gbs = BYTES_PER_STEP * steps_per_job / t / 1e9
-    kernel = "k_loop_local" if policy == "local" else "k_loop"
+    kernel = "k_loop_local" if policy in ("local", "data") else "k_loop"
     return {"kernel": kernel, "bound": "alu", "achieved": flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": flops / FP64_PEAK_TFLOPS, "traffic": DRAM_BYTES_PER_LAUNCH.get((workload, policy)) if full_size else None,
             "peak_kind": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (probe measured 1.02 TFLOP/s)",
@@ -589,7 +589,7 @@ def main():
     ap.add_argument("--split", action="store_true", help="one kernel per action in the host or graph loop")
     ap.add_argument("--primaries", type=int, default=0, help="override the workload's primary count")
     ap.add_argument("--slots", type=int, default=0, help="override the workload's track-slot count")
-    ap.add_argument("--policies", default="action_type,action,none,local")
+    ap.add_argument("--policies", default="action_type,action,none,data,local")
     ap.add_argument("--loop", default="persistent", choices=["host", "graph", "persistent"])
     ap.add_argument("--no-loop-compare", action="store_true")
     ap.add_argument("--no-kernel-timing", action="store_true")

@@ -60,7 +60,8 @@ enum {
 /* tally layouts: uniform z bins over the world, or one bin per layer */
 enum { CELER_TALLY_ZBINS = 0, CELER_TALLY_LAYERS = 1 };
 
-/* Track-reordering policies (Sec. 3.1, "Reindexing track slots"):
+/* Track-reordering policies (Sec. 3.1, "Reindexing track slots", and
+ * Sec. 3.2, "Partitioning track data"):
  *   NONE        every action kernel runs over all slots and masks the tracks
  *               that do not take part (Sec. 2, "masking");
  *   ACTION      slot indices are partitioned by along-step action (neutral
@@ -73,8 +74,20 @@ enum { CELER_TALLY_ZBINS = 0, CELER_TALLY_LAYERS = 1 };
  *               on-chip memory and gives each warp one group (no counterpart
  *               in the paper; it keeps the divergence cut of ACTION_TYPE
  *               without the partition's extra grid-wide pass). The per-action
- *               launch mode runs it like NONE. */
-enum { CELER_SORT_NONE = 0, CELER_SORT_ACTION = 1, CELER_SORT_ACTION_TYPE = 2, CELER_SORT_LOCAL = 3 };
+ *               launch mode runs it like NONE.
+ *   DATA        no reindexing (Sec. 3.2): the initializers that fill vacant
+ *               slots are partitioned by charge, the neutral ones placed at the
+ *               low end and the charged ones at the high end of each GPU
+ *               block's share of the slot array, and the tracks are stepped in
+ *               slot order with masking. The per-action launch mode runs it
+ *               like NONE.
+ * LOCAL and DATA fill the slots block by block (each block's lowest vacant
+ * slots, DATA: lowest and highest, take an even share of the initializers);
+ * the other policies fill the r-th vacant slot in slot order with the r-th
+ * queued initializer. Either way the fill is deterministic, and results do not
+ * depend on it (random streams follow the track, not the slot). */
+enum { CELER_SORT_NONE = 0, CELER_SORT_ACTION = 1, CELER_SORT_ACTION_TYPE = 2, CELER_SORT_LOCAL = 3,
+       CELER_SORT_DATA = 4 };
 
 typedef struct {
   double Z;       /* atomic number (effective Z for a compound) */
@@ -366,6 +379,13 @@ celer_status celer_autotune(const celer_problem* base, const celer_primary* prim
  * sorted policies. */
 celer_status celer_debug_partition(celer_ctx* ctx, uint8_t* keys_out, uint32_t* perm_out, uint32_t* offsets_out,
                                    int* n_keys, int* n_blocks);
+
+/* Per-slot status (0 vacant, 1 alive, 2 waiting for buffer space) and
+ * particle type (0 photon, 1 electron) into host arrays of n_slots bytes, and
+ * the number of GPU blocks B of the block-pass policies (LOCAL, DATA): block b
+ * owns the 32-slot chunks b, b + B, b + 2B, ... Checks the DATA policy's
+ * charge partition of the fill (Sec. 3.2). */
+celer_status celer_debug_slots(celer_ctx* ctx, uint8_t* status_out, uint8_t* ptype_out, int* n_blocks);
 
 /* Device table of material mat, column col (0 Compton, 1 photoelectric,
  * 2 pair, 3 Moller, 4 brems, 5 range), 200 values into host memory. */

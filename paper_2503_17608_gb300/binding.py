@@ -113,7 +113,7 @@ EXPORTS = [
     "celer_enable_kernel_timing", "celer_kernel_timing", "celer_debug_partition", "celer_debug_table",
     "celer_debug_philox", "celer_debug_curand_philox", "celer_partition_keys_noalloc", "celer_debug_math",
     "celer_run_iterations", "celer_read_event_live", "celer_serve", "celer_autotune", "celer_get_problem",
-    "celer_debug_sample",
+    "celer_debug_sample", "celer_debug_slots",
 ]
 
 _lib = None
@@ -155,6 +155,7 @@ def load(path: Optional[str] = None):
         "celer_debug_math": ([i32, vp, u64, vp], i32),
         "celer_debug_curand_philox": ([u64, u64, u64, vp, u64], i32),
         "celer_debug_sample": ([i32, u32, u32, vp, C.c_double, vp, vp, u64, vp, vp, vp, vp], i32),
+        "celer_debug_slots": ([vp, vp, vp, C.POINTER(i32)], i32),
         "celer_partition_keys_noalloc": ([vp, u64, i32, i32, vp, vp, vp], i32),
         "celer_run_iterations": ([vp, i32, u64, C.POINTER(u64)], i32),
         "celer_read_event_live": ([vp, u32, u32, vp], i32),
@@ -402,6 +403,22 @@ class Context:
                                             C.byref(nk), C.byref(nb)), self._h)
         self.partition_blocks = nb.value
         return keys, perm, offs[:nk.value + 1]
+
+    def debug_slots(self):
+        """Per-slot status and particle type (device state, host copies)."""
+        n = self.prob.n_slots
+        status = np.zeros(n, np.uint8)
+        ptype = np.zeros(n, np.uint8)
+        nb = C.c_int()
+        _check(load().celer_debug_slots(self._h, status.ctypes.data, ptype.ctypes.data, C.byref(nb)), self._h)
+        self._loop_blocks = nb.value
+        return dict(status=status, ptype=ptype)
+
+    def loop_blocks(self) -> int:
+        """GPU blocks of the block-pass policies (block b owns chunks b, b + B, ...)."""
+        if getattr(self, "_loop_blocks", None) is None:
+            self.debug_slots()
+        return self._loop_blocks
 
     def debug_table(self, mat: int, col: int):
         out = np.zeros(200)

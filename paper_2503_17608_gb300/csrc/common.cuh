@@ -65,8 +65,15 @@ constexpr int kKeysAlong = 3;
 // NONE: slot order. ACTION / ACTION_TYPE: a grid-wide partition of the live
 // slots by key before the step phase. LOCAL: no grid-wide partition; each
 // block groups its own live tracks by action and particle type in shared
-// memory during the step phase.
-enum Policy : int { POLICY_NONE = 0, POLICY_ACTION = 1, POLICY_ACTION_TYPE = 2, POLICY_LOCAL = 3 };
+// memory during the step phase. DATA: no reindexing; each block places its
+// neutral initializers at the low end of its slots and its charged ones at
+// the high end (Sec. 3.2) and steps its chunks in slot order.
+enum Policy : int { POLICY_NONE = 0, POLICY_ACTION = 1, POLICY_ACTION_TYPE = 2, POLICY_LOCAL = 3, POLICY_DATA = 4 };
+constexpr int kPolicyCount = 5;
+// LOCAL and DATA run one pass per block and iteration (block-owned chunks).
+__host__ __device__ __forceinline__ bool block_pass(int policy) {
+  return policy == POLICY_LOCAL || policy == POLICY_DATA;
+}
 __host__ __device__ __forceinline__ bool global_partition(int policy) {
   return policy == POLICY_ACTION || policy == POLICY_ACTION_TYPE;
 }

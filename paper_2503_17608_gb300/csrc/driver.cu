@@ -168,9 +168,10 @@ void timed(celer_ctx* ctx, cudaStream_t s, int kid, F&& launch, bool allow_timin
 // end of iteration). Per action (split_actions), as in the paper's loop over
 // actions: fill, step limit, scatter, one along-step kernel per particle kind,
 // one kernel per interaction, end of iteration.
-// The block-local policy runs one fused launch per iteration (phase-merged
-// modes); it needs the per-block vacancy scan at the start of each run.
-bool fused_local(const celer_ctx* ctx) { return !ctx->split_actions && ctx->p.policy == POLICY_LOCAL; }
+// The block-pass policies (LOCAL, DATA) run one launch per iteration in the
+// phase-merged modes; they need the per-block vacancy scan at the start of
+// each run.
+bool fused_local(const celer_ctx* ctx) { return !ctx->split_actions && block_pass(ctx->p.policy); }
 
 // Start of a run (or a single step): the block-local iterations start from a
 // fresh per-block vacancy scan; the others, after block-local ones, from a
@@ -190,7 +191,7 @@ void launch_iteration(celer_ctx* ctx, cudaStream_t s, unsigned long long handle,
   const LaunchShape& sh = ctx->shape;
   const bool t = use_handle == 0;
   const bool sorted = policy_sorted(p.policy);
-  if (!ctx->split_actions && p.policy == POLICY_LOCAL) {
+  if (!ctx->split_actions && block_pass(p.policy)) {
     timed(ctx, s, KID_LOCAL, [&] { launch_local(p, sh, handle, use_handle, s); }, t);
     return;
   }
@@ -332,7 +333,7 @@ celer_status validate_problem(const celer_problem* pb, std::string& why) {
   if (pb->n_slots < 1 || pb->n_slots > (1ull << 30)) return why = "n_slots must be in [1, 2^30]", CELER_ERR_INVALID;
   if (pb->init_capacity < 1 || pb->init_capacity > (1ull << 34)) return why = "bad init_capacity", CELER_ERR_INVALID;
   if (pb->max_events < 1) return why = "max_events must be >= 1", CELER_ERR_INVALID;
-  if (pb->sort_policy < 0 || pb->sort_policy > 3) return why = "unknown sort policy", CELER_ERR_INVALID;
+  if (pb->sort_policy < 0 || pb->sort_policy >= kPolicyCount) return why = "unknown sort policy", CELER_ERR_INVALID;
   if (pb->block_size != 0 && pb->block_size != 128 && pb->block_size != 256 && pb->block_size != 512)
     return why = "block_size must be 128, 256 or 512", CELER_ERR_INVALID;
   return CELER_OK;
@@ -851,7 +852,7 @@ celer_status celer_set_split_actions(celer_ctx* ctx, int split) {
 }
 
 celer_status celer_set_sort_policy(celer_ctx* ctx, int policy) {
-  if (!ctx || policy < 0 || policy > 3) return CELER_ERR_INVALID;
+  if (!ctx || policy < 0 || policy >= kPolicyCount) return CELER_ERR_INVALID;
   ctx->p.policy = policy;
   ctx->p.n_keys = keys_of(policy);
   // stored keys belong to the previous policy: rewrite them all at the next step
@@ -930,6 +931,16 @@ celer_status celer_debug_partition(celer_ctx* ctx, uint8_t* keys_out, uint32_t* 
   *n_keys = ctx->p.n_keys;
   *n_blocks = (int)ctx->h_ctl->part_blocks;
   for (int k = 0; k <= ctx->p.n_keys; ++k) offsets_out[k] = ctx->h_ctl->offsets[k];
+  return CELER_OK;
+}
+
+celer_status celer_debug_slots(celer_ctx* ctx, uint8_t* status_out, uint8_t* ptype_out, int* n_blocks) {
+  if (!ctx || !status_out || !ptype_out || !n_blocks) return CELER_ERR_INVALID;
+  const uint32_t N = ctx->p.n_slots;
+  CELER_CUDA(ctx, cudaMemcpyAsync(status_out, ctx->p.trk.status, N, cudaMemcpyDeviceToHost, ctx->stream));
+  CELER_CUDA(ctx, cudaMemcpyAsync(ptype_out, ctx->p.trk.ptype, N, cudaMemcpyDeviceToHost, ctx->stream));
+  CELER_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  *n_blocks = ctx->shape.loop_grid;
   return CELER_OK;
 }
 

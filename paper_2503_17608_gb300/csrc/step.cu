@@ -1189,11 +1189,29 @@ __device__ __forceinline__ void count_block_vacancies(const Params& p, int bid, 
 // thus spread over all SMs (a block fills its lowest vacancies, in its chunk
 // order), and the fill stays deterministic. s_v holds v_b; vmin and vmax
 // are their extremes. When every block has room for take/nb + 1 the level
-// is take/nb; otherwise one warp finds it by bisection.
-__device__ void plan_block_quotas(const Params& p, const uint32_t* s_v, int nb, unsigned vmin, unsigned vmax,
-                                  unsigned long long take) {
+// is take/nb; otherwise one warp finds it by bisection. A block takes at most
+// `cap` (its counts and the take are clamped); returns the take planned,
+// which the caller stores as the next fill_take.
+__device__ unsigned long long plan_block_quotas(const Params& p, uint32_t* s_v, int nb, unsigned vmin, unsigned vmax,
+                                                unsigned long long take, unsigned cap) {
   __shared__ unsigned s_level, s_extra;
+  __shared__ unsigned long long s_room;
   const int lane = threadIdx.x & 31;
+  if (vmax > cap) {  // a block takes at most `cap`: clamp the counts, and the take to their sum
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s_v[b] = min(s_v[b], cap);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      unsigned long long sm = 0;
+      for (int b = lane; b < nb; b += 32) sm += s_v[b];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
+      if (lane == 0) s_room = sm;
+    }
+    __syncthreads();
+    if (take > s_room) take = s_room;
+    vmin = min(vmin, cap);
+    vmax = cap;
+  }
   const unsigned long long l0 = take / (unsigned)nb;
   if (l0 + 1 <= vmin) {
     if (threadIdx.x == 0) {
@@ -1240,6 +1258,7 @@ __device__ void plan_block_quotas(const Params& p, const uint32_t* s_v, int nb, 
     above_before += round_above;
     quota_before += round_quota;
   }
+  return take;
 }
 
 // Per-block vacancy counts into shared memory (whole block) with their sum
@@ -1270,6 +1289,192 @@ __device__ __forceinline__ void load_block_vacancies(const Params& p, uint32_t* 
     }
   }
   __syncthreads();
+}
+
+// Largest quota a block takes in one iteration: the DATA policy keeps its
+// block's initializer list in shared memory.
+constexpr unsigned kDataMaxQuota = 8192;
+__device__ __forceinline__ unsigned block_quota_cap(int policy) { return policy == POLICY_DATA ? kDataMaxQuota : 0xFFFFFFFFu; }
+
+// End of a block pass (LOCAL, DATA): the block's vacancy count, and in the
+// last block to finish the commit of the fill, the vacancy totals from the
+// per-block counts (the per-tile prefix is left to the next run of another
+// policy), the end of the iteration and the plan of the next fill.
+__device__ void end_block_pass(const Params& p, int bid, int nb, unsigned long long head, unsigned long long take,
+                               cudaGraphConditionalHandle handle, int use_handle) {
+  Ctl* c = p.ctl;
+  count_block_vacancies(p, bid, nb);
+  if (last_block_done(&c->done_c, (unsigned)nb)) {
+    __shared__ uint32_t s_v[kMaxLoopBlocks];
+    __shared__ unsigned long long s_sum, s_take;
+    __shared__ unsigned s_vmin, s_vmax;
+    const long long t0 = clock64();
+    if (threadIdx.x == 0) {
+      if (c->filled_total != take) c->error |= ERR_VACANCY;
+      c->filled_total = 0;
+      c->head = head + take;
+      c->alive += take;
+    }
+    load_block_vacancies(p, s_v, nb, &s_sum, &s_vmin, &s_vmax);
+    if (threadIdx.x == 0) c->total_vacant = s_sum;
+    __syncthreads();
+    if (threadIdx.x < 32) loop_ctl_warp(p, &s_take);
+    __syncthreads();
+    const unsigned long long planned = plan_block_quotas(p, s_v, nb, s_vmin, s_vmax, s_take, block_quota_cap(p.policy));
+    if (threadIdx.x == 0) {
+      if (planned != s_take) c->fill_take = planned;
+      if (use_handle) cudaGraphSetConditional(handle, c->cont);
+      c->book_total[1] += (unsigned long long)(clock64() - t0);
+    }
+  }
+}
+
+// One whole iteration of the DATA policy (Sec. 3.2, "partitioning track
+// data"), in one pass per block: block b owns the chunks b, b + nb, ... and
+// takes its quota of initializers (level filling, as for LOCAL); among them
+// the neutral ones fill its lowest vacant slots (its chunk order, then slot
+// order) and the charged ones its highest, so that neutral and charged
+// tracks gather at opposite ends of the block's slots and most warps hold
+// one kind. There is no reindexing: each warp takes one of the block's
+// chunks that hold or receive tracks, fills it, and runs the step limit,
+// along-step and interaction of its live tracks in slot order, masking the
+// others (Sec. 2).
+__device__ void phase_data(const Params& p, int bid, int nb, const SharedStatic& ss, cudaGraphConditionalHandle handle,
+                           int use_handle) {
+  __shared__ uint32_t s_chunks[kTile];
+  __shared__ uint32_t s_cpre[kTile];
+  __shared__ unsigned s_wn[kTile / 32];
+  __shared__ unsigned short s_list[kDataMaxQuota];  // offsets in the quota: neutral from the front, charged from the back
+  __shared__ unsigned s_acts[A_COUNT];
+  Ctl* c = p.ctl;
+  const Tracks& t = p.trk;
+  const unsigned long long head = c->head, take = c->fill_take;
+  const bool tight = c->defer_local != 0u;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (int)(blockDim.x >> 5);
+  const unsigned lt = (1u << lane) - 1u;
+  if (bid == 0 && threadIdx.x == 0 && c->local_blocks != (unsigned)nb) atomicOr(&c->error, ERR_VACANCY);
+  if (threadIdx.x < A_COUNT) s_acts[threadIdx.x] = 0u;
+  const unsigned quota = min(p.block_quota[bid], kDataMaxQuota);
+  const unsigned long long first = head + p.block_prefix[bid];
+  const unsigned vtot = p.block_vacant[bid];  // the block's vacant slots at the start of the iteration
+  // the block's initializers by kind: offsets of the neutral ones in order
+  // from the front of s_list, of the charged ones from the back
+  unsigned n_neutral = 0;
+  for (unsigned e0 = 0; e0 < quota; e0 += blockDim.x) {
+    const unsigned e = e0 + threadIdx.x;
+    const bool in = e < quota;
+    const bool neutral = in && p.ring.ptype[(first + e) & p.ring_mask] == GAMMA;
+    unsigned round_n = 0;
+    const unsigned rn = n_neutral + block_exclusive_scan(neutral ? 1u : 0u, round_n);
+    if (neutral) {
+      s_list[rn] = (unsigned short)e;
+    } else if (in) {
+      s_list[quota - 1u - (e - rn)] = (unsigned short)e;  // e - rn charged ones precede it
+    }
+    n_neutral += round_n;
+  }
+  const unsigned n_charged = quota - n_neutral;
+  __syncthreads();
+  unsigned long long killed = 0, n_def = 0, my_steps = 0, my_fill = 0;
+  const uint32_t n_own = (uint32_t)bid < p.n_chunks ? (p.n_chunks - (uint32_t)bid + nb - 1) / nb : 0u;
+  unsigned run = 0;  // the block's vacancies before the next batch (ascending rank)
+  for (uint32_t c0 = 0; c0 < n_own; c0 += blockDim.x) {
+    const uint32_t m = c0 + threadIdx.x;
+    const uint32_t g = (uint32_t)bid + (uint32_t)nb * m;
+    unsigned vac = 0, csize = 0;
+    if (m < n_own) {
+      csize = (p.n_slots - g * 32u) < 32u ? (p.n_slots - g * 32u) : 32u;
+      vac = __ldcg(&p.vacant[g]);
+    }
+    unsigned batch_vac = 0;
+    const unsigned pre = block_exclusive_scan(vac, batch_vac);
+    // ascending ranks of the chunk's vacancies: [a, a + vac); it receives a
+    // neutral track if a < n_neutral, a charged one if its highest vacancy's
+    // descending rank, vtot - (a + vac), is below n_charged
+    const unsigned a = run + pre;
+    const bool cand = m < n_own && (vac < csize || (vac > 0 && (a < n_neutral || vtot - (a + vac) < n_charged)));
+    const unsigned bal = __ballot_sync(0xffffffffu, cand);
+    __syncthreads();
+    if (lane == 0) s_wn[warp] = __popc(bal);
+    __syncthreads();
+    unsigned before = 0, nch = 0;
+    for (int w = 0; w < nwarps; ++w) {
+      const unsigned cw = s_wn[w];
+      before += w < warp ? cw : 0u;
+      nch += cw;
+    }
+    if (cand) {
+      s_chunks[before + __popc(bal & lt)] = g;
+      s_cpre[before + __popc(bal & lt)] = pre;
+    }
+    __syncthreads();
+    const unsigned run0 = run;
+    run += batch_vac;
+    for (unsigned j = (unsigned)warp; j < nch; j += (unsigned)nwarps) {
+      const uint32_t gc = s_chunks[j];
+      const uint32_t slot = gc * 32u + lane;
+      const bool real = slot < p.n_slots;
+      const bool vac_l = real && t.status[slot] == VACANT;
+      const unsigned vb = __ballot_sync(0xffffffffu, vac_l);
+      const unsigned r = run0 + s_cpre[j] + __popc(vb & lt);
+      int off = -1;
+      if (vac_l) {
+        if (r < n_neutral) {
+          off = s_list[r];
+        } else if (vtot - 1u - r < n_charged) {
+          off = s_list[quota - 1u - (vtot - 1u - r)];
+        }
+      }
+      if (off >= 0) {
+        const unsigned long long i = (first + (unsigned)off) & p.ring_mask;
+        t.x[slot] = p.ring.x[i];
+        t.y[slot] = p.ring.y[i];
+        t.z[slot] = p.ring.z[i];
+        t.ux[slot] = p.ring.ux[i];
+        t.uy[slot] = p.ring.uy[i];
+        t.uz[slot] = p.ring.uz[i];
+        t.E[slot] = p.ring.E[i];
+        t.tid[slot] = p.ring.tid[i];
+        t.event[slot] = p.ring.event[i];
+        t.primary[slot] = p.ring.primary[i];
+        t.layer[slot] = p.ring.layer[i];
+        t.ptype[slot] = p.ring.ptype[i];
+        t.ctr[slot] = 0u;
+        t.nmfp[slot] = -1.0;
+        t.action[slot] = A_NONE;
+        t.status[slot] = ALIVE;
+      }
+      const unsigned nfill = __popc(__ballot_sync(0xffffffffu, off >= 0));
+      if (lane == 0 && nfill) {
+        atomicSub(&p.vacant[gc], nfill);
+        atomicSub(&p.tile_vacant[gc >> 3], nfill);
+        my_fill += nfill;
+      }
+      // the chunk's live tracks: step limit, along-step, interaction
+      if (real) {
+        const uint8_t st = t.status[slot];
+        if (st != VACANT) {
+          uint8_t act;
+          if (st == ALIVE) {
+            act = step_limit(p, slot, ss.tab, ss.zb, ss.lmat);
+            ++my_steps;
+          } else {
+            act = t.action[slot];
+          }
+          atomicAdd(&s_acts[act], 1u);
+          if (step_one(p, slot, st, ss, tight, n_def)) ++killed;
+        }
+      }
+    }
+  }
+  flush_counter(&c->alive, killed, true);
+  flush_counter(&c->steps_iter, my_steps, false);
+  flush_counter(&c->filled_total, my_fill, false);
+  if (n_def) atomicAdd(&c->n_deferred, (unsigned)n_def);
+  __syncthreads();
+  if (threadIdx.x < A_COUNT && s_acts[threadIdx.x] != 0) atomicAdd(&c->action_count[threadIdx.x], s_acts[threadIdx.x]);
+  end_block_pass(p, bid, nb, head, take, handle, use_handle);
 }
 
 // One whole iteration of the block-local policy, in one pass per block with
@@ -1495,32 +1700,7 @@ __device__ void phase_local(const Params& p, int bid, int nb, const SharedStatic
   if (n_def) atomicAdd(&c->n_deferred, (unsigned)n_def);
   __syncthreads();
   if (threadIdx.x < A_COUNT && s_acts[threadIdx.x] != 0) atomicAdd(&c->action_count[threadIdx.x], s_acts[threadIdx.x]);
-  count_block_vacancies(p, bid, nb);
-  if (last_block_done(&c->done_c, (unsigned)nb)) {
-    // commit the fill, vacancy totals from the per-block counts (the per-tile
-    // prefix is left to the next run of another policy), end the iteration,
-    // plan the next fill
-    __shared__ uint32_t s_v[kMaxLoopBlocks];
-    __shared__ unsigned long long s_sum, s_take;
-    __shared__ unsigned s_vmin, s_vmax;
-    const long long t0 = clock64();
-    if (threadIdx.x == 0) {
-      if (c->filled_total != take) c->error |= ERR_VACANCY;
-      c->filled_total = 0;
-      c->head = head + take;
-      c->alive += take;
-    }
-    load_block_vacancies(p, s_v, nb, &s_sum, &s_vmin, &s_vmax);
-    if (threadIdx.x == 0) c->total_vacant = s_sum;
-    __syncthreads();
-    if (threadIdx.x < 32) loop_ctl_warp(p, &s_take);
-    __syncthreads();
-    plan_block_quotas(p, s_v, nb, s_vmin, s_vmax, s_take);
-    if (threadIdx.x == 0) {
-      if (use_handle) cudaGraphSetConditional(handle, c->cont);
-      c->book_total[1] += (unsigned long long)(clock64() - t0);
-    }
-  }
+  end_block_pass(p, bid, nb, head, take, handle, use_handle);
 }
 
 // Per-block vacancy counts and the plan of the first fill (fill_take and the
@@ -1541,7 +1721,9 @@ __global__ void __launch_bounds__(kTile) k_local_prepare(Params p) {
       s_take = plan_local_fill(p, c->head, c->tail, c->alive, s_sum);
     }
     __syncthreads();
-    plan_block_quotas(p, s_v, (int)gridDim.x, s_vmin, s_vmax, s_take);
+    const unsigned long long planned =
+        plan_block_quotas(p, s_v, (int)gridDim.x, s_vmin, s_vmax, s_take, block_quota_cap(p.policy));
+    if (threadIdx.x == 0 && planned != s_take) c->fill_take = planned;
   }
 }
 
@@ -1660,12 +1842,16 @@ __global__ void k_step(Params p, cudaGraphConditionalHandle handle, int use_hand
   phase_step(p, blockIdx.x, gridDim.x, ss, true, handle, use_handle);
 }
 
-// The block-local policy: one launch per iteration (same grid as the loop).
+// The block-pass policies (LOCAL, DATA): one launch per iteration (same grid
+// as the loop).
 __global__ void __launch_bounds__(kTile) k_local(Params p, cudaGraphConditionalHandle handle, int use_handle) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SharedStatic ss = carve_static(p, smem_raw);
   stage_static(p, ss);
-  phase_local(p, blockIdx.x, gridDim.x, ss, handle, use_handle);
+  if (p.policy == POLICY_DATA)
+    phase_data(p, blockIdx.x, gridDim.x, ss, handle, use_handle);
+  else
+    phase_local(p, blockIdx.x, gridDim.x, ss, handle, use_handle);
 }
 
 // Per-action launches: fill, step limit (+ bookkeeping), scatter, one
@@ -1817,8 +2003,8 @@ __global__ void __launch_bounds__(kTile, 1) k_loop(Params p) {
   }
 }
 
-// The persistent loop of the block-local policy: one pass per block and
-// iteration (phase_local), one grid barrier per iteration.
+// The persistent loop of the block-pass policies: one pass per block and
+// iteration (phase_local or phase_data), one grid barrier per iteration.
 __global__ void __launch_bounds__(kTile, 1) k_loop_local(Params p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SharedStatic ss = carve_static(p, smem_raw);
@@ -1840,7 +2026,10 @@ __global__ void __launch_bounds__(kTile, 1) k_loop_local(Params p) {
       c->iter_max[parity ^ 1][2] = 0;
     }
     const long long t0 = clock64();
-    phase_local(p, bid, (int)nb, ss, 0, 0);
+    if (p.policy == POLICY_DATA)
+      phase_data(p, bid, (int)nb, ss, 0, 0);
+    else
+      phase_local(p, bid, (int)nb, ss, 0, 0);
     const long long work = clock64() - t0;
     if (!grid_barrier(p, nb)) break;
     if (threadIdx.x == 0) {
@@ -2022,7 +2211,7 @@ void launch_begin_run(const Params& p, unsigned long long budget, cudaStream_t s
 }
 cudaError_t launch_loop(const Params& p, const LaunchShape& sh, cudaStream_t s) {
   void* args[] = {const_cast<Params*>(&p)};
-  const void* fn = p.policy == POLICY_LOCAL ? (const void*)k_loop_local : (const void*)k_loop;
+  const void* fn = block_pass(p.policy) ? (const void*)k_loop_local : (const void*)k_loop;
   return cudaLaunchCooperativeKernel(fn, dim3(sh.loop_grid), dim3(kTile), args, sh.static_smem, s);
 }
 void launch_push_primaries(const Params& p, const StagedPrimary* d_prim, uint32_t n, cudaStream_t s) {

@@ -45,7 +45,9 @@ SORT_NONE = 0
 SORT_ACTION = 1
 SORT_ACTION_TYPE = 2
 SORT_LOCAL = 3
-SORT_NAMES = {"none": SORT_NONE, "action": SORT_ACTION, "action_type": SORT_ACTION_TYPE, "local": SORT_LOCAL}
+SORT_DATA = 4
+SORT_NAMES = {"none": SORT_NONE, "action": SORT_ACTION, "action_type": SORT_ACTION_TYPE, "local": SORT_LOCAL,
+              "data": SORT_DATA}
 
 DEFAULT_SEED = 20250321
 

@@ -16,7 +16,7 @@ from gpu_helpers import assert_conservation, match_fraction, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
-POLICIES = [wl.SORT_NONE, wl.SORT_ACTION, wl.SORT_ACTION_TYPE, wl.SORT_LOCAL]
+POLICIES = [wl.SORT_NONE, wl.SORT_ACTION, wl.SORT_ACTION_TYPE, wl.SORT_LOCAL, wl.SORT_DATA]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -216,7 +216,7 @@ def test_calorimeter_profile_statistics_independent_seeds():
 
 
 # ------------------------------------------------------------------ calorimeter in a 4 T field
-@pytest.mark.parametrize("policy", [wl.SORT_NONE, wl.SORT_ACTION_TYPE, wl.SORT_LOCAL])
+@pytest.mark.parametrize("policy", [wl.SORT_NONE, wl.SORT_ACTION_TYPE, wl.SORT_LOCAL, wl.SORT_DATA])
 @pytest.mark.parametrize("mode", [binding.LOOP_GRAPH, binding.LOOP_PERSISTENT])
 def test_field_histories(policy, mode):
     prob, prim = wl.calorimeter_field_10gev(40, n_slots=1 << 16)
@@ -247,7 +247,7 @@ def test_event_results_same_alone_and_mixed():
 
 
 # ------------------------------------------------------------------ capacity
-@pytest.mark.parametrize("policy", [wl.SORT_ACTION_TYPE, wl.SORT_LOCAL])
+@pytest.mark.parametrize("policy", [wl.SORT_ACTION_TYPE, wl.SORT_LOCAL, wl.SORT_DATA])
 def test_small_initializer_buffer_defers_without_changing_results(policy):
     """A buffer far smaller than the shower forces interactions to wait for
     space; deferred interactions replay with the same random numbers, so every
@@ -261,7 +261,7 @@ def test_small_initializer_buffer_defers_without_changing_results(policy):
     assert_conservation(prim, g["tally"])
 
 
-@pytest.mark.parametrize("policy", [wl.SORT_ACTION_TYPE, wl.SORT_LOCAL])
+@pytest.mark.parametrize("policy", [wl.SORT_ACTION_TYPE, wl.SORT_LOCAL, wl.SORT_DATA])
 def test_full_buffer_reports_capacity_and_stays_usable(policy):
     """One slot and a one-entry buffer: the electron's second secondary can
     never be placed, so the run stops with CELER_ERR_CAPACITY instead of
@@ -322,7 +322,7 @@ def test_policies_switched_between_runs_and_single_steps():
     history still matches the oracle."""
     prob = wl.water_cube_problem(n_slots=1024, history_capacity=2000)
     prim = wl.water_cube_primaries()
-    order = [wl.SORT_LOCAL, wl.SORT_NONE, wl.SORT_LOCAL, wl.SORT_ACTION_TYPE, wl.SORT_ACTION]
+    order = [wl.SORT_LOCAL, wl.SORT_NONE, wl.SORT_DATA, wl.SORT_ACTION_TYPE, wl.SORT_DATA, wl.SORT_ACTION]
     modes = [binding.LOOP_PERSISTENT, binding.LOOP_GRAPH, binding.LOOP_HOST]
     with binding.Context(prob) as ctx:
         ctx.add_events(prim)
@@ -346,3 +346,36 @@ def test_policies_switched_between_runs_and_single_steps():
     np.testing.assert_array_equal(hist["secondaries"], o["hist"]["secondaries"])
     np.testing.assert_allclose(edep, o["edep"], rtol=1e-9, atol=1e-9 * 10.0)
     assert_conservation(prim, tally)
+
+
+def test_data_policy_places_neutral_low_and_charged_high():
+    """The charge partition of the fill (Sec. 3.2): after one iteration on a
+    store with room for everything, every block's photons sit below its
+    electrons in the block's own slot order (chunks b, b + nb, ...)."""
+    prob, _ = wl.calorimeter_1gev(1)
+    prob = prob.replace(n_slots=8192, sort_policy=wl.SORT_DATA)
+    rng = np.random.default_rng(3)
+    n = 3000
+    prim = wl.electron_beam(n, 1000.0)
+    prim["ptype"] = rng.integers(0, 2, n)  # photons and electrons mixed in queue order
+    with binding.Context(prob) as ctx:
+        ctx.add_events(prim)
+        ctx.step()
+        state = ctx.debug_slots()
+        nb = ctx.loop_blocks()
+    status, ptype = state["status"], state["ptype"]
+    slots = np.arange(len(status))
+    chunk = slots // 32
+    owner = chunk % nb
+    order = (chunk // nb) * 32 + slots % 32  # position within the owning block's slots
+    checked = 0
+    for b in range(nb):
+        sel = (owner == b) & (status != 0)
+        if not sel.any():
+            continue
+        pos_g = order[sel & (ptype == 0)]
+        pos_e = order[sel & (ptype != 0)]
+        if len(pos_g) and len(pos_e):
+            assert pos_g.max() < pos_e.min(), b
+            checked += 1
+    assert checked > nb // 2
