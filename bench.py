@@ -413,7 +413,7 @@ def run_extras(args, binding, stream, flush):
     c2 = binding.to_c_primaries(prim2)
     dev2 = torch.from_numpy(c2.view(np.uint8).copy()).cuda()
     pol = {}
-    for name in ("action_type", "action", "none", "local"):
+    for name in ("action_type", "action", "none", "data", "local"):
         ctx = binding.Context(prob2.replace(sort_policy=wl.SORT_NAMES[name], max_events=1), stream=stream.cuda_stream)
         times, steps = [], 0
         for rep in range(1 + args.extra_steps):
