@@ -1296,15 +1296,44 @@ __device__ __forceinline__ void load_block_vacancies(const Params& p, uint32_t* 
 constexpr unsigned kDataMaxQuota = 8192;
 __device__ __forceinline__ unsigned block_quota_cap(int policy) { return policy == POLICY_DATA ? kDataMaxQuota : 0xFFFFFFFFu; }
 
-// End of a block pass (LOCAL, DATA): the block's vacancy count, and in the
-// last block to finish the commit of the fill, the vacancy totals from the
-// per-block counts (the per-tile prefix is left to the next run of another
-// policy), the end of the iteration and the plan of the next fill.
-__device__ void end_block_pass(const Params& p, int bid, int nb, unsigned long long head, unsigned long long take,
-                               cudaGraphConditionalHandle handle, int use_handle) {
+// End of a block pass (LOCAL, DATA). The block's vacancy count is its count
+// at the start plus its releases minus its fills (only the block touches its
+// chunks). The last block to take a ticket commits the fill, takes the
+// vacancy totals from the per-block counts (the per-tile prefix is left to
+// the next run of another policy), ends the iteration and plans the next
+// fill. In the persistent loop the ticket doubles as the grid barrier: the
+// other blocks wait (bounded) for the last one to bump the generation word,
+// so an iteration costs one global atomic per block. Returns false if the
+// wait gave up (abort word set, ERR_BARRIER_TIMEOUT).
+__device__ bool end_block_pass(const Params& p, int bid, int nb, unsigned long long head, unsigned long long take,
+                               long long vdelta, bool persistent, cudaGraphConditionalHandle handle,
+                               int use_handle, long long t_work0) {
+  __shared__ long long s_delta;
+  __shared__ unsigned s_last, s_gen;
+  __shared__ int s_ok;
   Ctl* c = p.ctl;
-  count_block_vacancies(p, bid, nb);
-  if (last_block_done(&c->done_c, (unsigned)nb)) {
+  unsigned* gen = p.barrier + 1;
+  unsigned* abort_word = p.barrier + 2;
+  if (threadIdx.x == 0) s_delta = 0;
+  __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) vdelta += __shfl_xor_sync(0xffffffffu, vdelta, o);
+  if ((threadIdx.x & 31) == 0 && vdelta != 0) atomicAdd((unsigned long long*)&s_delta, (unsigned long long)vdelta);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    p.block_vacant[bid] = (uint32_t)((long long)p.block_vacant[bid] + s_delta);
+    if (persistent) {
+      atomicMax(&c->iter_max[c->iteration & 1][2], (unsigned long long)(clock64() - t_work0));
+      s_gen = *reinterpret_cast<volatile unsigned*>(gen);
+    }
+    __threadfence();
+    const unsigned ticket = atomicAdd(&c->done_c, 1u);
+    s_last = (ticket == (unsigned)nb - 1u) ? 1u : 0u;
+    if (s_last) *reinterpret_cast<volatile unsigned*>(&c->done_c) = 0u;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
     __shared__ uint32_t s_v[kMaxLoopBlocks];
     __shared__ unsigned long long s_sum, s_take;
     __shared__ unsigned s_vmin, s_vmax;
@@ -1326,7 +1355,35 @@ __device__ void end_block_pass(const Params& p, int bid, int nb, unsigned long l
       if (use_handle) cudaGraphSetConditional(handle, c->cont);
       c->book_total[1] += (unsigned long long)(clock64() - t0);
     }
+    __syncthreads();
+    if (persistent && threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(gen, 1u);
+    }
+    return true;
   }
+  if (!persistent) return true;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const long long t0 = clock64();
+    for (;;) {
+      if (*reinterpret_cast<volatile unsigned*>(gen) != s_gen) break;
+      if (*reinterpret_cast<volatile unsigned*>(abort_word) != 0u) {
+        ok = 0;
+        break;
+      }
+      if (clock64() - t0 > kBarrierTimeoutCycles) {
+        atomicExch(abort_word, 1u);
+        atomicOr(&c->error, ERR_BARRIER_TIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
 }
 
 // One whole iteration of the DATA policy (Sec. 3.2, "partitioning track
@@ -1339,8 +1396,9 @@ __device__ void end_block_pass(const Params& p, int bid, int nb, unsigned long l
 // chunks that hold or receive tracks, fills it, and runs the step limit,
 // along-step and interaction of its live tracks in slot order, masking the
 // others (Sec. 2).
-__device__ void phase_data(const Params& p, int bid, int nb, const SharedStatic& ss, cudaGraphConditionalHandle handle,
-                           int use_handle) {
+__device__ bool phase_data(const Params& p, int bid, int nb, const SharedStatic& ss, cudaGraphConditionalHandle handle,
+                           int use_handle, bool persistent) {
+  const long long t_work0 = clock64();
   __shared__ uint32_t s_chunks[kTile];
   __shared__ uint32_t s_cpre[kTile];
   __shared__ unsigned s_wn[kTile / 32];
@@ -1474,7 +1532,8 @@ __device__ void phase_data(const Params& p, int bid, int nb, const SharedStatic&
   if (n_def) atomicAdd(&c->n_deferred, (unsigned)n_def);
   __syncthreads();
   if (threadIdx.x < A_COUNT && s_acts[threadIdx.x] != 0) atomicAdd(&c->action_count[threadIdx.x], s_acts[threadIdx.x]);
-  end_block_pass(p, bid, nb, head, take, handle, use_handle);
+  return end_block_pass(p, bid, nb, head, take, (long long)killed - (long long)my_fill, persistent, handle, use_handle,
+                        t_work0);
 }
 
 // One whole iteration of the block-local policy, in one pass per block with
@@ -1497,8 +1556,9 @@ __device__ void phase_data(const Params& p, int bid, int nb, const SharedStatic&
 //    fill).
 // Secondaries go to the buffer's tail while the taken entries are being read:
 // the capacity checks count from the uncommitted head.
-__device__ void phase_local(const Params& p, int bid, int nb, const SharedStatic& ss, cudaGraphConditionalHandle handle,
-                            int use_handle) {
+__device__ bool phase_local(const Params& p, int bid, int nb, const SharedStatic& ss, cudaGraphConditionalHandle handle,
+                            int use_handle, bool persistent) {
+  const long long t_work0 = clock64();
   constexpr int kCap = 2 * kTile;
   constexpr int kMaxPieces = kCap / 8 + kMaxKeys;
   __shared__ uint32_t s_slot[kCap];
@@ -1700,7 +1760,8 @@ __device__ void phase_local(const Params& p, int bid, int nb, const SharedStatic
   if (n_def) atomicAdd(&c->n_deferred, (unsigned)n_def);
   __syncthreads();
   if (threadIdx.x < A_COUNT && s_acts[threadIdx.x] != 0) atomicAdd(&c->action_count[threadIdx.x], s_acts[threadIdx.x]);
-  end_block_pass(p, bid, nb, head, take, handle, use_handle);
+  return end_block_pass(p, bid, nb, head, take, (long long)killed - (long long)my_fill, persistent, handle, use_handle,
+                        t_work0);
 }
 
 // Per-block vacancy counts and the plan of the first fill (fill_take and the
@@ -1849,9 +1910,9 @@ __global__ void __launch_bounds__(kTile) k_local(Params p, cudaGraphConditionalH
   const SharedStatic ss = carve_static(p, smem_raw);
   stage_static(p, ss);
   if (p.policy == POLICY_DATA)
-    phase_data(p, blockIdx.x, gridDim.x, ss, handle, use_handle);
+    phase_data(p, blockIdx.x, gridDim.x, ss, handle, use_handle, false);
   else
-    phase_local(p, blockIdx.x, gridDim.x, ss, handle, use_handle);
+    phase_local(p, blockIdx.x, gridDim.x, ss, handle, use_handle, false);
 }
 
 // Per-action launches: fill, step limit (+ bookkeeping), scatter, one
@@ -2018,29 +2079,21 @@ __global__ void __launch_bounds__(kTile, 1) k_loop_local(Params p) {
   }
   if (!grid_barrier(p, nb)) return;
   long long t_prev = clock64();
-  unsigned parity = 0;
   for (;;) {
     if (*reinterpret_cast<volatile unsigned*>(&c->cont) == 0u) break;
+    const unsigned parity = (unsigned)(c->iteration & 1);
+    if (bid == 0 && threadIdx.x == 0) {  // the slowest block's work of the previous iteration
+      c->max_total[2] += c->iter_max[parity ^ 1u][2];
+      c->iter_max[parity ^ 1u][2] = 0;
+    }
+    const bool ok = p.policy == POLICY_DATA ? phase_data(p, bid, (int)nb, ss, 0, 0, true)
+                                            : phase_local(p, bid, (int)nb, ss, 0, 0, true);
+    if (!ok) break;
     if (bid == 0 && threadIdx.x == 0) {
-      c->max_total[2] += c->iter_max[parity ^ 1][2];
-      c->iter_max[parity ^ 1][2] = 0;
+      const long long now = clock64();
+      c->phase_cycles[2] += (unsigned long long)(now - t_prev);
+      t_prev = now;
     }
-    const long long t0 = clock64();
-    if (p.policy == POLICY_DATA)
-      phase_data(p, bid, (int)nb, ss, 0, 0);
-    else
-      phase_local(p, bid, (int)nb, ss, 0, 0);
-    const long long work = clock64() - t0;
-    if (!grid_barrier(p, nb)) break;
-    if (threadIdx.x == 0) {
-      atomicMax(&c->iter_max[parity][2], (unsigned long long)work);
-      if (bid == 0) {
-        const long long now = clock64();
-        c->phase_cycles[2] += (unsigned long long)(now - t_prev);
-        t_prev = now;
-      }
-    }
-    parity ^= 1u;
   }
   if (bid == 0 && threadIdx.x == 0) {
     c->max_total[2] += c->iter_max[0][2] + c->iter_max[1][2];
