@@ -488,6 +488,7 @@ def run_extras(args, binding, stream, flush):
                      events_per_s=256 / t_batch),
         sequential=dict(value=steps_seq / t_seq, wall_s=t_seq, track_steps=int(steps_seq), events_per_s=256 / t_seq),
         speedup=t_seq / t_batch, max_rel_tally_diff_batched_vs_sequential=max_rel)
+    out["event_per_stream"] = event_per_stream(binding, tuned, events[:64], seq_tallies[:64], flush)
 
     # --- serving: Poisson arrivals of offload events
     rate, dur = args.serve_rate, args.serve_seconds
@@ -514,6 +515,95 @@ def run_extras(args, binding, stream, flush):
             window_s=stop)
     out["serving"] = dict(rate_hz=rate, duration_s=dur, mode=mode, chunk_iterations=args.serve_chunk, **served)
     return out
+
+
+def event_per_stream(binding, prob, events, ref_tallies, flush):
+    """Event-per-stream mode (paper Sec. 4.1, Fig. 3) with per-iteration hit
+    copies (Sec. 3.4): K contexts, each on its own stream with slots/K track
+    slots and SMs/K blocks, each stepping one event at a time in the host loop
+    and copying its hits to pinned memory after every iteration, against one
+    mixed context stepping all events in one track array (persistent loop)."""
+    import torch
+
+    n_ev = len(events)
+    prim = wl.concat_primaries(events)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    res = {}
+    # one mixed track array, all events at once
+    stream = torch.cuda.Stream()
+    ctx = binding.Context(prob.replace(max_events=n_ev, sort_policy=wl.SORT_LOCAL), stream=stream.cuda_stream)
+    ctx.add_events(prim)
+    ctx.run_events(binding.LOOP_PERSISTENT)
+    for e in range(n_ev):
+        ctx.reset_event(e)
+    flush.zero_()
+    torch.cuda.synchronize()
+    s0 = ctx.stats()["steps_total"]
+    t0 = time.perf_counter()
+    ctx.add_events(prim)
+    ctx.run_events(binding.LOOP_PERSISTENT)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    res["mixed_one_array"] = dict(events_per_s=n_ev / dt, value=(ctx.stats()["steps_total"] - s0) / dt)
+    ctx.close()
+
+    def run(k_streams, hit_mode):
+        ctxs, hits = [], []
+        for k in range(k_streams):
+            st = torch.cuda.Stream()
+            c = binding.Context(prob.replace(n_slots=max(prob.n_slots // k_streams, 1024), max_events=1,
+                                             sort_policy=wl.SORT_LOCAL), stream=st.cuda_stream)
+            c.set_grid_blocks(max(sms // k_streams, 1))
+            h = torch.zeros(c.n_bins, dtype=torch.float64, pin_memory=True)
+            c.set_hit_readout(hit_mode, h)
+            ctxs.append(c)
+            hits.append(h)
+        out_t = [None] * n_ev
+        steps = [0] * k_streams
+        errors = []
+
+        def worker(k):
+            try:
+                c = ctxs[k]
+                s_begin = c.stats()["steps_total"]
+                for e in range(k, n_ev, k_streams):
+                    c.reset_event(e)
+                    c.add_primaries(e, events[e])
+                    c.run_events(binding.LOOP_HOST)
+                    out_t[e] = c.read_tallies(e)
+                steps[k] = c.stats()["steps_total"] - s_begin
+            except Exception as exc:  # reported below
+                errors.append(repr(exc))
+
+        for c in ctxs:  # warm-up: one event each
+            c.reset_event(0)
+            c.add_primaries(0, events[0])
+            c.run_events(binding.LOOP_HOST)
+        flush.zero_()
+        torch.cuda.synchronize()
+        th = [threading.Thread(target=worker, args=(k,)) for k in range(k_streams)]
+        t0 = time.perf_counter()
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        for c in ctxs:
+            c.close()
+        if errors:
+            return dict(error=errors[0])
+        max_rel = max(float(np.max(np.abs(a[0] - b[0]) / np.maximum(np.abs(b[0]), 1e-300)))
+                      for a, b in zip(out_t, ref_tallies))
+        return dict(events_per_s=n_ev / dt, value=sum(steps) / dt, max_rel_tally_diff_vs_sequential=max_rel)
+
+    for k_streams in (1, 4, 8):
+        res[f"streams_{k_streams}_async_hits"] = run(k_streams, 1)
+    for k_streams in (4, 8):
+        res[f"streams_{k_streams}_sync_hits"] = run(k_streams, 2)
+    res["events"] = n_ev
+    res["slots_total"] = prob.n_slots
+    return res
 
 
 def binding_policy(name):

@@ -260,6 +260,27 @@ celer_status celer_get_stats(celer_ctx* ctx, celer_step_stats* out);
 /* Change the reordering policy between runs. */
 celer_status celer_set_sort_policy(celer_ctx* ctx, int policy);
 
+/* Per-iteration hit readout (Sec. 3.4, "Asynchronous memory management"):
+ * during host-loop runs (CELER_LOOP_HOST), after every step iteration the
+ * tally rows (max_events x bins doubles, row-major as in celer_read_tallies)
+ * are copied into host_hits. mode 0: off. mode 1: stream-ordered
+ * (cudaMemcpyAsync on the context's stream; other streams keep running).
+ * mode 2: synchronous (the whole device is synchronised, then cudaMemcpy:
+ * every stream waits for the copy, the behaviour the paper measured against).
+ * host_hits: caller-owned, pinned (cudaHostAlloc or a pinned torch tensor) for
+ * mode 1, at least max_events x bins doubles, valid while the mode is on.
+ * Graph and persistent runs do not return to the host per iteration and copy
+ * nothing. Bad mode, null or short buffer: CELER_ERR_INVALID. */
+celer_status celer_set_hit_readout(celer_ctx* ctx, int mode, double* host_hits, uint64_t n);
+
+/* Cap the GPU blocks of this context's kernels (0: the default, one block per
+ * SM for the persistent and block-pass kernels), so that several contexts,
+ * each on its own stream, can run their events side by side: the event-per-
+ * stream mode the paper compares with one mixed track array (Sec. 4.1). The
+ * next run starts with the new grids (a captured graph is rebuilt).
+ * blocks < 0: CELER_ERR_INVALID. */
+celer_status celer_set_grid_blocks(celer_ctx* ctx, int blocks);
+
 /* Per-iteration counters (alive, queued, steps, tracks per action) of the
  * last min(n_max, recorded) iterations, the analogue of the paper's counter
  * tracks (Sec. 4). *n_out receives the row count. */

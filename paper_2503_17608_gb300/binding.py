@@ -113,7 +113,7 @@ EXPORTS = [
     "celer_enable_kernel_timing", "celer_kernel_timing", "celer_debug_partition", "celer_debug_table",
     "celer_debug_philox", "celer_debug_curand_philox", "celer_partition_keys_noalloc", "celer_debug_math",
     "celer_run_iterations", "celer_read_event_live", "celer_serve", "celer_autotune", "celer_get_problem",
-    "celer_debug_sample", "celer_debug_slots",
+    "celer_debug_sample", "celer_debug_slots", "celer_set_hit_readout", "celer_set_grid_blocks",
 ]
 
 _lib = None
@@ -156,6 +156,8 @@ def load(path: Optional[str] = None):
         "celer_debug_curand_philox": ([u64, u64, u64, vp, u64], i32),
         "celer_debug_sample": ([i32, u32, u32, vp, C.c_double, vp, vp, u64, vp, vp, vp, vp], i32),
         "celer_debug_slots": ([vp, vp, vp, C.POINTER(i32)], i32),
+        "celer_set_hit_readout": ([vp, i32, vp, u64], i32),
+        "celer_set_grid_blocks": ([vp, i32], i32),
         "celer_partition_keys_noalloc": ([vp, u64, i32, i32, vp, vp, vp], i32),
         "celer_run_iterations": ([vp, i32, u64, C.POINTER(u64)], i32),
         "celer_read_event_live": ([vp, u32, u32, vp], i32),
@@ -368,6 +370,23 @@ class Context:
         s = celer_step_stats()
         _check(load().celer_get_stats(self._h, C.byref(s)), self._h)
         return _stats_dict(s)
+
+    def set_hit_readout(self, mode: int, host_hits=None):
+        """Per-iteration copy of the tally rows into host_hits during host-loop
+        runs: mode 0 off, 1 stream-ordered, 2 synchronous. host_hits: a pinned
+        float64 torch tensor (or array) of at least max_events x bins."""
+        if mode == 0:
+            _check(load().celer_set_hit_readout(self._h, 0, None, 0), self._h)
+            self._hits = None
+            return
+        ptr = host_hits.data_ptr() if hasattr(host_hits, "data_ptr") else host_hits.ctypes.data
+        n = host_hits.numel() if hasattr(host_hits, "numel") else host_hits.size
+        _check(load().celer_set_hit_readout(self._h, int(mode), C.c_void_p(ptr), int(n)), self._h)
+        self._hits = host_hits  # keep it alive while the mode is on
+
+    def set_grid_blocks(self, blocks: int):
+        """Cap the GPU blocks of this context's kernels (0: one per SM)."""
+        _check(load().celer_set_grid_blocks(self._h, int(blocks)), self._h)
 
     def set_sort_policy(self, policy: int):
         _check(load().celer_set_sort_policy(self._h, int(policy)), self._h)

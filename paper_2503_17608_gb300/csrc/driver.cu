@@ -66,6 +66,9 @@ struct celer_ctx {
   std::vector<int> t_kid;
   int t_used = 0;
   bool tiles_stale = false;  // the per-tile vacancy prefix predates the last block-local iterations
+  // per-iteration hit readout of the host loop: 0 off, 1 stream-ordered, 2 synchronous
+  int hit_mode = 0;
+  double* h_hits = nullptr;
   double t_total_ms[KID_COUNT] = {};
   uint64_t t_launches[KID_COUNT] = {};
 };
@@ -713,8 +716,19 @@ celer_status celer_run_iterations(celer_ctx* ctx, int mode, uint64_t budget, uin
     const int batch = 8;
     int cur = 0;
     bool have_prev = false;
+    const size_t hit_bytes = sizeof(double) * (size_t)ctx->p.max_events * (size_t)ctx->p.n_bins;
     for (;;) {
-      for (int i = 0; i < batch; ++i) launch_iteration(ctx, ctx->stream, 0, 0);
+      for (int i = 0; i < batch; ++i) {
+        launch_iteration(ctx, ctx->stream, 0, 0);
+        if (ctx->hit_mode == 1) {
+          CELER_CUDA(ctx, cudaMemcpyAsync(ctx->h_hits, ctx->p.tally, hit_bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        } else if (ctx->hit_mode == 2) {
+          // a synchronous copy: the whole device waits (every stream), then the
+          // host thread copies
+          CELER_CUDA(ctx, cudaDeviceSynchronize());
+          CELER_CUDA(ctx, cudaMemcpy(ctx->h_hits, ctx->p.tally, hit_bytes, cudaMemcpyDeviceToHost));
+        }
+      }
       CELER_CUDA(ctx, cudaGetLastError());
       CELER_CUDA(ctx, cudaMemcpyAsync(&ctx->h_cont[cur], &ctx->p.ctl->cont, sizeof(unsigned), cudaMemcpyDeviceToHost,
                                       ctx->stream));
@@ -841,6 +855,31 @@ celer_status celer_read_loop_profile(celer_ctx* ctx, uint64_t* cycles_out, int n
                                       c.max_total[0], c.max_total[1], c.max_total[2], c.max_total[3],
                                       c.book_total[0], c.book_total[1]};
   for (int k = 0; k < n; ++k) cycles_out[k] = k < 10 ? all[k] : 0;
+  return CELER_OK;
+}
+
+celer_status celer_set_hit_readout(celer_ctx* ctx, int mode, double* host_hits, uint64_t n) {
+  if (!ctx || mode < 0 || mode > 2) return CELER_ERR_INVALID;
+  if (mode != 0 && (!host_hits || n < (uint64_t)ctx->p.max_events * (uint64_t)ctx->p.n_bins))
+    return fail(ctx, CELER_ERR_INVALID, "hit buffer missing or smaller than max_events x bins");
+  ctx->hit_mode = mode;
+  ctx->h_hits = mode ? host_hits : nullptr;
+  return CELER_OK;
+}
+
+celer_status celer_set_grid_blocks(celer_ctx* ctx, int blocks) {
+  if (!ctx || blocks < 0) return CELER_ERR_INVALID;
+  LaunchShape sh{};
+  CELER_CUDA(ctx, configure_kernels(ctx->p, ctx->shape.block, &sh));
+  if (blocks > 0) {
+    sh.loop_grid = std::min(sh.loop_grid, blocks);
+    sh.tile_grid = std::min(sh.tile_grid, blocks);
+    sh.step_grid = std::min(sh.step_grid, blocks);
+    sh.along_grid = std::min(sh.along_grid, blocks);
+    sh.post_grid = std::min(sh.post_grid, blocks);
+  }
+  ctx->shape = sh;
+  destroy_graph(ctx);  // captured with the old grids
   return CELER_OK;
 }
 
