@@ -440,6 +440,35 @@ def run_extras(args, binding, stream, flush):
                              for part, vals in prof.items()})
     out["calorimeter_field_10gev"] = dict(desc2, sorted_vs_unsorted=pol)
 
+    # --- parent-slot reuse (paper Sec. 3.2) on the headline workload, per policy
+    prob1, prim1, _ = make_workload(args.workload)
+    c1 = binding.to_c_primaries(prim1)
+    dev1 = torch.from_numpy(c1.view(np.uint8).copy()).cuda()
+    reuse = {}
+    for name in ("none", "data", "local"):
+        row = {}
+        for on in (False, True):
+            ctx = binding.Context(prob1.replace(sort_policy=wl.SORT_NAMES[name], max_events=1), stream=stream.cuda_stream)
+            ctx.set_parent_reuse(on)
+            times, steps = [], 0
+            for rep in range(3 + args.extra_steps):
+                flush.zero_()
+                ctx.reset_event(rep)
+                s0 = ctx.stats()["steps_total"]
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.add_primaries_device(rep, dev1.data_ptr(), len(c1))
+                ctx.run_events(binding.LOOP_PERSISTENT)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if rep >= 3:
+                    times.append(e0.elapsed_time(e1))
+                    steps += ctx.stats()["steps_total"] - s0
+            ctx.close()
+            row["reuse" if on else "queued"] = steps / (sum(times) / 1e3)
+        reuse[name] = row
+    out["parent_slot_reuse"] = dict(workload=args.workload, track_steps_per_s=reuse)
+
     # --- 256 offload events: autotune on a sample, then all in one loop vs one by one
     events = wl.offload_events(256)
     prim3 = wl.concat_primaries(events)

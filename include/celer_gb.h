@@ -281,6 +281,14 @@ celer_status celer_set_hit_readout(celer_ctx* ctx, int mode, double* host_hits, 
  * blocks < 0: CELER_ERR_INVALID. */
 celer_status celer_set_grid_blocks(celer_ctx* ctx, int blocks);
 
+/* Parent-slot reuse (Sec. 3.2, second paragraph): on = 1 makes the first of
+ * the two photons of a pair conversion start in the slot of the photon that
+ * converted, without passing through the initializer buffer; the second is
+ * queued as before. Off by default. Histories do not change (a track's
+ * history depends only on its initial state and id); the buffer traffic and
+ * the fill work do. Takes effect at the next run. */
+celer_status celer_set_parent_reuse(celer_ctx* ctx, int on);
+
 /* Per-iteration counters (alive, queued, steps, tracks per action) of the
  * last min(n_max, recorded) iterations, the analogue of the paper's counter
  * tracks (Sec. 4). *n_out receives the row count. */

@@ -114,6 +114,7 @@ EXPORTS = [
     "celer_debug_philox", "celer_debug_curand_philox", "celer_partition_keys_noalloc", "celer_debug_math",
     "celer_run_iterations", "celer_read_event_live", "celer_serve", "celer_autotune", "celer_get_problem",
     "celer_debug_sample", "celer_debug_slots", "celer_set_hit_readout", "celer_set_grid_blocks",
+    "celer_set_parent_reuse",
 ]
 
 _lib = None
@@ -158,6 +159,7 @@ def load(path: Optional[str] = None):
         "celer_debug_slots": ([vp, vp, vp, C.POINTER(i32)], i32),
         "celer_set_hit_readout": ([vp, i32, vp, u64], i32),
         "celer_set_grid_blocks": ([vp, i32], i32),
+        "celer_set_parent_reuse": ([vp, i32], i32),
         "celer_partition_keys_noalloc": ([vp, u64, i32, i32, vp, vp, vp], i32),
         "celer_run_iterations": ([vp, i32, u64, C.POINTER(u64)], i32),
         "celer_read_event_live": ([vp, u32, u32, vp], i32),
@@ -383,6 +385,10 @@ class Context:
         n = host_hits.numel() if hasattr(host_hits, "numel") else host_hits.size
         _check(load().celer_set_hit_readout(self._h, int(mode), C.c_void_p(ptr), int(n)), self._h)
         self._hits = host_hits  # keep it alive while the mode is on
+
+    def set_parent_reuse(self, on: bool):
+        """A pair's first photon starts in the converted photon's slot."""
+        _check(load().celer_set_parent_reuse(self._h, int(bool(on))), self._h)
 
     def set_grid_blocks(self, blocks: int):
         """Cap the GPU blocks of this context's kernels (0: one per SM)."""

@@ -181,6 +181,7 @@ struct Params {
   // physics
   double cut_track, cut_moller, cut_brems;
   int processes;
+  int reuse_parent;        // 1: a pair's first photon starts in the parent's slot (Sec. 3.2)
   const double2* tables;   // [mat][col][kGrid] (value, next - value)
   const double* mtab;      // log/exp reduction tables (fastmath.cuh)
   double lnEmin, inv_dl, dl;

@@ -867,6 +867,13 @@ celer_status celer_set_hit_readout(celer_ctx* ctx, int mode, double* host_hits, 
   return CELER_OK;
 }
 
+celer_status celer_set_parent_reuse(celer_ctx* ctx, int on) {
+  if (!ctx) return CELER_ERR_INVALID;
+  ctx->p.reuse_parent = on ? 1 : 0;
+  destroy_graph(ctx);  // captured with the old parameters
+  return CELER_OK;
+}
+
 celer_status celer_set_grid_blocks(celer_ctx* ctx, int blocks) {
   if (!ctx || blocks < 0) return CELER_ERR_INVALID;
   LaunchShape sh{};

@@ -883,8 +883,9 @@ __device__ __forceinline__ bool pair_one(const Params& p, uint32_t slot, uint8_t
                                          unsigned long long& n_def) {
   const Tracks& t = p.trk;
   const bool keep = kMe >= p.cut_track;
+  const bool reuse = keep && p.reuse_parent != 0;  // the first photon takes the parent's slot
   unsigned long long base;
-  if (!reserve_entries(p, keep ? 2u : 0u, tight, base)) {
+  if (!reserve_entries(p, keep ? (reuse ? 1u : 2u) : 0u, tight, base)) {
     defer_track(p, slot, st, n_def);
     return false;
   }
@@ -903,10 +904,27 @@ __device__ __forceinline__ bool pair_one(const Params& p, uint32_t slot, uint8_t
   if (keep) {
     const unsigned long long tid1 = rng.raw();
     const unsigned long long tid2 = rng.raw();
+    if (prim < p.hist_cap) atomicAdd(&p.hist_secondaries[prim], 2ull);
+    if (reuse) {
+      // parent-slot reuse (Sec. 3.2): the first photon starts in the slot the
+      // pair ended (position, layer, event and primary are the parent's), as
+      // a fresh track; the second goes to the initializer buffer
+      write_initializer(p, base, x, y, z, -dx, -dy, -dz, kMe, tid2, ev, prim, layer, GAMMA);
+      atomicAdd(&p.event_live[row_of(p, ev)], 1u);
+      t.ux[slot] = dx;
+      t.uy[slot] = dy;
+      t.uz[slot] = dz;
+      t.E[slot] = kMe;
+      t.tid[slot] = tid1;
+      t.ctr[slot] = 0u;
+      t.nmfp[slot] = -1.0;
+      t.action[slot] = A_NONE;
+      t.status[slot] = ALIVE;
+      return false;
+    }
     write_initializer(p, base, x, y, z, dx, dy, dz, kMe, tid1, ev, prim, layer, GAMMA);
     write_initializer(p, base + 1, x, y, z, -dx, -dy, -dz, kMe, tid2, ev, prim, layer, GAMMA);
     atomicAdd(&p.event_live[row_of(p, ev)], 2u);
-    if (prim < p.hist_cap) atomicAdd(&p.hist_secondaries[prim], 2ull);
   } else {
     deposit(p, ev, prim, layer, z, kMe);
     deposit(p, ev, prim, layer, z, kMe);
