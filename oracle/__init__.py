@@ -32,7 +32,7 @@ class om_problem(C.Structure):
         ("half_x", C.c_double), ("half_y", C.c_double), ("Bz", C.c_double),
         ("cut_track", C.c_double), ("cut_moller", C.c_double), ("cut_brems", C.c_double),
         ("processes", C.c_int), ("tally_mode", C.c_int), ("n_zbins", C.c_int),
-        ("seed", C.c_uint32),
+        ("seed", C.c_uint32), ("field_substep_cap", C.c_int),
     ]
 
 
@@ -108,6 +108,9 @@ def lib():
         L.om_sample_isotropic.argtypes = [C.POINTER(om_rng), _dp]
         L.om_rotate.argtypes = [_dp, C.c_double, C.c_double, _dp]
         L.om_helix_move.argtypes = [C.c_double, C.c_double, _dp, _dp]
+        L.om_rk_move.argtypes = [C.c_double, C.c_double, C.c_int, _dp, _dp]
+        L.om_rk_substeps.argtypes = [C.c_double, C.c_double]
+        L.om_rk_substeps.restype = C.c_int
         L.om_helix_side_distance.argtypes = [C.c_double, _dp, _dp, C.c_double, C.c_double, C.POINTER(C.c_int)]
         L.om_helix_side_distance.restype = C.c_double
         L.om_curvature.argtypes = [C.c_int, C.c_double, C.c_double]
@@ -143,6 +146,7 @@ class World:
         p.cut_track, p.cut_moller, p.cut_brems = prob.cut_track, prob.cut_moller, prob.cut_brems
         p.processes, p.tally_mode, p.n_zbins = prob.processes, prob.tally_mode, prob.n_zbins
         p.seed = prob.seed
+        p.field_substep_cap = prob.field_substep_cap
         err = C.create_string_buffer(256)
         self._h = L.om_world_create(C.byref(p), err, 256)
         if not self._h:
@@ -328,6 +332,17 @@ def helix_move(kappa, s, pos, direction):
     p = (C.c_double * 3)(*pos)
     d = (C.c_double * 3)(*direction)
     lib().om_helix_move(float(kappa), float(s), p, d)
+    return np.array(list(p)), np.array(list(d))
+
+
+def rk_substeps(kappa, s):
+    return lib().om_rk_substeps(float(kappa), float(s))
+
+
+def rk_move(kappa, s, n, pos, direction):
+    p = (C.c_double * 3)(*pos)
+    d = (C.c_double * 3)(*direction)
+    lib().om_rk_move(float(kappa), float(s), int(n), p, d)
     return np.array(list(p)), np.array(list(d))
 
 

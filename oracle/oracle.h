@@ -65,6 +65,7 @@ typedef struct {
   int tally_mode;
   int n_zbins;
   uint32_t seed;
+  int field_substep_cap; /* 0: exact helix; > 0: Runge-Kutta substeps, at most this many per step */
 } om_problem;
 
 typedef struct {
@@ -136,6 +137,8 @@ double om_sample_brems(double T, double kcut, om_rng* r);
 void om_sample_isotropic(om_rng* r, double dir[3]);
 void om_rotate(const double u[3], double cost, double phi, double out[3]);
 void om_helix_move(double kappa, double s, double pos[3], double dir[3]);
+int om_rk_substeps(double kappa, double s);
+void om_rk_move(double kappa, double s, int n, double pos[3], double dir[3]);
 double om_helix_side_distance(double kappa, const double pos[3], const double dir[3],
                               double hx, double hy, int* hit);
 double om_curvature(int ptype, double E, double Bz);

@@ -17,7 +17,8 @@
  *   - continuous loss: restricted collision stopping power (Berger-Seltzer
  *     form for electrons, no density effect) plus restricted radiative loss
  *     min(T, k_cut)/X0; range by 16-point Gauss-Legendre quadrature of 1/S;
- *   - motion in a uniform field along z: exact helix.
+ *   - motion in a uniform field along z: exact helix, or Runge-Kutta substeps
+ *     with a cap on the substeps of one step (Sec. 3.3).
  */
 #include "oracle.h"
 
@@ -28,6 +29,7 @@
 #define OM_NA 6.02214076e23
 #define OM_PI 3.14159265358979323846
 #define OM_FIELD_K 2.99792458 /* curvature [1/cm] = K * B[T] / p[MeV/c] */
+#define OM_RK_TURN 0.1        /* largest turn angle of one Runge-Kutta substep, rad */
 
 double om_electron_density(const om_material* m) {
   if (m->ne > 0.0) return m->ne;
@@ -227,6 +229,51 @@ void om_helix_move(double kappa, double s, double pos[3], double dir[3]) {
   pos[2] += dir[2] * s;
   dir[0] = ux * cphi + uy * sphi;
   dir[1] = uy * cphi - ux * sphi;
+}
+
+/* Numerical field propagation (paper Sec. 3.3: the curved path is divided
+ * into substeps, each found by numerical integration of the equation of
+ * motion). A field step of length s takes n = ceil(s |kappa| / 0.1) equal
+ * substeps, i.e. at most 0.1 rad of turn each (at least one). */
+int om_rk_substeps(double kappa, double s) {
+  double a = s * fabs(kappa) / OM_RK_TURN;
+  int n = (int)ceil(a);
+  return n < 1 ? 1 : n;
+}
+
+/* Classical fourth-order Runge-Kutta for the transverse motion in B along z,
+ * dx/ds = ux, dy/ds = uy, dux/ds = kappa uy, duy/ds = -kappa ux, over n equal
+ * substeps of length s / n; z advances by uz s exactly (uz is constant). The
+ * transverse direction is rescaled at the end to its length at the start
+ * (Runge-Kutta does not keep it). */
+void om_rk_move(double kappa, double s, int n, double pos[3], double dir[3]) {
+  double x = pos[0], y = pos[1], ux = dir[0], uy = dir[1];
+  const double q0 = ux * ux + uy * uy;
+  const double h = s / n;
+  for (int i = 0; i < n; ++i) {
+    double c1 = kappa * uy, d1 = -kappa * ux;
+    double ux2 = ux + 0.5 * h * c1, uy2 = uy + 0.5 * h * d1;
+    double c2 = kappa * uy2, d2 = -kappa * ux2;
+    double ux3 = ux + 0.5 * h * c2, uy3 = uy + 0.5 * h * d2;
+    double c3 = kappa * uy3, d3 = -kappa * ux3;
+    double ux4 = ux + h * c3, uy4 = uy + h * d3;
+    double c4 = kappa * uy4, d4 = -kappa * ux4;
+    x += h / 6.0 * (ux + 2.0 * ux2 + 2.0 * ux3 + ux4);
+    y += h / 6.0 * (uy + 2.0 * uy2 + 2.0 * uy3 + uy4);
+    ux += h / 6.0 * (c1 + 2.0 * c2 + 2.0 * c3 + c4);
+    uy += h / 6.0 * (d1 + 2.0 * d2 + 2.0 * d3 + d4);
+  }
+  double q = ux * ux + uy * uy;
+  if (q > 0.0) {
+    double f = sqrt(q0 / q);
+    ux *= f;
+    uy *= f;
+  }
+  pos[0] = x;
+  pos[1] = y;
+  pos[2] += dir[2] * s;
+  dir[0] = ux;
+  dir[1] = uy;
 }
 
 /* Smallest turn angle t in [0, 2 pi) with sin(sigma t + beta) = d. */

@@ -73,6 +73,7 @@ struct om_world {
   double* zb;      /* L + 1 boundaries */
   int* layer_mat;  /* L */
   double hx, hy, Bz;
+  int field_substep_cap;
   double cut_track, cut_moller, cut_brems;
   int processes;
   int tally_mode, nbins;
@@ -145,6 +146,7 @@ om_world* om_world_create(const om_problem* p, char* err, int errlen) {
   w->hx = p->half_x;
   w->hy = p->half_y;
   w->Bz = p->Bz;
+  w->field_substep_cap = p->field_substep_cap > 0 ? p->field_substep_cap : 0;
   w->cut_track = p->cut_track;
   w->cut_moller = p->cut_moller;
   w->cut_brems = p->cut_brems;
@@ -345,7 +347,7 @@ static void push_secondary(const om_world* w, tally* tl, om_rng* r, const om_tra
 }
 
 enum { GEO_NONE = 0, GEO_ZUP, GEO_ZDOWN, GEO_SIDE };
-enum { ACT_GEOM = 0, ACT_RANGE, ACT_INTERACT, ACT_TRAPPED };
+enum { ACT_GEOM = 0, ACT_RANGE, ACT_INTERACT, ACT_TRAPPED, ACT_FIELD };
 
 /* One step of one track. Returns 0 when the track ends, 1 when it lives on,
  * and sets *escaped_flag when it left the world. */
@@ -412,6 +414,15 @@ static int step_track(const om_world* w, uint32_t event, om_track* t, tally* tl,
     act = ACT_INTERACT;
   }
   if (s == INFINITY) act = ACT_TRAPPED;
+  /* Runge-Kutta field propagation with a substep cap (Sec. 3.3): a step
+   * needing more than `cap` substeps of 0.1 rad of turn is cut to cap of them
+   * and ends without a boundary crossing or an interaction ("paused");
+   * the track goes on from there at its next step. */
+  const int cap = w->field_substep_cap;
+  if (helix && cap > 0 && act != ACT_TRAPPED && s * fabs(kappa) > 0.1 * cap) {
+    s = 0.1 * cap / fabs(kappa);
+    act = ACT_FIELD;
+  }
 
   if (act == ACT_TRAPPED) {
     /* no finite step limit (possible only with processes switched off): the
@@ -428,7 +439,10 @@ static int step_track(const om_world* w, uint32_t event, om_track* t, tally* tl,
   int old_layer = t->layer;
   if (helix) {
     double pos[3] = {t->x, t->y, t->z}, dir[3] = {t->ux, t->uy, t->uz};
-    om_helix_move(kappa, s, pos, dir);
+    if (cap > 0)
+      om_rk_move(kappa, s, act == ACT_FIELD ? cap : om_rk_substeps(kappa, s), pos, dir);
+    else
+      om_helix_move(kappa, s, pos, dir);
     t->x = pos[0];
     t->y = pos[1];
     t->z = pos[2];

@@ -102,6 +102,7 @@ class Problem:
     block_size: int = 256
     split_actions: int = 0
     seed: int = DEFAULT_SEED
+    field_substep_cap: int = 0  # 0: exact helix; > 0: Runge-Kutta substeps, at most this many per step
     name: str = ""
 
     @property

@@ -151,3 +151,23 @@ def test_tally_bins_water_cube():
     prof = edep.sum(0)
     # 10 MeV photons along +z deposit mostly downstream of the entry face
     assert prof[:50].sum() > prof[50:].sum() > 0
+
+
+def test_field_substep_cap_splits_steps_and_conserves_energy():
+    """Runge-Kutta field propagation with a cap on the substeps of one step
+    (Sec. 3.3): a cap cuts long curved steps into several, so the step count
+    grows as the cap shrinks, while the shower's energy stays conserved and
+    without a binding cap the substeps reproduce the exact helix's step count
+    closely."""
+    prob, prim = wl.calorimeter_field_10gev(6)
+    hist_exact, edep_exact = oracle.World(prob).run(prim)
+    steps = {}
+    for cap in (1 << 30, 50, 3):
+        p = prob.replace(field_substep_cap=cap)
+        hist, edep = oracle.World(p).run(prim)
+        total = edep.sum() + hist["escaped"].sum()
+        assert total == pytest.approx(prim["E"].sum(), rel=1e-12)
+        steps[cap] = int(hist["steps"].sum())
+    exact = int(hist_exact["steps"].sum())
+    assert abs(steps[1 << 30] - exact) < 0.01 * exact
+    assert steps[1 << 30] <= steps[50] < steps[3]
