@@ -444,6 +444,36 @@ def run_extras(args, binding, stream, flush):
                              for part, vals in prof.items()})
     out["calorimeter_field_10gev"] = dict(desc2, sorted_vs_unsorted=pol)
 
+    # --- Runge-Kutta field propagation with a substep cap (paper Sec. 3.3, Fig. 2):
+    # the 4 T workload with substeps of at most 0.1 rad, caps of 10^9 (none),
+    # 1000 and 10 substeps per step, block-local policy
+    rk = {}
+    for cap in (1 << 30, 1000, 10):
+        ctx = binding.Context(prob2.replace(sort_policy=wl.SORT_LOCAL, max_events=1, field_substep_cap=cap),
+                              stream=stream.cuda_stream)
+        times, steps, iters = [], 0, 0
+        for rep in range(1 + args.extra_steps):
+            flush.zero_()
+            ctx.reset_event(rep)
+            s0 = ctx.stats()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.add_primaries_device(rep, dev2.data_ptr(), len(c2))
+            ctx.run_events(binding.LOOP_PERSISTENT)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep >= 1:
+                s1 = ctx.stats()
+                times.append(e0.elapsed_time(e1))
+                steps += s1["steps_total"] - s0["steps_total"]
+                iters += s1["iteration"] - s0["iteration"]
+        ctx.close()
+        nrep = len(times)
+        rk["no_cap" if cap == 1 << 30 else f"cap_{cap}"] = dict(
+            value=steps / (sum(times) / 1e3), ms_per_job=sum(times) / nrep, track_steps_per_job=steps / nrep,
+            iterations_per_job=iters / nrep)
+    out["field_runge_kutta_substep_cap"] = dict(workload=desc2["workload"], substep_turn_rad=0.1, runs=rk)
+
     # --- parent-slot reuse (paper Sec. 3.2) on the headline workload, per policy
     prob1, prim1, _ = make_workload(args.workload)
     c1 = binding.to_c_primaries(prim1)

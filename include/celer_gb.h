@@ -124,6 +124,11 @@ typedef struct {
   uint32_t seed;                     /* first word of every Philox key */
   uint64_t max_iterations;           /* celer_run_events limit (0: 10^6) */
   void* cuda_stream;                 /* cudaStream_t for all work (NULL: legacy default stream) */
+  int field_substep_cap;             /* charged tracks in the field (Sec. 3.3): 0 the exact helix;
+                                        > 0 classical Runge-Kutta substeps of at most 0.1 rad of
+                                        turn, at most this many per step: a longer step is cut
+                                        there and ends without crossing or interaction (action
+                                        "field"), to go on at the next iteration; < 0 invalid */
 } celer_problem;
 
 typedef struct {

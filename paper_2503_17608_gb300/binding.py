@@ -46,6 +46,7 @@ class celer_problem(C.Structure):
         ("history_capacity", C.c_uint64), ("sort_policy", C.c_int), ("block_size", C.c_int),
         ("split_actions", C.c_int),
         ("seed", C.c_uint32), ("max_iterations", C.c_uint64), ("cuda_stream", C.c_void_p),
+        ("field_substep_cap", C.c_int),
     ]
 
 
@@ -101,7 +102,7 @@ class celer_tune_trial(C.Structure):
 
 
 ACTION_NAMES = ["none", "zup", "zdown", "side", "range", "trapped", "compton", "photoelectric", "pair", "moller",
-                "brems"]
+                "brems", "field"]
 
 # Every entry point declared in include/celer_gb.h.
 EXPORTS = [
@@ -228,6 +229,7 @@ class ProblemStruct:
         cp.split_actions = prob.split_actions
         cp.max_iterations = max_iterations
         cp.cuda_stream = stream
+        cp.field_substep_cap = prob.field_substep_cap
         self.c = cp
 
 

@@ -44,6 +44,7 @@ enum Action : uint8_t {
   A_PAIR,
   A_MOLLER,
   A_BREMS,
+  A_FIELD,    // a field step cut at the substep cap: no crossing, no interaction
   A_COUNT
 };
 
@@ -182,6 +183,7 @@ struct Params {
   double cut_track, cut_moller, cut_brems;
   int processes;
   int reuse_parent;        // 1: a pair's first photon starts in the parent's slot (Sec. 3.2)
+  int field_cap;           // 0: exact helix; > 0: Runge-Kutta substeps, at most this many per step
   const double2* tables;   // [mat][col][kGrid] (value, next - value)
   const double* mtab;      // log/exp reduction tables (fastmath.cuh)
   double lnEmin, inv_dl, dl;

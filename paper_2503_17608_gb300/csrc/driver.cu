@@ -326,6 +326,7 @@ celer_status validate_problem(const celer_problem* pb, std::string& why) {
   }
   if (!(pb->half_x > 0.0) || !(pb->half_y > 0.0)) return why = "half widths must be positive", CELER_ERR_INVALID;
   if (!std::isfinite(pb->Bz)) return why = "Bz must be finite", CELER_ERR_INVALID;
+  if (pb->field_substep_cap < 0) return why = "field_substep_cap must be >= 0", CELER_ERR_INVALID;
   if (!(pb->cut_track >= kGridEmin) || !(pb->cut_track < kGridEmax))
     return why = "cut_track must be in [1 keV, 10 GeV)", CELER_ERR_INVALID;
   if (!(pb->cut_moller > 0.0) || !(pb->cut_brems > 0.0)) return why = "production cuts must be positive", CELER_ERR_INVALID;
@@ -443,6 +444,7 @@ celer_status celer_create(const celer_problem* pb, celer_ctx** out) {
   p.hx = pb->half_x;
   p.hy = pb->half_y;
   p.Bz = pb->Bz;
+  p.field_cap = pb->field_substep_cap;
   p.cut_track = pb->cut_track;
   p.cut_moller = pb->cut_moller;
   p.cut_brems = pb->cut_brems;

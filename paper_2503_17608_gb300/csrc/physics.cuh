@@ -202,6 +202,48 @@ __device__ __forceinline__ void helix_move(Curvature c, double s, double& x, dou
   uy = oy * cphi - ox * sphi;
 }
 
+// Numerical field propagation (Sec. 3.3): a field step of length s takes
+// n = ceil(s |kappa| / 0.1) equal substeps (at most 0.1 rad of turn each, at
+// least one) of classical fourth-order Runge-Kutta for the transverse motion,
+// dx/ds = ux, dy/ds = uy, dux/ds = kappa uy, duy/ds = -kappa ux; z advances
+// by uz s exactly; the transverse direction is rescaled at the end to its
+// length at the start.
+constexpr double kRkTurn = 0.1;
+__device__ __forceinline__ int rk_substeps(double kappa, double s) {
+  const int n = (int)ceil(s * fabs(kappa) / kRkTurn);
+  return n < 1 ? 1 : n;
+}
+__device__ __forceinline__ void rk_move(double kappa, double s, int n, double& x, double& y, double& z, double& ux,
+                                        double& uy, double uz) {
+  const double q0 = ux * ux + uy * uy;
+  const double h = s / n;
+  double X = x, Y = y, U = ux, V = uy;
+  for (int i = 0; i < n; ++i) {
+    const double c1 = kappa * V, d1 = -kappa * U;
+    const double U2 = U + 0.5 * h * c1, V2 = V + 0.5 * h * d1;
+    const double c2 = kappa * V2, d2 = -kappa * U2;
+    const double U3 = U + 0.5 * h * c2, V3 = V + 0.5 * h * d2;
+    const double c3 = kappa * V3, d3 = -kappa * U3;
+    const double U4 = U + h * c3, V4 = V + h * d3;
+    const double c4 = kappa * V4, d4 = -kappa * U4;
+    X += h / 6.0 * (U + 2.0 * U2 + 2.0 * U3 + U4);
+    Y += h / 6.0 * (V + 2.0 * V2 + 2.0 * V3 + V4);
+    U += h / 6.0 * (c1 + 2.0 * c2 + 2.0 * c3 + c4);
+    V += h / 6.0 * (d1 + 2.0 * d2 + 2.0 * d3 + d4);
+  }
+  const double q = U * U + V * V;
+  if (q > 0.0) {
+    const double f = sqrt(q0 / q);
+    U *= f;
+    V *= f;
+  }
+  x = X;
+  y = Y;
+  z += uz * s;
+  ux = U;
+  uy = V;
+}
+
 // Smallest turn angle t in [0, 2 pi) with sin(sigma t + beta) = d.
 __device__ __forceinline__ double first_turn(double d, double beta, double sigma) {
   const double a1 = asin(d);

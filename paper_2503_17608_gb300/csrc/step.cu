@@ -158,8 +158,11 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
     act = up ? A_ZUP : A_ZDOWN;
   }
   double s_side = kInf;
-  if (charged && p.Bz != 0.0) {
-    s_side = helix_side_distance(curvature(pt, E, p.Bz), x, y, ux, uy, p.hx, p.hy);
+  const bool helix = charged && p.Bz != 0.0;
+  Curvature cv{0.0, 0.0};
+  if (helix) {
+    cv = curvature(pt, E, p.Bz);
+    s_side = helix_side_distance(cv, x, y, ux, uy, p.hx, p.hy);
   } else {
     const double reach = s_geo * kLimitMargin;
     if (ux != 0.0) {
@@ -203,6 +206,14 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
     act = A_TRAPPED;
     s = 0.0;
   } else {
+    // Runge-Kutta field propagation with a substep cap (Sec. 3.3): a step
+    // needing more than `cap` substeps of 0.1 rad of turn is cut there and
+    // ends without a crossing or an interaction, to go on next iteration
+    if (helix && p.field_cap > 0 && s * fabs(cv.kappa) > kRkTurn * p.field_cap) {
+      s = kRkTurn * p.field_cap / fabs(cv.kappa);
+      act = A_FIELD;
+      interact = false;
+    }
     nmfp -= s * mu;
   }
   if (interact) {
@@ -726,7 +737,11 @@ __device__ __forceinline__ bool along_one(const Params& p, uint32_t slot, uint8_
   double ux = t.ux[slot], uy = t.uy[slot];
   const double uz = t.uz[slot];
   if (helix) {
-    helix_move(curvature(pt, E, p.Bz), s, x, y, z, ux, uy, uz);
+    const Curvature cv = curvature(pt, E, p.Bz);
+    if (p.field_cap > 0)
+      rk_move(cv.kappa, s, act == A_FIELD ? p.field_cap : rk_substeps(cv.kappa, s), x, y, z, ux, uy, uz);
+    else
+      helix_move(cv, s, x, y, z, ux, uy, uz);
   } else {
     x += s * ux;
     y += s * uy;
