@@ -705,9 +705,17 @@ def load_peaks():
 # DRAM bytes per launch of that kernel from the same captures, for the
 # workloads that were captured whole. Keys: (workload, policy).
 BYTES_PER_STEP = 160.0
-FP64_FLOP_PER_STEP = {("calorimeter-1gev", "local"): 119.7, ("calorimeter-1gev", None): 119.7,
-                      ("calorimeter-field-10gev", None): 132.2, ("water-cube-10mev", None): 119.7}
-DRAM_BYTES_PER_LAUNCH = {("calorimeter-1gev", "local"): 1.374e6}
+FP64_FLOP_PER_STEP = {("calorimeter-1gev", "none"): 131.0, ("calorimeter-1gev", "action"): 131.0,
+                      ("calorimeter-1gev", "action_type"): 131.0, ("calorimeter-1gev", "data"): 119.5,
+                      ("calorimeter-1gev", "local"): 119.5,
+                      ("calorimeter-field-10gev", "none"): 138.4, ("calorimeter-field-10gev", "action"): 138.4,
+                      ("calorimeter-field-10gev", "action_type"): 138.4, ("calorimeter-field-10gev", "data"): 129.5,
+                      ("calorimeter-field-10gev", "local"): 129.5,
+                      ("water-cube-10mev", None): 119.5}
+DRAM_BYTES_PER_LAUNCH = {("calorimeter-1gev", "none"): 0.79e6, ("calorimeter-1gev", "action_type"): 0.94e6,
+                         ("calorimeter-1gev", "data"): 1.64e6, ("calorimeter-1gev", "local"): 1.42e6,
+                         ("calorimeter-field-10gev", "none"): 28.26e6, ("calorimeter-field-10gev", "action_type"): 28.53e6,
+                         ("calorimeter-field-10gev", "data"): 26.94e6, ("calorimeter-field-10gev", "local"): 24.50e6}
 # FP64 peak of GB300: 2 DFMA per SM-cycle (ncu peak_sustained) x 152 SMs x 2.07 GHz x 2 flop
 FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
@@ -717,7 +725,7 @@ def roofline_loop(workload, policy, steps_per_job, job_ms, full_size=True):
     launch per job): FP64 ALU bound, with the HBM fraction beside it."""
     peaks, kind = load_peaks()
     t = job_ms / 1e3
-    fpstep = FP64_FLOP_PER_STEP.get((workload, policy), FP64_FLOP_PER_STEP[(workload, None)])
+    fpstep = FP64_FLOP_PER_STEP.get((workload, policy), FP64_FLOP_PER_STEP.get((workload, None), 119.5))
     flops = fpstep * steps_per_job / t / 1e12
     gbs = BYTES_PER_STEP * steps_per_job / t / 1e9
     kernel = "k_loop_local" if policy in ("local", "data") else "k_loop"

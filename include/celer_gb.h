@@ -421,6 +421,18 @@ celer_status celer_debug_partition(celer_ctx* ctx, uint8_t* keys_out, uint32_t* 
  * charge partition of the fill (Sec. 3.2). */
 celer_status celer_debug_slots(celer_ctx* ctx, uint8_t* status_out, uint8_t* ptype_out, int* n_blocks);
 
+/* Check of the bounded waits of the persistent loops (no counterpart in the
+ * paper): a cooperative launch of `blocks` (2-8) blocks meets at the loops'
+ * grid barrier, which block `absent_block` never reaches (-1: every block
+ * arrives, and the barrier must pass). The others must give
+ * up after timeout_cycles SM cycles (at most 4e9), set the abort word and the
+ * barrier-timeout error bit, and end. Returns CELER_ERR_TIMEOUT when they did
+ * (error_bits and abort_word receive what the kernel left), CELER_OK if the
+ * barrier passed, CELER_ERR_INVALID for bad arguments. Uses its own device
+ * memory (allocated and freed here) and the legacy default stream. */
+celer_status celer_debug_barrier_timeout(int blocks, int absent_block, uint64_t timeout_cycles, uint32_t* error_bits,
+                                         uint32_t* abort_word);
+
 /* Device table of material mat, column col (0 Compton, 1 photoelectric,
  * 2 pair, 3 Moller, 4 brems, 5 range), 200 values into host memory. */
 celer_status celer_debug_table(celer_ctx* ctx, int mat, int col, double* host_out);

@@ -115,7 +115,7 @@ EXPORTS = [
     "celer_debug_philox", "celer_debug_curand_philox", "celer_partition_keys_noalloc", "celer_debug_math",
     "celer_run_iterations", "celer_read_event_live", "celer_serve", "celer_autotune", "celer_get_problem",
     "celer_debug_sample", "celer_debug_slots", "celer_set_hit_readout", "celer_set_grid_blocks",
-    "celer_set_parent_reuse",
+    "celer_set_parent_reuse", "celer_debug_barrier_timeout",
 ]
 
 _lib = None
@@ -161,6 +161,7 @@ def load(path: Optional[str] = None):
         "celer_set_hit_readout": ([vp, i32, vp, u64], i32),
         "celer_set_grid_blocks": ([vp, i32], i32),
         "celer_set_parent_reuse": ([vp, i32], i32),
+        "celer_debug_barrier_timeout": ([i32, i32, u64, C.POINTER(u32), C.POINTER(u32)], i32),
         "celer_partition_keys_noalloc": ([vp, u64, i32, i32, vp, vp, vp], i32),
         "celer_run_iterations": ([vp, i32, u64, C.POINTER(u64)], i32),
         "celer_read_event_live": ([vp, u32, u32, vp], i32),
@@ -529,3 +530,14 @@ def debug_sample(which: int, E: np.ndarray, tid: np.ndarray, ctr: np.ndarray, se
                                      t.ctypes.data, c.ctypes.data, C.c_uint64(n), eps.ctypes.data, cost.ctypes.data,
                                      ctr_out.ctypes.data, ok.ctypes.data))
     return eps, cost, ctr_out, ok
+
+
+def debug_barrier_timeout(blocks: int, absent_block: int, timeout_cycles: int):
+    """Bounded grid-barrier wait with one block that never arrives: returns
+    (status, error bits, abort word); status 4 (CELER_ERR_TIMEOUT) when the
+    waiting blocks gave up as they should."""
+    err = C.c_uint32()
+    ab = C.c_uint32()
+    st = load().celer_debug_barrier_timeout(int(blocks), int(absent_block), C.c_uint64(timeout_cycles), C.byref(err),
+                                            C.byref(ab))
+    return st, err.value, ab.value

@@ -992,6 +992,40 @@ celer_status celer_debug_slots(celer_ctx* ctx, uint8_t* status_out, uint8_t* pty
   return CELER_OK;
 }
 
+celer_status celer_debug_barrier_timeout(int blocks, int absent_block, uint64_t timeout_cycles, uint32_t* error_bits,
+                                         uint32_t* abort_word) {
+  if (blocks < 2 || blocks > 8 || absent_block < -1 || absent_block >= blocks || timeout_cycles == 0 ||
+      timeout_cycles > 4000000000ull || !error_bits || !abort_word)
+    return CELER_ERR_INVALID;
+  Ctl* d_ctl = nullptr;
+  unsigned* d_bar = nullptr;
+  if (cudaMalloc(&d_ctl, sizeof(Ctl)) != cudaSuccess) return CELER_ERR_CUDA;
+  if (cudaMalloc(&d_bar, 4 * sizeof(unsigned)) != cudaSuccess) {
+    cudaFree(d_ctl);
+    return CELER_ERR_CUDA;
+  }
+  celer_status st = CELER_OK;
+  if (cudaMemset(d_ctl, 0, sizeof(Ctl)) != cudaSuccess || cudaMemset(d_bar, 0, 4 * sizeof(unsigned)) != cudaSuccess)
+    st = CELER_ERR_CUDA;
+  Params p{};
+  p.ctl = d_ctl;
+  p.barrier = d_bar;
+  if (st == CELER_OK && (launch_barrier_probe(p, blocks, absent_block, (long long)timeout_cycles, 0) != cudaSuccess ||
+                         cudaDeviceSynchronize() != cudaSuccess))
+    st = CELER_ERR_CUDA;
+  Ctl h{};
+  unsigned bar[4] = {0, 0, 0, 0};
+  if (st == CELER_OK && (cudaMemcpy(&h, d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess ||
+                         cudaMemcpy(bar, d_bar, sizeof(bar), cudaMemcpyDeviceToHost) != cudaSuccess))
+    st = CELER_ERR_CUDA;
+  cudaFree(d_ctl);
+  cudaFree(d_bar);
+  if (st != CELER_OK) return st;
+  *error_bits = h.error;
+  *abort_word = bar[2];
+  return (h.error & ERR_BARRIER_TIMEOUT) ? CELER_ERR_TIMEOUT : CELER_OK;
+}
+
 celer_status celer_debug_table(celer_ctx* ctx, int mat, int col, double* out) {
   if (!ctx || !out || mat < 0 || mat >= ctx->p.n_materials || col < 0 || col >= kCols) return CELER_ERR_INVALID;
   std::vector<double2> v(kGrid);

@@ -35,6 +35,8 @@ void launch_local(const Params& p, const LaunchShape& sh, unsigned long long han
 void launch_local_prepare(const Params& p, const LaunchShape& sh, cudaStream_t s);
 // per-tile vacancy scan for a slot-order run after block-local iterations
 void launch_scan_tiles(const Params& p, cudaStream_t s);
+// check of the bounded grid-barrier wait (one block never arrives)
+cudaError_t launch_barrier_probe(const Params& p, int blocks, int absent, long long timeout, cudaStream_t s);
 // per-action launches
 void launch_fill(const Params& p, const LaunchShape& sh, cudaStream_t s);
 void launch_pre_step(const Params& p, const LaunchShape& sh, cudaStream_t s);

@@ -1329,6 +1329,30 @@ __device__ __forceinline__ void load_block_vacancies(const Params& p, uint32_t* 
 constexpr unsigned kDataMaxQuota = 8192;
 __device__ __forceinline__ unsigned block_quota_cap(int policy) { return policy == POLICY_DATA ? kDataMaxQuota : 0xFFFFFFFFu; }
 
+// Bounded wait of one thread for the generation word (barrier[1]) to move
+// past g: the persistent loops' grid barriers. After `timeout` cycles (about
+// 1 s by default) the thread sets the abort word (barrier[2]) and
+// ERR_BARRIER_TIMEOUT and gives up; a waiter that sees the abort word gives
+// up too, so every block leaves its loop at its next barrier and the kernel
+// ends with an error status the host reads. Returns true if the generation
+// moved and no abort was raised.
+__device__ __forceinline__ bool wait_generation(const Params& p, unsigned g, long long timeout) {
+  unsigned int* gen = p.barrier + 1;
+  unsigned int* abort_word = p.barrier + 2;
+  const long long t0 = clock64();
+  for (;;) {
+    if (*reinterpret_cast<volatile unsigned*>(gen) != g) break;
+    if (*reinterpret_cast<volatile unsigned*>(abort_word) != 0u) return false;
+    if (clock64() - t0 > timeout) {
+      atomicExch(abort_word, 1u);
+      atomicOr(&p.ctl->error, ERR_BARRIER_TIMEOUT);
+      return false;
+    }
+    __nanosleep(32);
+  }
+  return *reinterpret_cast<volatile unsigned*>(abort_word) == 0u;
+}
+
 // End of a block pass (LOCAL, DATA). The block's vacancy count is its count
 // at the start plus its releases minus its fills (only the block touches its
 // chunks). The last block to take a ticket commits the fill, takes the
@@ -1346,7 +1370,6 @@ __device__ bool end_block_pass(const Params& p, int bid, int nb, unsigned long l
   __shared__ int s_ok;
   Ctl* c = p.ctl;
   unsigned* gen = p.barrier + 1;
-  unsigned* abort_word = p.barrier + 2;
   if (threadIdx.x == 0) s_delta = 0;
   __syncthreads();
 #pragma unroll
@@ -1397,23 +1420,9 @@ __device__ bool end_block_pass(const Params& p, int bid, int nb, unsigned long l
   }
   if (!persistent) return true;
   if (threadIdx.x == 0) {
-    int ok = 1;
-    const long long t0 = clock64();
-    for (;;) {
-      if (*reinterpret_cast<volatile unsigned*>(gen) != s_gen) break;
-      if (*reinterpret_cast<volatile unsigned*>(abort_word) != 0u) {
-        ok = 0;
-        break;
-      }
-      if (clock64() - t0 > kBarrierTimeoutCycles) {
-        atomicExch(abort_word, 1u);
-        atomicOr(&c->error, ERR_BARRIER_TIMEOUT);
-        ok = 0;
-        break;
-      }
-    }
+    const bool ok = wait_generation(p, s_gen, kBarrierTimeoutCycles);
     __threadfence();
-    s_ok = ok;
+    s_ok = ok ? 1 : 0;
   }
   __syncthreads();
   return s_ok != 0;
@@ -1993,11 +2002,11 @@ __global__ void k_begin_run(Ctl* c, unsigned long long budget) {
 // Grid-wide barrier of the persistent loop (generation counter). Every wait
 // is bounded: after ~1 s a block gives up, sets the abort word and the error
 // bit, and every block then leaves the loop at its next barrier.
-__device__ __forceinline__ bool grid_barrier(const Params& p, unsigned nblocks) {
+__device__ __forceinline__ bool grid_barrier(const Params& p, unsigned nblocks,
+                                             long long timeout = kBarrierTimeoutCycles) {
   __shared__ int s_ok;
   unsigned int* count = p.barrier;
   unsigned int* gen = p.barrier + 1;
-  unsigned int* abort_word = p.barrier + 2;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -2007,24 +2016,10 @@ __device__ __forceinline__ bool grid_barrier(const Params& p, unsigned nblocks) 
       *reinterpret_cast<volatile unsigned*>(count) = 0u;
       __threadfence();
       atomicAdd(gen, 1u);
+      if (*reinterpret_cast<volatile unsigned*>(p.barrier + 2) != 0u) ok = 0;
     } else {
-      const long long t0 = clock64();
-      for (;;) {
-        if (*reinterpret_cast<volatile unsigned*>(gen) != g) break;
-        if (*reinterpret_cast<volatile unsigned*>(abort_word) != 0u) {
-          ok = 0;
-          break;
-        }
-        if (clock64() - t0 > kBarrierTimeoutCycles) {
-          atomicExch(abort_word, 1u);
-          atomicOr(&p.ctl->error, ERR_BARRIER_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
+      ok = wait_generation(p, g, timeout) ? 1 : 0;
     }
-    if (*reinterpret_cast<volatile unsigned*>(abort_word) != 0u) ok = 0;
     __threadfence();
     s_ok = ok;
   }
@@ -2132,6 +2127,14 @@ __global__ void __launch_bounds__(kTile, 1) k_loop_local(Params p) {
     c->max_total[2] += c->iter_max[0][2] + c->iter_max[1][2];
     c->iter_max[0][2] = c->iter_max[1][2] = 0;
   }
+}
+
+// Check of the bounded waits: every block but `absent` meets at a grid
+// barrier that `absent` never reaches, so the waiters must give up after
+// `timeout` cycles, set the abort word and the error bit, and return.
+__global__ void k_barrier_probe(Params p, int absent, long long timeout) {
+  if ((int)blockIdx.x == absent) return;
+  grid_barrier(p, gridDim.x, timeout);
 }
 
 // Queue staged primaries at the tail of the initializer buffer.
@@ -2277,6 +2280,10 @@ void launch_local_prepare(const Params& p, const LaunchShape& sh, cudaStream_t s
   k_local_prepare<<<sh.loop_grid, kTile, 0, s>>>(p);
 }
 void launch_scan_tiles(const Params& p, cudaStream_t s) { k_scan_tiles<<<1, kTile, 0, s>>>(p); }
+cudaError_t launch_barrier_probe(const Params& p, int blocks, int absent, long long timeout, cudaStream_t s) {
+  void* args[] = {const_cast<Params*>(&p), &absent, &timeout};
+  return cudaLaunchCooperativeKernel((const void*)k_barrier_probe, dim3(blocks), dim3(32), args, 0, s);
+}
 void launch_fill(const Params& p, const LaunchShape& sh, cudaStream_t s) {
   k_fill<<<sh.tile_grid, kTile, sh.static_smem, s>>>(p);
 }
