@@ -1353,6 +1353,33 @@ __device__ __forceinline__ bool wait_generation(const Params& p, unsigned g, lon
   return *reinterpret_cast<volatile unsigned*>(abort_word) == 0u;
 }
 
+// Per-iteration inputs of a block pass, read in one batch of loads (from
+// L2) right after the previous iteration's barrier: the loop condition, the
+// fill plan (buffer head, entries taken, whether secondaries may overflow),
+// this block's quota, first entry and vacancy count, and this thread's
+// chunk vacancy of the first batch (chunk bid + nb * threadIdx.x).
+struct BlockIter {
+  unsigned long long head, take, prefix, iteration;
+  unsigned quota, vtot, vac0;
+  bool cont, tight, blocks_ok;
+};
+__device__ __forceinline__ BlockIter load_block_iter(const Params& p, int bid, int nb) {
+  const Ctl* c = p.ctl;
+  BlockIter it;
+  it.cont = __ldcg(&c->cont) != 0u;
+  it.head = __ldcg(&c->head);
+  it.take = __ldcg(&c->fill_take);
+  it.iteration = __ldcg(&c->iteration);
+  it.tight = __ldcg(&c->defer_local) != 0u;
+  it.blocks_ok = __ldcg(&c->local_blocks) == (unsigned)nb;
+  it.quota = __ldcg(&p.block_quota[bid]);
+  it.prefix = __ldcg(&p.block_prefix[bid]);
+  it.vtot = __ldcg(&p.block_vacant[bid]);
+  const uint32_t n_own = (uint32_t)bid < p.n_chunks ? (p.n_chunks - (uint32_t)bid + nb - 1) / nb : 0u;
+  it.vac0 = threadIdx.x < n_own ? __ldcg(&p.vacant[(uint32_t)bid + (uint32_t)nb * threadIdx.x]) : 0u;
+  return it;
+}
+
 // End of a block pass (LOCAL, DATA). The block's vacancy count is its count
 // at the start plus its releases minus its fills (only the block touches its
 // chunks). The last block to take a ticket commits the fill, takes the
@@ -1362,9 +1389,9 @@ __device__ __forceinline__ bool wait_generation(const Params& p, unsigned g, lon
 // other blocks wait (bounded) for the last one to bump the generation word,
 // so an iteration costs one global atomic per block. Returns false if the
 // wait gave up (abort word set, ERR_BARRIER_TIMEOUT).
-__device__ bool end_block_pass(const Params& p, int bid, int nb, unsigned long long head, unsigned long long take,
-                               long long vdelta, bool persistent, cudaGraphConditionalHandle handle,
-                               int use_handle, long long t_work0) {
+__device__ bool end_block_pass(const Params& p, int bid, int nb, const BlockIter& it, long long vdelta, bool persistent,
+                               cudaGraphConditionalHandle handle, int use_handle, long long t_work0) {
+  const unsigned long long head = it.head, take = it.take;
   __shared__ long long s_delta;
   __shared__ unsigned s_last, s_gen;
   __shared__ int s_ok;
@@ -1377,9 +1404,9 @@ __device__ bool end_block_pass(const Params& p, int bid, int nb, unsigned long l
   if ((threadIdx.x & 31) == 0 && vdelta != 0) atomicAdd((unsigned long long*)&s_delta, (unsigned long long)vdelta);
   __syncthreads();
   if (threadIdx.x == 0) {
-    p.block_vacant[bid] = (uint32_t)((long long)p.block_vacant[bid] + s_delta);
+    p.block_vacant[bid] = (uint32_t)((long long)it.vtot + s_delta);
     if (persistent) {
-      atomicMax(&c->iter_max[c->iteration & 1][2], (unsigned long long)(clock64() - t_work0));
+      atomicMax(&c->iter_max[it.iteration & 1][2], (unsigned long long)(clock64() - t_work0));
       s_gen = *reinterpret_cast<volatile unsigned*>(gen);
     }
     __threadfence();
@@ -1439,7 +1466,7 @@ __device__ bool end_block_pass(const Params& p, int bid, int nb, unsigned long l
 // along-step and interaction of its live tracks in slot order, masking the
 // others (Sec. 2).
 __device__ bool phase_data(const Params& p, int bid, int nb, const SharedStatic& ss, cudaGraphConditionalHandle handle,
-                           int use_handle, bool persistent) {
+                           int use_handle, bool persistent, const BlockIter& it) {
   const long long t_work0 = clock64();
   __shared__ uint32_t s_chunks[kTile];
   __shared__ uint32_t s_cpre[kTile];
@@ -1448,16 +1475,16 @@ __device__ bool phase_data(const Params& p, int bid, int nb, const SharedStatic&
   __shared__ unsigned s_acts[A_COUNT];
   Ctl* c = p.ctl;
   const Tracks& t = p.trk;
-  const unsigned long long head = c->head, take = c->fill_take;
-  const bool tight = c->defer_local != 0u;
+  const unsigned long long head = it.head;
+  const bool tight = it.tight;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = (int)(blockDim.x >> 5);
   const unsigned lt = (1u << lane) - 1u;
-  if (bid == 0 && threadIdx.x == 0 && c->local_blocks != (unsigned)nb) atomicOr(&c->error, ERR_VACANCY);
+  if (bid == 0 && threadIdx.x == 0 && !it.blocks_ok) atomicOr(&c->error, ERR_VACANCY);
   if (threadIdx.x < A_COUNT) s_acts[threadIdx.x] = 0u;
-  const unsigned quota = min(p.block_quota[bid], kDataMaxQuota);
-  const unsigned long long first = head + p.block_prefix[bid];
-  const unsigned vtot = p.block_vacant[bid];  // the block's vacant slots at the start of the iteration
+  const unsigned quota = min(it.quota, kDataMaxQuota);
+  const unsigned long long first = head + it.prefix;
+  const unsigned vtot = it.vtot;  // the block's vacant slots at the start of the iteration
   // the block's initializers by kind: offsets of the neutral ones in order
   // from the front of s_list, of the charged ones from the back
   unsigned n_neutral = 0;
@@ -1485,7 +1512,7 @@ __device__ bool phase_data(const Params& p, int bid, int nb, const SharedStatic&
     unsigned vac = 0, csize = 0;
     if (m < n_own) {
       csize = (p.n_slots - g * 32u) < 32u ? (p.n_slots - g * 32u) : 32u;
-      vac = __ldcg(&p.vacant[g]);
+      vac = c0 == 0 ? it.vac0 : __ldcg(&p.vacant[g]);  // the first batch's came with the iteration's inputs
     }
     unsigned batch_vac = 0;
     const unsigned pre = block_exclusive_scan(vac, batch_vac);
@@ -1574,8 +1601,7 @@ __device__ bool phase_data(const Params& p, int bid, int nb, const SharedStatic&
   if (n_def) atomicAdd(&c->n_deferred, (unsigned)n_def);
   __syncthreads();
   if (threadIdx.x < A_COUNT && s_acts[threadIdx.x] != 0) atomicAdd(&c->action_count[threadIdx.x], s_acts[threadIdx.x]);
-  return end_block_pass(p, bid, nb, head, take, (long long)killed - (long long)my_fill, persistent, handle, use_handle,
-                        t_work0);
+  return end_block_pass(p, bid, nb, it, (long long)killed - (long long)my_fill, persistent, handle, use_handle, t_work0);
 }
 
 // One whole iteration of the block-local policy, in one pass per block with
@@ -1599,7 +1625,7 @@ __device__ bool phase_data(const Params& p, int bid, int nb, const SharedStatic&
 // Secondaries go to the buffer's tail while the taken entries are being read:
 // the capacity checks count from the uncommitted head.
 __device__ bool phase_local(const Params& p, int bid, int nb, const SharedStatic& ss, cudaGraphConditionalHandle handle,
-                            int use_handle, bool persistent) {
+                            int use_handle, bool persistent, const BlockIter& it) {
   const long long t_work0 = clock64();
   constexpr int kCap = 2 * kTile;
   constexpr int kMaxPieces = kCap / 8 + kMaxKeys;
@@ -1616,16 +1642,16 @@ __device__ bool phase_local(const Params& p, int bid, int nb, const SharedStatic
   __shared__ unsigned s_acts[A_COUNT];
   Ctl* c = p.ctl;
   const Tracks& t = p.trk;
-  const unsigned long long head = c->head, take = c->fill_take;
-  const bool tight = c->defer_local != 0u;
+  const unsigned long long head = it.head;
+  const bool tight = it.tight;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = (int)(blockDim.x >> 5);
   const unsigned lt = (1u << lane) - 1u;
-  if (bid == 0 && threadIdx.x == 0 && c->local_blocks != (unsigned)nb) atomicOr(&c->error, ERR_VACANCY);
+  if (bid == 0 && threadIdx.x == 0 && !it.blocks_ok) atomicOr(&c->error, ERR_VACANCY);
   if (threadIdx.x < A_COUNT) s_acts[threadIdx.x] = 0u;
   unsigned long long killed = 0, n_def = 0, my_steps = 0, my_fill = 0;
-  const unsigned quota = p.block_quota[bid];     // initializers this block takes
-  const unsigned long long first = head + p.block_prefix[bid];
+  const unsigned quota = it.quota;  // initializers this block takes
+  const unsigned long long first = head + it.prefix;
   unsigned run = 0;  // the block's vacancies before the next batch
   // group the n gathered slots by key and run them, one piece per warp
   auto flush = [&](unsigned n) {
@@ -1692,7 +1718,7 @@ __device__ bool phase_local(const Params& p, int bid, int nb, const SharedStatic
     unsigned vac = 0, csize = 0;
     if (m < n_own) {
       csize = (p.n_slots - g * 32u) < 32u ? (p.n_slots - g * 32u) : 32u;
-      vac = __ldcg(&p.vacant[g]);
+      vac = c0 == 0 ? it.vac0 : __ldcg(&p.vacant[g]);  // the first batch's came with the iteration's inputs
     }
     unsigned batch_vac = 0;
     const unsigned pre = block_exclusive_scan(vac, batch_vac);
@@ -1802,8 +1828,7 @@ __device__ bool phase_local(const Params& p, int bid, int nb, const SharedStatic
   if (n_def) atomicAdd(&c->n_deferred, (unsigned)n_def);
   __syncthreads();
   if (threadIdx.x < A_COUNT && s_acts[threadIdx.x] != 0) atomicAdd(&c->action_count[threadIdx.x], s_acts[threadIdx.x]);
-  return end_block_pass(p, bid, nb, head, take, (long long)killed - (long long)my_fill, persistent, handle, use_handle,
-                        t_work0);
+  return end_block_pass(p, bid, nb, it, (long long)killed - (long long)my_fill, persistent, handle, use_handle, t_work0);
 }
 
 // Per-block vacancy counts and the plan of the first fill (fill_take and the
@@ -1951,10 +1976,11 @@ __global__ void __launch_bounds__(kTile) k_local(Params p, cudaGraphConditionalH
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SharedStatic ss = carve_static(p, smem_raw);
   stage_static(p, ss);
+  const BlockIter it = load_block_iter(p, blockIdx.x, gridDim.x);
   if (p.policy == POLICY_DATA)
-    phase_data(p, blockIdx.x, gridDim.x, ss, handle, use_handle, false);
+    phase_data(p, blockIdx.x, gridDim.x, ss, handle, use_handle, false, it);
   else
-    phase_local(p, blockIdx.x, gridDim.x, ss, handle, use_handle, false);
+    phase_local(p, blockIdx.x, gridDim.x, ss, handle, use_handle, false, it);
 }
 
 // Per-action launches: fill, step limit (+ bookkeeping), scatter, one
@@ -2108,14 +2134,15 @@ __global__ void __launch_bounds__(kTile, 1) k_loop_local(Params p) {
   if (!grid_barrier(p, nb)) return;
   long long t_prev = clock64();
   for (;;) {
-    if (*reinterpret_cast<volatile unsigned*>(&c->cont) == 0u) break;
-    const unsigned parity = (unsigned)(c->iteration & 1);
+    const BlockIter it = load_block_iter(p, bid, (int)nb);  // one batch of loads per iteration
+    if (!it.cont) break;
+    const unsigned parity = (unsigned)(it.iteration & 1);
     if (bid == 0 && threadIdx.x == 0) {  // the slowest block's work of the previous iteration
       c->max_total[2] += c->iter_max[parity ^ 1u][2];
       c->iter_max[parity ^ 1u][2] = 0;
     }
-    const bool ok = p.policy == POLICY_DATA ? phase_data(p, bid, (int)nb, ss, 0, 0, true)
-                                            : phase_local(p, bid, (int)nb, ss, 0, 0, true);
+    const bool ok = p.policy == POLICY_DATA ? phase_data(p, bid, (int)nb, ss, 0, 0, true, it)
+                                            : phase_local(p, bid, (int)nb, ss, 0, 0, true, it);
     if (!ok) break;
     if (bid == 0 && threadIdx.x == 0) {
       const long long now = clock64();
