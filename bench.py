@@ -701,7 +701,7 @@ def load_peaks():
 # algorithmic state bytes (state read and written back once per step, without
 # secondaries or scratch) and thread-level FP64 operations
 # (2 x DFMA + DADD + DMUL) counted by ncu on the persistent loop kernel
-# (profiles/loop_local_calorimeter_1gev.md, profiles/loop_kernel_calorimeters.md);
+# (the ncu summaries committed beside this script, one per kernel and workload);
 # DRAM bytes per launch of that kernel from the same captures, for the
 # workloads that were captured whole. Keys: (workload, policy).
 BYTES_PER_STEP = 160.0
