@@ -448,11 +448,11 @@ celer_status celer_debug_curand_philox(uint64_t seed, uint64_t subsequence, uint
 
 /* Evaluate a binary64 function on n host arguments on the device: fn 0 the
  * table-driven logarithm of the step kernels, 1 their exponential, 4 and 5
- * their sin(2 pi x) and cos(2 pi x); 2, 3, 6, 7 CUDA's log, exp,
- * sin(2 pi x), cos(2 pi x) for comparison. No counterpart in the paper: it
- * checks the step kernels' elementary functions against the library's
- * (accuracy about 1 ulp). fn outside 0-7 or null pointers give
- * CELER_ERR_INVALID. */
+ * their sin(2 pi x) and cos(2 pi x), 8 and 9 their sin(x) and cos(x) (helix
+ * turns); 2, 3, 6, 7, 10, 11 CUDA's log, exp, sin(2 pi x), cos(2 pi x),
+ * sin(x), cos(x) for comparison. No counterpart in the paper: it checks the
+ * step kernels' elementary functions against the library's (accuracy about
+ * 1 ulp). fn outside 0-11 or null pointers give CELER_ERR_INVALID. */
 celer_status celer_debug_math(int fn, const double* host_x, uint64_t n, double* host_out);
 
 /* Draw one rejection sample per record on the device: which 0 the Compton

@@ -501,7 +501,8 @@ def debug_philox(ctr_key: np.ndarray) -> np.ndarray:
 
 def debug_math(fn: int, x: np.ndarray) -> np.ndarray:
     """Device elementary function fn on x: 0/1 table-driven log/exp, 2/3 CUDA
-    log/exp, 4/5 table-driven sin/cos of 2 pi x, 6/7 CUDA sin/cos of 2 pi x."""
+    log/exp, 4/5 table-driven sin/cos of 2 pi x, 6/7 CUDA sin/cos of 2 pi x,
+    8/9 table-driven sin/cos of x, 10/11 CUDA sin/cos of x."""
     a = np.ascontiguousarray(x, dtype=np.float64)
     out = np.zeros_like(a)
     _check(load().celer_debug_math(int(fn), a.ctypes.data, len(a), out.ctypes.data))

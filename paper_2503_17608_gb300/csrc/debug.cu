@@ -48,7 +48,11 @@ __global__ void k_math(int fn, const double* mt, const double* x, double* out, u
       case 4: { double sn, cs; celer::fast_sincos_2pi(v, mt, &sn, &cs); r = sn; break; }
       case 5: { double sn, cs; celer::fast_sincos_2pi(v, mt, &sn, &cs); r = cs; break; }
       case 6: r = sin(2.0 * celer::kPi * v); break;
-      default: r = cos(2.0 * celer::kPi * v); break;
+      case 7: r = cos(2.0 * celer::kPi * v); break;
+      case 8: { double sn, cs; celer::fast_sincos(v, mt, &sn, &cs); r = sn; break; }
+      case 9: { double sn, cs; celer::fast_sincos(v, mt, &sn, &cs); r = cs; break; }
+      case 10: r = sin(v); break;
+      default: r = cos(v); break;
     }
     out[i] = r;
   }
@@ -83,7 +87,7 @@ __global__ void k_sample(int which, uint32_t seed, uint32_t event, const double*
 extern "C" {
 
 celer_status celer_debug_math(int fn, const double* host_x, uint64_t n, double* host_out) {
-  if (!host_x || !host_out || fn < 0 || fn > 7) return CELER_ERR_INVALID;
+  if (!host_x || !host_out || fn < 0 || fn > 11) return CELER_ERR_INVALID;
   if (n == 0) return CELER_OK;
   std::vector<double> table(celer::kMathTableSize);
   celer::build_math_table(table.data());

@@ -39,7 +39,10 @@ constexpr int kMtCHi = kMtConst + 3;                   // ln 2 / 64 rounded to a
 constexpr int kMtCLo = kMtConst + 4;                   // ln 2 / 64 - kMtCHi
 constexpr int kMt2PiHi = kMtConst + 5;                 // 2 pi
 constexpr int kMt2PiLo = kMtConst + 6;                 // 2 pi - kMt2PiHi
-constexpr int kMathTableSize = kMtConst + 8;           // doubles
+constexpr int kMtStepInv = kMtConst + 7;               // 256 / (2 pi)
+constexpr int kMtStepHi = kMtConst + 8;                // 2 pi / 256 rounded to a multiple of 2^-35 (30 bits)
+constexpr int kMtStepLo = kMtConst + 9;                // 2 pi / 256 - kMtStepHi
+constexpr int kMathTableSize = kMtConst + 10;          // doubles
 
 // Fill the table (kMathTableSize doubles). Host code, extended precision.
 //  log: interval j of the reduced mantissa has centre c_j (c = 1 exactly for
@@ -91,7 +94,12 @@ inline void build_math_table(double* out) {
   const double tp = (double)twopi;
   out[kMt2PiHi] = tp;
   out[kMt2PiLo] = (double)(twopi - (ld)tp);
-  for (int i = kMt2PiLo + 1; i < kMathTableSize; ++i) out[i] = 0.0;
+  const ld step = twopi / (ld)kSinTable;
+  out[kMtStepInv] = (double)(1.0L / step);
+  const double shi = (double)(nearbyintl(step * 0x1p35L) / 0x1p35L);
+  out[kMtStepHi] = shi;
+  out[kMtStepLo] = (double)(step - (ld)shi);
+  for (int i = kMtStepLo + 1; i < kMathTableSize; ++i) out[i] = 0.0;
 }
 
 #ifdef __CUDACC__
@@ -163,6 +171,28 @@ __device__ __forceinline__ void fast_sincos_2pi(double u, const double* __restri
   const double sn = fma(th * t2, sp, th);
   const double cm1 = t2 * fma(t2, fma(t2, -1.0 / 720.0, 1.0 / 24.0), -0.5);
   const double2 sc = __ldg(reinterpret_cast<const double2*>(mt + kMtSin + 2 * j));
+  *s = sc.x + fma(sc.x, cm1, sc.y * sn);
+  *c = sc.y + fma(sc.y, cm1, -sc.x * sn);
+}
+
+// sin and cos of an angle x (|x| < 1e5; others go to sincos): j = nearest
+// multiple of 2 pi / 256, r = x - j 2pi/256 in two steps (Cody and Waite: the
+// head has 30 bits, so j head is exact for |j| < 2^22 and the first step is
+// exact), |r| <= pi/256, then the table and the series of fast_sincos_2pi
+// with theta = r.
+__device__ __forceinline__ void fast_sincos(double x, const double* __restrict__ mt, double* s, double* c) {
+  if (!(fabs(x) < 1e5)) {
+    sincos(x, s, c);
+    return;
+  }
+  const double jd = rint(x * __ldg(mt + kMtStepInv));
+  const int j = (int)jd;
+  const double th = fma(-jd, __ldg(mt + kMtStepLo), fma(-jd, __ldg(mt + kMtStepHi), x));
+  const double t2 = th * th;
+  const double sp = fma(t2, fma(t2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0);
+  const double sn = fma(th * t2, sp, th);
+  const double cm1 = t2 * fma(t2, fma(t2, -1.0 / 720.0, 1.0 / 24.0), -0.5);
+  const double2 sc = __ldg(reinterpret_cast<const double2*>(mt + kMtSin + 2 * (j & (kSinTable - 1))));
   *s = sc.x + fma(sc.x, cm1, sc.y * sn);
   *c = sc.y + fma(sc.y, cm1, -sc.x * sn);
 }

@@ -187,10 +187,10 @@ __device__ __forceinline__ Curvature curvature(uint8_t ptype, double E, double B
 
 // Exact helix for du/ds = kappa (u x z), with 1 - cos(phi) = 2 sin^2(phi/2).
 __device__ __forceinline__ void helix_move(Curvature c, double s, double& x, double& y, double& z, double& ux,
-                                           double& uy, double uz) {
+                                           double& uy, double uz, const double* mt) {
   const double phi = c.kappa * s;
   double hs, hc;
-  sincos(0.5 * phi, &hs, &hc);
+  fast_sincos(0.5 * phi, mt, &hs, &hc);
   const double sphi = 2.0 * hs * hc;
   const double omc = 2.0 * hs * hs;
   const double cphi = 1.0 - omc;

@@ -741,7 +741,7 @@ __device__ __forceinline__ bool along_one(const Params& p, uint32_t slot, uint8_
     if (p.field_cap > 0)
       rk_move(cv.kappa, s, act == A_FIELD ? p.field_cap : rk_substeps(cv.kappa, s), x, y, z, ux, uy, uz);
     else
-      helix_move(cv, s, x, y, z, ux, uy, uz);
+      helix_move(cv, s, x, y, z, ux, uy, uz, p.mtab);
   } else {
     x += s * ux;
     y += s * uy;

@@ -1,5 +1,5 @@
-"""Table-driven log/exp of the step kernels (Tang's method) against CUDA's
-own routines and numpy's, in units in the last place."""
+"""Table-driven log/exp and sin/cos of the step kernels (Tang's method)
+against CUDA's own routines and numpy's, in units in the last place."""
 import numpy as np
 import pytest
 
@@ -71,8 +71,9 @@ def test_fast_log_exp_round_trip():
 
 
 def test_invalid_function_code_is_rejected():
-    with pytest.raises(Exception):
-        binding.debug_math(8, np.ones(3))
+    for fn in (-1, 12):
+        with pytest.raises(Exception):
+            binding.debug_math(fn, np.ones(3))
 
 
 def test_fast_sincos_2pi_absolute_error():
@@ -99,3 +100,31 @@ def test_fast_sincos_outside_unit_interval_follows_library():
     u = np.array([-0.25, 1.25, 3.5, -2.0])
     np.testing.assert_allclose(binding.debug_math(4, u), np.sin(2 * np.pi * u), atol=1e-15)
     np.testing.assert_allclose(binding.debug_math(5, u), np.cos(2 * np.pi * u), atol=1e-15)
+
+
+def test_fast_sincos_of_turn_angles_within_two_ulp():
+    """sin and cos of a helix half-turn (any angle up to ~1e5 rad, Cody-Waite
+    reduction onto the 256-entry table) against CUDA's and numpy's."""
+    rng = np.random.default_rng(8)
+    x = np.concatenate([rng.uniform(-50, 50, 300000), rng.uniform(-1e4, 1e4, 100000),
+                        rng.uniform(-1e-3, 1e-3, 100000), np.exp(rng.uniform(-30, 11, 100000)),
+                        np.array([0.0, 1e-300, np.pi, -np.pi, np.pi / 2, 1e5 * 0.999])])
+    for fast_fn, cuda_fn, ref in ((8, 10, np.sin), (9, 11, np.cos)):
+        fast = binding.debug_math(fast_fn, x)
+        cuda = binding.debug_math(cuda_fn, x)
+        exact = ref(x)
+        # ulps of the result, or absolute 2.5e-16 near zeros of sin / cos
+        ok_c = (ulps(fast, cuda) <= 2.0) | (np.abs(fast - cuda) <= 2.5e-16)
+        ok_r = (ulps(fast, exact) <= 2.0) | (np.abs(fast - exact) <= 2.5e-16)
+        assert ok_c.all(), x[~ok_c][:5]
+        assert ok_r.all(), x[~ok_r][:5]
+
+
+def test_fast_sincos_outside_range_follows_cuda():
+    x = np.array([1e5, -2e5, 1e300, np.inf, np.nan])
+    for fast_fn, cuda_fn in ((8, 10), (9, 11)):
+        fast = binding.debug_math(fast_fn, x)
+        cuda = binding.debug_math(cuda_fn, x)
+        np.testing.assert_array_equal(np.isnan(fast), np.isnan(cuda))
+        ok = ~np.isnan(cuda)
+        np.testing.assert_array_equal(fast[ok], cuda[ok])
