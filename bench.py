@@ -189,6 +189,31 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- ranks
+# Replicas: each rank transports its own events (no data-path exchange, the
+# histories are independent and the random streams are keyed by event);
+# only the timing is combined over the ranks.
+EVENTS_PER_RANK = 1_000_000
+
+
+def replica_event_base(rank: int) -> int:
+    """First event id of a rank: the ranks' event ranges are disjoint."""
+    return rank * EVENTS_PER_RANK
+
+
+def reduce_over_ranks(value, op_name, dist=None, device="cpu"):
+    """The job-wide figure of a per-rank value: "max" (times: the job ends
+    with its slowest rank) or "sum" (track-steps: all ranks' work); the value
+    itself without a process group."""
+    if dist is None:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op_name == "max" else dist.ReduceOp.SUM)
+    return t.item()
+
+
 # ---------------------------------------------------------------- GPU
 def run_ours(args):
     import torch
@@ -211,13 +236,9 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     def reduce(v, op):
-        t = torch.tensor([float(v)], device="cuda")
-        if dist is not None:
-            dist.all_reduce(t, op=op)
-        return t.item()
+        return reduce_over_ranks(v, op, dist, device="cuda")
 
-    MAX = dist.ReduceOp.MAX if dist is not None else None
-    SUM = dist.ReduceOp.SUM if dist is not None else None
+    MAX, SUM = "max", "sum"
 
     prob, prim, desc = make_workload(args.workload, args.primaries, args.slots)
     n = len(prim)
@@ -234,7 +255,7 @@ def run_ours(args):
     if headline is not None and headline not in policies:
         policies.insert(0, headline)
     loop = binding.LOOP_NAMES[args.loop]
-    base_event = rank * 1_000_000
+    base_event = replica_event_base(rank)
 
     def timed_jobs(pol, mode, split, steps, warmup, sample_clocks=False):
         """K whole jobs, primaries resident on the device; returns ms, steps, per-job ms."""
