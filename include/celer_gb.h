@@ -212,9 +212,20 @@ enum {
   CELER_LOOP_HOST = 0,       /* host loop of per-iteration launches, polling the counters every few iterations */
   CELER_LOOP_GRAPH = 1,      /* the iteration captured once into a CUDA graph whose conditional while-node
                                 repeats it on the device with no host round trip */
-  CELER_LOOP_PERSISTENT = 2  /* one cooperative launch that runs every iteration: one block per SM slot,
+  CELER_LOOP_PERSISTENT = 2, /* one cooperative launch that runs every iteration: one block per SM slot,
                                 tables staged into shared memory once, phases separated by grid barriers
                                 whose waits are bounded (about 1 s, then CELER_ERR_TIMEOUT) */
+  CELER_LOOP_ASYNC = 3       /* block-pass policies (CELER_SORT_LOCAL, CELER_SORT_DATA) only: one cooperative
+                                launch in which every block runs its own step iterations ("passes") over its
+                                own slots with no grid barrier, sharing the initializer buffer as a
+                                concurrent queue (a block takes ceil(queued / blocks) entries per pass, at
+                                most its vacant slots; an entry's state word orders its writer and its
+                                reader). Histories are those of the synchronous modes (every track's random
+                                stream is keyed by its own id); tallies differ only in summation order.
+                                Runs to completion: celer_run_iterations rejects a budget, and no
+                                per-iteration trace or action count is recorded; the iteration count grows
+                                by the most passes any block ran. Waits are bounded: if no track steps for
+                                about 1 s the run ends with CELER_ERR_TIMEOUT or CELER_ERR_CAPACITY. */
 };
 
 /* Step until no track is alive or queued, in one of the CELER_LOOP_* modes.

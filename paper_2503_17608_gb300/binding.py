@@ -18,8 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libceler_gb.so")
 
 CELER_OK = 0
-LOOP_HOST, LOOP_GRAPH, LOOP_PERSISTENT = 0, 1, 2
-LOOP_NAMES = {"host": LOOP_HOST, "graph": LOOP_GRAPH, "persistent": LOOP_PERSISTENT}
+LOOP_HOST, LOOP_GRAPH, LOOP_PERSISTENT, LOOP_ASYNC = 0, 1, 2, 3
+LOOP_NAMES = {"host": LOOP_HOST, "graph": LOOP_GRAPH, "persistent": LOOP_PERSISTENT, "async": LOOP_ASYNC}
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "capacity exceeded", 3: "CUDA error",
                 4: "iteration limit reached", 5: "invalid state"}
 
@@ -292,8 +292,9 @@ class Context:
         _check(load().celer_step(self._h, None), self._h)
 
     def run_events(self, mode=LOOP_GRAPH, use_graph=None):
-        """Step until done. mode: LOOP_HOST, LOOP_GRAPH or LOOP_PERSISTENT
-        (use_graph=True/False is accepted as LOOP_GRAPH/LOOP_HOST)."""
+        """Step until done. mode: LOOP_HOST, LOOP_GRAPH, LOOP_PERSISTENT or
+        LOOP_ASYNC (block-pass policies only; use_graph=True/False is accepted
+        as LOOP_GRAPH/LOOP_HOST)."""
         if use_graph is not None:
             mode = LOOP_GRAPH if use_graph else LOOP_HOST
         _check(load().celer_run_events(self._h, int(mode)), self._h)

@@ -140,6 +140,13 @@ struct Ctl {
   unsigned int defer_local;
   unsigned int done_p;
   unsigned int local_blocks;
+  // asynchronous block loop: tracks ended since the buffer's first entry
+  // (head - alive at the start of the run; the run is over when it reaches
+  // tail), the most block passes any block ran, and the exit ticket
+  unsigned long long finished;
+  unsigned long long avail;          // written entries not yet claimed by a reader (may dip below 0 briefly)
+  unsigned long long async_passes;
+  unsigned int done_x;
 };
 
 struct TraceRow {
@@ -167,6 +174,8 @@ struct Params {
   uint32_t* block_vacant;  // block-local policy: vacant slots of each block's chunks (grid of the loop)
   uint32_t* block_quota;   // initializers each block takes in the next iteration (level filling)
   unsigned long long* block_prefix;  // exclusive scan of the quotas: each block's first initializer
+  uint32_t* ring_state;    // asynchronous block loop only (null otherwise): per buffer entry, 2 lap + 1
+                           // once written and 2 lap + 2 once read, lap = index / capacity
   // partition
   int policy;
   int n_keys;

@@ -65,6 +65,7 @@ struct celer_ctx {
   std::vector<cudaEvent_t> t_start, t_stop;
   std::vector<int> t_kid;
   int t_used = 0;
+  uint32_t* ring_state = nullptr;  // buffer entry states, set in the Params of asynchronous runs only
   bool tiles_stale = false;  // the per-tile vacancy prefix predates the last block-local iterations
   // per-iteration hit readout of the host loop: 0 off, 1 stream-ordered, 2 synchronous
   int hit_mode = 0;
@@ -298,7 +299,7 @@ celer_status status_from_error(celer_ctx* ctx, unsigned err) {
     return fail(ctx, CELER_ERR_CAPACITY, "initializer buffer full and no track can make progress");
   if (err & ERR_PRIMARIES_REJECTED)
     return fail(ctx, CELER_ERR_INVALID, "device primaries rejected (invalid record or buffer full)");
-  if (err & ERR_BARRIER_TIMEOUT) return fail(ctx, CELER_ERR_TIMEOUT, "persistent loop: grid barrier timed out");
+  if (err & ERR_BARRIER_TIMEOUT) return fail(ctx, CELER_ERR_TIMEOUT, "persistent loop: a bounded wait (grid barrier or buffer entry) timed out");
   if (err & ERR_VACANCY) return fail(ctx, CELER_ERR_STATE, "vacancy bookkeeping inconsistent");
   if (err & ERR_SAMPLING) return fail(ctx, CELER_ERR_STATE, "rejection sampling hit its attempt limit");
   if (err) return fail(ctx, CELER_ERR_STATE, "device error flag set");
@@ -529,6 +530,7 @@ celer_status celer_create(const celer_problem* pb, celer_ctx** out) {
   CREATE_CUDA(dalloc(ctx, &p.block_vacant, (size_t)kMaxLoopBlocks));
   CREATE_CUDA(dalloc(ctx, &p.block_quota, (size_t)kMaxLoopBlocks));
   CREATE_CUDA(dalloc(ctx, &p.block_prefix, (size_t)kMaxLoopBlocks));
+  CREATE_CUDA(dalloc(ctx, &ctx->ring_state, (size_t)p.ring_capacity));
   double* d_zb = nullptr;
   int32_t* d_lmat = nullptr;
   CREATE_CUDA(dalloc(ctx, &d_zb, L + 1));
@@ -693,7 +695,12 @@ celer_status celer_run_events(celer_ctx* ctx, int mode) { return celer_run_itera
 
 celer_status celer_run_iterations(celer_ctx* ctx, int mode, uint64_t budget, uint64_t* done) {
   if (!ctx) return CELER_ERR_INVALID;
-  if (mode < CELER_LOOP_HOST || mode > CELER_LOOP_PERSISTENT) return fail(ctx, CELER_ERR_INVALID, "unknown loop mode");
+  if (mode < CELER_LOOP_HOST || mode > CELER_LOOP_ASYNC) return fail(ctx, CELER_ERR_INVALID, "unknown loop mode");
+  if (mode == CELER_LOOP_ASYNC) {
+    if (!fused_local(ctx))
+      return fail(ctx, CELER_ERR_INVALID, "the asynchronous loop needs a block-pass policy (local, data) without split actions");
+    if (budget != 0) return fail(ctx, CELER_ERR_INVALID, "the asynchronous loop runs to completion: budget must be 0");
+  }
   // iteration budget of this run; last-block tickets start from zero (an
   // aborted run could leave them set)
   launch_begin_run(ctx->p, budget, ctx->stream);
@@ -708,9 +715,13 @@ celer_status celer_run_iterations(celer_ctx* ctx, int mode, uint64_t budget, uin
   } else if (mode == CELER_LOOP_PERSISTENT) {
     CELER_CUDA(ctx, cudaMemsetAsync(ctx->p.barrier, 0, 4 * sizeof(unsigned int), ctx->stream));
     CELER_CUDA(ctx, launch_loop(ctx->p, ctx->shape, ctx->stream));
-    if (ctx->timing) {
-      // the persistent loop is one launch: time it as such
-    }
+  } else if (mode == CELER_LOOP_ASYNC) {
+    Params pa = ctx->p;
+    pa.ring_state = ctx->ring_state;
+    CELER_CUDA(ctx, cudaMemsetAsync(ctx->p.barrier, 0, 4 * sizeof(unsigned int), ctx->stream));
+    launch_async_prepare(pa, ctx->stream);
+    CELER_CUDA(ctx, cudaGetLastError());
+    CELER_CUDA(ctx, launch_loop_async(pa, ctx->shape, ctx->stream));
   } else {
     // Host loop: launch batches of iterations; before each new batch, look at
     // the loop condition copied back after the batch before the previous one,

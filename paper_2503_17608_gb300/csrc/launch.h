@@ -47,6 +47,10 @@ void launch_loop_ctl(const Params& p, unsigned long long handle, int use_handle,
 void launch_begin_run(const Params& p, unsigned long long budget, cudaStream_t s);
 // persistent loop
 cudaError_t launch_loop(const Params& p, const LaunchShape& sh, cudaStream_t s);
+// Asynchronous block loop (block-pass policies): the buffer entries' states,
+// then one cooperative launch; p.ring_state must be set.
+void launch_async_prepare(const Params& p, cudaStream_t s);
+cudaError_t launch_loop_async(const Params& p, const LaunchShape& sh, cudaStream_t s);
 void launch_push_primaries(const Params& p, const StagedPrimary* d_prim, uint32_t n, cudaStream_t s);
 
 // Primary record as laid out by the C ABI (celer_primary).

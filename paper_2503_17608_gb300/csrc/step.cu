@@ -57,11 +57,61 @@ __device__ __forceinline__ void flush_counter(unsigned long long* dst, unsigned 
   if ((threadIdx.x & 31) == 0 && v != 0) atomicAdd(dst, negate ? (0ull - v) : v);
 }
 
+// ---- the initializer buffer as a concurrent queue (asynchronous block loop)
+//
+// Entry i of the buffer (stored at i & ring_mask) carries a state word: with
+// lap = i / capacity, 2 lap means free for the writer of i, 2 lap + 1 written
+// and not yet read, 2 lap + 2 read (free for the writer of i + capacity).
+// A writer reserves i on the tail only while i < head + capacity, so the
+// reader of i - capacity has reserved its entry already and every wait below
+// is for a reservation that the other side completes without waiting on the
+// waiter: reads and writes follow their reservations directly.
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* a) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* a) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* a, unsigned v) {
+  asm volatile("st.release.gpu.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ring_lap_code(const Params& p, unsigned long long index) {
+  return (unsigned)(index >> __popcll(p.ring_mask)) * 2u;
+}
+// Bounded wait of one thread for entry `index` to reach state `code`. After
+// ~1 s, or if another wait gave up first (abort word), it sets the abort word
+// and ERR_BARRIER_TIMEOUT and returns false.
+__device__ __noinline__ bool ring_wait(const Params& p, unsigned long long index, unsigned code) {
+  const unsigned* st = p.ring_state + (index & p.ring_mask);
+  if (ld_acquire_u32(st) == code) return true;
+  unsigned* abort_word = p.barrier + 2;
+  const long long t0 = clock64();
+  for (;;) {
+    __nanosleep(32);
+    if (ld_acquire_u32(st) == code) return true;
+    if (*reinterpret_cast<volatile unsigned*>(abort_word) != 0u) return false;
+    if (clock64() - t0 > kBarrierTimeoutCycles) {
+      atomicExch(abort_word, 1u);
+      atomicOr(&p.ctl->error, ERR_BARRIER_TIMEOUT);
+      return false;
+    }
+  }
+}
+
 __device__ __forceinline__ void write_initializer(const Params& p, unsigned long long index, double x, double y,
                                                   double z, double ux, double uy, double uz, double E,
                                                   unsigned long long tid, uint32_t ev, uint32_t prim, int32_t layer,
                                                   uint8_t ptype) {
   const unsigned long long i = index & p.ring_mask;
+  unsigned code = 0;
+  if (p.ring_state) {  // asynchronous loop: wait until the entry's last reader is done
+    code = ring_lap_code(p, index);
+    if (!ring_wait(p, index, code)) return;
+  }
   p.ring.x[i] = x;
   p.ring.y[i] = y;
   p.ring.z[i] = z;
@@ -74,6 +124,10 @@ __device__ __forceinline__ void write_initializer(const Params& p, unsigned long
   p.ring.primary[i] = prim;
   p.ring.layer[i] = layer;
   p.ring.ptype[i] = ptype;
+  if (p.ring_state) {
+    st_release_u32(p.ring_state + i, code + 1u);
+    atomicAdd(&p.ctl->avail, 1ull);  // one more entry readers may claim
+  }
 }
 
 struct Span {
@@ -855,17 +909,38 @@ __device__ __forceinline__ bool reserve_entries(const Params& p, unsigned n, boo
     base = 0;
     return true;
   }
+  // The asynchronous loop checks the room against the current head. With
+  // room for the largest reservation every thread of the grid could make
+  // (two entries each), one atomic add; otherwise compare-and-swap. (A
+  // reservation past the room would only make its writer wait, bounded, for
+  // the entry's previous reader.)
+  const bool async = p.ring_state != nullptr;
+  if (async) {
+    unsigned long long h = 0, cur = 0;
+    if (g.thread_rank() == 0) {
+      h = ld_acquire_u64(&c->head);  // before the tail: h <= tail
+      cur = *reinterpret_cast<volatile unsigned long long*>(&c->tail);
+    }
+    h = g.shfl(h, 0);
+    cur = g.shfl(cur, 0);
+    const unsigned long long in_flight = 2ull * blockDim.x * gridDim.x;
+    tight = cur - h + in_flight > p.ring_capacity;
+  }
   if (!tight) {
     unsigned long long old = 0;
     if (g.thread_rank() == 0) old = atomicAdd(&c->tail, (unsigned long long)total);
     base = g.shfl(old, 0) + prefix;
     return true;
   }
-  const unsigned long long head = c->head;
+  unsigned long long head = c->head;
   for (int attempt = 0; attempt < kMaxCasAttempts; ++attempt) {
     unsigned long long cur = 0;
-    if (g.thread_rank() == 0) cur = *reinterpret_cast<volatile unsigned long long*>(&c->tail);
+    if (g.thread_rank() == 0) {
+      if (async) head = ld_acquire_u64(&c->head);  // read before the tail: head <= tail
+      cur = *reinterpret_cast<volatile unsigned long long*>(&c->tail);
+    }
     cur = g.shfl(cur, 0);
+    if (async) head = g.shfl(head, 0);
     const unsigned long long used = cur - head;
     const unsigned long long room = used < p.ring_capacity ? p.ring_capacity - used : 0ull;
     const unsigned fits_mask = g.ballot((unsigned long long)end <= room);
@@ -1455,19 +1530,65 @@ __device__ bool end_block_pass(const Params& p, int bid, int nb, const BlockIter
   return s_ok != 0;
 }
 
-// One whole iteration of the DATA policy (Sec. 3.2, "partitioning track
-// data"), in one pass per block: block b owns the chunks b, b + nb, ... and
-// takes its quota of initializers (level filling, as for LOCAL); among them
-// the neutral ones fill its lowest vacant slots (its chunk order, then slot
-// order) and the charged ones its highest, so that neutral and charged
-// tracks gather at opposite ends of the block's slots and most warps hold
-// one kind. There is no reindexing: each warp takes one of the block's
+// Plan of one block pass: the first initializer the block takes and how many,
+// its vacant slots at the start of the pass, whether secondaries reserve
+// their entries by compare-and-swap, and (synchronous loops) this thread's
+// chunk vacancy of the first batch, read with the iteration's other inputs.
+struct PassPlan {
+  unsigned long long first;
+  unsigned quota, vtot;
+  bool tight, have_vac0;
+  unsigned vac0;
+};
+// Per-thread counts of a pass: tracks ended, deferred, stepped; slots filled.
+struct PassCounts {
+  unsigned long long killed, n_def, steps, fill;
+};
+
+// Copy buffer entry `index` into `slot` as a fresh track. In the asynchronous
+// loop the entry may still be in its writer's hands: wait (bounded) until it
+// is written, read it from L2, and mark it read. A wait that gives up leaves
+// the slot vacant; the run then ends with ERR_BARRIER_TIMEOUT.
+template <bool kAsync>
+__device__ __forceinline__ void take_initializer(const Params& p, unsigned long long index, uint32_t slot) {
+  const Tracks& t = p.trk;
+  const unsigned long long i = index & p.ring_mask;
+  unsigned code = 0;
+  if (kAsync) {
+    code = ring_lap_code(p, index) + 1u;
+    if (!ring_wait(p, index, code)) return;
+  }
+  t.x[slot] = __ldcg(&p.ring.x[i]);
+  t.y[slot] = __ldcg(&p.ring.y[i]);
+  t.z[slot] = __ldcg(&p.ring.z[i]);
+  t.ux[slot] = __ldcg(&p.ring.ux[i]);
+  t.uy[slot] = __ldcg(&p.ring.uy[i]);
+  t.uz[slot] = __ldcg(&p.ring.uz[i]);
+  t.E[slot] = __ldcg(&p.ring.E[i]);
+  t.tid[slot] = __ldcg(&p.ring.tid[i]);
+  t.event[slot] = __ldcg(&p.ring.event[i]);
+  t.primary[slot] = __ldcg(&p.ring.primary[i]);
+  t.layer[slot] = __ldcg(&p.ring.layer[i]);
+  t.ptype[slot] = __ldcg(&p.ring.ptype[i]);
+  t.ctr[slot] = 0u;
+  t.nmfp[slot] = -1.0;
+  t.action[slot] = A_NONE;
+  t.status[slot] = ALIVE;
+  if (kAsync) st_release_u32(p.ring_state + i, code + 1u);
+}
+
+// One pass of the DATA policy (Sec. 3.2, "partitioning track data") over
+// block b's chunks b, b + nb, ...: the block takes its initializers (pl);
+// among them the neutral ones fill its lowest vacant slots (its chunk order,
+// then slot order) and the charged ones its highest, so that neutral and
+// charged tracks gather at opposite ends of the block's slots and most warps
+// hold one kind. There is no reindexing: each warp takes one of the block's
 // chunks that hold or receive tracks, fills it, and runs the step limit,
 // along-step and interaction of its live tracks in slot order, masking the
 // others (Sec. 2).
-__device__ bool phase_data(const Params& p, int bid, int nb, const SharedStatic& ss, cudaGraphConditionalHandle handle,
-                           int use_handle, bool persistent, const BlockIter& it) {
-  const long long t_work0 = clock64();
+template <bool kAsync>
+__device__ void data_pass(const Params& p, int bid, int nb, const SharedStatic& ss, const PassPlan& pl,
+                          PassCounts& n) {
   __shared__ uint32_t s_chunks[kTile];
   __shared__ uint32_t s_cpre[kTile];
   __shared__ unsigned s_wn[kTile / 32];
@@ -1475,23 +1596,24 @@ __device__ bool phase_data(const Params& p, int bid, int nb, const SharedStatic&
   __shared__ unsigned s_acts[A_COUNT];
   Ctl* c = p.ctl;
   const Tracks& t = p.trk;
-  const unsigned long long head = it.head;
-  const bool tight = it.tight;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = (int)(blockDim.x >> 5);
   const unsigned lt = (1u << lane) - 1u;
-  if (bid == 0 && threadIdx.x == 0 && !it.blocks_ok) atomicOr(&c->error, ERR_VACANCY);
-  if (threadIdx.x < A_COUNT) s_acts[threadIdx.x] = 0u;
-  const unsigned quota = min(it.quota, kDataMaxQuota);
-  const unsigned long long first = head + it.prefix;
-  const unsigned vtot = it.vtot;  // the block's vacant slots at the start of the iteration
+  if (!kAsync && threadIdx.x < A_COUNT) s_acts[threadIdx.x] = 0u;
+  const unsigned quota = min(pl.quota, kDataMaxQuota);
+  const unsigned long long first = pl.first;
+  const unsigned vtot = pl.vtot;  // the block's vacant slots at the start of the pass
   // the block's initializers by kind: offsets of the neutral ones in order
   // from the front of s_list, of the charged ones from the back
   unsigned n_neutral = 0;
   for (unsigned e0 = 0; e0 < quota; e0 += blockDim.x) {
     const unsigned e = e0 + threadIdx.x;
     const bool in = e < quota;
-    const bool neutral = in && p.ring.ptype[(first + e) & p.ring_mask] == GAMMA;
+    bool neutral = false;
+    if (in) {
+      if (!kAsync || ring_wait(p, first + e, ring_lap_code(p, first + e) + 1u))
+        neutral = __ldcg(&p.ring.ptype[(first + e) & p.ring_mask]) == GAMMA;
+    }
     unsigned round_n = 0;
     const unsigned rn = n_neutral + block_exclusive_scan(neutral ? 1u : 0u, round_n);
     if (neutral) {
@@ -1503,7 +1625,6 @@ __device__ bool phase_data(const Params& p, int bid, int nb, const SharedStatic&
   }
   const unsigned n_charged = quota - n_neutral;
   __syncthreads();
-  unsigned long long killed = 0, n_def = 0, my_steps = 0, my_fill = 0;
   const uint32_t n_own = (uint32_t)bid < p.n_chunks ? (p.n_chunks - (uint32_t)bid + nb - 1) / nb : 0u;
   unsigned run = 0;  // the block's vacancies before the next batch (ascending rank)
   for (uint32_t c0 = 0; c0 < n_own; c0 += blockDim.x) {
@@ -1512,7 +1633,7 @@ __device__ bool phase_data(const Params& p, int bid, int nb, const SharedStatic&
     unsigned vac = 0, csize = 0;
     if (m < n_own) {
       csize = (p.n_slots - g * 32u) < 32u ? (p.n_slots - g * 32u) : 32u;
-      vac = c0 == 0 ? it.vac0 : __ldcg(&p.vacant[g]);  // the first batch's came with the iteration's inputs
+      vac = (c0 == 0 && pl.have_vac0) ? pl.vac0 : __ldcg(&p.vacant[g]);
     }
     unsigned batch_vac = 0;
     const unsigned pre = block_exclusive_scan(vac, batch_vac);
@@ -1553,30 +1674,12 @@ __device__ bool phase_data(const Params& p, int bid, int nb, const SharedStatic&
           off = s_list[quota - 1u - (vtot - 1u - r)];
         }
       }
-      if (off >= 0) {
-        const unsigned long long i = (first + (unsigned)off) & p.ring_mask;
-        t.x[slot] = p.ring.x[i];
-        t.y[slot] = p.ring.y[i];
-        t.z[slot] = p.ring.z[i];
-        t.ux[slot] = p.ring.ux[i];
-        t.uy[slot] = p.ring.uy[i];
-        t.uz[slot] = p.ring.uz[i];
-        t.E[slot] = p.ring.E[i];
-        t.tid[slot] = p.ring.tid[i];
-        t.event[slot] = p.ring.event[i];
-        t.primary[slot] = p.ring.primary[i];
-        t.layer[slot] = p.ring.layer[i];
-        t.ptype[slot] = p.ring.ptype[i];
-        t.ctr[slot] = 0u;
-        t.nmfp[slot] = -1.0;
-        t.action[slot] = A_NONE;
-        t.status[slot] = ALIVE;
-      }
+      if (off >= 0) take_initializer<kAsync>(p, first + (unsigned)off, slot);
       const unsigned nfill = __popc(__ballot_sync(0xffffffffu, off >= 0));
       if (lane == 0 && nfill) {
         atomicSub(&p.vacant[gc], nfill);
         atomicSub(&p.tile_vacant[gc >> 3], nfill);
-        my_fill += nfill;
+        n.fill += nfill;
       }
       // the chunk's live tracks: step limit, along-step, interaction
       if (real) {
@@ -1585,48 +1688,39 @@ __device__ bool phase_data(const Params& p, int bid, int nb, const SharedStatic&
           uint8_t act;
           if (st == ALIVE) {
             act = step_limit(p, slot, ss.tab, ss.zb, ss.lmat);
-            ++my_steps;
+            ++n.steps;
           } else {
             act = t.action[slot];
           }
-          atomicAdd(&s_acts[act], 1u);
-          if (step_one(p, slot, st, ss, tight, n_def)) ++killed;
+          if (!kAsync) atomicAdd(&s_acts[act], 1u);
+          if (step_one(p, slot, st, ss, pl.tight, n.n_def)) ++n.killed;
         }
       }
     }
   }
-  flush_counter(&c->alive, killed, true);
-  flush_counter(&c->steps_iter, my_steps, false);
-  flush_counter(&c->filled_total, my_fill, false);
-  if (n_def) atomicAdd(&c->n_deferred, (unsigned)n_def);
-  __syncthreads();
-  if (threadIdx.x < A_COUNT && s_acts[threadIdx.x] != 0) atomicAdd(&c->action_count[threadIdx.x], s_acts[threadIdx.x]);
-  return end_block_pass(p, bid, nb, it, (long long)killed - (long long)my_fill, persistent, handle, use_handle, t_work0);
+  if (!kAsync) {
+    __syncthreads();
+    if (threadIdx.x < A_COUNT && s_acts[threadIdx.x] != 0) atomicAdd(&c->action_count[threadIdx.x], s_acts[threadIdx.x]);
+  }
 }
 
-// One whole iteration of the block-local policy, in one pass per block with
-// no grid barrier between the fill and the step. Block b owns the 32-slot
-// chunks b, b + nb, b + 2 nb, ...:
+// One pass of the block-local policy over block b's chunks b, b + nb, ...,
+// with no grid barrier between the fill and the step:
 //  * fill: the block's lowest vacant slots (its chunk order, then slot order
-//    within a chunk) take its quota of initializers, planned at the end of
-//    the previous iteration by level filling (plan_block_quotas): a
-//    deterministic fill that needs no other block's counts during the
-//    iteration and spreads fresh tracks over all SMs;
+//    within a chunk) take its initializers (pl);
 //  * step limit of each live track of the chunk, by the warp that filled it;
 //  * the live tracks gathered into shared memory a few hundred at a time and
 //    grouped by key (action and particle type) with a counting sort; each
 //    group is cut into pieces of 8, 16 or 32 (the smallest size whose piece
 //    count fits the warps) and the pieces are dealt to the warps: every warp
 //    runs one kind of along-step and interaction, and few tracks spread over
-//    all warps;
-//  * the last block to finish commits the fill, scans the per-block and
-//    per-tile vacancy counts and ends the iteration (which plans the next
-//    fill).
+//    all warps.
 // Secondaries go to the buffer's tail while the taken entries are being read:
-// the capacity checks count from the uncommitted head.
-__device__ bool phase_local(const Params& p, int bid, int nb, const SharedStatic& ss, cudaGraphConditionalHandle handle,
-                            int use_handle, bool persistent, const BlockIter& it) {
-  const long long t_work0 = clock64();
+// the capacity checks count from the uncommitted head (synchronous loops) or
+// wait for the entries' readers (asynchronous loop).
+template <bool kAsync>
+__device__ void local_pass(const Params& p, int bid, int nb, const SharedStatic& ss, const PassPlan& pl,
+                           PassCounts& n) {
   constexpr int kCap = 2 * kTile;
   constexpr int kMaxPieces = kCap / 8 + kMaxKeys;
   __shared__ uint32_t s_slot[kCap];
@@ -1642,22 +1736,19 @@ __device__ bool phase_local(const Params& p, int bid, int nb, const SharedStatic
   __shared__ unsigned s_acts[A_COUNT];
   Ctl* c = p.ctl;
   const Tracks& t = p.trk;
-  const unsigned long long head = it.head;
-  const bool tight = it.tight;
+  const bool tight = pl.tight;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = (int)(blockDim.x >> 5);
   const unsigned lt = (1u << lane) - 1u;
-  if (bid == 0 && threadIdx.x == 0 && !it.blocks_ok) atomicOr(&c->error, ERR_VACANCY);
-  if (threadIdx.x < A_COUNT) s_acts[threadIdx.x] = 0u;
-  unsigned long long killed = 0, n_def = 0, my_steps = 0, my_fill = 0;
-  const unsigned quota = it.quota;  // initializers this block takes
-  const unsigned long long first = head + it.prefix;
+  if (!kAsync && threadIdx.x < A_COUNT) s_acts[threadIdx.x] = 0u;
+  const unsigned quota = pl.quota;  // initializers this block takes
+  const unsigned long long first = pl.first;
   unsigned run = 0;  // the block's vacancies before the next batch
   // group the n gathered slots by key and run them, one piece per warp
-  auto flush = [&](unsigned n) {
+  auto flush = [&](unsigned ng) {
     if (threadIdx.x < kMaxKeys) s_cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_cnt[s_key[i]], 1u);
+    for (unsigned i = threadIdx.x; i < ng; i += blockDim.x) atomicAdd(&s_cnt[s_key[i]], 1u);
     __syncthreads();
     if (threadIdx.x < 32) {
       // one lane per key, keys taken in the order of kPieceOrder (the
@@ -1697,28 +1788,28 @@ __device__ bool phase_local(const Params& p, int bid, int nb, const SharedStatic
       if (lane == 31) s_npieces = pstart + mine;
     }
     __syncthreads();
-    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) s_sorted[atomicAdd(&s_cur[s_key[i]], 1u)] = s_slot[i];
+    for (unsigned i = threadIdx.x; i < ng; i += blockDim.x) s_sorted[atomicAdd(&s_cur[s_key[i]], 1u)] = s_slot[i];
     __syncthreads();
     const unsigned npieces = s_npieces;
     for (unsigned q = (unsigned)warp; q < npieces; q += (unsigned)nwarps) {
       if ((unsigned)lane >= s_plen[q]) continue;
       const uint32_t sl = s_sorted[s_pstart[q] + lane];
-      if (step_one(p, sl, t.status[sl], ss, tight, n_def)) ++killed;
+      if (step_one(p, sl, t.status[sl], ss, tight, n.n_def)) ++n.killed;
     }
     __syncthreads();  // the lists are reused by the next gather
   };
   const uint32_t n_own = (uint32_t)bid < p.n_chunks ? (p.n_chunks - (uint32_t)bid + nb - 1) / nb : 0u;
   unsigned pending = 0;  // gathered and not yet run (block-uniform)
   for (uint32_t c0 = 0; c0 < n_own; c0 += blockDim.x) {
-    // this batch's chunks: start-of-iteration vacancies and their exclusive
-    // scan (fill ranks); a chunk is visited if it holds live tracks or
-    // receives initializers
+    // this batch's chunks: start-of-pass vacancies and their exclusive scan
+    // (fill ranks); a chunk is visited if it holds live tracks or receives
+    // initializers
     const uint32_t m = c0 + threadIdx.x;
     const uint32_t g = (uint32_t)bid + (uint32_t)nb * m;
     unsigned vac = 0, csize = 0;
     if (m < n_own) {
       csize = (p.n_slots - g * 32u) < 32u ? (p.n_slots - g * 32u) : 32u;
-      vac = c0 == 0 ? it.vac0 : __ldcg(&p.vacant[g]);  // the first batch's came with the iteration's inputs
+      vac = (c0 == 0 && pl.have_vac0) ? pl.vac0 : __ldcg(&p.vacant[g]);
     }
     unsigned batch_vac = 0;
     const unsigned pre = block_exclusive_scan(vac, batch_vac);
@@ -1756,31 +1847,13 @@ __device__ bool phase_local(const Params& p, int bid, int nb, const SharedStatic
           const bool vac_l = real && t.status[slot] == VACANT;
           const unsigned vb = __ballot_sync(0xffffffffu, vac_l);
           const unsigned r = q + __popc(vb & lt);
-          if (vac_l && r < quota) {
-            const unsigned long long i = (first + r) & p.ring_mask;
-            t.x[slot] = p.ring.x[i];
-            t.y[slot] = p.ring.y[i];
-            t.z[slot] = p.ring.z[i];
-            t.ux[slot] = p.ring.ux[i];
-            t.uy[slot] = p.ring.uy[i];
-            t.uz[slot] = p.ring.uz[i];
-            t.E[slot] = p.ring.E[i];
-            t.tid[slot] = p.ring.tid[i];
-            t.event[slot] = p.ring.event[i];
-            t.primary[slot] = p.ring.primary[i];
-            t.layer[slot] = p.ring.layer[i];
-            t.ptype[slot] = p.ring.ptype[i];
-            t.ctr[slot] = 0u;
-            t.nmfp[slot] = -1.0;
-            t.action[slot] = A_NONE;
-            t.status[slot] = ALIVE;
-          }
+          if (vac_l && r < quota) take_initializer<kAsync>(p, first + r, slot);
           const unsigned left = quota - q;
           const unsigned nfill = (unsigned)__popc(vb) < left ? (unsigned)__popc(vb) : left;
           if (lane == 0 && nfill) {
             atomicSub(&p.vacant[gc], nfill);
             atomicSub(&p.tile_vacant[gc >> 3], nfill);
-            my_fill += nfill;
+            n.fill += nfill;
           }
         }
         if (real) {
@@ -1788,12 +1861,12 @@ __device__ bool phase_local(const Params& p, int bid, int nb, const SharedStatic
           uint8_t act = A_NONE;
           if (st == ALIVE) {
             act = step_limit(p, slot, ss.tab, ss.zb, ss.lmat);
-            ++my_steps;
+            ++n.steps;
           } else if (st == DEFERRED) {
             act = t.action[slot];
           }
           if (st != VACANT) {
-            atomicAdd(&s_acts[act], 1u);
+            if (!kAsync) atomicAdd(&s_acts[act], 1u);
             live = true;
             key = key_of(POLICY_ACTION_TYPE, t.ptype[slot], act);
           }
@@ -1822,13 +1895,37 @@ __device__ bool phase_local(const Params& p, int bid, int nb, const SharedStatic
     }
   }
   if (pending > 0) flush(pending);
-  flush_counter(&c->alive, killed, true);
-  flush_counter(&c->steps_iter, my_steps, false);
-  flush_counter(&c->filled_total, my_fill, false);
-  if (n_def) atomicAdd(&c->n_deferred, (unsigned)n_def);
-  __syncthreads();
-  if (threadIdx.x < A_COUNT && s_acts[threadIdx.x] != 0) atomicAdd(&c->action_count[threadIdx.x], s_acts[threadIdx.x]);
-  return end_block_pass(p, bid, nb, it, (long long)killed - (long long)my_fill, persistent, handle, use_handle, t_work0);
+  if (!kAsync) {
+    __syncthreads();
+    if (threadIdx.x < A_COUNT && s_acts[threadIdx.x] != 0) atomicAdd(&c->action_count[threadIdx.x], s_acts[threadIdx.x]);
+  }
+}
+
+// One whole iteration of a block-pass policy in the synchronous loops: the
+// pass over the block's chunks with the fill planned at the end of the
+// previous iteration by level filling (plan_block_quotas: a deterministic
+// fill that needs no other block's counts during the iteration and spreads
+// fresh tracks over all SMs), then the end of the block's pass, where the
+// last block to finish commits the fill, scans the per-block and per-tile
+// vacancy counts and ends the iteration (which plans the next fill).
+__device__ bool block_iteration(const Params& p, int bid, int nb, const SharedStatic& ss,
+                                cudaGraphConditionalHandle handle, int use_handle, bool persistent,
+                                const BlockIter& it) {
+  const long long t_work0 = clock64();
+  Ctl* c = p.ctl;
+  if (bid == 0 && threadIdx.x == 0 && !it.blocks_ok) atomicOr(&c->error, ERR_VACANCY);
+  const PassPlan pl{it.head + it.prefix, it.quota, it.vtot, it.tight, true, it.vac0};
+  PassCounts n{0, 0, 0, 0};
+  if (p.policy == POLICY_DATA)
+    data_pass<false>(p, bid, nb, ss, pl, n);
+  else
+    local_pass<false>(p, bid, nb, ss, pl, n);
+  flush_counter(&c->alive, n.killed, true);
+  flush_counter(&c->steps_iter, n.steps, false);
+  flush_counter(&c->filled_total, n.fill, false);
+  if (n.n_def) atomicAdd(&c->n_deferred, (unsigned)n.n_def);
+  return end_block_pass(p, bid, nb, it, (long long)n.killed - (long long)n.fill, persistent, handle, use_handle,
+                        t_work0);
 }
 
 // Per-block vacancy counts and the plan of the first fill (fill_take and the
@@ -1977,10 +2074,7 @@ __global__ void __launch_bounds__(kTile) k_local(Params p, cudaGraphConditionalH
   const SharedStatic ss = carve_static(p, smem_raw);
   stage_static(p, ss);
   const BlockIter it = load_block_iter(p, blockIdx.x, gridDim.x);
-  if (p.policy == POLICY_DATA)
-    phase_data(p, blockIdx.x, gridDim.x, ss, handle, use_handle, false, it);
-  else
-    phase_local(p, blockIdx.x, gridDim.x, ss, handle, use_handle, false, it);
+  block_iteration(p, blockIdx.x, gridDim.x, ss, handle, use_handle, false, it);
 }
 
 // Per-action launches: fill, step limit (+ bookkeeping), scatter, one
@@ -2119,7 +2213,7 @@ __global__ void __launch_bounds__(kTile, 1) k_loop(Params p) {
 }
 
 // The persistent loop of the block-pass policies: one pass per block and
-// iteration (phase_local or phase_data), one grid barrier per iteration.
+// iteration (block_iteration), one grid barrier per iteration.
 __global__ void __launch_bounds__(kTile, 1) k_loop_local(Params p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SharedStatic ss = carve_static(p, smem_raw);
@@ -2141,8 +2235,7 @@ __global__ void __launch_bounds__(kTile, 1) k_loop_local(Params p) {
       c->max_total[2] += c->iter_max[parity ^ 1u][2];
       c->iter_max[parity ^ 1u][2] = 0;
     }
-    const bool ok = p.policy == POLICY_DATA ? phase_data(p, bid, (int)nb, ss, 0, 0, true, it)
-                                            : phase_local(p, bid, (int)nb, ss, 0, 0, true, it);
+    const bool ok = block_iteration(p, bid, (int)nb, ss, 0, 0, true, it);
     if (!ok) break;
     if (bid == 0 && threadIdx.x == 0) {
       const long long now = clock64();
@@ -2153,6 +2246,193 @@ __global__ void __launch_bounds__(kTile, 1) k_loop_local(Params p) {
   if (bid == 0 && threadIdx.x == 0) {
     c->max_total[2] += c->iter_max[0][2] + c->iter_max[1][2];
     c->iter_max[0][2] = c->iter_max[1][2] = 0;
+  }
+}
+
+// Block-wide sums of a pass's counts (every thread gets them).
+__device__ PassCounts block_total(const PassCounts& n) {
+  __shared__ unsigned long long s_n[4];
+  if (threadIdx.x < 4) s_n[threadIdx.x] = 0;
+  __syncthreads();
+  unsigned long long v[4] = {n.killed, n.n_def, n.steps, n.fill};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if ((threadIdx.x & 31) == 0 && v[k] != 0) atomicAdd(&s_n[k], v[k]);
+  }
+  __syncthreads();
+  const PassCounts out{s_n[0], s_n[1], s_n[2], s_n[3]};
+  __syncthreads();  // s_n is reused by the next call
+  return out;
+}
+
+// Start of an asynchronous run: the buffer entries' states from head and
+// tail (entries in [head, tail) written and unread, the others free for
+// their next writer) and the count of ended tracks, head - alive (every
+// track came from a buffer entry; a pair photon that reuses its parent's
+// slot continues the parent's count).
+__global__ void k_async_prepare(Params p) {
+  const unsigned long long head = p.ctl->head, tail = p.ctl->tail;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < p.ring_capacity;
+       j += stride) {
+    const unsigned long long index = head + ((j - head) & p.ring_mask);  // the index in [head, head + capacity) at j
+    p.ring_state[j] = ring_lap_code(p, index) + (index < tail ? 1u : 0u);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    p.ctl->finished = head - p.ctl->alive;
+    p.ctl->avail = tail - head;
+    p.ctl->async_passes = 0;
+    p.ctl->done_x = 0u;
+  }
+}
+
+// Live tracks a block of the asynchronous loop fills itself up to when
+// entries are queued (it takes at least ceil(queued / blocks) in any case):
+// a few per warp keeps every sub-partition busy without lengthening the pass.
+constexpr unsigned kAsyncFill = 32;
+
+// The asynchronous block loop of the block-pass policies (LOCAL, DATA): one
+// cooperative launch in which every block runs its own passes over its own
+// chunks with no grid barrier. At the start of a pass a block claims
+// written entries on an availability count (atomic, undone if short) and
+// takes their indices from the head: ceil(queued / blocks) or enough to hold
+// kAsyncFill live tracks, at most its vacant slots. Secondaries are reserved
+// at the tail against the current head, and each entry's state word orders
+// its writer and its reader. A track's steps and draws do not depend
+// on where or when it runs (its random stream is keyed by its own id), so
+// histories are those of the synchronous loops; only the tally summation
+// order differs. The run ends when every track taken from the buffer has
+// ended (finished reaches tail). Every wait is bounded: a block with nothing
+// to do polls, and if no track anywhere steps for ~1 s it sets
+// ERR_NO_PROGRESS and the abort word; all blocks leave at their next pass.
+// The last block to leave adds the most passes any block ran to the
+// iteration count.
+__global__ void __launch_bounds__(kTile, 1) k_loop_async(Params p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SharedStatic ss = carve_static(p, smem_raw);
+  stage_static(p, ss);
+  const int nb = (int)gridDim.x, bid = (int)blockIdx.x;
+  Ctl* c = p.ctl;
+  unsigned* abort_word = p.barrier + 2;
+  __shared__ unsigned long long s_first;
+  __shared__ unsigned s_take, s_vtot;
+  __shared__ int s_go;  // 0 leave, 1 nothing to do yet, 2 run a pass
+  const uint32_t n_own = (uint32_t)bid < p.n_chunks ? (p.n_chunks - (uint32_t)bid + nb - 1) / nb : 0u;
+  const bool owns_last = n_own > 0 && (uint32_t)bid + (uint32_t)nb * (n_own - 1u) == p.n_chunks - 1u;
+  const unsigned owned = n_own * 32u - (owns_last ? p.n_chunks * 32u - p.n_slots : 0u);
+  const unsigned quota_cap = block_quota_cap(p.policy);
+  unsigned long long passes = 0, seen = ~0ull;
+  const unsigned long long it0 = __ldcg(&c->iteration), it_max = __ldcg(&c->max_iterations);
+  const unsigned long long max_passes = it_max > it0 ? it_max - it0 : 0ull;  // the iteration limit
+  long long t_seen = clock64();
+  if (threadIdx.x == 0) {
+    s_vtot = __ldcg(&p.block_vacant[bid]);
+    if (__ldcg(&c->local_blocks) != (unsigned)nb) {  // vacancy counts made for another grid
+      atomicOr(&c->error, ERR_VACANCY);
+      atomicExch(abort_word, 1u);
+    }
+  }
+  // thread 0: no track anywhere stepped for ~1 s
+  auto watchdog = [&]() {
+    const unsigned long long now_steps = *reinterpret_cast<volatile unsigned long long*>(&c->steps_total);
+    const long long now = clock64();
+    if (now_steps != seen) {
+      seen = now_steps;
+      t_seen = now;
+    } else if (now - t_seen > kBarrierTimeoutCycles) {
+      atomicOr(&c->error, ERR_NO_PROGRESS);
+      atomicExch(abort_word, 1u);
+    }
+  };
+  for (;;) {
+    __syncthreads();  // every thread has read the previous decision
+    if (threadIdx.x == 0) {
+      int go = 1;
+      unsigned take = 0;
+      unsigned long long first = 0;
+      const unsigned vtot = s_vtot;
+      if (*reinterpret_cast<volatile unsigned*>(abort_word) != 0u) {
+        go = 0;
+      } else {
+        // claim `want` written entries on the availability count (undone if
+        // there were fewer), then their indices on the head: at least
+        // ceil(avail / blocks), and up to kAsyncFill live tracks in the block
+        const unsigned room = vtot < quota_cap ? vtot : quota_cap;
+        const long long a = (long long)*reinterpret_cast<volatile unsigned long long*>(&c->avail);
+        if (room > 0 && a > 0) {
+          const unsigned live = owned - vtot;
+          unsigned long long want = ((unsigned long long)a + (unsigned long long)nb - 1ull) / (unsigned long long)nb;
+          const unsigned long long fill_up = live < kAsyncFill ? (unsigned long long)(kAsyncFill - live) : 0ull;
+          if (want < fill_up) want = fill_up < (unsigned long long)a ? fill_up : (unsigned long long)a;
+          if (want > room) want = room;
+          const long long old = (long long)atomicAdd(&c->avail, 0ull - want);
+          if (old >= (long long)want) {
+            take = (unsigned)want;
+            first = atomicAdd(&c->head, want);
+          } else {
+            atomicAdd(&c->avail, want);
+          }
+        }
+        if (take > 0 || vtot < owned) {
+          go = 2;
+        } else {
+          const unsigned long long f = ld_acquire_u64(&c->finished);
+          if (f == *reinterpret_cast<volatile unsigned long long*>(&c->tail)) go = 0;  // every track has ended
+        }
+      }
+      s_go = go;
+      s_take = take;
+      s_first = first;
+    }
+    __syncthreads();
+    const int go = s_go;
+    if (go == 0) break;
+    if (go == 1) {
+      if (threadIdx.x == 0) {
+        watchdog();
+        __nanosleep(1000);  // about a microsecond between polls of the shared counters
+      }
+      continue;
+    }
+    const PassPlan pl{s_first, s_take, s_vtot, true, false, 0u};
+    PassCounts n{0, 0, 0, 0};
+    if (p.policy == POLICY_DATA)
+      data_pass<true>(p, bid, nb, ss, pl, n);
+    else
+      local_pass<true>(p, bid, nb, ss, pl, n);
+    const PassCounts tot = block_total(n);
+    if (threadIdx.x == 0) {
+      if (tot.fill != pl.quota) atomicOr(&c->error, ERR_VACANCY);
+      s_vtot = (unsigned)((long long)pl.vtot + (long long)tot.killed - (long long)tot.fill);
+      if (tot.steps) atomicAdd(&c->steps_total, tot.steps);
+      const long long dalive = (long long)tot.fill - (long long)tot.killed;
+      if (dalive != 0) atomicAdd(&c->alive, (unsigned long long)dalive);
+      if (tot.killed) {
+        __threadfence();  // the block's reservations on the tail precede its count of ended tracks
+        atomicAdd(&c->finished, tot.killed);
+      }
+      ++passes;
+      if (passes >= max_passes) {
+        atomicOr(&c->error, ERR_ITERATIONS);
+        atomicExch(abort_word, 1u);
+      }
+      if (tot.steps == 0) watchdog();
+    }
+  }
+  if (threadIdx.x == 0) {
+    p.block_vacant[bid] = s_vtot;
+    atomicMax(&c->async_passes, passes);
+    __threadfence();
+    if (atomicAdd(&c->done_x, 1u) == (unsigned)nb - 1u) {
+      __threadfence();
+      c->iteration = __ldcg(&c->iteration) + __ldcg(&c->async_passes);
+      const unsigned long long queued = __ldcg(&c->tail) - __ldcg(&c->head), alive = __ldcg(&c->alive);
+      c->total_vacant = (unsigned long long)p.n_slots - alive;
+      c->cont = (alive + queued > 0 && __ldcg(&c->error) == 0u) ? 1u : 0u;
+      c->done_x = 0u;
+    }
   }
 }
 
@@ -2269,7 +2549,7 @@ cudaError_t configure_kernels(const Params& p, int block, LaunchShape* sh) {
   sh->block = block;
   const void* with_smem[] = {(const void*)k_fill_step, (const void*)k_step, (const void*)k_fill,
                              (const void*)k_pre_step, (const void*)k_along, (const void*)k_loop,
-                             (const void*)k_local, (const void*)k_loop_local};
+                             (const void*)k_local, (const void*)k_loop_local, (const void*)k_loop_async};
   for (const void* fn : with_smem) {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stat);
     if (e != cudaSuccess) return e;
@@ -2285,7 +2565,11 @@ cudaError_t configure_kernels(const Params& p, int block, LaunchShape* sh) {
   int nb_local = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_local, (const void*)k_loop_local, kTile, stat);
   if (e != cudaSuccess) return e;
-  if (nb_local < nb) nb = nb_local;  // one grid for both loops (and the block-local launches)
+  if (nb_local < nb) nb = nb_local;  // one grid for every loop (and the block-local launches)
+  int nb_async = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb_async, (const void*)k_loop_async, kTile, stat);
+  if (e != cudaSuccess) return e;
+  if (nb_async < nb) nb = nb_async;
   sh->loop_grid = (nb < 1 ? 1 : nb) * sms;
   if (sh->loop_grid > kMaxLoopBlocks) sh->loop_grid = kMaxLoopBlocks;  // size of the per-block arrays
   return cudaGetLastError();
@@ -2328,6 +2612,12 @@ void launch_loop_ctl(const Params& p, unsigned long long handle, int use_handle,
 }
 void launch_begin_run(const Params& p, unsigned long long budget, cudaStream_t s) {
   k_begin_run<<<1, 1, 0, s>>>(p.ctl, budget);
+}
+void launch_async_prepare(const Params& p, cudaStream_t s) { k_async_prepare<<<256, 256, 0, s>>>(p); }
+cudaError_t launch_loop_async(const Params& p, const LaunchShape& sh, cudaStream_t s) {
+  void* args[] = {const_cast<Params*>(&p)};
+  return cudaLaunchCooperativeKernel((const void*)k_loop_async, dim3(sh.loop_grid), dim3(kTile), args, sh.static_smem,
+                                     s);
 }
 cudaError_t launch_loop(const Params& p, const LaunchShape& sh, cudaStream_t s) {
   void* args[] = {const_cast<Params*>(&p)};
