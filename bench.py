@@ -254,8 +254,18 @@ def run_ours(args):
     headline = None if auto else binding_policy(args.policy)
     if headline is not None and headline not in policies:
         policies.insert(0, headline)
-    loop = binding.LOOP_NAMES[args.loop]
     base_event = replica_event_base(rank)
+    block_pass = (wl.SORT_LOCAL, wl.SORT_DATA)
+
+    def loops_for(pol):
+        """Loop modes timed for a policy: the one named, else the persistent
+        loop and, for the block-pass policies, the asynchronous one."""
+        if args.loop != "auto":
+            mode = binding.LOOP_NAMES[args.loop]
+            if mode == binding.LOOP_ASYNC and pol not in block_pass:
+                mode = binding.LOOP_PERSISTENT  # the policy comparison runs every policy
+            return [mode]
+        return [binding.LOOP_PERSISTENT] + ([binding.LOOP_ASYNC] if pol in block_pass else [])
 
     def timed_jobs(pol, mode, split, steps, warmup, sample_clocks=False):
         """K whole jobs, primaries resident on the device; returns ms, steps, per-job ms."""
@@ -306,18 +316,20 @@ def run_ours(args):
         return ctx, dict(ms=reduce(sum(per_job), MAX), region_ms=reduce(region_ms, MAX), steps=reduce(steps_done, SUM),
                          job_ms=per_job, clocks=clocks)
 
-    # every policy is timed the same way; the headline is the one named, or
-    # with "auto" the fastest (what the autotuner would pick for this workload)
+    # every (policy, loop) pair is timed the same way; the headline is the
+    # fastest pair (of the named policy, if one is named): what the autotuner
+    # would pick for this workload
     results = {}
     ctxs = {}
     for pol in policies:
-        ctx, r = timed_jobs(pol, loop, args.split, args.steps, args.warmup, sample_clocks=True)
-        results[pol] = r
-        ctxs[pol] = ctx
-    if auto:
-        headline = max(policies, key=lambda q: results[q]["steps"] / results[q]["ms"])
-    clocks = results[headline]["clocks"]
-    head_ctx = ctxs.pop(headline)
+        for mode in loops_for(pol):
+            ctx, r = timed_jobs(pol, mode, args.split, args.steps, args.warmup, sample_clocks=True)
+            results[(pol, mode)] = r
+            ctxs[(pol, mode)] = ctx
+    pairs = [k for k in results if auto or k[0] == headline]
+    headline, loop = max(pairs, key=lambda k: results[k]["steps"] / results[k]["ms"])
+    clocks = results[(headline, loop)]["clocks"]
+    head_ctx = ctxs.pop((headline, loop))
     for ctx in ctxs.values():
         ctx.close()
 
@@ -326,7 +338,10 @@ def run_ours(args):
         for name, mode, split in (("host_per_action", binding.LOOP_HOST, True),
                                   ("graph_per_action", binding.LOOP_GRAPH, True),
                                   ("graph_per_phase", binding.LOOP_GRAPH, False),
-                                  ("persistent", binding.LOOP_PERSISTENT, False)):
+                                  ("persistent", binding.LOOP_PERSISTENT, False),
+                                  ("async", binding.LOOP_ASYNC, False)):
+            if mode == binding.LOOP_ASYNC and headline not in block_pass:
+                continue
             ctx, r = timed_jobs(headline, mode, split, max(2, args.steps // 2), 2)
             ctx.close()
             loop_modes[name] = dict(value=r["steps"] / (r["ms"] / 1e3), ms_per_step=r["ms"] / max(2, args.steps // 2))
@@ -376,21 +391,30 @@ def run_ours(args):
 
     if rank != 0:
         return
-    h = results[headline]
+    h = results[(headline, loop)]
     value = h["steps"] / (h["ms"] / 1e3)
     steps_per_job = h["steps"] / args.steps / world
-    by_policy = {binding_name(p): dict(value=r["steps"] / (r["ms"] / 1e3), ms_per_step=r["ms"] / args.steps,
-                                       track_steps_per_job=r["steps"] / args.steps / world)
-                 for p, r in results.items()}
-    # persistent loop, per job: primaries push, run start, (block-local policy:
-    # per-block vacancy scan), loop kernel
-    launches_per_job = (4 if headline in (wl.SORT_LOCAL, wl.SORT_DATA) else 3) if loop == binding.LOOP_PERSISTENT else None
+    loop_name = {v: k for k, v in binding.LOOP_NAMES.items()}
+    # per policy, in the persistent loop (the sorted vs unsorted comparison),
+    # and the block-pass policies again in the asynchronous loop
+    by_policy = {binding_name(p) + ("" if m == binding.LOOP_PERSISTENT else f" ({loop_name[m]} loop)"):
+                 dict(value=r["steps"] / (r["ms"] / 1e3), ms_per_step=r["ms"] / args.steps,
+                      track_steps_per_job=r["steps"] / args.steps / world)
+                 for (p, m), r in results.items()}
+    # per job: primaries push, run start, (block-pass policies: per-block
+    # vacancy scan; asynchronous loop: buffer entry states), loop kernel
+    if loop == binding.LOOP_ASYNC:
+        launches_per_job = 5
+    elif loop == binding.LOOP_PERSISTENT:
+        launches_per_job = 4 if headline in block_pass else 3
+    else:
+        launches_per_job = None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": h["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
         "timed_region_ms": h["region_ms"],
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(desc, sort_policy=binding_name(headline), loop=args.loop + (" per-action" if args.split else ""),
+        "config": dict(desc, sort_policy=binding_name(headline), loop=loop_name[loop] + (" per-action" if args.split else ""),
                        parallelism=f"replicas x{world} (independent events per rank)",
                        l2="512 MiB buffer written between timed jobs (outside the jobs' CUDA-event intervals; timed_region_ms includes it)"),
         "sorted_vs_unsorted": by_policy,
@@ -404,7 +428,7 @@ def run_ours(args):
         line["loop_profile_us_per_iteration"] = {
             part: {name: round(c / it / 2.07e3, 3) for name, c in vals.items()} for part, vals in prof.items()}
     job_ms = statistics.median(h["job_ms"])
-    line["roofline"] = roofline_loop(args.workload, binding_name(headline), steps_per_job, job_ms,
+    line["roofline"] = roofline_loop(args.workload, binding_name(headline), loop_name[loop], steps_per_job, job_ms,
                                      full_size=not (args.primaries or args.slots))
     if launches_per_job:
         line["gpu_launches"] = int(launches_per_job * args.steps)
@@ -438,7 +462,9 @@ def run_extras(args, binding, stream, flush):
     c2 = binding.to_c_primaries(prim2)
     dev2 = torch.from_numpy(c2.view(np.uint8).copy()).cuda()
     pol = {}
-    for name in ("action_type", "action", "none", "data", "local"):
+    runs = [(name, binding.LOOP_PERSISTENT) for name in ("action_type", "action", "none", "data", "local")]
+    runs += [("data", binding.LOOP_ASYNC), ("local", binding.LOOP_ASYNC)]
+    for name, mode in runs:
         ctx = binding.Context(prob2.replace(sort_policy=wl.SORT_NAMES[name], max_events=1), stream=stream.cuda_stream)
         times, steps = [], 0
         for rep in range(1 + args.extra_steps):
@@ -448,21 +474,22 @@ def run_extras(args, binding, stream, flush):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             ctx.add_primaries_device(rep, dev2.data_ptr(), len(c2))
-            ctx.run_events(binding.LOOP_PERSISTENT)
+            ctx.run_events(mode)
             e1.record(stream)
             torch.cuda.synchronize()
             if rep >= 1:
                 times.append(e0.elapsed_time(e1))
                 steps += ctx.stats()["steps_total"] - s0
         it = ctx.stats()["iteration"]
-        prof = ctx.loop_profile()
+        prof = ctx.loop_profile() if mode == binding.LOOP_PERSISTENT else None
         ctx.close()
         ms = sum(times)
-        pol[name] = dict(value=steps / (ms / 1e3), ms_per_job=ms / len(times), track_steps_per_job=steps / len(times),
-                         iterations_per_job=it / (1 + args.extra_steps),
-                         loop_profile_us_per_iteration={
-                             part: {k: round(v / max(it, 1) / 2.07e3, 2) for k, v in vals.items()}
-                             for part, vals in prof.items()})
+        row = dict(value=steps / (ms / 1e3), ms_per_job=ms / len(times), track_steps_per_job=steps / len(times),
+                   iterations_per_job=it / (1 + args.extra_steps))
+        if prof is not None:
+            row["loop_profile_us_per_iteration"] = {
+                part: {k: round(v / max(it, 1) / 2.07e3, 2) for k, v in vals.items()} for part, vals in prof.items()}
+        pol[name if mode == binding.LOOP_PERSISTENT else name + " (async loop)"] = row
     out["calorimeter_field_10gev"] = dict(desc2, sorted_vs_unsorted=pol)
 
     # --- Runge-Kutta field propagation with a substep cap (paper Sec. 3.3, Fig. 2):
@@ -531,7 +558,8 @@ def run_extras(args, binding, stream, flush):
     sample = wl.concat_primaries(events[:24])
     best, trials = binding.autotune(base3, sample, [1 << 18, 1 << 19, 1 << 20, 1 << 21], [128, 256, 512],
                                     [wl.SORT_NONE, wl.SORT_ACTION, wl.SORT_ACTION_TYPE, wl.SORT_LOCAL, wl.SORT_DATA],
-                                    [binding.LOOP_PERSISTENT, binding.LOOP_GRAPH], stream=stream.cuda_stream)
+                                    [binding.LOOP_PERSISTENT, binding.LOOP_GRAPH, binding.LOOP_ASYNC],
+                                    stream=stream.cuda_stream)
     tuned = base3.replace(n_slots=best["n_slots"], block_size=best["block_size"], sort_policy=best["sort_policy"],
                           init_capacity=max(8 * best["n_slots"], 1 << 22))
     mode = best["mode"]
@@ -581,11 +609,13 @@ def run_extras(args, binding, stream, flush):
     reqs = [(float(t), i, e) for i, (t, e) in enumerate(zip(arrivals, sev))]
     served = {}
     sprob = tuned.replace(max_events=4096)
+    # serving admits events between chunks of iterations: a budgeted loop
+    serve_mode = binding.LOOP_PERSISTENT if mode == binding.LOOP_ASYNC else mode
     for label, kw in (("continuous_batching", dict()), ("one_event_at_a_time", dict(max_in_flight=1))):
         ctx = binding.Context(sprob, stream=stream.cuda_stream)
         stop = dur if label == "continuous_batching" else min(dur, args.serve_plain_seconds)
         r_list = [r for r in reqs if r[0] <= stop]
-        res, summ, _ = ctx.serve(r_list, mode=mode, chunk_iterations=args.serve_chunk, stop_admitting_s=stop + 0.5,
+        res, summ, _ = ctx.serve(r_list, mode=serve_mode, chunk_iterations=args.serve_chunk, stop_admitting_s=stop + 0.5,
                                  **kw)
         ctx.close()
         done = res["done_s"] >= 0
@@ -597,7 +627,7 @@ def run_extras(args, binding, stream, flush):
             latency_ms=dict(p50=float(np.percentile(lat, 50) * 1e3), p95=float(np.percentile(lat, 95) * 1e3),
                             p99=float(np.percentile(lat, 99) * 1e3)) if len(lat) else None,
             window_s=stop)
-    out["serving"] = dict(rate_hz=rate, duration_s=dur, mode=mode, chunk_iterations=args.serve_chunk, **served)
+    out["serving"] = dict(rate_hz=rate, duration_s=dur, mode=serve_mode, chunk_iterations=args.serve_chunk, **served)
     return out
 
 
@@ -724,7 +754,8 @@ def load_peaks():
 # (2 x DFMA + DADD + DMUL) counted by ncu on the persistent loop kernel
 # (the ncu summaries committed beside this script, one per kernel and workload);
 # DRAM bytes per launch of that kernel from the same captures, for the
-# workloads that were captured whole. Keys: (workload, policy).
+# workloads that were captured whole. Keys: (workload, policy), and
+# (workload, policy, "async") for the asynchronous loop kernel.
 BYTES_PER_STEP = 160.0
 FP64_FLOP_PER_STEP = {("calorimeter-1gev", "none"): 131.0, ("calorimeter-1gev", "action"): 131.0,
                       ("calorimeter-1gev", "action_type"): 131.0, ("calorimeter-1gev", "data"): 119.5,
@@ -732,26 +763,33 @@ FP64_FLOP_PER_STEP = {("calorimeter-1gev", "none"): 131.0, ("calorimeter-1gev", 
                       ("calorimeter-field-10gev", "none"): 138.4, ("calorimeter-field-10gev", "action"): 138.4,
                       ("calorimeter-field-10gev", "action_type"): 138.4, ("calorimeter-field-10gev", "data"): 129.5,
                       ("calorimeter-field-10gev", "local"): 129.5,
+                      ("calorimeter-1gev", "local", "async"): 119.5, ("calorimeter-1gev", "data", "async"): 119.5,
                       ("water-cube-10mev", None): 119.5}
 DRAM_BYTES_PER_LAUNCH = {("calorimeter-1gev", "none"): 0.79e6, ("calorimeter-1gev", "action_type"): 0.94e6,
                          ("calorimeter-1gev", "data"): 1.64e6, ("calorimeter-1gev", "local"): 1.42e6,
                          ("calorimeter-field-10gev", "none"): 28.26e6, ("calorimeter-field-10gev", "action_type"): 28.53e6,
-                         ("calorimeter-field-10gev", "data"): 26.94e6, ("calorimeter-field-10gev", "local"): 24.50e6}
+                         ("calorimeter-field-10gev", "data"): 26.94e6, ("calorimeter-field-10gev", "local"): 24.50e6,
+                         ("calorimeter-1gev", "local", "async"): 1.375e6, ("calorimeter-1gev", "data", "async"): 1.631e6}
 # FP64 peak of GB300: 2 DFMA per SM-cycle (ncu peak_sustained) x 152 SMs x 2.07 GHz x 2 flop
 FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
 
-def roofline_loop(workload, policy, steps_per_job, job_ms, full_size=True):
+def roofline_loop(workload, policy, loop, steps_per_job, job_ms, full_size=True):
     """Roofline of the dominant kernel, the persistent step-loop kernel (one
     launch per job): FP64 ALU bound, with the HBM fraction beside it."""
     peaks, kind = load_peaks()
     t = job_ms / 1e3
-    fpstep = FP64_FLOP_PER_STEP.get((workload, policy), FP64_FLOP_PER_STEP.get((workload, None), 119.5))
+    key = (workload, policy) if loop != "async" else (workload, policy, "async")
+    fpstep = FP64_FLOP_PER_STEP.get(key, FP64_FLOP_PER_STEP.get((workload, policy),
+                                                                FP64_FLOP_PER_STEP.get((workload, None), 119.5)))
     flops = fpstep * steps_per_job / t / 1e12
     gbs = BYTES_PER_STEP * steps_per_job / t / 1e9
-    kernel = "k_loop_local" if policy in ("local", "data") else "k_loop"
+    if loop == "async":
+        kernel = "k_loop_async"
+    else:
+        kernel = "k_loop_local" if policy in ("local", "data") else "k_loop"
     return {"kernel": kernel, "bound": "alu", "achieved": flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": flops / FP64_PEAK_TFLOPS, "traffic": DRAM_BYTES_PER_LAUNCH.get((workload, policy)) if full_size else None,
+            "frac": flops / FP64_PEAK_TFLOPS, "traffic": DRAM_BYTES_PER_LAUNCH.get(key) if full_size else None,
             "peak_kind": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (probe measured 1.02 TFLOP/s)",
             "fp64_flop_per_track_step": fpstep,
             "hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
@@ -772,7 +810,8 @@ def main():
     ap.add_argument("--primaries", type=int, default=0, help="override the workload's primary count")
     ap.add_argument("--slots", type=int, default=0, help="override the workload's track-slot count")
     ap.add_argument("--policies", default="action_type,action,none,data,local")
-    ap.add_argument("--loop", default="persistent", choices=["host", "graph", "persistent"])
+    ap.add_argument("--loop", default="auto", choices=["auto", "host", "graph", "persistent", "async"],
+                    help="auto: the persistent loop for every policy, and the asynchronous one for local and data")
     ap.add_argument("--no-loop-compare", action="store_true")
     ap.add_argument("--no-kernel-timing", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")

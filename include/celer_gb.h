@@ -407,7 +407,9 @@ typedef struct {
  * ids, events[i] for primaries[i]): a fresh context per combination, one
  * warm-up run, one timed run (CUDA events around celer_run_events). trials
  * (nullable, max_trials entries) receives every trial; best the fastest.
- * The base problem supplies everything else. */
+ * The base problem supplies everything else. CELER_LOOP_ASYNC pairs only
+ * with the block-pass policies; other pairs are recorded with no
+ * throughput. */
 celer_status celer_autotune(const celer_problem* base, const celer_primary* primaries, const uint32_t* events,
                             uint64_t n, const uint64_t* slot_counts, int n_slot_counts, const int* block_sizes,
                             int n_block_sizes, const int* policies, int n_policies, const int* modes, int n_modes,

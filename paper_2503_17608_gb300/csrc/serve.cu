@@ -188,8 +188,13 @@ extern "C" celer_status celer_autotune(const celer_problem* base, const celer_pr
           pb.sort_policy = policies[c];
           if (pb.max_events < order.size()) pb.max_events = (uint32_t)order.size();
           celer_tune_trial t{pb.n_slots, pb.block_size, pb.sort_policy, modes[d], 0.0, 0.0};
+          // the asynchronous loop runs the block-pass policies only: other
+          // pairs are recorded with no throughput
+          const bool runnable = modes[d] != CELER_LOOP_ASYNC ||
+                                ((pb.sort_policy == CELER_SORT_LOCAL || pb.sort_policy == CELER_SORT_DATA) &&
+                                 !pb.split_actions);
           celer_ctx* ctx = nullptr;
-          if (celer_create(&pb, &ctx) == CELER_OK) {
+          if (runnable && celer_create(&pb, &ctx) == CELER_OK) {
             bool ok = true;
             uint64_t steps = 0;
             for (int rep = 0; rep < 2 && ok; ++rep) {
