@@ -35,6 +35,9 @@ sys.path.insert(0, ROOT)
 from paper_2503_17608_gb300 import workloads as wl  # noqa: E402
 
 METRIC = "track-steps/s on 1 GB300, sorted vs unsorted; p50/p99 event latency served"
+# loop keys of the bench: (celer loop mode, per-warp scheduling of the asynchronous loop)
+LOOP_KEYS = {"host": (0, False), "graph": (1, False), "persistent": (2, False), "async": (3, False),
+             "async-warps": (3, True)}
 UNIT = "track-steps/s"
 
 
@@ -258,19 +261,29 @@ def run_ours(args):
     block_pass = (wl.SORT_LOCAL, wl.SORT_DATA)
 
     def loops_for(pol):
-        """Loop modes timed for a policy: the one named, else the persistent
-        loop and, for the block-pass policies, the asynchronous one."""
+        """Loops timed for a policy: the one named, else the persistent loop
+        and, for the block-pass policies, the asynchronous one (block passes,
+        and for local per-warp scheduling too)."""
         if args.loop != "auto":
-            mode = binding.LOOP_NAMES[args.loop]
-            if mode == binding.LOOP_ASYNC and pol not in block_pass:
-                mode = binding.LOOP_PERSISTENT  # the policy comparison runs every policy
-            return [mode]
-        return [binding.LOOP_PERSISTENT] + ([binding.LOOP_ASYNC] if pol in block_pass else [])
+            key = args.loop
+            if key.startswith("async") and pol not in block_pass:
+                key = "persistent"  # the policy comparison runs every policy
+            if key == "async-warps" and pol != wl.SORT_LOCAL:
+                key = "async"
+            return [key]
+        keys = ["persistent"]
+        if pol in block_pass:
+            keys.append("async")
+        if pol == wl.SORT_LOCAL:
+            keys.append("async-warps")
+        return keys
 
-    def timed_jobs(pol, mode, split, steps, warmup, sample_clocks=False):
+    def timed_jobs(pol, key, split, steps, warmup, sample_clocks=False):
         """K whole jobs, primaries resident on the device; returns ms, steps, per-job ms."""
+        mode, warps = LOOP_KEYS[key]
         ctx = binding.Context(prob.replace(sort_policy=pol, max_events=1, split_actions=int(split)),
                               stream=stream.cuda_stream)
+        ctx.set_async_warps(warps)
         ev = [base_event]
 
         def job():
@@ -322,10 +335,10 @@ def run_ours(args):
     results = {}
     ctxs = {}
     for pol in policies:
-        for mode in loops_for(pol):
-            ctx, r = timed_jobs(pol, mode, args.split, args.steps, args.warmup, sample_clocks=True)
-            results[(pol, mode)] = r
-            ctxs[(pol, mode)] = ctx
+        for key in loops_for(pol):
+            ctx, r = timed_jobs(pol, key, args.split, args.steps, args.warmup, sample_clocks=True)
+            results[(pol, key)] = r
+            ctxs[(pol, key)] = ctx
     pairs = [k for k in results if auto or k[0] == headline]
     headline, loop = max(pairs, key=lambda k: results[k]["steps"] / results[k]["ms"])
     clocks = results[(headline, loop)]["clocks"]
@@ -335,14 +348,17 @@ def run_ours(args):
 
     loop_modes = {}
     if not args.no_loop_compare:
-        for name, mode, split in (("host_per_action", binding.LOOP_HOST, True),
-                                  ("graph_per_action", binding.LOOP_GRAPH, True),
-                                  ("graph_per_phase", binding.LOOP_GRAPH, False),
-                                  ("persistent", binding.LOOP_PERSISTENT, False),
-                                  ("async", binding.LOOP_ASYNC, False)):
-            if mode == binding.LOOP_ASYNC and headline not in block_pass:
+        for name, key, split in (("host_per_action", "host", True),
+                                 ("graph_per_action", "graph", True),
+                                 ("graph_per_phase", "graph", False),
+                                 ("persistent", "persistent", False),
+                                 ("async", "async", False),
+                                 ("async_warps", "async-warps", False)):
+            if key.startswith("async") and headline not in block_pass:
                 continue
-            ctx, r = timed_jobs(headline, mode, split, max(2, args.steps // 2), 2)
+            if key == "async-warps" and headline != wl.SORT_LOCAL:
+                continue
+            ctx, r = timed_jobs(headline, key, split, max(2, args.steps // 2), 2)
             ctx.close()
             loop_modes[name] = dict(value=r["steps"] / (r["ms"] / 1e3), ms_per_step=r["ms"] / max(2, args.steps // 2))
 
@@ -359,14 +375,14 @@ def run_ours(args):
         t0 = time.perf_counter()
         ctx.reset_event(ev_e2e)
         ctx.add_primaries(ev_e2e, pinned_np)
-        ctx.run_events(loop)
+        ctx.run_events(LOOP_KEYS[loop][0])
         tally, esc = ctx.read_tallies(ev_e2e)
         t1 = time.perf_counter()
         if k >= args.warmup:
             e2e_ms += (t1 - t0) * 1e3
             e2e_steps += ctx.stats()["steps_total"] - s0
         ev_e2e += 1
-    prof = ctx.loop_profile() if loop == binding.LOOP_PERSISTENT else None
+    prof = ctx.loop_profile() if loop == "persistent" else None
     e2e_ms = reduce(e2e_ms, MAX)
     e2e_steps = reduce(e2e_steps, SUM)
     iterations = ctx.stats()["iteration"]
@@ -394,18 +410,17 @@ def run_ours(args):
     h = results[(headline, loop)]
     value = h["steps"] / (h["ms"] / 1e3)
     steps_per_job = h["steps"] / args.steps / world
-    loop_name = {v: k for k, v in binding.LOOP_NAMES.items()}
     # per policy, in the persistent loop (the sorted vs unsorted comparison),
     # and the block-pass policies again in the asynchronous loop
-    by_policy = {binding_name(p) + ("" if m == binding.LOOP_PERSISTENT else f" ({loop_name[m]} loop)"):
+    by_policy = {binding_name(p) + ("" if m == "persistent" else f" ({m} loop)"):
                  dict(value=r["steps"] / (r["ms"] / 1e3), ms_per_step=r["ms"] / args.steps,
                       track_steps_per_job=r["steps"] / args.steps / world)
                  for (p, m), r in results.items()}
     # per job: primaries push, run start, (block-pass policies: per-block
     # vacancy scan; asynchronous loop: buffer entry states), loop kernel
-    if loop == binding.LOOP_ASYNC:
+    if loop.startswith("async"):
         launches_per_job = 5
-    elif loop == binding.LOOP_PERSISTENT:
+    elif loop == "persistent":
         launches_per_job = 4 if headline in block_pass else 3
     else:
         launches_per_job = None
@@ -414,7 +429,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": h["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
         "timed_region_ms": h["region_ms"],
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(desc, sort_policy=binding_name(headline), loop=loop_name[loop] + (" per-action" if args.split else ""),
+        "config": dict(desc, sort_policy=binding_name(headline), loop=loop + (" per-action" if args.split else ""),
                        parallelism=f"replicas x{world} (independent events per rank)",
                        l2="512 MiB buffer written between timed jobs (outside the jobs' CUDA-event intervals; timed_region_ms includes it)"),
         "sorted_vs_unsorted": by_policy,
@@ -428,7 +443,7 @@ def run_ours(args):
         line["loop_profile_us_per_iteration"] = {
             part: {name: round(c / it / 2.07e3, 3) for name, c in vals.items()} for part, vals in prof.items()}
     job_ms = statistics.median(h["job_ms"])
-    line["roofline"] = roofline_loop(args.workload, binding_name(headline), loop_name[loop], steps_per_job, job_ms,
+    line["roofline"] = roofline_loop(args.workload, binding_name(headline), loop, steps_per_job, job_ms,
                                      full_size=not (args.primaries or args.slots))
     if launches_per_job:
         line["gpu_launches"] = int(launches_per_job * args.steps)
@@ -463,9 +478,13 @@ def run_extras(args, binding, stream, flush):
     dev2 = torch.from_numpy(c2.view(np.uint8).copy()).cuda()
     pol = {}
     runs = [(name, binding.LOOP_PERSISTENT) for name in ("action_type", "action", "none", "data", "local")]
-    runs += [("data", binding.LOOP_ASYNC), ("local", binding.LOOP_ASYNC)]
+    runs += [("data", binding.LOOP_ASYNC), ("local", binding.LOOP_ASYNC), ("local", "async-warps")]
     for name, mode in runs:
         ctx = binding.Context(prob2.replace(sort_policy=wl.SORT_NAMES[name], max_events=1), stream=stream.cuda_stream)
+        label = name if mode == binding.LOOP_PERSISTENT else f"{name} ({mode if isinstance(mode, str) else 'async'} loop)"
+        if mode == "async-warps":
+            ctx.set_async_warps(True)
+            mode = binding.LOOP_ASYNC
         times, steps = [], 0
         for rep in range(1 + args.extra_steps):
             flush.zero_()
@@ -489,7 +508,7 @@ def run_extras(args, binding, stream, flush):
         if prof is not None:
             row["loop_profile_us_per_iteration"] = {
                 part: {k: round(v / max(it, 1) / 2.07e3, 2) for k, v in vals.items()} for part, vals in prof.items()}
-        pol[name if mode == binding.LOOP_PERSISTENT else name + " (async loop)"] = row
+        pol[label] = row
     out["calorimeter_field_10gev"] = dict(desc2, sorted_vs_unsorted=pol)
 
     # --- Runge-Kutta field propagation with a substep cap (paper Sec. 3.3, Fig. 2):
@@ -779,12 +798,12 @@ def roofline_loop(workload, policy, loop, steps_per_job, job_ms, full_size=True)
     launch per job): FP64 ALU bound, with the HBM fraction beside it."""
     peaks, kind = load_peaks()
     t = job_ms / 1e3
-    key = (workload, policy) if loop != "async" else (workload, policy, "async")
+    key = (workload, policy) if not loop.startswith("async") else (workload, policy, loop)
     fpstep = FP64_FLOP_PER_STEP.get(key, FP64_FLOP_PER_STEP.get((workload, policy),
                                                                 FP64_FLOP_PER_STEP.get((workload, None), 119.5)))
     flops = fpstep * steps_per_job / t / 1e12
     gbs = BYTES_PER_STEP * steps_per_job / t / 1e9
-    if loop == "async":
+    if loop.startswith("async"):
         kernel = "k_loop_async"
     else:
         kernel = "k_loop_local" if policy in ("local", "data") else "k_loop"
@@ -810,8 +829,9 @@ def main():
     ap.add_argument("--primaries", type=int, default=0, help="override the workload's primary count")
     ap.add_argument("--slots", type=int, default=0, help="override the workload's track-slot count")
     ap.add_argument("--policies", default="action_type,action,none,data,local")
-    ap.add_argument("--loop", default="auto", choices=["auto", "host", "graph", "persistent", "async"],
-                    help="auto: the persistent loop for every policy, and the asynchronous one for local and data")
+    ap.add_argument("--loop", default="auto", choices=["auto"] + list(LOOP_KEYS),
+                    help="auto: the persistent loop for every policy, the asynchronous one for local and data, "
+                         "and its per-warp scheduling for local")
     ap.add_argument("--no-loop-compare", action="store_true")
     ap.add_argument("--no-kernel-timing", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")

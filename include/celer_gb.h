@@ -305,6 +305,18 @@ celer_status celer_set_grid_blocks(celer_ctx* ctx, int blocks);
  * the fill work do. Takes effect at the next run. */
 celer_status celer_set_parent_reuse(celer_ctx* ctx, int on);
 
+/* Scheduling of the asynchronous loop (CELER_LOOP_ASYNC) for the block-local
+ * policy. on = 0: block passes, as in the synchronous loops. on = 1: every
+ * warp runs its own loop. It takes up to 32 tracks waiting for the same kind
+ * of step (particle type and next action) from its block's queues in shared
+ * memory, steps them, and queues the survivors again by their next kind. A
+ * track then moves on as soon as its own step is done instead of waiting for
+ * its block's slowest group. A block holds at most 1024 live tracks in this
+ * mode; a block that starts a run with more runs block passes. Histories do
+ * not change. On by default. Takes effect at the next run. on outside
+ * {0, 1}: CELER_ERR_INVALID. */
+celer_status celer_set_async_warps(celer_ctx* ctx, int on);
+
 /* Per-iteration counters (alive, queued, steps, tracks per action) of the
  * last min(n_max, recorded) iterations, the analogue of the paper's counter
  * tracks (Sec. 4). *n_out receives the row count. */

@@ -115,7 +115,7 @@ EXPORTS = [
     "celer_debug_philox", "celer_debug_curand_philox", "celer_partition_keys_noalloc", "celer_debug_math",
     "celer_run_iterations", "celer_read_event_live", "celer_serve", "celer_autotune", "celer_get_problem",
     "celer_debug_sample", "celer_debug_slots", "celer_set_hit_readout", "celer_set_grid_blocks",
-    "celer_set_parent_reuse", "celer_debug_barrier_timeout",
+    "celer_set_parent_reuse", "celer_set_async_warps", "celer_debug_barrier_timeout",
 ]
 
 _lib = None
@@ -161,6 +161,7 @@ def load(path: Optional[str] = None):
         "celer_set_hit_readout": ([vp, i32, vp, u64], i32),
         "celer_set_grid_blocks": ([vp, i32], i32),
         "celer_set_parent_reuse": ([vp, i32], i32),
+        "celer_set_async_warps": ([vp, i32], i32),
         "celer_debug_barrier_timeout": ([i32, i32, u64, C.POINTER(u32), C.POINTER(u32)], i32),
         "celer_partition_keys_noalloc": ([vp, u64, i32, i32, vp, vp, vp], i32),
         "celer_run_iterations": ([vp, i32, u64, C.POINTER(u64)], i32),
@@ -393,6 +394,11 @@ class Context:
     def set_parent_reuse(self, on: bool):
         """A pair's first photon starts in the converted photon's slot."""
         _check(load().celer_set_parent_reuse(self._h, int(bool(on))), self._h)
+
+    def set_async_warps(self, on: bool):
+        """Asynchronous loop, block-local policy: per-warp scheduling from the
+        block's queues (True) or block passes (False)."""
+        _check(load().celer_set_async_warps(self._h, int(bool(on))), self._h)
 
     def set_grid_blocks(self, blocks: int):
         """Cap the GPU blocks of this context's kernels (0: one per SM)."""

@@ -193,6 +193,7 @@ struct Params {
   int processes;
   int reuse_parent;        // 1: a pair's first photon starts in the parent's slot (Sec. 3.2)
   int field_cap;           // 0: exact helix; > 0: Runge-Kutta substeps, at most this many per step
+  int async_warps;         // asynchronous loop, block-local policy: 1 per-warp scheduling, 0 block passes
   const double2* tables;   // [mat][col][kGrid] (value, next - value)
   const double* mtab;      // log/exp reduction tables (fastmath.cuh)
   double lnEmin, inv_dl, dl;

@@ -446,6 +446,7 @@ celer_status celer_create(const celer_problem* pb, celer_ctx** out) {
   p.hy = pb->half_y;
   p.Bz = pb->Bz;
   p.field_cap = pb->field_substep_cap;
+  p.async_warps = 1;  // the asynchronous loop schedules per warp for the block-local policy
   p.cut_track = pb->cut_track;
   p.cut_moller = pb->cut_moller;
   p.cut_brems = pb->cut_brems;
@@ -884,6 +885,12 @@ celer_status celer_set_parent_reuse(celer_ctx* ctx, int on) {
   if (!ctx) return CELER_ERR_INVALID;
   ctx->p.reuse_parent = on ? 1 : 0;
   destroy_graph(ctx);  // captured with the old parameters
+  return CELER_OK;
+}
+
+celer_status celer_set_async_warps(celer_ctx* ctx, int on) {
+  if (!ctx || (on != 0 && on != 1)) return CELER_ERR_INVALID;
+  ctx->p.async_warps = on;
   return CELER_OK;
 }
 

@@ -12,7 +12,9 @@ from gpu_helpers import assert_conservation, match_fraction, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
-BLOCK_PASS = [wl.SORT_LOCAL, wl.SORT_DATA]
+# (policy, per-warp scheduling) pairs of the asynchronous loop
+SCHEDULES = [(wl.SORT_LOCAL, False), (wl.SORT_LOCAL, True), (wl.SORT_DATA, False)]
+SCHED_IDS = ["local-passes", "local-warps", "data-passes"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -23,6 +25,19 @@ def _cuda():
     binding.load()
 
 
+def run_async(prob, prim, policy, warps):
+    """run_gpu in the asynchronous loop with the given scheduling."""
+    prob = prob.replace(sort_policy=policy, history_capacity=len(prim))
+    with binding.Context(prob) as ctx:
+        ctx.set_async_warps(warps)
+        ctx.add_events(prim)
+        ctx.run_events(binding.LOOP_ASYNC)
+        out = dict(stats=ctx.stats())
+        out["hist"], out["edep"] = ctx.read_history(0, len(prim))
+        out["tally"] = {e: ctx.read_tallies(e) for e in dict.fromkeys(prim["event"].tolist())}
+    return out
+
+
 def assert_same_histories(a, b, rtol=1e-12):
     np.testing.assert_array_equal(a["hist"]["steps"], b["hist"]["steps"])
     np.testing.assert_array_equal(a["hist"]["secondaries"], b["hist"]["secondaries"])
@@ -30,11 +45,11 @@ def assert_same_histories(a, b, rtol=1e-12):
     np.testing.assert_allclose(a["hist"]["escaped"], b["hist"]["escaped"], rtol=rtol, atol=1e-12)
 
 
-@pytest.mark.parametrize("policy", BLOCK_PASS)
-def test_water_cube_histories_bit_exact(policy):
+@pytest.mark.parametrize("policy,warps", SCHEDULES, ids=SCHED_IDS)
+def test_water_cube_histories_bit_exact(policy, warps):
     prob = wl.water_cube_problem()
     prim = wl.water_cube_primaries()
-    g = run_gpu(prob, prim, mode=binding.LOOP_ASYNC, policy=policy)
+    g = run_async(prob, prim, policy, warps)
     o = run_oracle(prob, prim)
     np.testing.assert_array_equal(g["hist"]["steps"], o["hist"]["steps"])
     np.testing.assert_array_equal(g["hist"]["secondaries"], o["hist"]["secondaries"])
@@ -47,10 +62,10 @@ def test_water_cube_histories_bit_exact(policy):
     assert g["stats"]["alive"] == 0 and g["stats"]["queued"] == 0
 
 
-@pytest.mark.parametrize("policy", BLOCK_PASS)
-def test_calorimeter_histories_equal_the_synchronous_loop(policy):
+@pytest.mark.parametrize("policy,warps", SCHEDULES, ids=SCHED_IDS)
+def test_calorimeter_histories_equal_the_synchronous_loop(policy, warps):
     prob, prim = wl.calorimeter_1gev(200)
-    a = run_gpu(prob, prim, mode=binding.LOOP_ASYNC, policy=policy)
+    a = run_async(prob, prim, policy, warps)
     s = run_gpu(prob, prim, mode=binding.LOOP_PERSISTENT, policy=policy)
     assert_same_histories(a, s)
     assert a["stats"]["steps_total"] == s["stats"]["steps_total"]
@@ -60,53 +75,58 @@ def test_calorimeter_histories_equal_the_synchronous_loop(policy):
     np.testing.assert_allclose(a["tally"][0][0], s["tally"][0][0], rtol=1e-12, atol=1e-9)
 
 
-@pytest.mark.parametrize("policy", BLOCK_PASS)
-def test_field_histories_equal_the_synchronous_loop(policy):
+@pytest.mark.parametrize("policy,warps", SCHEDULES, ids=SCHED_IDS)
+def test_field_histories_equal_the_synchronous_loop(policy, warps):
     prob, prim = wl.calorimeter_field_10gev(40, n_slots=1 << 16)
-    a = run_gpu(prob, prim, mode=binding.LOOP_ASYNC, policy=policy)
+    a = run_async(prob, prim, policy, warps)
     s = run_gpu(prob, prim, mode=binding.LOOP_PERSISTENT, policy=policy)
     assert_same_histories(a, s)
     assert_conservation(prim, a["tally"])
 
 
+@pytest.mark.parametrize("warps", [False, True])
 @pytest.mark.parametrize("n_slots", [1, 7, 1000, 2049])
-def test_ragged_slot_counts(n_slots):
+def test_ragged_slot_counts(n_slots, warps):
     """Fewer slots than blocks (most blocks own none), and partial chunks."""
     prim = wl.water_cube_primaries(150)
     prob = wl.water_cube_problem(n_slots=n_slots, init_capacity=4096)
-    g = run_gpu(prob, prim, mode=binding.LOOP_ASYNC, policy=wl.SORT_LOCAL)
+    g = run_async(prob, prim, wl.SORT_LOCAL, warps)
     o = run_oracle(prob, prim)
     np.testing.assert_array_equal(g["hist"]["steps"], o["hist"]["steps"])
     np.testing.assert_allclose(g["edep"], o["edep"], rtol=1e-9, atol=1e-8)
 
 
-@pytest.mark.parametrize("policy", BLOCK_PASS)
-def test_small_buffer_defers_without_changing_histories(policy):
+@pytest.mark.parametrize("policy,warps", SCHEDULES, ids=SCHED_IDS)
+def test_small_buffer_defers_without_changing_histories(policy, warps):
     """A 64-entry buffer against a 1 GeV shower: writers find no room and
     defer, readers free entries; the histories are the synchronous loop's."""
     prob, prim = wl.calorimeter_1gev(20)
     prob = prob.replace(n_slots=256, init_capacity=64)
-    a = run_gpu(prob, prim, mode=binding.LOOP_ASYNC, policy=policy)
+    a = run_async(prob, prim, policy, warps)
     s = run_gpu(prob, prim, mode=binding.LOOP_PERSISTENT, policy=policy)
     assert_same_histories(a, s)
     assert_conservation(prim, a["tally"])
 
 
-def test_empty_run():
+@pytest.mark.parametrize("warps", [False, True])
+def test_empty_run(warps):
     prob = wl.water_cube_problem(sort_policy=wl.SORT_LOCAL)
     with binding.Context(prob) as ctx:
+        ctx.set_async_warps(warps)
         ctx.run_events(binding.LOOP_ASYNC)
         s = ctx.stats()
         assert s["steps_total"] == 0 and s["alive"] == 0 and s["queued"] == 0
 
 
-def test_finishes_runs_begun_by_the_synchronous_loops():
+@pytest.mark.parametrize("warps", [False, True])
+def test_finishes_runs_begun_by_the_synchronous_loops(warps):
     """Live tracks in slots and entries queued at the start of the run (left
     by budgeted synchronous runs of both block-pass policies): the run's end
     condition counts them, and every history matches the oracle."""
     prob = wl.water_cube_problem(n_slots=1024, history_capacity=2000)
     prim = wl.water_cube_primaries()
     with binding.Context(prob) as ctx:
+        ctx.set_async_warps(warps)
         ctx.add_events(prim)
         ctx.set_sort_policy(wl.SORT_DATA)
         ctx.run_iterations(binding.LOOP_PERSISTENT, budget=4)
@@ -138,6 +158,7 @@ def test_synchronous_runs_after_an_asynchronous_one():
     runs = ((wl.SORT_LOCAL, binding.LOOP_ASYNC), (wl.SORT_ACTION_TYPE, binding.LOOP_GRAPH),
             (wl.SORT_DATA, binding.LOOP_ASYNC), (wl.SORT_NONE, binding.LOOP_PERSISTENT))
     with binding.Context(prob) as ctx:
+        ctx.set_async_warps(True)
         for (policy, mode), b in zip(runs, batches):
             ctx.set_sort_policy(policy)
             ctx.add_events(b)
@@ -150,10 +171,12 @@ def test_synchronous_runs_after_an_asynchronous_one():
         np.testing.assert_array_equal(hist["secondaries"][k * n:(k + 1) * n], o["hist"]["secondaries"])
 
 
-def test_parent_slot_reuse_keeps_histories():
+@pytest.mark.parametrize("warps", [False, True])
+def test_parent_slot_reuse_keeps_histories(warps):
     prob = wl.water_cube_problem(history_capacity=2000, sort_policy=wl.SORT_LOCAL)
     prim = wl.water_cube_primaries()
     with binding.Context(prob) as ctx:
+        ctx.set_async_warps(warps)
         ctx.set_parent_reuse(True)
         ctx.add_events(prim)
         ctx.run_events(binding.LOOP_ASYNC)
@@ -164,11 +187,12 @@ def test_parent_slot_reuse_keeps_histories():
     np.testing.assert_allclose(edep, o["edep"], rtol=1e-9, atol=1e-9 * 10.0)
 
 
-def test_event_results_same_alone_and_mixed():
+@pytest.mark.parametrize("warps", [False, True])
+def test_event_results_same_alone_and_mixed(warps):
     events = [e[:80] for e in wl.offload_events(6)]
     prob = wl.calorimeter_problem(1 << 15, Bz=4.0, max_events=8, sort_policy=wl.SORT_LOCAL)
     mix = wl.concat_primaries(events)
-    g_mix = run_gpu(prob, mix, mode=binding.LOOP_ASYNC)
+    g_mix = run_async(prob, mix, wl.SORT_LOCAL, warps)
     for k, ev in enumerate(events):
         g1 = run_gpu(prob, ev, mode=binding.LOOP_PERSISTENT)
         sl = slice(sum(len(e) for e in events[:k]), sum(len(e) for e in events[: k + 1]))
@@ -197,7 +221,8 @@ def test_rejects_budgets_and_other_policies():
         assert ctx.stats()["alive"] == 0
 
 
-def test_stuck_run_ends_with_capacity_status():
+@pytest.mark.parametrize("warps", [False, True])
+def test_stuck_run_ends_with_capacity_status(warps):
     """One slot and a one-entry buffer: the electron's second secondary can
     never be placed and no block can read the queued entry. No track steps
     any more, so after about a second every block leaves its loop and the
@@ -205,9 +230,19 @@ def test_stuck_run_ends_with_capacity_status():
     prob = wl.calorimeter_problem(1, init_capacity=1, history_capacity=1, sort_policy=wl.SORT_LOCAL)
     prim = wl.electron_beam(1, 1000.0)
     with binding.Context(prob, max_iterations=10**9) as ctx:
+        ctx.set_async_warps(warps)
         ctx.add_events(prim)
         with pytest.raises(binding.CelerError) as ei:
             ctx.run_events(binding.LOOP_ASYNC)
         assert ei.value.status == 2
         s = ctx.stats()
         assert s["alive"] == 1 and s["queued"] == 1
+
+
+def test_warp_scheduling_switch_is_validated():
+    prob = wl.water_cube_problem(sort_policy=wl.SORT_LOCAL)
+    with binding.Context(prob) as ctx:
+        lib = binding.load()
+        assert lib.celer_set_async_warps(ctx._h, 2) == 1
+        assert lib.celer_set_async_warps(ctx._h, -1) == 1
+        assert lib.celer_set_async_warps(ctx._h, 1) == 0

@@ -83,3 +83,16 @@ def test_single_process_reduction_is_identity():
 
     assert bench.reduce_over_ranks(3.5, "max") == 3.5
     assert bench.replica_event_base(0) == 0
+
+
+def test_bench_loop_keys_name_the_library_modes():
+    """The bench's loop keys map onto the C ABI's loop modes."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2503_17608_gb300 import binding
+
+    assert bench.LOOP_KEYS["host"] == (binding.LOOP_HOST, False)
+    assert bench.LOOP_KEYS["graph"] == (binding.LOOP_GRAPH, False)
+    assert bench.LOOP_KEYS["persistent"] == (binding.LOOP_PERSISTENT, False)
+    assert bench.LOOP_KEYS["async"] == (binding.LOOP_ASYNC, False)
+    assert bench.LOOP_KEYS["async-warps"] == (binding.LOOP_ASYNC, True)
