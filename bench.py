@@ -583,6 +583,7 @@ def run_extras(args, binding, stream, flush):
                           init_capacity=max(8 * best["n_slots"], 1 << 22))
     mode = best["mode"]
     ctx = binding.Context(tuned, stream=stream.cuda_stream)
+    ctx.set_async_warps(best["async_warps"])
     ctx.add_events(prim3)  # warm-up pass
     ctx.run_events(mode)
     for e in range(256):
@@ -599,6 +600,7 @@ def run_extras(args, binding, stream, flush):
     batched_tallies = [ctx.read_tallies(e) for e in range(256)]
     ctx.close()
     ctx = binding.Context(tuned.replace(max_events=1), stream=stream.cuda_stream)
+    ctx.set_async_warps(best["async_warps"])
     s0 = ctx.stats()["steps_total"]
     t0 = time.perf_counter()
     seq_tallies = []

@@ -412,6 +412,8 @@ typedef struct {
   int block_size, sort_policy, mode;
   double track_steps_per_s;         /* measured on the sample (0: the trial failed) */
   double ms;
+  int async_warps;                  /* celer_set_async_warps of the trial (CELER_LOOP_ASYNC with the
+                                       block-local policy is tried both ways; 1 elsewhere) */
 } celer_tune_trial;
 
 /* Try every combination of the given slot counts, block sizes, sort
@@ -421,7 +423,9 @@ typedef struct {
  * (nullable, max_trials entries) receives every trial; best the fastest.
  * The base problem supplies everything else. CELER_LOOP_ASYNC pairs only
  * with the block-pass policies; other pairs are recorded with no
- * throughput. */
+ * throughput. With the block-local policy it is tried with both of its
+ * schedules (async_warps 1 and 0), so max_trials should allow for that
+ * trial count. */
 celer_status celer_autotune(const celer_problem* base, const celer_primary* primaries, const uint32_t* events,
                             uint64_t n, const uint64_t* slot_counts, int n_slot_counts, const int* block_sizes,
                             int n_block_sizes, const int* policies, int n_policies, const int* modes, int n_modes,

@@ -98,7 +98,7 @@ class celer_serve_summary(C.Structure):
 
 class celer_tune_trial(C.Structure):
     _fields_ = [("n_slots", C.c_uint64), ("block_size", C.c_int), ("sort_policy", C.c_int), ("mode", C.c_int),
-                ("track_steps_per_s", C.c_double), ("ms", C.c_double)]
+                ("track_steps_per_s", C.c_double), ("ms", C.c_double), ("async_warps", C.c_int)]
 
 
 ACTION_NAMES = ["none", "zup", "zdown", "side", "range", "trapped", "compton", "photoelectric", "pair", "moller",
@@ -484,7 +484,7 @@ def autotune(prob: wl.Problem, primaries: np.ndarray, slot_counts, block_sizes, 
     bs = (C.c_int * len(block_sizes))(*block_sizes)
     po = (C.c_int * len(policies))(*policies)
     mo = (C.c_int * len(modes))(*modes)
-    n_max = len(slot_counts) * len(block_sizes) * len(policies) * len(modes)
+    n_max = 2 * len(slot_counts) * len(block_sizes) * len(policies) * len(modes)  # local + async: two schedules
     trials = (celer_tune_trial * n_max)()
     n_out = C.c_int()
     best = celer_tune_trial()
@@ -493,7 +493,7 @@ def autotune(prob: wl.Problem, primaries: np.ndarray, slot_counts, block_sizes, 
 
     def d(t):
         return dict(n_slots=t.n_slots, block_size=t.block_size, sort_policy=t.sort_policy, mode=t.mode,
-                    track_steps_per_s=t.track_steps_per_s, ms=t.ms)
+                    track_steps_per_s=t.track_steps_per_s, ms=t.ms, async_warps=t.async_warps)
 
     return d(best), [d(trials[i]) for i in range(n_out.value)]
 

@@ -181,47 +181,50 @@ extern "C" celer_status celer_autotune(const celer_problem* base, const celer_pr
   for (int a = 0; a < n_slot_counts; ++a)
     for (int b = 0; b < n_block_sizes; ++b)
       for (int c = 0; c < n_policies; ++c)
-        for (int d = 0; d < n_modes; ++d) {
-          celer_problem pb = *base;
-          pb.n_slots = slot_counts[a];
-          pb.block_size = block_sizes[b];
-          pb.sort_policy = policies[c];
-          if (pb.max_events < order.size()) pb.max_events = (uint32_t)order.size();
-          celer_tune_trial t{pb.n_slots, pb.block_size, pb.sort_policy, modes[d], 0.0, 0.0};
-          // the asynchronous loop runs the block-pass policies only: other
-          // pairs are recorded with no throughput
-          const bool runnable = modes[d] != CELER_LOOP_ASYNC ||
-                                ((pb.sort_policy == CELER_SORT_LOCAL || pb.sort_policy == CELER_SORT_DATA) &&
-                                 !pb.split_actions);
-          celer_ctx* ctx = nullptr;
-          if (runnable && celer_create(&pb, &ctx) == CELER_OK) {
-            bool ok = true;
-            uint64_t steps = 0;
-            for (int rep = 0; rep < 2 && ok; ++rep) {
-              for (size_t g = 0; g < order.size() && ok; ++g) {
-                ok = celer_reset_event(ctx, order[g]) == CELER_OK &&
-                     celer_add_primaries(ctx, order[g], groups[g].data(), groups[g].size()) == CELER_OK;
+        for (int d = 0; d < n_modes; ++d)
+          for (int warps = 1; warps >= 0; --warps) {
+            // the asynchronous loop's two schedules for the block-local policy
+            if (warps == 0 && !(modes[d] == CELER_LOOP_ASYNC && policies[c] == CELER_SORT_LOCAL)) continue;
+            celer_problem pb = *base;
+            pb.n_slots = slot_counts[a];
+            pb.block_size = block_sizes[b];
+            pb.sort_policy = policies[c];
+            if (pb.max_events < order.size()) pb.max_events = (uint32_t)order.size();
+            celer_tune_trial t{pb.n_slots, pb.block_size, pb.sort_policy, modes[d], 0.0, 0.0, warps};
+            // the asynchronous loop runs the block-pass policies only: other
+            // pairs are recorded with no throughput
+            const bool runnable = modes[d] != CELER_LOOP_ASYNC ||
+                                  ((pb.sort_policy == CELER_SORT_LOCAL || pb.sort_policy == CELER_SORT_DATA) &&
+                                   !pb.split_actions);
+            celer_ctx* ctx = nullptr;
+            if (runnable && celer_create(&pb, &ctx) == CELER_OK) {
+              bool ok = celer_set_async_warps(ctx, warps) == CELER_OK;
+              uint64_t steps = 0;
+              for (int rep = 0; rep < 2 && ok; ++rep) {
+                for (size_t g = 0; g < order.size() && ok; ++g) {
+                  ok = celer_reset_event(ctx, order[g]) == CELER_OK &&
+                       celer_add_primaries(ctx, order[g], groups[g].data(), groups[g].size()) == CELER_OK;
+                }
+                celer_step_stats s0{}, s1{};
+                ok = ok && celer_get_stats(ctx, &s0) == CELER_OK;
+                cudaEventRecord(e0, stream);
+                ok = ok && celer_run_events(ctx, modes[d]) == CELER_OK;
+                cudaEventRecord(e1, stream);
+                ok = ok && cudaEventSynchronize(e1) == cudaSuccess && celer_get_stats(ctx, &s1) == CELER_OK;
+                if (ok && rep == 1) {
+                  float ms = 0.f;
+                  cudaEventElapsedTime(&ms, e0, e1);
+                  steps = s1.steps_total - s0.steps_total;
+                  t.ms = ms;
+                  t.track_steps_per_s = ms > 0.f ? steps / (ms * 1e-3) : 0.0;
+                }
               }
-              celer_step_stats s0{}, s1{};
-              ok = ok && celer_get_stats(ctx, &s0) == CELER_OK;
-              cudaEventRecord(e0, stream);
-              ok = ok && celer_run_events(ctx, modes[d]) == CELER_OK;
-              cudaEventRecord(e1, stream);
-              ok = ok && cudaEventSynchronize(e1) == cudaSuccess && celer_get_stats(ctx, &s1) == CELER_OK;
-              if (ok && rep == 1) {
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                steps = s1.steps_total - s0.steps_total;
-                t.ms = ms;
-                t.track_steps_per_s = ms > 0.f ? steps / (ms * 1e-3) : 0.0;
-              }
+              celer_destroy(ctx);
             }
-            celer_destroy(ctx);
+            if (trials && count < max_trials) trials[count] = t;
+            ++count;
+            if (t.track_steps_per_s > best->track_steps_per_s) *best = t;
           }
-          if (trials && count < max_trials) trials[count] = t;
-          ++count;
-          if (t.track_steps_per_s > best->track_steps_per_s) *best = t;
-        }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (n_trials) *n_trials = count;

@@ -78,3 +78,19 @@ def test_autotuner_picks_a_measured_best():
     assert len(trials) == 8
     assert all(t["track_steps_per_s"] > 0 for t in trials)
     assert best["track_steps_per_s"] == max(t["track_steps_per_s"] for t in trials)
+
+
+def test_autotuner_tries_both_schedules_of_the_asynchronous_loop():
+    events = small_events(8, cap=40)
+    prim = wl.concat_primaries(events)
+    prob = wl.calorimeter_problem(1 << 12, Bz=4.0, max_events=16)
+    best, trials = binding.autotune(prob, prim, [1 << 12], [256], [wl.SORT_LOCAL, wl.SORT_DATA, wl.SORT_NONE],
+                                    [binding.LOOP_ASYNC, binding.LOOP_PERSISTENT])
+    combos = sorted((t["sort_policy"], t["mode"], t["async_warps"]) for t in trials)
+    A, P = binding.LOOP_ASYNC, binding.LOOP_PERSISTENT
+    assert combos == sorted([(wl.SORT_LOCAL, A, 1), (wl.SORT_LOCAL, A, 0), (wl.SORT_LOCAL, P, 1),
+                             (wl.SORT_DATA, A, 1), (wl.SORT_DATA, P, 1), (wl.SORT_NONE, A, 1), (wl.SORT_NONE, P, 1)])
+    for t in trials:
+        runnable = not (t["mode"] == A and t["sort_policy"] == wl.SORT_NONE)
+        assert (t["track_steps_per_s"] > 0) == runnable
+    assert best["track_steps_per_s"] == max(t["track_steps_per_s"] for t in trials)
