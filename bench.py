@@ -630,11 +630,17 @@ def run_extras(args, binding, stream, flush):
     reqs = [(float(t), i, e) for i, (t, e) in enumerate(zip(arrivals, sev))]
     served = {}
     sprob = tuned.replace(max_events=4096)
-    # serving admits events between chunks of iterations: a budgeted loop
-    serve_mode = binding.LOOP_PERSISTENT if mode == binding.LOOP_ASYNC else mode
-    for label, kw in (("continuous_batching", dict()), ("one_event_at_a_time", dict(max_in_flight=1))):
+    # continuous batching in the persistent loop and, for a block-pass policy,
+    # in the asynchronous loop (chunks of a budget of passes or pieces); the
+    # one-event-at-a-time baseline in the persistent loop
+    runs = [("continuous_batching", binding.LOOP_PERSISTENT, dict())]
+    if sprob.sort_policy in (wl.SORT_LOCAL, wl.SORT_DATA):
+        runs.append(("continuous_batching_async", binding.LOOP_ASYNC, dict()))
+    runs.append(("one_event_at_a_time", binding.LOOP_PERSISTENT, dict(max_in_flight=1)))
+    for label, serve_mode, kw in runs:
         ctx = binding.Context(sprob, stream=stream.cuda_stream)
-        stop = dur if label == "continuous_batching" else min(dur, args.serve_plain_seconds)
+        ctx.set_async_warps(best["async_warps"])
+        stop = dur if label.startswith("continuous") else min(dur, args.serve_plain_seconds)
         r_list = [r for r in reqs if r[0] <= stop]
         res, summ, _ = ctx.serve(r_list, mode=serve_mode, chunk_iterations=args.serve_chunk, stop_admitting_s=stop + 0.5,
                                  **kw)
@@ -642,13 +648,14 @@ def run_extras(args, binding, stream, flush):
         done = res["done_s"] >= 0
         lat = (res["done_s"] - res["arrival_s"])[done]
         served[label] = dict(
-            offered_events=len(r_list), offered_rate=len(r_list) / stop, completed=int(done.sum()),
+            mode=serve_mode, offered_events=len(r_list), offered_rate=len(r_list) / stop, completed=int(done.sum()),
             sustained_rate=float(done.sum() / max(summ["wall_s"], 1e-9)), wall_s=summ["wall_s"],
             track_steps_per_s=summ["track_steps"] / max(summ["wall_s"], 1e-9),
             latency_ms=dict(p50=float(np.percentile(lat, 50) * 1e3), p95=float(np.percentile(lat, 95) * 1e3),
                             p99=float(np.percentile(lat, 99) * 1e3)) if len(lat) else None,
             window_s=stop)
-    out["serving"] = dict(rate_hz=rate, duration_s=dur, mode=serve_mode, chunk_iterations=args.serve_chunk, **served)
+    out["serving"] = dict(rate_hz=rate, duration_s=dur, chunk_iterations=args.serve_chunk,
+                          sort_policy=binding_name(sprob.sort_policy), **served)
     return out
 
 

@@ -222,10 +222,14 @@ enum {
                                 most its vacant slots; an entry's state word orders its writer and its
                                 reader). Histories are those of the synchronous modes (every track's random
                                 stream is keyed by its own id); tallies differ only in summation order.
-                                Runs to completion: celer_run_iterations rejects a budget, and no
-                                per-iteration trace or action count is recorded; the iteration count grows
-                                by the most passes any block ran. Waits are bounded: if no track steps for
-                                about 1 s the run ends with CELER_ERR_TIMEOUT or CELER_ERR_CAPACITY. */
+                                No per-iteration trace or action count is recorded; the iteration count
+                                grows by the most passes any block ran (pieces any warp ran, with per-warp
+                                scheduling, celer_set_async_warps). With a budget (celer_run_iterations) a
+                                block stops after that many passes, or, per warp, the block drains once a
+                                warp has run that many pieces: its queued tracks take their step without a
+                                new step limit, so every track ends the run between two steps, as after a
+                                synchronous iteration. Waits are bounded: if no track steps for about 1 s
+                                the run ends with CELER_ERR_TIMEOUT or CELER_ERR_CAPACITY. */
 };
 
 /* Step until no track is alive or queued, in one of the CELER_LOOP_* modes.

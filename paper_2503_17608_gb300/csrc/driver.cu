@@ -700,7 +700,6 @@ celer_status celer_run_iterations(celer_ctx* ctx, int mode, uint64_t budget, uin
   if (mode == CELER_LOOP_ASYNC) {
     if (!fused_local(ctx))
       return fail(ctx, CELER_ERR_INVALID, "the asynchronous loop needs a block-pass policy (local, data) without split actions");
-    if (budget != 0) return fail(ctx, CELER_ERR_INVALID, "the asynchronous loop runs to completion: budget must be 0");
   }
   // iteration budget of this run; last-block tickets start from zero (an
   // aborted run could leave them set)

@@ -2405,12 +2405,17 @@ __device__ __forceinline__ void wq_flush_counts(const Params& p, unsigned long l
 }
 
 // The per-warp loop of one block. live0: the block's live tracks at the
-// start (at most kWarpLive). Returns the most pieces any of its warps ran.
+// start (at most kWarpLive). A run with an iteration budget ends by draining:
+// once a warp has run `budget` pieces the block stops filling, its warps step
+// the queued tracks without computing new step limits (the survivors stay
+// alive in their slots, between two steps, as a synchronous iteration leaves
+// them), and every warp leaves when no track waits. Returns the most pieces
+// any of its warps ran.
 __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, const SharedStatic& ss, unsigned owned,
-                                              unsigned live0) {
+                                              unsigned live0, unsigned long long budget) {
   __shared__ unsigned s_q[(kLiveKeys + 1) * kWarpLive];
   __shared__ unsigned s_head[kLiveKeys + 1], s_tail[kLiveKeys + 1];
-  __shared__ unsigned s_live, s_filling, s_budget, s_exit;
+  __shared__ unsigned s_live, s_filling, s_budget, s_exit, s_drain;
   __shared__ unsigned long long s_pieces;
   Ctl* c = p.ctl;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (int)(blockDim.x >> 5);
@@ -2422,6 +2427,7 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
     s_filling = 0u;
     s_budget = kWarpLive - live0;  // free slots the block may hold
     s_exit = 0u;
+    s_drain = budget == 0ull ? 1u : 0u;
     s_pieces = 0ull;
   }
   __syncthreads();
@@ -2448,7 +2454,16 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
   unsigned long long seen = ~0ull;
   long long t_seen = clock64();
   for (;;) {
-    if (*reinterpret_cast<volatile unsigned*>(&s_exit) != 0u) break;
+    // the loop's flags, read by lane 0 and broadcast: every decision below
+    // must be the same for the whole warp (its lanes may arrive here
+    // diverged, and a lane leaving alone would strand the others' shuffles)
+    unsigned flags = 0;
+    if (lane == 0)
+      flags = (*reinterpret_cast<volatile unsigned*>(&s_exit) != 0u ? 1u : 0u) |
+              (*reinterpret_cast<volatile unsigned*>(&s_drain) != 0u ? 2u : 0u);
+    flags = __shfl_sync(0xffffffffu, flags, 0);
+    if (flags & 1u) break;
+    const bool drain = (flags & 2u) != 0u;
     // the kind with the most tracks waiting (lanes 0..7 look at one each)
     unsigned waiting = 0;
     if (lane < kLiveKeys) {
@@ -2473,7 +2488,8 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
     const unsigned live = *reinterpret_cast<volatile unsigned*>(&s_live);
     unsigned take = 0, f0 = 0;
     unsigned long long first = 0;
-    if (best < 32u && lane == 0 && atomicCAS(&s_filling, 0u, 1u) == 0u) {
+    if (drain && best == 0) break;  // budget spent and nothing queued: the block's tracks sit between steps
+    if (!drain && best < 32u && lane == 0 && atomicCAS(&s_filling, 0u, 1u) == 0u) {
       const unsigned free_now = *reinterpret_cast<volatile unsigned*>(&s_tail[kFreeQueue]) -
                                 *reinterpret_cast<volatile unsigned*>(&s_head[kFreeQueue]);
       const long long a = (long long)*reinterpret_cast<volatile unsigned long long*>(&c->avail);
@@ -2544,7 +2560,7 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
             ++killed;
             atomicSub(&s_live, 1u);
             wq_push(p, w, kFreeQueue, li);
-          } else {
+          } else if (!drain) {
             wq_requeue(p, w, ss, slot, li, steps);
           }
         }
@@ -2553,6 +2569,7 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
         wq_flush_counts(p, steps, killed, fill);
         steps = killed = fill = 0;
       }
+      if (pieces >= budget && lane == 0) atomicExch(&s_drain, 1u);
       if (pieces >= max_pieces && lane == 0) {
         atomicOr(&c->error, ERR_ITERATIONS);
         atomicExch(p.barrier + 2, 1u);
@@ -2568,6 +2585,8 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
     if (lane == 0) {
       if (*reinterpret_cast<volatile unsigned*>(p.barrier + 2) != 0u) {
         atomicExch(&s_exit, 1u);
+      } else if (budget != ~0ull && *reinterpret_cast<volatile unsigned*>(&s_live) == 0u) {
+        atomicExch(&s_drain, 1u);  // a budgeted run and no track here: the rest is left to the next run
       } else if (*reinterpret_cast<volatile unsigned*>(&s_live) == 0u) {
         const unsigned long long f = ld_acquire_u64(&c->finished);
         if (f == *reinterpret_cast<volatile unsigned long long*>(&c->tail)) atomicExch(&s_exit, 1u);
@@ -2625,6 +2644,8 @@ __global__ void __launch_bounds__(kTile, 1) k_loop_async(Params p) {
   const unsigned quota_cap = block_quota_cap(p.policy);
   unsigned long long passes = 0, seen = ~0ull;
   const unsigned long long max_passes = __ldcg(&c->max_iterations);  // per run
+  const unsigned long long budget_end = __ldcg(&c->budget_end);
+  const unsigned long long budget = budget_end == ~0ull ? ~0ull : budget_end - __ldcg(&c->iteration);
   long long t_seen = clock64();
   if (threadIdx.x == 0) {
     s_vtot = __ldcg(&p.block_vacant[bid]);
@@ -2639,7 +2660,7 @@ __global__ void __launch_bounds__(kTile, 1) k_loop_async(Params p) {
   // slot indices their 16 bits
   if (p.policy == POLICY_LOCAL && p.async_warps && owned - s_vtot <= kWarpLive && owned <= 0xFFFFu &&
       *reinterpret_cast<volatile unsigned*>(abort_word) == 0u) {
-    passes = warp_queue_loop(p, bid, nb, ss, owned, owned - s_vtot);
+    passes = warp_queue_loop(p, bid, nb, ss, owned, owned - s_vtot, budget);
     if (threadIdx.x == 0) s_vtot = p.block_vacant[bid];
   } else {
   // thread 0: no track anywhere stepped for ~1 s
@@ -2661,8 +2682,8 @@ __global__ void __launch_bounds__(kTile, 1) k_loop_async(Params p) {
       unsigned take = 0;
       unsigned long long first = 0;
       const unsigned vtot = s_vtot;
-      if (*reinterpret_cast<volatile unsigned*>(abort_word) != 0u) {
-        go = 0;
+      if (*reinterpret_cast<volatile unsigned*>(abort_word) != 0u || passes >= budget) {
+        go = 0;  // aborted, or the run's budget of passes is spent
       } else {
         // claim `want` written entries on the availability count (undone if
         // there were fewer), then their indices on the head: at least
@@ -2685,6 +2706,8 @@ __global__ void __launch_bounds__(kTile, 1) k_loop_async(Params p) {
         }
         if (take > 0 || vtot < owned) {
           go = 2;
+        } else if (budget != ~0ull) {
+          go = 0;  // a budgeted run: nothing here now, the rest is left to the next run
         } else {
           const unsigned long long f = ld_acquire_u64(&c->finished);
           if (f == *reinterpret_cast<volatile unsigned long long*>(&c->tail)) go = 0;  // every track has ended

@@ -24,10 +24,15 @@ def small_events(n_events=12, cap=60):
     return [e[:cap] for e in wl.offload_events(n_events)]
 
 
-@pytest.mark.parametrize("mode", [binding.LOOP_PERSISTENT, binding.LOOP_GRAPH])
-def test_served_events_match_alone(mode):
+@pytest.mark.parametrize("mode,policy", [(binding.LOOP_PERSISTENT, wl.SORT_ACTION_TYPE),
+                                         (binding.LOOP_GRAPH, wl.SORT_ACTION_TYPE),
+                                         (binding.LOOP_ASYNC, wl.SORT_LOCAL), (binding.LOOP_ASYNC, wl.SORT_DATA)])
+def test_served_events_match_alone(mode, policy):
+    """Chunks of the asynchronous loop end by draining (per-warp schedule)
+    or after whole passes, so events admitted between chunks see the same
+    histories as in the synchronous loops."""
     events = small_events()
-    prob = wl.calorimeter_problem(1 << 14, Bz=4.0, max_events=64, sort_policy=wl.SORT_ACTION_TYPE)
+    prob = wl.calorimeter_problem(1 << 14, Bz=4.0, max_events=64, sort_policy=policy)
     # arrivals close together so that events overlap on the device
     reqs = [(0.002 * i, int(e["event"][0]), e) for i, e in enumerate(events)]
     with binding.Context(prob) as ctx:
