@@ -2623,11 +2623,12 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
 // on where or when it runs (its random stream is keyed by its own id), so
 // histories are those of the synchronous loops; only the tally summation
 // order differs. The run ends when every track taken from the buffer has
-// ended (finished reaches tail). Every wait is bounded: a block with nothing
-// to do polls, and if no track anywhere steps for ~1 s it sets
-// ERR_NO_PROGRESS and the abort word; all blocks leave at their next pass.
-// The last block to leave adds the most passes any block ran to the
-// iteration count.
+// ended (finished reaches tail), or, with an iteration budget, when every
+// block has run that many passes or holds no track (warp_queue_loop: has
+// drained). Every wait is bounded: a block with nothing to do polls, and if
+// no track anywhere steps for ~1 s it sets ERR_NO_PROGRESS and the abort
+// word; all blocks leave at their next pass. The last block to leave adds
+// the most passes (pieces) any block ran to the iteration count.
 __global__ void __launch_bounds__(kTile, 1) k_loop_async(Params p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SharedStatic ss = carve_static(p, smem_raw);
