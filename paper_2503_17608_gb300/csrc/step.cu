@@ -2517,25 +2517,29 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
       atomicExch(&s_filling, 0u);
     }
     take = __shfl_sync(0xffffffffu, take, 0);
+    // this lane's track: a freshly filled one (step limit only) or one of a
+    // claimed piece (its step, then the step limit), both through one code
+    // path so that the step functions exist once in the loop
+    unsigned my_li = 0xFFFFFFFFu;
+    bool fresh = false;
+    unsigned n = 0;
     if (take > 0) {
       first = __shfl_sync(0xffffffffu, first, 0);
       f0 = __shfl_sync(0xffffffffu, f0, 0);
       if ((unsigned)lane < take) {
-        const unsigned li = wq_read(p, w, kFreeQueue, f0 + (unsigned)lane);
-        if (li != 0xFFFFFFFFu) {
-          const uint32_t slot = local_slot(li, bid, nb);
+        my_li = wq_read(p, w, kFreeQueue, f0 + (unsigned)lane);
+        if (my_li != 0xFFFFFFFFu) {
+          const uint32_t slot = local_slot(my_li, bid, nb);
           take_initializer<true>(p, first + (unsigned)lane, slot);
           atomicSub(&p.vacant[slot >> 5], 1u);
           atomicSub(&p.tile_vacant[slot >> 8], 1u);
           ++fill;
-          wq_requeue(p, w, ss, slot, li, steps);
+          fresh = true;
         }
       }
-      continue;
-    }
-    if (best > 0) {
-      // claim up to 32 tracks of kind best_k and step them
-      unsigned h = 0, n = 0;
+    } else if (best > 0) {
+      // claim up to 32 tracks of kind best_k
+      unsigned h = 0;
       if (lane == 0) {
         for (int a = 0; a < 8; ++a) {
           h = *reinterpret_cast<volatile unsigned*>(&s_head[best_k]);
@@ -2551,20 +2555,21 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
       n = __shfl_sync(0xffffffffu, n, 0);
       if (n == 0) continue;
       h = __shfl_sync(0xffffffffu, h, 0);
+      if ((unsigned)lane < n) my_li = wq_read(p, w, (int)best_k, h + (unsigned)lane);
+    }
+    if (take > 0 || n > 0) {
       unsigned long long n_def = 0;
-      if ((unsigned)lane < n) {
-        const unsigned li = wq_read(p, w, (int)best_k, h + (unsigned)lane);
-        if (li != 0xFFFFFFFFu) {
-          const uint32_t slot = local_slot(li, bid, nb);
-          if (step_one(p, slot, p.trk.status[slot], ss, true, n_def)) {
-            ++killed;
-            atomicSub(&s_live, 1u);
-            wq_push(p, w, kFreeQueue, li);
-          } else if (!drain) {
-            wq_requeue(p, w, ss, slot, li, steps);
-          }
+      if (my_li != 0xFFFFFFFFu) {
+        const uint32_t slot = local_slot(my_li, bid, nb);
+        if (!fresh && step_one(p, slot, p.trk.status[slot], ss, true, n_def)) {
+          ++killed;
+          atomicSub(&s_live, 1u);
+          wq_push(p, w, kFreeQueue, my_li);
+        } else if (fresh || !drain) {
+          wq_requeue(p, w, ss, slot, my_li, steps);
         }
       }
+      if (take > 0) continue;
       if ((++pieces & 15u) == 0) {  // the device counters every 16 pieces, and whenever the warp idles
         wq_flush_counts(p, steps, killed, fill);
         steps = killed = fill = 0;
