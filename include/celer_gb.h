@@ -248,7 +248,10 @@ celer_status celer_read_loop_profile(celer_ctx* ctx, uint64_t* cycles_out, int n
 /* As celer_run_events, but stop after at most `budget` more step iterations
  * (0: no limit); *done (nullable) receives the iterations run. A serving
  * loop uses this to return to the host between chunks of iterations, to
- * admit new events and collect finished ones while tracks stay resident. */
+ * admit new events and collect finished ones while tracks stay resident.
+ * In CELER_LOOP_ASYNC the budget counts each block's passes (or, with
+ * per-warp scheduling, each warp's pieces, after which the block drains);
+ * every track still ends the run between two steps. */
 celer_status celer_run_iterations(celer_ctx* ctx, int mode, uint64_t budget, uint64_t* done);
 
 /* Choose per-action launches (1) or per-phase launches (0) for the host and
