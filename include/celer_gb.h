@@ -466,6 +466,19 @@ celer_status celer_debug_slots(celer_ctx* ctx, uint8_t* status_out, uint8_t* pty
  * (error_bits and abort_word receive what the kernel left), CELER_OK if the
  * barrier passed, CELER_ERR_INVALID for bad arguments. Uses its own device
  * memory (allocated and freed here) and the legacy default stream. */
+/* Check of the bounded queue waits of the asynchronous loop (no counterpart
+ * in the paper): one thread waits for an entry to be written, either entry 0
+ * of a one-entry initializer buffer (which = 0 or 2) or an entry of a
+ * shared-memory queue of the per-warp schedule (which = 1 or 3). For
+ * which = 0, 1 nothing writes the entry: the wait must give up after
+ * timeout_cycles SM cycles (at most 4e9), set the abort word and the
+ * timeout error bit, and end, and the call returns CELER_ERR_TIMEOUT
+ * (error_bits and abort_word receive what the kernel left). For which = 2, 3
+ * the entry was written first, the wait passes and the call returns
+ * CELER_OK. CELER_ERR_INVALID for bad arguments. Uses its own device memory
+ * (allocated and freed here) and the legacy default stream. */
+celer_status celer_debug_queue_wait(int which, uint64_t timeout_cycles, uint32_t* error_bits, uint32_t* abort_word);
+
 celer_status celer_debug_barrier_timeout(int blocks, int absent_block, uint64_t timeout_cycles, uint32_t* error_bits,
                                          uint32_t* abort_word);
 

@@ -115,7 +115,7 @@ EXPORTS = [
     "celer_debug_philox", "celer_debug_curand_philox", "celer_partition_keys_noalloc", "celer_debug_math",
     "celer_run_iterations", "celer_read_event_live", "celer_serve", "celer_autotune", "celer_get_problem",
     "celer_debug_sample", "celer_debug_slots", "celer_set_hit_readout", "celer_set_grid_blocks",
-    "celer_set_parent_reuse", "celer_set_async_warps", "celer_debug_barrier_timeout",
+    "celer_set_parent_reuse", "celer_set_async_warps", "celer_debug_barrier_timeout", "celer_debug_queue_wait",
 ]
 
 _lib = None
@@ -163,6 +163,7 @@ def load(path: Optional[str] = None):
         "celer_set_parent_reuse": ([vp, i32], i32),
         "celer_set_async_warps": ([vp, i32], i32),
         "celer_debug_barrier_timeout": ([i32, i32, u64, C.POINTER(u32), C.POINTER(u32)], i32),
+        "celer_debug_queue_wait": ([i32, u64, C.POINTER(u32), C.POINTER(u32)], i32),
         "celer_partition_keys_noalloc": ([vp, u64, i32, i32, vp, vp, vp], i32),
         "celer_run_iterations": ([vp, i32, u64, C.POINTER(u64)], i32),
         "celer_read_event_live": ([vp, u32, u32, vp], i32),
@@ -548,4 +549,14 @@ def debug_barrier_timeout(blocks: int, absent_block: int, timeout_cycles: int):
     ab = C.c_uint32()
     st = load().celer_debug_barrier_timeout(int(blocks), int(absent_block), C.c_uint64(timeout_cycles), C.byref(err),
                                             C.byref(ab))
+    return st, err.value, ab.value
+
+
+def debug_queue_wait(which: int, timeout_cycles: int):
+    """Bounded wait of the asynchronous loop for a buffer entry (which 0, 2)
+    or a shared-memory queue entry (1, 3) that nothing writes (0, 1) or that
+    was written first (2, 3): returns (status, error bits, abort word)."""
+    err = C.c_uint32()
+    ab = C.c_uint32()
+    st = load().celer_debug_queue_wait(int(which), C.c_uint64(timeout_cycles), C.byref(err), C.byref(ab))
     return st, err.value, ab.value

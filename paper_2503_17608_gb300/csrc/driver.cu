@@ -1043,6 +1043,43 @@ celer_status celer_debug_barrier_timeout(int blocks, int absent_block, uint64_t 
   return (h.error & ERR_BARRIER_TIMEOUT) ? CELER_ERR_TIMEOUT : CELER_OK;
 }
 
+celer_status celer_debug_queue_wait(int which, uint64_t timeout_cycles, uint32_t* error_bits, uint32_t* abort_word) {
+  if (which < 0 || which > 3 || timeout_cycles == 0 || timeout_cycles > 4000000000ull || !error_bits || !abort_word)
+    return CELER_ERR_INVALID;
+  Ctl* d_ctl = nullptr;
+  unsigned* d_bar = nullptr;
+  uint32_t* d_state = nullptr;
+  celer_status st = CELER_OK;
+  if (cudaMalloc(&d_ctl, sizeof(Ctl)) != cudaSuccess || cudaMalloc(&d_bar, 4 * sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&d_state, sizeof(uint32_t)) != cudaSuccess)
+    st = CELER_ERR_CUDA;
+  if (st == CELER_OK && (cudaMemset(d_ctl, 0, sizeof(Ctl)) != cudaSuccess ||
+                         cudaMemset(d_bar, 0, 4 * sizeof(unsigned)) != cudaSuccess ||
+                         cudaMemset(d_state, 0, sizeof(uint32_t)) != cudaSuccess))
+    st = CELER_ERR_CUDA;
+  Params p{};
+  p.ctl = d_ctl;
+  p.barrier = d_bar;
+  p.ring_state = d_state;  // a one-entry buffer: entry 0, lap 0
+  p.ring_capacity = 1;
+  p.ring_mask = 0;
+  if (st == CELER_OK && (launch_queue_wait_probe(p, which, (long long)timeout_cycles, 0) != cudaSuccess ||
+                         cudaDeviceSynchronize() != cudaSuccess))
+    st = CELER_ERR_CUDA;
+  Ctl h{};
+  unsigned bar[4] = {0, 0, 0, 0};
+  if (st == CELER_OK && (cudaMemcpy(&h, d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess ||
+                         cudaMemcpy(bar, d_bar, sizeof(bar), cudaMemcpyDeviceToHost) != cudaSuccess))
+    st = CELER_ERR_CUDA;
+  if (d_ctl) cudaFree(d_ctl);
+  if (d_bar) cudaFree(d_bar);
+  if (d_state) cudaFree(d_state);
+  if (st != CELER_OK) return st;
+  *error_bits = h.error;
+  *abort_word = bar[2];
+  return (h.error & ERR_BARRIER_TIMEOUT) ? CELER_ERR_TIMEOUT : CELER_OK;
+}
+
 celer_status celer_debug_table(celer_ctx* ctx, int mat, int col, double* out) {
   if (!ctx || !out || mat < 0 || mat >= ctx->p.n_materials || col < 0 || col >= kCols) return CELER_ERR_INVALID;
   std::vector<double2> v(kGrid);

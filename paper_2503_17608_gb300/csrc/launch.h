@@ -50,6 +50,8 @@ cudaError_t launch_loop(const Params& p, const LaunchShape& sh, cudaStream_t s);
 // Asynchronous block loop (block-pass policies): the buffer entries' states,
 // then one cooperative launch; p.ring_state must be set.
 void launch_async_prepare(const Params& p, cudaStream_t s);
+// Check of the asynchronous loop's queue waits (k_queue_wait_probe).
+cudaError_t launch_queue_wait_probe(const Params& p, int which, long long timeout, cudaStream_t s);
 cudaError_t launch_loop_async(const Params& p, const LaunchShape& sh, cudaStream_t s);
 void launch_push_primaries(const Params& p, const StagedPrimary* d_prim, uint32_t n, cudaStream_t s);
 

@@ -83,9 +83,10 @@ __device__ __forceinline__ unsigned ring_lap_code(const Params& p, unsigned long
   return (unsigned)(index >> __popcll(p.ring_mask)) * 2u;
 }
 // Bounded wait of one thread for entry `index` to reach state `code`. After
-// ~1 s, or if another wait gave up first (abort word), it sets the abort word
-// and ERR_BARRIER_TIMEOUT and returns false.
-__device__ __noinline__ bool ring_wait(const Params& p, unsigned long long index, unsigned code) {
+// `timeout` cycles (~1 s by default), or if another wait gave up first (abort
+// word), it sets the abort word and ERR_BARRIER_TIMEOUT and returns false.
+__device__ __noinline__ bool ring_wait(const Params& p, unsigned long long index, unsigned code,
+                                       long long timeout = kBarrierTimeoutCycles) {
   const unsigned* st = p.ring_state + (index & p.ring_mask);
   if (ld_acquire_u32(st) == code) return true;
   unsigned* abort_word = p.barrier + 2;
@@ -94,7 +95,7 @@ __device__ __noinline__ bool ring_wait(const Params& p, unsigned long long index
     __nanosleep(32);
     if (ld_acquire_u32(st) == code) return true;
     if (*reinterpret_cast<volatile unsigned*>(abort_word) != 0u) return false;
-    if (clock64() - t0 > kBarrierTimeoutCycles) {
+    if (clock64() - t0 > timeout) {
       atomicExch(abort_word, 1u);
       atomicOr(&p.ctl->error, ERR_BARRIER_TIMEOUT);
       return false;
@@ -2322,13 +2323,16 @@ struct WarpQueues {
 };
 constexpr int kFreeQueue = kLiveKeys;
 
-__device__ __forceinline__ bool wq_wait(const Params& p, volatile unsigned* e, unsigned state) {
+// Bounded wait of one thread for a shared-memory queue entry to reach
+// `state` (as ring_wait).
+__device__ __forceinline__ bool wq_wait(const Params& p, volatile unsigned* e, unsigned state,
+                                        long long timeout = kBarrierTimeoutCycles) {
   if ((*e >> 16) == state) return true;
   const long long t0 = clock64();
   for (;;) {
     __nanosleep(20);
     if ((*e >> 16) == state) return true;
-    if (clock64() - t0 > kBarrierTimeoutCycles) {
+    if (clock64() - t0 > timeout) {
       atomicExch(p.barrier + 2, 1u);
       atomicOr(&p.ctl->error, ERR_BARRIER_TIMEOUT);
       return false;
@@ -2782,6 +2786,27 @@ __global__ void k_barrier_probe(Params p, int absent, long long timeout) {
   grid_barrier(p, gridDim.x, timeout);
 }
 
+// Check of the queue waits of the asynchronous loop: one thread waits for
+// an entry to be written, either buffer entry 0 (which = 0, 2) or an entry
+// of a shared-memory queue (which = 1, 3). For which = 0, 1 nothing writes
+// it, so the wait must give up after `timeout` cycles, set the abort word
+// and ERR_BARRIER_TIMEOUT; for which = 2, 3 it was written first and the
+// wait must pass.
+__global__ void k_queue_wait_probe(Params p, int which, long long timeout) {
+  __shared__ unsigned s_e;
+  if (threadIdx.x == 0) {
+    s_e = (which & 2) ? (1u << 16) : 0u;  // lap 0: 0 free, 1 written
+    if (which & 2) p.ring_state[0] = 1u;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (which & 1)
+      wq_wait(p, &s_e, 1u, timeout);
+    else
+      ring_wait(p, 0ull, 1u, timeout);
+  }
+}
+
 // Queue staged primaries at the tail of the initializer buffer.
 __global__ void __launch_bounds__(1024) k_push_primaries(Params p, const StagedPrimary* src, uint32_t n) {
   __shared__ unsigned long long s_base;
@@ -2929,6 +2954,10 @@ void launch_local_prepare(const Params& p, const LaunchShape& sh, cudaStream_t s
   k_local_prepare<<<sh.loop_grid, kTile, 0, s>>>(p);
 }
 void launch_scan_tiles(const Params& p, cudaStream_t s) { k_scan_tiles<<<1, kTile, 0, s>>>(p); }
+cudaError_t launch_queue_wait_probe(const Params& p, int which, long long timeout, cudaStream_t s) {
+  k_queue_wait_probe<<<1, 32, 0, s>>>(p, which, timeout);
+  return cudaGetLastError();
+}
 cudaError_t launch_barrier_probe(const Params& p, int blocks, int absent, long long timeout, cudaStream_t s) {
   void* args[] = {const_cast<Params*>(&p), &absent, &timeout};
   return cudaLaunchCooperativeKernel((const void*)k_barrier_probe, dim3(blocks), dim3(32), args, 0, s);
