@@ -2457,6 +2457,7 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
   const unsigned long long max_pieces = __ldcg(&c->max_iterations);  // per run
   unsigned long long seen = ~0ull;
   long long t_seen = clock64();
+  unsigned last_k = 0xFFu;  // the kind of the warp's last piece
   for (;;) {
     // the loop's flags, read by lane 0 and broadcast: every decision below
     // must be the same for the whole warp (its lanes may arrive here
@@ -2482,6 +2483,12 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
         best = ob;
         best_k = ok;
       }
+    }
+    {
+      // keep the kind this warp ran last while at least half as many of it
+      // wait: its code is still in the sub-partition's instruction cache
+      const unsigned w_last = __shfl_sync(0xffffffffu, waiting, last_k & 31u);
+      if (last_k < (unsigned)kLiveKeys && w_last > 0 && 2u * w_last >= best) best_k = last_k;
     }
     // fill (one warp at a time) when nothing waits, or when no full piece
     // waits and the block holds fewer than half its share of the tracks,
@@ -2558,6 +2565,7 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
       }
       n = __shfl_sync(0xffffffffu, n, 0);
       if (n == 0) continue;
+      last_k = best_k;
       h = __shfl_sync(0xffffffffu, h, 0);
       if ((unsigned)lane < n) my_li = wq_read(p, w, (int)best_k, h + (unsigned)lane);
     }
