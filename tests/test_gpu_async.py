@@ -271,3 +271,39 @@ def test_warp_scheduling_switch_is_validated():
         assert lib.celer_set_async_warps(ctx._h, 2) == 1
         assert lib.celer_set_async_warps(ctx._h, -1) == 1
         assert lib.celer_set_async_warps(ctx._h, 1) == 0
+
+
+def test_blocks_over_the_warp_queue_capacity_fall_back_to_passes():
+    """Per-warp scheduling holds at most 1024 live tracks per block: two
+    blocks that start the run with ~1500 each (left by one synchronous
+    iteration) run block passes instead, with the oracle's histories."""
+    prob = wl.water_cube_problem(n_slots=8192, history_capacity=3000, sort_policy=wl.SORT_LOCAL)
+    prim = wl.water_cube_primaries(3000)
+    with binding.Context(prob) as ctx:
+        ctx.set_grid_blocks(2)
+        ctx.add_events(prim)
+        ctx.run_iterations(binding.LOOP_PERSISTENT, budget=1)
+        assert ctx.stats()["alive"] > 2 * 1024
+        ctx.set_async_warps(True)
+        ctx.run_events(binding.LOOP_ASYNC)
+        hist, edep = ctx.read_history(0, len(prim))
+    o = run_oracle(prob, prim)
+    np.testing.assert_array_equal(hist["steps"], o["hist"]["steps"])
+    np.testing.assert_array_equal(hist["secondaries"], o["hist"]["secondaries"])
+    np.testing.assert_allclose(edep, o["edep"], rtol=1e-9, atol=1e-9 * 10.0)
+
+
+def test_blocks_owning_more_than_16_bit_slot_indices_fall_back_to_passes():
+    """One block owning 70,000 slots: its queue entries could not hold the
+    slot indices, so it runs block passes."""
+    prob = wl.water_cube_problem(n_slots=70000, history_capacity=500, sort_policy=wl.SORT_LOCAL)
+    prim = wl.water_cube_primaries(500)
+    with binding.Context(prob) as ctx:
+        ctx.set_grid_blocks(1)
+        ctx.set_async_warps(True)
+        ctx.add_events(prim)
+        ctx.run_events(binding.LOOP_ASYNC)
+        hist, edep = ctx.read_history(0, len(prim))
+    o = run_oracle(prob, prim)
+    np.testing.assert_array_equal(hist["steps"], o["hist"]["steps"])
+    np.testing.assert_allclose(edep, o["edep"], rtol=1e-9, atol=1e-9 * 10.0)
