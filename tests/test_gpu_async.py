@@ -277,13 +277,16 @@ def test_blocks_over_the_warp_queue_capacity_fall_back_to_passes():
     """Per-warp scheduling holds at most 1024 live tracks per block: two
     blocks that start the run with ~1500 each (left by one synchronous
     iteration) run block passes instead, with the oracle's histories."""
-    prob = wl.water_cube_problem(n_slots=8192, history_capacity=3000, sort_policy=wl.SORT_LOCAL)
-    prim = wl.water_cube_primaries(3000)
+    prob = wl.water_cube_problem(n_slots=16384, history_capacity=8000, sort_policy=wl.SORT_LOCAL)
+    prim = wl.water_cube_primaries(8000)
     with binding.Context(prob) as ctx:
         ctx.set_grid_blocks(2)
         ctx.add_events(prim)
         ctx.run_iterations(binding.LOOP_PERSISTENT, budget=1)
-        assert ctx.stats()["alive"] > 2 * 1024
+        state = ctx.debug_slots()
+        live = state["status"] != 0
+        owner = (np.arange(len(live)) // 32) % 2
+        assert min(live[owner == 0].sum(), live[owner == 1].sum()) > 1024
         ctx.set_async_warps(True)
         ctx.run_events(binding.LOOP_ASYNC)
         hist, edep = ctx.read_history(0, len(prim))
