@@ -799,7 +799,7 @@ DRAM_BYTES_PER_LAUNCH = {("calorimeter-1gev", "none"): 0.79e6, ("calorimeter-1ge
                          ("calorimeter-field-10gev", "none"): 28.26e6, ("calorimeter-field-10gev", "action_type"): 28.53e6,
                          ("calorimeter-field-10gev", "data"): 26.94e6, ("calorimeter-field-10gev", "local"): 24.50e6,
                          ("calorimeter-1gev", "local", "async"): 1.374e6, ("calorimeter-1gev", "data", "async"): 1.712e6,
-                         ("calorimeter-1gev", "local", "async-warps"): 4.515e6}
+                         ("calorimeter-1gev", "local", "async-warps"): 4.401e6}
 # FP64 peak of GB300: 2 DFMA per SM-cycle (ncu peak_sustained) x 152 SMs x 2.07 GHz x 2 flop
 FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
