@@ -62,10 +62,14 @@ __device__ __forceinline__ void flush_counter(unsigned long long* dst, unsigned 
 // Entry i of the buffer (stored at i & ring_mask) carries a state word: with
 // lap = i / capacity, 2 lap means free for the writer of i, 2 lap + 1 written
 // and not yet read, 2 lap + 2 read (free for the writer of i + capacity).
-// A writer reserves i on the tail only while i < head + capacity, so the
-// reader of i - capacity has reserved its entry already and every wait below
+// A writer reserves i on the tail only while i < head + capacity (head read
+// just before: by compare-and-swap, or by one atomic add while the room
+// exceeds what every thread of the grid could reserve at once), so the
+// reader of i - capacity has claimed its entry already and every wait below
 // is for a reservation that the other side completes without waiting on the
-// waiter: reads and writes follow their reservations directly.
+// waiter: reads and writes follow their claims and reservations directly.
+// Readers claim written entries on an availability count (avail) before
+// taking their indices from the head, so the head never passes the tail.
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* a) {
   unsigned v;
   asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
