@@ -62,11 +62,13 @@ __device__ __forceinline__ void flush_counter(unsigned long long* dst, unsigned 
 // Entry i of the buffer (stored at i & ring_mask) carries a state word: with
 // lap = i / capacity, 2 lap means free for the writer of i, 2 lap + 1 written
 // and not yet read, 2 lap + 2 read (free for the writer of i + capacity).
-// A writer reserves i on the tail only while i < head + capacity (head read
-// just before: by compare-and-swap, or by one atomic add while the room
-// exceeds what every thread of the grid could reserve at once), so the
-// reader of i - capacity has claimed its entry already and every wait below
-// is for a reservation that the other side completes without waiting on the
+// A writer reserves i on the tail only while i < head + capacity, with the
+// head read just before: by compare-and-swap, or by one atomic add while the
+// room exceeds what every thread of the grid could reserve at once (should
+// the buffer still fill within that window, the writer's wait below for the
+// entry's reader is bounded like every other). So the reader of
+// i - capacity has claimed its entry already, and every wait is for a claim
+// or reservation that the other side completes without waiting on the
 // waiter: reads and writes follow their claims and reservations directly.
 // Readers claim written entries on an availability count (avail) before
 // taking their indices from the head, so the head never passes the tail.
