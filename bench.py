@@ -218,6 +218,27 @@ def reduce_over_ranks(value, op_name, dist=None, device="cpu"):
 
 
 # ---------------------------------------------------------------- GPU
+def loop_keys_for(policy, loop_arg):
+    """Loops timed for a policy: the one named (the asynchronous loop only for
+    the block-pass policies, its per-warp schedule only for local), else the
+    persistent loop and, for the block-pass policies, the asynchronous one
+    (block passes, and for local per-warp scheduling too)."""
+    block_pass = (wl.SORT_LOCAL, wl.SORT_DATA)
+    if loop_arg != "auto":
+        key = loop_arg
+        if key.startswith("async") and policy not in block_pass:
+            key = "persistent"  # the policy comparison runs every policy
+        if key == "async-warps" and policy != wl.SORT_LOCAL:
+            key = "async"
+        return [key]
+    keys = ["persistent"]
+    if policy in block_pass:
+        keys.append("async")
+    if policy == wl.SORT_LOCAL:
+        keys.append("async-warps")
+    return keys
+
+
 def run_ours(args):
     import torch
 
@@ -261,22 +282,7 @@ def run_ours(args):
     block_pass = (wl.SORT_LOCAL, wl.SORT_DATA)
 
     def loops_for(pol):
-        """Loops timed for a policy: the one named, else the persistent loop
-        and, for the block-pass policies, the asynchronous one (block passes,
-        and for local per-warp scheduling too)."""
-        if args.loop != "auto":
-            key = args.loop
-            if key.startswith("async") and pol not in block_pass:
-                key = "persistent"  # the policy comparison runs every policy
-            if key == "async-warps" and pol != wl.SORT_LOCAL:
-                key = "async"
-            return [key]
-        keys = ["persistent"]
-        if pol in block_pass:
-            keys.append("async")
-        if pol == wl.SORT_LOCAL:
-            keys.append("async-warps")
-        return keys
+        return loop_keys_for(pol, args.loop)
 
     def timed_jobs(pol, key, split, steps, warmup, sample_clocks=False):
         """K whole jobs, primaries resident on the device; returns ms, steps, per-job ms."""

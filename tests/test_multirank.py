@@ -96,3 +96,32 @@ def test_bench_loop_keys_name_the_library_modes():
     assert bench.LOOP_KEYS["persistent"] == (binding.LOOP_PERSISTENT, False)
     assert bench.LOOP_KEYS["async"] == (binding.LOOP_ASYNC, False)
     assert bench.LOOP_KEYS["async-warps"] == (binding.LOOP_ASYNC, True)
+
+
+def test_bench_times_each_policy_in_its_loops():
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2503_17608_gb300 import workloads as wl
+
+    assert bench.loop_keys_for(wl.SORT_LOCAL, "auto") == ["persistent", "async", "async-warps"]
+    assert bench.loop_keys_for(wl.SORT_DATA, "auto") == ["persistent", "async"]
+    for pol in (wl.SORT_NONE, wl.SORT_ACTION, wl.SORT_ACTION_TYPE):
+        assert bench.loop_keys_for(pol, "auto") == ["persistent"]
+        assert bench.loop_keys_for(pol, "async-warps") == ["persistent"]
+    assert bench.loop_keys_for(wl.SORT_DATA, "async-warps") == ["async"]
+    assert bench.loop_keys_for(wl.SORT_LOCAL, "graph") == ["graph"]
+
+
+def test_bench_roofline_names_the_timed_kernel():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    r = bench.roofline_loop("calorimeter-1gev", "local", "async-warps", 454824.0, 2.0)
+    assert r["kernel"] == "k_loop_async" and r["bound"] == "alu"
+    assert r["traffic"] == bench.DRAM_BYTES_PER_LAUNCH[("calorimeter-1gev", "local", "async-warps")]
+    assert r["frac"] == r["achieved"] / r["peak"]
+    assert abs(r["achieved"] - 119.6 * 454824.0 / 2e-3 / 1e12) < 1e-12
+    assert bench.roofline_loop("calorimeter-1gev", "local", "persistent", 1.0, 1.0)["kernel"] == "k_loop_local"
+    assert bench.roofline_loop("calorimeter-1gev", "none", "persistent", 1.0, 1.0)["kernel"] == "k_loop"
+    # a reduced workload carries no traffic figure (the captures were of the full one)
+    assert bench.roofline_loop("calorimeter-1gev", "local", "async", 1.0, 1.0, full_size=False)["traffic"] is None
