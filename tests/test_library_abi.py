@@ -50,3 +50,20 @@ def test_status_strings():
     lib = binding.load()
     assert lib.celer_status_string(0) == b"ok"
     assert lib.celer_status_string(2) == b"capacity exceeded"
+
+
+@pytest.mark.parametrize("lang,std", [("c", "-std=c99"), ("c++", "-std=c++17")])
+def test_header_is_plain_c(tmp_path, lang, std):
+    """The boundary header compiles on its own as C99 and as C++ (no torch
+    or CUDA types in the signatures)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = tmp_path / ("use." + ("c" if lang == "c" else "cpp"))
+    src.write_text('#include "celer_gb.h"\nint main(void) { celer_tune_trial t; (void)t; return 0; }\n')
+    r = subprocess.run([cc, std, "-Wall", "-Werror", "-fsyntax-only", "-I", os.path.join(ROOT, "include"), str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
