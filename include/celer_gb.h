@@ -457,6 +457,15 @@ celer_status celer_debug_partition(celer_ctx* ctx, uint8_t* keys_out, uint32_t* 
  * charge partition of the fill (Sec. 3.2). */
 celer_status celer_debug_slots(celer_ctx* ctx, uint8_t* status_out, uint8_t* ptype_out, int* n_blocks);
 
+/* Per-slot track state into host arrays of n_slots entries: track id, event,
+ * layer, and state_out = 7 x n_slots doubles, column-major (x, y, z, ux, uy,
+ * uz, E; cm and MeV). Values of vacant slots are left over from their last
+ * track (celer_debug_slots gives the status). For the kernel-level parity
+ * test: one celer_step of primaries with given states against the oracle's
+ * single step of each. Synchronises the context's stream. */
+celer_status celer_debug_tracks(celer_ctx* ctx, uint64_t* tid_out, uint32_t* event_out, int32_t* layer_out,
+                                double* state_out);
+
 /* Check of the bounded waits of the persistent loops (no counterpart in the
  * paper): a cooperative launch of `blocks` (2-8) blocks meets at the loops'
  * grid barrier, which block `absent_block` never reaches (-1: every block

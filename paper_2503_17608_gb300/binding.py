@@ -116,6 +116,7 @@ EXPORTS = [
     "celer_run_iterations", "celer_read_event_live", "celer_serve", "celer_autotune", "celer_get_problem",
     "celer_debug_sample", "celer_debug_slots", "celer_set_hit_readout", "celer_set_grid_blocks",
     "celer_set_parent_reuse", "celer_set_async_warps", "celer_debug_barrier_timeout", "celer_debug_queue_wait",
+    "celer_debug_tracks",
 ]
 
 _lib = None
@@ -164,6 +165,7 @@ def load(path: Optional[str] = None):
         "celer_set_async_warps": ([vp, i32], i32),
         "celer_debug_barrier_timeout": ([i32, i32, u64, C.POINTER(u32), C.POINTER(u32)], i32),
         "celer_debug_queue_wait": ([i32, u64, C.POINTER(u32), C.POINTER(u32)], i32),
+        "celer_debug_tracks": ([vp, vp, vp, vp, vp], i32),
         "celer_partition_keys_noalloc": ([vp, u64, i32, i32, vp, vp, vp], i32),
         "celer_run_iterations": ([vp, i32, u64, C.POINTER(u64)], i32),
         "celer_read_event_live": ([vp, u32, u32, vp], i32),
@@ -449,6 +451,18 @@ class Context:
         _check(load().celer_debug_slots(self._h, status.ctypes.data, ptype.ctypes.data, C.byref(nb)), self._h)
         self._loop_blocks = nb.value
         return dict(status=status, ptype=ptype)
+
+    def debug_tracks(self):
+        """Per-slot track id, event, layer and state (x, y, z, ux, uy, uz, E)."""
+        n = self.prob.n_slots
+        tid = np.zeros(n, np.uint64)
+        event = np.zeros(n, np.uint32)
+        layer = np.zeros(n, np.int32)
+        state = np.zeros((7, n), np.float64)
+        _check(load().celer_debug_tracks(self._h, tid.ctypes.data, event.ctypes.data, layer.ctypes.data,
+                                         state.ctypes.data), self._h)
+        return dict(tid=tid, event=event, layer=layer, pos=state[0:3].T.copy(), dir=state[3:6].T.copy(),
+                    E=state[6].copy())
 
     def loop_blocks(self) -> int:
         """GPU blocks of the block-pass policies (block b owns chunks b, b + B, ...)."""

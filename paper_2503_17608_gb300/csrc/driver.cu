@@ -1009,6 +1009,22 @@ celer_status celer_debug_slots(celer_ctx* ctx, uint8_t* status_out, uint8_t* pty
   return CELER_OK;
 }
 
+celer_status celer_debug_tracks(celer_ctx* ctx, uint64_t* tid_out, uint32_t* event_out, int32_t* layer_out,
+                                double* state_out) {
+  if (!ctx || !tid_out || !event_out || !layer_out || !state_out) return CELER_ERR_INVALID;
+  const size_t N = ctx->p.n_slots;
+  const Tracks& t = ctx->p.trk;
+  CELER_CUDA(ctx, cudaMemcpyAsync(tid_out, t.tid, sizeof(uint64_t) * N, cudaMemcpyDeviceToHost, ctx->stream));
+  CELER_CUDA(ctx, cudaMemcpyAsync(event_out, t.event, sizeof(uint32_t) * N, cudaMemcpyDeviceToHost, ctx->stream));
+  CELER_CUDA(ctx, cudaMemcpyAsync(layer_out, t.layer, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, ctx->stream));
+  const double* cols[7] = {t.x, t.y, t.z, t.ux, t.uy, t.uz, t.E};
+  for (int k = 0; k < 7; ++k)
+    CELER_CUDA(ctx, cudaMemcpyAsync(state_out + (size_t)k * N, cols[k], sizeof(double) * N, cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+  CELER_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return CELER_OK;
+}
+
 celer_status celer_debug_barrier_timeout(int blocks, int absent_block, uint64_t timeout_cycles, uint32_t* error_bits,
                                          uint32_t* abort_word) {
   if (blocks < 2 || blocks > 8 || absent_block < -1 || absent_block >= blocks || timeout_cycles == 0 ||
