@@ -67,3 +67,27 @@ def test_header_is_plain_c(tmp_path, lang, std):
     r = subprocess.run([cc, std, "-Wall", "-Werror", "-fsyntax-only", "-I", os.path.join(ROOT, "include"), str(src)],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_argument_checks_before_any_device_call():
+    """Calls with a null context or out-of-range arguments return
+    CELER_ERR_INVALID from the host-side checks, before the device is
+    touched (so they run here, with no GPU)."""
+    import ctypes as C
+
+    lib = binding.load()
+    u32 = C.c_uint32()
+    INVALID = 1
+    assert lib.celer_set_async_warps(None, 1) == INVALID
+    assert lib.celer_set_parent_reuse(None, 1) == INVALID
+    assert lib.celer_set_grid_blocks(None, 2) == INVALID
+    assert lib.celer_run_events(None, binding.LOOP_ASYNC) == INVALID
+    assert lib.celer_run_iterations(None, binding.LOOP_ASYNC, 4, None) == INVALID
+    for which, timeout in ((-1, 1000), (4, 1000), (0, 0), (1, 5_000_000_000)):
+        assert lib.celer_debug_queue_wait(which, C.c_uint64(timeout), C.byref(u32), C.byref(u32)) == INVALID
+    assert lib.celer_debug_queue_wait(0, C.c_uint64(1000), None, None) == INVALID
+    for args in ((1, 0, 1000), (9, 0, 1000), (4, 4, 1000), (4, -2, 1000), (4, 0, 0)):
+        blocks, absent, timeout = args
+        assert lib.celer_debug_barrier_timeout(blocks, absent, C.c_uint64(timeout), C.byref(u32),
+                                               C.byref(u32)) == INVALID
+    assert lib.celer_debug_tracks(None, None, None, None, None) == INVALID
