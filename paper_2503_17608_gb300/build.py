@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libceler_gb.so")
 SOURCES = ["step.cu", "tables.cu", "driver.cu", "debug.cu", "noalloc.cu", "serve.cu"]
-HEADERS = ["common.cuh", "physics.cuh", "fastmath.cuh", "launch.h", "tables.h", "async_loop.cuh"]
+HEADERS = ["common.cuh", "physics.cuh", "fastmath.cuh", "launch.h", "tables.h", "block_pass.cuh", "async_loop.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
