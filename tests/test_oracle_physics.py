@@ -273,6 +273,36 @@ def lorentz_rhs(kappa):
     return f
 
 
+def test_rotation_frame_is_the_written_convention():
+    """The rotation frame (e1 = u x z / |u x z|, e2 = u x e1; along the z axis
+    e1 = x, e2 = u x x / |u x x|) fixes where the azimuth phi = 0 and pi/2
+    point: a reflected or rotated azimuth fails here.
+
+    u = x: u x z = (0, -1, 0) = e1, e2 = x x (0, -1, 0) = (0, 0, -1).
+    u = z: e1 = x, e2 = z x x = (0, 1, 0). u = -z: e2 = -z x x = (0, -1, 0).
+    u = y: e1 = y x z = (1, 0, 0), e2 = y x x = (0, 0, -1).
+    With cos(theta) = 0 the result is cos(phi) e1 + sin(phi) e2."""
+    cases = [((1.0, 0.0, 0.0), (0.0, -1.0, 0.0), (0.0, 0.0, -1.0)),
+             ((0.0, 0.0, 1.0), (1.0, 0.0, 0.0), (0.0, 1.0, 0.0)),
+             ((0.0, 0.0, -1.0), (1.0, 0.0, 0.0), (0.0, -1.0, 0.0)),
+             ((0.0, 1.0, 0.0), (1.0, 0.0, 0.0), (0.0, 0.0, -1.0))]
+    for u, e1, e2 in cases:
+        np.testing.assert_allclose(oracle.rotate(u, 0.0, 0.0), e1, atol=1e-15)
+        np.testing.assert_allclose(oracle.rotate(u, 0.0, np.pi / 2), e2, atol=1e-15)
+        np.testing.assert_allclose(oracle.rotate(u, 0.0, np.pi), -np.array(e1), atol=1e-15)
+        # cos(theta) = 1 leaves the direction alone, -1 reverses it
+        np.testing.assert_allclose(oracle.rotate(u, 1.0, 0.7), u, atol=1e-15)
+        np.testing.assert_allclose(oracle.rotate(u, -1.0, 0.7), -np.array(u), atol=1e-15)
+    # an oblique direction: e1 and e2 from the cross products, by hand
+    u = np.array([0.36, 0.48, 0.8])
+    n = np.hypot(u[0], u[1])
+    e1 = np.array([u[1], -u[0], 0.0]) / n
+    e2 = np.array([u[2] * u[0] / n, u[2] * u[1] / n, -n])
+    c, phi = 0.3, 1.1
+    want = c * u + np.sqrt(1 - c * c) * (np.cos(phi) * e1 + np.sin(phi) * e2)
+    np.testing.assert_allclose(oracle.rotate(u, c, phi), want, atol=1e-15)
+
+
 def test_helix_matches_equation_of_motion():
     from scipy.integrate import solve_ivp
     E, B = 7.0, 4.0

@@ -171,3 +171,61 @@ def test_field_substep_cap_splits_steps_and_conserves_energy():
     exact = int(hist_exact["steps"].sum())
     assert abs(steps[1 << 30] - exact) < 0.01 * exact
     assert steps[1 << 30] <= steps[50] < steps[3]
+
+
+def _first_steps(w, E0, n):
+    """Path length of each of the first n steps of a continuous-loss-only
+    electron (one thick layer, no discrete process: every step is range
+    limited), from cumulative one-step-at-a-time runs."""
+    paths, prev = [], 0.0
+    for k in range(1, n + 1):
+        r = w.transport_track(E0, (0.0, 0.0, 0.0), (0.0, 0.0, 1.0), wl.ELECTRON, max_steps=k)
+        if r["steps"] < k:
+            break
+        paths.append(r["path"] - prev)
+        prev = r["path"]
+    return paths, r
+
+
+def test_range_step_function_properties():
+    """The range step limit (alpha_r = 0.2, f_r = 0.1 cm) is fixed by properties
+    that any swap or misreading breaks:
+
+    * at or below f_r the whole residual range is one step (s = R);
+    * s is continuous at R = f_r (both sides give f_r);
+    * s / R -> alpha_r = 0.2 as R grows (R = 3009 cm at 10 GeV in LAr);
+    * a 1 MeV electron in LAr (R0 = 0.42431 cm, R(0.1 MeV) = 0.01473 cm) takes
+      exactly 3 steps. By hand: s1 = 0.2 R0 + 0.08 (2 - 0.1 / R0)
+      = 0.08486 + 0.14115 = 0.22601, R1 = 0.19830; s2 = 0.03966 + 0.11966
+      = 0.15932, R2 = 0.03898 <= 0.1; s3 = R2 and the track stops. With
+      alpha and f_r swapped it would take 2 steps (s1 = 0.31759, R1 = 0.10672 <= 0.2).
+    """
+    w = oracle.World(slab_problem(1e5, wl.LAR, wl.PROC_ELOSS, cut_track=0.1))
+    R = lambda E: w.lookup(0, oracle.COL_RANGE, E)  # noqa: E731
+    # s = R at and below f_r: one step ranges the electron out
+    for E0 in (0.15, 0.3):
+        assert R(E0) < 0.1
+        r = w.transport_track(E0, (0.0, 0.0, 0.0), (0.0, 0.0, 1.0), wl.ELECTRON)
+        assert r["steps"] == 1 and r["status"] == 0
+        assert r["path"] == pytest.approx(R(E0), rel=1e-12)
+    # continuity at f_r: energies whose range brackets 0.1 cm step by ~0.1 cm
+    from scipy.optimize import brentq
+    E_f = brentq(lambda E: R(E) - 0.1, 0.2, 1.0, xtol=1e-15)
+    for dE in (-1e-6, 1e-6):
+        paths, _ = _first_steps(w, E_f + dE, 1)
+        assert paths[0] == pytest.approx(0.1, abs=1e-5)
+    # s / R -> 0.2 for a long residual range
+    paths, _ = _first_steps(w, 1e4, 1)
+    assert R(1e4) > 1000.0
+    assert abs(paths[0] / R(1e4) - 0.2) < 1e-4
+    # the hand-derived sequence at 1 MeV
+    paths, r = _first_steps(w, 1.0, 5)
+    assert len(paths) == 3 and r["status"] == 0
+    np.testing.assert_allclose(paths[:2], [0.22601, 0.15932], atol=2e-5)
+    assert sum(paths) == pytest.approx(R(1.0), rel=1e-12)
+    # every range-limited step is shorter than the residual range
+    paths, _ = _first_steps(w, 50.0, 8)
+    Rk = R(50.0)
+    for s in paths:
+        assert 0.2 * Rk < s < Rk
+        Rk -= s
