@@ -26,7 +26,9 @@ constexpr int kNaMaxDevices = 64;
 // 16 x 4096 x 4 bytes = 256 KiB, held by every device that loads the library.
 __device__ __align__(256) uint32_t g_partition_scratch[kNaMaxKeys * kNaMaxTiles + kNaMaxKeys + 1];
 
-// Device address of g_partition_scratch per device ordinal, looked up once.
+// Device address of g_partition_scratch per device ordinal, looked up once
+// per process. cudaDeviceReset destroys the context this address belongs to,
+// so the entry point must not be called on a device after it was reset.
 uint32_t* g_scratch_ptr[kNaMaxDevices] = {};
 std::mutex g_scratch_mutex;
 
@@ -65,7 +67,8 @@ __global__ void __launch_bounds__(kNaTile) k_na_count(const uint8_t* keys, uint3
 
 // Pass 2 (one block): exclusive scan of the counts in key-major order, so
 // that entry (k, t) becomes the output position of tile t's first key-k slot;
-// offsets[k] = first position of key k, offsets[n_keys] = n.
+// offsets[k] = first position of key k, offsets[n_keys] = the number of slots
+// whose key is below n_keys (n when every key is in range).
 __global__ void __launch_bounds__(1024) k_na_scan(uint32_t* counts, int n_keys, uint32_t n_tiles, uint32_t* offsets) {
   __shared__ unsigned s_warp[32];
   __shared__ unsigned s_total;
@@ -132,15 +135,22 @@ __global__ void __launch_bounds__(kNaTile) k_na_scatter(const uint8_t* keys, uin
 
 extern "C" celer_status celer_partition_keys_noalloc(const uint8_t* d_keys, uint64_t n, int n_keys, int skip_key,
                                                      uint32_t* d_perm, uint32_t* d_offsets, void* cuda_stream) {
-  if (n == 0) return CELER_OK;
-  if (!d_keys || !d_perm || !d_offsets) return CELER_ERR_INVALID;
+  if (!d_offsets || (n > 0 && (!d_keys || !d_perm))) return CELER_ERR_INVALID;
   if (n > kNaMaxSlots || n_keys < 1 || n_keys > kNaMaxKeys || skip_key >= n_keys) return CELER_ERR_INVALID;
+  // An error left pending by earlier work on this thread is not ours to
+  // report or clear: launch nothing and leave it in place.
+  if (cudaPeekAtLastError() != cudaSuccess) return CELER_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (n == 0) {  // every offset is 0; d_perm is not touched
+    return cudaMemsetAsync(d_offsets, 0, sizeof(uint32_t) * (size_t)(n_keys + 1), s) == cudaSuccess ? CELER_OK
+                                                                                              : CELER_ERR_CUDA;
+  }
   uint32_t* scratch = nullptr;
   if (scratch_for_current_device(&scratch) != cudaSuccess) return CELER_ERR_CUDA;
-  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const uint32_t n_tiles = (uint32_t)((n + kNaTile - 1) / kNaTile);
   k_na_count<<<n_tiles, kNaTile, 0, s>>>(d_keys, (uint32_t)n, n_keys, n_tiles, scratch);
   k_na_scan<<<1, 1024, 0, s>>>(scratch, n_keys, n_tiles, d_offsets);
   k_na_scatter<<<n_tiles, kNaTile, 0, s>>>(d_keys, (uint32_t)n, n_keys, n_tiles, scratch, skip_key, d_perm);
+  // nothing was pending before the launches, so an error now is theirs
   return cudaGetLastError() == cudaSuccess ? CELER_OK : CELER_ERR_CUDA;
 }
