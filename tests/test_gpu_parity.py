@@ -18,6 +18,12 @@ pytestmark = pytest.mark.gpu
 
 POLICIES = [wl.SORT_NONE, wl.SORT_ACTION, wl.SORT_ACTION_TYPE, wl.SORT_LOCAL, wl.SORT_DATA]
 
+# Every calorimeter history matched the oracle in every recorded GPU run
+# (integer counts equal, deposits within 1e-9; match_fraction prints the
+# observed fraction), so all of them must: a lower fraction is a change in
+# the device arithmetic to be explained, not noise.
+CALORIMETER_MIN = 1.0
+
 
 @pytest.fixture(scope="module", autouse=True)
 def _cuda():
@@ -188,7 +194,7 @@ def test_calorimeter_histories(policy, mode):
     g = run_gpu(prob, prim, policy=policy, mode=mode, split=(mode == binding.LOOP_GRAPH))
     o = run_oracle(prob, prim)
     frac, _ = match_fraction(g, o)
-    assert frac >= 0.95, frac
+    assert frac >= CALORIMETER_MIN, frac
     assert_conservation(prim, g["tally"])
     np.testing.assert_allclose(g["hist"]["edep"] + g["hist"]["escaped"], prim["E"], rtol=1e-12)
 
@@ -223,7 +229,7 @@ def test_field_histories(policy, mode):
     g = run_gpu(prob, prim, policy=policy, mode=mode)
     o = run_oracle(prob, prim)
     frac, _ = match_fraction(g, o)
-    assert frac >= 0.9, frac
+    assert frac >= CALORIMETER_MIN, frac
     assert_conservation(prim, g["tally"])
 
 
@@ -239,7 +245,7 @@ def test_field_runge_kutta_substep_cap_histories(cap, policy):
     g = run_gpu(prob, prim, policy=policy)
     o = run_oracle(prob, prim)
     frac, _ = match_fraction(g, o)
-    assert frac >= 0.9, frac
+    assert frac >= CALORIMETER_MIN, frac
     assert_conservation(prim, g["tally"])
     if cap == 10:
         uncapped = run_oracle(prob.replace(field_substep_cap=1 << 30), prim)
@@ -276,7 +282,7 @@ def test_small_initializer_buffer_defers_without_changing_results(policy):
     g = run_gpu(prob, prim, policy=policy)
     o = run_oracle(prob, prim)
     frac, _ = match_fraction(g, o)
-    assert frac >= 0.9
+    assert frac >= CALORIMETER_MIN, frac
     assert_conservation(prim, g["tally"])
 
 
@@ -426,5 +432,5 @@ def test_parent_slot_reuse_keeps_histories(policy):
         g["hist"], g["edep"] = ctx.read_history(0, len(cprim))
         g["tally"] = {0: ctx.read_tallies(0)}
     frac, _ = match_fraction(g, run_oracle(cprob, cprim))
-    assert frac >= 0.95
+    assert frac >= CALORIMETER_MIN, frac
     assert_conservation(cprim, g["tally"])

@@ -1,0 +1,129 @@
+"""CUDA path vs oracle at the benchmark's own size and launch configuration,
+statistically on the full layer profiles, and in a narrow world where the
+field decides where tracks leave.
+
+* The 4 T calorimeter (10,000 x 10 GeV e-, 2^20 slots) in the benchmark's
+  headline loop (asynchronous loop, per-warp scheduling, block-local policy,
+  primaries queued from device memory): the first 1,000 histories against the
+  oracle one by one, energy conservation for all 10,000 histories, including
+  those a last-bit branch flip made differ, and for the event.
+* Layer profiles, 80 layers, GPU and oracle with independent seeds, per-layer
+  Welch tests and Hotelling's T^2, for the 1 GeV and the 4 T calorimeters.
+* A 4 cm x 4 cm world in 4 T with oblique primaries: the helix decides most
+  electron histories (the oracle's step counts change for ~60 % of them
+  without the field), so histories pin the helix and the side-plane distance
+  along many steps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2503_17608_gb300 import binding, workloads as wl
+
+from gpu_helpers import assert_conservation, assert_history_conservation, match_fraction, run_gpu, run_oracle
+from stats_helpers import layer_profile_tests
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    binding.load()
+
+
+def run_headline(prob, prim, policy=wl.SORT_LOCAL, mode=binding.LOOP_ASYNC, warps=True):
+    """One job as the benchmark times it: primaries queued from device memory,
+    then the loop; per-primary records kept."""
+    import torch
+
+    prob = prob.replace(sort_policy=policy, history_capacity=len(prim), max_events=1)
+    cprim = binding.to_c_primaries(prim)
+    dev = torch.from_numpy(cprim.view(np.uint8).copy()).cuda()
+    with binding.Context(prob) as ctx:
+        ctx.set_async_warps(warps)
+        ctx.reset_event(0)
+        ctx.add_primaries_device(0, dev.data_ptr(), len(prim))
+        ctx.run_events(mode)
+        hist, edep = ctx.read_history(0, len(prim))
+        tally = ctx.read_tallies(0)
+        stats = ctx.stats()
+    return dict(hist=hist, edep=edep, tally={0: tally}, stats=stats)
+
+
+# every history matched the oracle in every recorded run (match_fraction
+# prints the observed fraction), so all of them must
+FULL_SIZE_MIN = 1.0
+NARROW_MIN = 1.0
+
+
+def test_full_size_field_workload_in_headline_loop():
+    prob, prim = wl.calorimeter_field_10gev()
+    assert len(prim) == 10000 and prob.n_slots == 1 << 20
+    g = run_headline(prob, prim)
+    n_cmp = 1000
+    o = run_oracle(prob, prim[:n_cmp])
+    sub = dict(hist=g["hist"][:n_cmp], edep=g["edep"][:n_cmp])
+    frac, mask = match_fraction(sub, o)
+    assert frac >= FULL_SIZE_MIN, frac
+    # every history conserves energy, those that differ from the oracle too
+    assert_history_conservation(prim, g["hist"])
+    assert_conservation(prim, g["tally"])
+    assert g["stats"]["steps_total"] == int(g["hist"]["steps"].sum())
+    # the event tally is the sum of the histories
+    np.testing.assert_allclose(g["tally"][0][0], g["edep"].sum(0), rtol=1e-11, atol=1e-9)
+
+
+@pytest.mark.parametrize("workload", ["calorimeter-1gev", "calorimeter-field-10gev"])
+def test_layer_profiles_independent_seeds(workload):
+    """GPU seed 11 (headline loop) against oracle seed 12, 10,000 primaries
+    each, all 80 layers."""
+    if workload == "calorimeter-1gev":
+        prob, prim = wl.calorimeter_1gev(10000)
+    else:
+        prob, prim = wl.calorimeter_field_10gev()
+    g = run_headline(prob.replace(seed=11), prim)
+    o = run_oracle(prob.replace(seed=12), prim)
+    p_layer, p_t2, k = layer_profile_tests(g["edep"], o["edep"])
+    print(f"PROFILE {workload}: per-layer Bonferroni p = {p_layer:.3g}, Hotelling T^2 p = {p_t2:.3g}, {k} layers")
+    assert k == prob.n_layers_total
+    assert p_layer > 1e-3 and p_t2 > 1e-3, (p_layer, p_t2)
+
+
+def narrow_primaries(n=400, seed=5, event=0):
+    """Photons and electrons, 20 MeV - 2 GeV log-uniform, polar angles up to
+    60 degrees, start points uniform in a 3 cm x 3 cm patch."""
+    rng = np.random.default_rng(seed)
+    E = np.exp(rng.uniform(math.log(20.0), math.log(2000.0), n))
+    cost = rng.uniform(0.5, 1.0, n)
+    phi = rng.uniform(0.0, 2.0 * np.pi, n)
+    sint = np.sqrt(1.0 - cost * cost)
+    d = np.stack([sint * np.cos(phi), sint * np.sin(phi), cost], 1)
+    pos = np.zeros((n, 3))
+    pos[:, :2] = rng.uniform(-1.5, 1.5, (n, 2))
+    ptype = np.where(rng.uniform(size=n) < 0.5, wl.GAMMA, wl.ELECTRON).astype(np.int32)
+    return wl.make_primaries(E, pos, d, ptype, np.full(n, event, np.uint32))
+
+
+@pytest.mark.parametrize("policy,mode,warps", [(wl.SORT_LOCAL, binding.LOOP_ASYNC, True),
+                                               (wl.SORT_DATA, binding.LOOP_ASYNC, False),
+                                               (wl.SORT_ACTION_TYPE, binding.LOOP_PERSISTENT, False),
+                                               (wl.SORT_NONE, binding.LOOP_GRAPH, False)])
+def test_narrow_world_field_histories(policy, mode, warps):
+    prob = wl.calorimeter_problem(1 << 16, Bz=4.0, half_x=2.0, half_y=2.0)
+    prim = narrow_primaries()
+    g = run_headline(prob, prim, policy=policy, mode=mode, warps=warps)
+    o = run_oracle(prob, prim)
+    frac, mask = match_fraction(g, o)
+    assert frac >= NARROW_MIN, frac
+    np.testing.assert_allclose(g["hist"]["escaped"][mask], o["hist"]["escaped"][mask], rtol=1e-9, atol=1e-9)
+    assert_history_conservation(prim, g["hist"])
+    assert_conservation(prim, g["tally"])
+    # the field matters here: without it most electron histories change
+    o0 = run_oracle(prob.replace(Bz=0.0), prim)
+    el = prim["ptype"] == wl.ELECTRON
+    assert np.mean(o0["hist"]["steps"][el] != o["hist"]["steps"][el]) > 0.4
+    assert o["hist"]["escaped"].sum() > 0.05 * prim["E"].sum()

@@ -70,5 +70,6 @@ def test_one_step_matches_the_oracle_track_by_track(policy, Bz):
             good &= np.all(np.abs(tr["dir"][k] - np.array(r["dir"])) <= 1e-9)
             good &= tr["layer"][k] == r["layer"]
         ok += bool(good)
+    print(f"PARITY single step policy={policy} Bz={Bz}: {ok} of {n} tracks match the oracle", flush=True)
     # a last-bit difference of the math libraries may flip a rare tie
     assert ok >= n - 3, (ok, n)
