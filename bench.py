@@ -8,9 +8,12 @@ per second over K such jobs with the primaries already resident in HBM;
 ``e2e`` is the same through the host-pointer C ABI with the primaries copied
 from pinned host memory and the tallies copied back inside the timed region.
 
-Default workload: the lead/liquid-argon sampling calorimeter, 1,000 x 1 GeV
-electrons, 65,536 slots, no field; run with sorting on (partition by particle
-type and action) and off.
+Default workload: the lead/liquid-argon sampling calorimeter in a uniform
+4 T field along z, 10,000 x 10 GeV electrons over a 10 cm x 10 cm patch of
+the front face, 2^20 track slots; run with every sort policy (none, by
+action, by action and particle type, charge partition of the data, block-
+local grouping). The 1 GeV calorimeter without field, batched offload
+events, event-per-stream and Poisson-arrival serving are reported beside it.
 
 --impl reference times the CPU oracle (the plain history-based transport)
 on the host cores on a bounded sample of the same workload.
@@ -266,6 +269,10 @@ def run_ours(args):
 
     prob, prim, desc = make_workload(args.workload, args.primaries, args.slots)
     n = len(prim)
+    # the device's FP64 throughput (the ALU roofline's peak), measured here
+    fp64_tflops = None
+    if not args.no_fp64_probe:
+        fp64_tflops = max(binding.debug_fp64_rate()[0] for _ in range(3))
     cprim = binding.to_c_primaries(prim)
     dev_prim = torch.from_numpy(cprim.view(np.uint8).copy()).cuda()
     pinned = torch.empty(cprim.nbytes, dtype=torch.uint8, pin_memory=True)
@@ -450,7 +457,9 @@ def run_ours(args):
             part: {name: round(c / it / 2.07e3, 3) for name, c in vals.items()} for part, vals in prof.items()}
     job_ms = statistics.median(h["job_ms"])
     line["roofline"] = roofline_loop(args.workload, binding_name(headline), loop, steps_per_job, job_ms,
-                                     full_size=not (args.primaries or args.slots))
+                                     full_size=not (args.primaries or args.slots), fp64_measured=fp64_tflops,
+                                     sm_mhz=(clocks or {}).get("sm_mhz"),
+                                     sms=torch.cuda.get_device_properties(local).multi_processor_count)
     if launches_per_job:
         line["gpu_launches"] = int(launches_per_job * args.steps)
     if kt is not None:
@@ -478,44 +487,43 @@ def run_extras(args, binding, stream, flush):
     import torch
 
     out = {}
-    # --- 10,000 x 10 GeV e- in 4 T, 2^20 slots
-    prob2, prim2, desc2 = make_workload("calorimeter-field-10gev")
-    c2 = binding.to_c_primaries(prim2)
-    dev2 = torch.from_numpy(c2.view(np.uint8).copy()).cuda()
+    # --- 1,000 x 1 GeV e-, no field, 65,536 slots: every policy in the
+    # persistent loop, the block-pass policies in the asynchronous one
+    prob1, prim1, desc1 = make_workload("calorimeter-1gev")
+    c1 = binding.to_c_primaries(prim1)
+    dev1 = torch.from_numpy(c1.view(np.uint8).copy()).cuda()
     pol = {}
     runs = [(name, binding.LOOP_PERSISTENT) for name in ("action_type", "action", "none", "data", "local")]
     runs += [("data", binding.LOOP_ASYNC), ("local", binding.LOOP_ASYNC), ("local", "async-warps")]
     for name, mode in runs:
-        ctx = binding.Context(prob2.replace(sort_policy=wl.SORT_NAMES[name], max_events=1), stream=stream.cuda_stream)
+        ctx = binding.Context(prob1.replace(sort_policy=wl.SORT_NAMES[name], max_events=1), stream=stream.cuda_stream)
         label = name if mode == binding.LOOP_PERSISTENT else f"{name} ({mode if isinstance(mode, str) else 'async'} loop)"
         ctx.set_async_warps(mode == "async-warps")
         if mode == "async-warps":
             mode = binding.LOOP_ASYNC
         times, steps = [], 0
-        for rep in range(1 + args.extra_steps):
+        for rep in range(3 + 2 * args.extra_steps):
             flush.zero_()
             ctx.reset_event(rep)
             s0 = ctx.stats()["steps_total"]
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ctx.add_primaries_device(rep, dev2.data_ptr(), len(c2))
+            ctx.add_primaries_device(rep, dev1.data_ptr(), len(c1))
             ctx.run_events(mode)
             e1.record(stream)
             torch.cuda.synchronize()
-            if rep >= 1:
+            if rep >= 3:
                 times.append(e0.elapsed_time(e1))
                 steps += ctx.stats()["steps_total"] - s0
         it = ctx.stats()["iteration"]
-        prof = ctx.loop_profile() if mode == binding.LOOP_PERSISTENT else None
         ctx.close()
         ms = sum(times)
-        row = dict(value=steps / (ms / 1e3), ms_per_job=ms / len(times), track_steps_per_job=steps / len(times),
-                   iterations_per_job=it / (1 + args.extra_steps))
-        if prof is not None:
-            row["loop_profile_us_per_iteration"] = {
-                part: {k: round(v / max(it, 1) / 2.07e3, 2) for k, v in vals.items()} for part, vals in prof.items()}
-        pol[label] = row
-    out["calorimeter_field_10gev"] = dict(desc2, sorted_vs_unsorted=pol)
+        pol[label] = dict(value=steps / (ms / 1e3), ms_per_job=ms / len(times), track_steps_per_job=steps / len(times),
+                          iterations_per_job=it / (3 + 2 * args.extra_steps))
+    out["calorimeter_1gev"] = dict(desc1, sorted_vs_unsorted=pol)
+    prob2, prim2, desc2 = make_workload("calorimeter-field-10gev")
+    c2 = binding.to_c_primaries(prim2)
+    dev2 = torch.from_numpy(c2.view(np.uint8).copy()).cuda()
 
     # --- Runge-Kutta field propagation with a substep cap (paper Sec. 3.3, Fig. 2):
     # the 4 T workload with substeps of at most 0.1 rad, caps of 10^9 (none),
@@ -547,10 +555,7 @@ def run_extras(args, binding, stream, flush):
             iterations_per_job=iters / nrep)
     out["field_runge_kutta_substep_cap"] = dict(workload=desc2["workload"], substep_turn_rad=0.1, runs=rk)
 
-    # --- parent-slot reuse (paper Sec. 3.2) on the headline workload, per policy
-    prob1, prim1, _ = make_workload(args.workload)
-    c1 = binding.to_c_primaries(prim1)
-    dev1 = torch.from_numpy(c1.view(np.uint8).copy()).cuda()
+    # --- parent-slot reuse (paper Sec. 3.2) on the 1 GeV calorimeter, per policy
     reuse = {}
     for name in ("none", "data", "local"):
         row = {}
@@ -574,7 +579,7 @@ def run_extras(args, binding, stream, flush):
             ctx.close()
             row["reuse" if on else "queued"] = steps / (sum(times) / 1e3)
         reuse[name] = row
-    out["parent_slot_reuse"] = dict(workload=args.workload, track_steps_per_s=reuse)
+    out["parent_slot_reuse"] = dict(workload=desc1["workload"], track_steps_per_s=reuse)
 
     # --- 256 offload events: autotune on a sample, then all in one loop vs one by one
     events = wl.offload_events(256)
@@ -629,39 +634,50 @@ def run_extras(args, binding, stream, flush):
         speedup=t_seq / t_batch, max_rel_tally_diff_batched_vs_sequential=max_rel)
     out["event_per_stream"] = event_per_stream(binding, tuned, events[:64], seq_tallies[:64], flush)
 
-    # --- serving: Poisson arrivals of offload events
-    rate, dur = args.serve_rate, args.serve_seconds
-    arrivals = wl.poisson_arrivals(rate, dur)
-    sev = wl.offload_events(len(arrivals), first_event=0)
-    reqs = [(float(t), i, e) for i, (t, e) in enumerate(zip(arrivals, sev))]
-    served = {}
+    # --- serving: Poisson arrivals of offload events. The configured stream
+    # (2,000 events/s for 60 s) with continuous batching; then the capacity of
+    # the one-event-at-a-time loop (offered the same stream for a few seconds,
+    # its queue grows, so its sustained rate is its capacity), and both loops
+    # at 0.5x and 0.8x of that capacity, where both queues are stable and the
+    # latency percentiles describe a steady state
     sprob = tuned.replace(max_events=4096)
-    # continuous batching in the persistent loop and, for a block-pass policy,
-    # in the asynchronous loop (chunks of a budget of passes or pieces); the
-    # one-event-at-a-time baseline in the persistent loop
-    runs = [("continuous_batching", binding.LOOP_PERSISTENT, dict())]
-    if sprob.sort_policy in (wl.SORT_LOCAL, wl.SORT_DATA):
-        runs.append(("continuous_batching_async", binding.LOOP_ASYNC, dict()))
-    runs.append(("one_event_at_a_time", binding.LOOP_PERSISTENT, dict(max_in_flight=1)))
-    for label, serve_mode, kw in runs:
+    cb_mode = binding.LOOP_ASYNC if sprob.sort_policy in (wl.SORT_LOCAL, wl.SORT_DATA) else binding.LOOP_PERSISTENT
+
+    def serve_run(rate_hz, seconds, mode, max_in_flight=0):
+        arrivals = wl.poisson_arrivals(rate_hz, seconds)
+        sev = wl.offload_events(len(arrivals), first_event=0)
+        reqs = [(float(t), i, e) for i, (t, e) in enumerate(zip(arrivals, sev))]
         ctx = binding.Context(sprob, stream=stream.cuda_stream)
         ctx.set_async_warps(best["async_warps"])
-        stop = dur if label.startswith("continuous") else min(dur, args.serve_plain_seconds)
-        r_list = [r for r in reqs if r[0] <= stop]
-        res, summ, _ = ctx.serve(r_list, mode=serve_mode, chunk_iterations=args.serve_chunk, stop_admitting_s=stop + 0.5,
-                                 **kw)
+        res, summ, _ = ctx.serve(reqs, mode=mode, chunk_iterations=args.serve_chunk,
+                                 stop_admitting_s=seconds + 0.5, max_in_flight=max_in_flight)
         ctx.close()
         done = res["done_s"] >= 0
         lat = (res["done_s"] - res["arrival_s"])[done]
-        served[label] = dict(
-            mode=serve_mode, offered_events=len(r_list), offered_rate=len(r_list) / stop, completed=int(done.sum()),
+        return dict(
+            mode={binding.LOOP_PERSISTENT: "persistent", binding.LOOP_ASYNC: "async"}[mode],
+            offered_events=len(reqs), offered_rate=len(reqs) / seconds, completed=int(done.sum()),
             sustained_rate=float(done.sum() / max(summ["wall_s"], 1e-9)), wall_s=summ["wall_s"],
             track_steps_per_s=summ["track_steps"] / max(summ["wall_s"], 1e-9),
             latency_ms=dict(p50=float(np.percentile(lat, 50) * 1e3), p95=float(np.percentile(lat, 95) * 1e3),
                             p99=float(np.percentile(lat, 99) * 1e3)) if len(lat) else None,
-            window_s=stop)
-    out["serving"] = dict(rate_hz=rate, duration_s=dur, chunk_iterations=args.serve_chunk,
-                          sort_policy=binding_name(sprob.sort_policy), **served)
+            window_s=seconds)
+
+    served = {}
+    served["continuous_batching"] = serve_run(args.serve_rate, args.serve_seconds, cb_mode)
+    cap = serve_run(args.serve_rate, args.serve_plain_seconds, binding.LOOP_PERSISTENT, max_in_flight=1)
+    served["one_event_at_a_time_overloaded"] = cap
+    capacity = cap["sustained_rate"]
+    stable = {}
+    for frac in (0.5, 0.8):
+        r = frac * capacity
+        stable[f"{frac}x_capacity"] = dict(
+            offered_rate_hz=r,
+            one_event_at_a_time=serve_run(r, args.serve_stable_seconds, binding.LOOP_PERSISTENT, max_in_flight=1),
+            continuous_batching=serve_run(r, args.serve_stable_seconds, cb_mode))
+    out["serving"] = dict(rate_hz=args.serve_rate, duration_s=args.serve_seconds, chunk_iterations=args.serve_chunk,
+                          sort_policy=binding_name(sprob.sort_policy), one_event_at_a_time_capacity_hz=capacity,
+                          stable_queue_comparison=stable, **served)
     return out
 
 
@@ -806,13 +822,24 @@ DRAM_BYTES_PER_LAUNCH = {("calorimeter-1gev", "none"): 0.79e6, ("calorimeter-1ge
                          ("calorimeter-field-10gev", "data"): 26.94e6, ("calorimeter-field-10gev", "local"): 24.50e6,
                          ("calorimeter-1gev", "local", "async"): 1.374e6, ("calorimeter-1gev", "data", "async"): 1.712e6,
                          ("calorimeter-1gev", "local", "async-warps"): 4.401e6}
-# FP64 peak of GB300: 2 DFMA per SM-cycle (ncu peak_sustained) x 152 SMs x 2.07 GHz x 2 flop
+# FP64 warp instructions per track-step (sm__inst_executed_pipe_fp64 / track-steps)
+# of the loop kernel's one-launch ncu captures: an FP64 warp instruction holds
+# its sub-partition's FP64 pipe for 64 cycles whatever its active lanes, so
+# these set how busy the FP64 pipe is at a measured track-step rate.
+FP64_WARP_INSTR_PER_STEP = {("calorimeter-1gev", "local", "async-warps"): 21.3,
+                            ("calorimeter-field-10gev", "local", "async-warps"): 6.29}
+FP64_PIPE_CYCLES_PER_WARP_INSTR = 64.0
+# FP64 peak of GB300 derived from its unit counts: 2 DFMA per SM-cycle
+# (ncu peak_sustained) x 152 SMs x 2.07 GHz x 2 flop
 FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
 
-def roofline_loop(workload, policy, loop, steps_per_job, job_ms, full_size=True):
-    """Roofline of the dominant kernel, the persistent step-loop kernel (one
-    launch per job): FP64 ALU bound, with the HBM fraction beside it."""
+def roofline_loop(workload, policy, loop, steps_per_job, job_ms, full_size=True, fp64_measured=None, sm_mhz=None,
+                  sms=152):
+    """Roofline of the dominant kernel, the step-loop kernel (one launch per
+    job): FP64 ALU bound against the FP64 throughput measured on this device
+    in the same run (the derived peak beside it), with the FP64 pipe's busy
+    fraction and the HBM fraction."""
     peaks, kind = load_peaks()
     t = job_ms / 1e3
     key = (workload, policy) if not loop.startswith("async") else (workload, policy, loop)
@@ -824,13 +851,70 @@ def roofline_loop(workload, policy, loop, steps_per_job, job_ms, full_size=True)
         kernel = "k_loop_async"
     else:
         kernel = "k_loop_local" if policy in ("local", "data") else "k_loop"
-    return {"kernel": kernel, "bound": "alu", "achieved": flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": flops / FP64_PEAK_TFLOPS, "traffic": DRAM_BYTES_PER_LAUNCH.get(key) if full_size else None,
-            "peak_kind": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (probe measured 1.02 TFLOP/s)",
-            "fp64_flop_per_track_step": fpstep,
-            "hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
-                    "bytes_per_track_step": BYTES_PER_STEP, "peak_kind": kind},
-            "launch_ms": job_ms, "track_steps_per_launch": steps_per_job}
+    peak = fp64_measured if fp64_measured else FP64_PEAK_TFLOPS
+    out = {"kernel": kernel, "bound": "alu", "achieved": flops, "peak": peak, "unit": "TFLOP/s",
+           "frac": flops / peak, "traffic": DRAM_BYTES_PER_LAUNCH.get(key) if full_size else None,
+           "peak_kind": ("measured in this run: FP64 FMA chains on every SM (celer_debug_fp64_rate)"
+                         if fp64_measured else "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz"),
+           "peak_derived": FP64_PEAK_TFLOPS, "frac_of_derived": flops / FP64_PEAK_TFLOPS,
+           "fp64_flop_per_track_step": fpstep,
+           "hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                   "bytes_per_track_step": BYTES_PER_STEP, "peak_kind": kind},
+           "launch_ms": job_ms, "track_steps_per_launch": steps_per_job}
+    wi = FP64_WARP_INSTR_PER_STEP.get(key) if full_size else None
+    if wi is not None:
+        clock_hz = (sm_mhz or 2070.0) * 1e6
+        busy = wi * steps_per_job * FP64_PIPE_CYCLES_PER_WARP_INSTR / (t * 4 * sms * clock_hz)
+        out["fp64_pipe"] = {"warp_instr_per_track_step": wi, "busy_frac": busy,
+                            "how": "ncu FP64 warp instructions per track-step x 64 pipe cycles each x track-steps "
+                                   "per job / (job time x 4 sub-partitions x SMs x median SM clock)"}
+    return out
+
+
+def run_lane_counters(args):
+    """Mean active lanes per instrumented site for every (policy, loop) pair on
+    the workload, from the diagnostic build of the library (active-lane
+    counters compiled in; its timing is not a benchmark number). Prints one
+    JSON line."""
+    import torch
+
+    from paper_2503_17608_gb300 import binding, build
+
+    binding.load(build.build(lanes=True))
+    torch.cuda.set_device(0)
+    prob, prim, desc = make_workload(args.workload, args.primaries, args.slots)
+    cprim = binding.to_c_primaries(prim)
+    dev_prim = torch.from_numpy(cprim.view(np.uint8).copy()).cuda()
+    stream = torch.cuda.current_stream()
+    table = {}
+    for name in [p for p in args.policies.split(",") if p]:
+        pol = wl.SORT_NAMES[name]
+        for key in loop_keys_for(pol, args.loop):
+            mode, warps = LOOP_KEYS[key]
+            ctx = binding.Context(prob.replace(sort_policy=pol, max_events=1), stream=stream.cuda_stream)
+            ctx.set_async_warps(warps)
+            ctx.reset_event(0)
+            ctx.add_primaries_device(0, dev_prim.data_ptr(), len(prim))
+            ctx.run_events(mode)  # warm-up job
+            torch.cuda.synchronize()
+            binding.debug_lane_counts()  # clears
+            s0 = ctx.stats()["steps_total"]
+            ctx.reset_event(1)
+            ctx.add_primaries_device(1, dev_prim.data_ptr(), len(prim))
+            ctx.run_events(mode)
+            torch.cuda.synchronize()
+            counts = binding.debug_lane_counts()
+            steps = ctx.stats()["steps_total"] - s0
+            ctx.close()
+            row = {}
+            for site, (v, l, cyc) in counts.items():
+                if v == 0:
+                    continue
+                row[site] = dict(visits=v, mean_lanes=round(l / v, 3), per_track_step=round(v / max(steps, 1), 4))
+                if cyc:
+                    row[site]["mean_us"] = round(cyc / v / 2070.0, 3)
+            table[name + ("" if key == "persistent" else f" ({key} loop)")] = row
+    print(json.dumps({"lane_counters": table, "config": desc}), flush=True)
 
 
 def main():
@@ -839,7 +923,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="calorimeter-1gev",
+    ap.add_argument("--workload", default="calorimeter-field-10gev",
                     choices=["calorimeter-1gev", "calorimeter-field-10gev", "water-cube-10mev"])
     ap.add_argument("--policy", default="auto", choices=["auto"] + list(wl.SORT_NAMES))
     ap.add_argument("--split", action="store_true", help="one kernel per action in the host or graph loop")
@@ -855,13 +939,21 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=3.0)
     ap.add_argument("--reference-primaries", type=int, default=0)
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-fp64-probe", action="store_true", help="use the derived FP64 peak instead of measuring it")
     ap.add_argument("--extra-steps", type=int, default=2)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--serve-seconds", type=float, default=20.0)
-    ap.add_argument("--serve-plain-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-plain-seconds", type=float, default=3.0,
+                    help="window of the overloaded one-event-at-a-time run that measures its capacity")
+    ap.add_argument("--serve-stable-seconds", type=float, default=20.0,
+                    help="window of each run at 0.5x and 0.8x of the one-event-at-a-time capacity")
     ap.add_argument("--serve-chunk", type=int, default=8)
+    ap.add_argument("--lane-counters", action="store_true",
+                    help="print mean active lanes per site and policy from the diagnostic build, then exit")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.lane_counters:
+        run_lane_counters(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -170,14 +170,23 @@ const char* celer_status_string(celer_status s);
 /* Message of the last error on this context (static per context; "" if none). */
 const char* celer_last_error(const celer_ctx* ctx);
 
-/* Build a context: validate the problem, allocate the slot store, the
- * initializer buffer, tallies and history on the current CUDA device, and
- * build the cross-section, stopping-power and range tables on the device.
- * *out receives the context, or NULL on error. CELER_ERR_INVALID for an
- * inconsistent problem, CELER_ERR_CUDA if an allocation or launch fails. */
+/* Build a context (Sec. 2: the state of the active tracks is a struct of
+ * arrays with one entry per track slot, and new tracks wait in a separate
+ * buffer of track initializers): validate the problem, allocate the slot
+ * store (n_slots slots, one device array per field), the initializer buffer
+ * (init_capacity entries), tallies and history on the current CUDA device,
+ * and build the cross-section, stopping-power and range tables on the
+ * device. problem: host, read during the call only. *out receives the
+ * context, or NULL on error; the caller releases it with celer_destroy.
+ * CELER_ERR_INVALID for an inconsistent problem (nothing allocated),
+ * CELER_ERR_CUDA if an allocation or launch fails (everything allocated so
+ * far is released). */
 celer_status celer_create(const celer_problem* problem, celer_ctx** out);
 
-/* Release every resource of the context. NULL is allowed. */
+/* Release every resource of the context (Sec. 2: the track-slot store and
+ * the initializer buffer, with the tables, tallies and pinned staging
+ * memory): synchronises the context's stream, then frees. NULL is allowed;
+ * the pointer is invalid afterwards. */
 void celer_destroy(celer_ctx* ctx);
 
 /* Queue n primaries of one event as track initializers (Sec. 2: new tracks
@@ -232,9 +241,15 @@ enum {
                                 the run ends with CELER_ERR_TIMEOUT or CELER_ERR_CAPACITY. */
 };
 
-/* Step until no track is alive or queued, in one of the CELER_LOOP_* modes.
- * Returns CELER_ERR_TIMEOUT at max_iterations, CELER_ERR_CAPACITY if the
- * initializer buffer is full and no track can make progress. */
+/* Step until no track is alive or queued (Sec. 2: the outer loop over step
+ * iterations, each applying the actions in turn to all active tracks and
+ * refilling vacant slots from the initializer buffer; Sec. 3.4: all device
+ * work and copies stay ordered on the context's stream), in one of the
+ * CELER_LOOP_* modes. Synchronises the stream at the end. Returns
+ * CELER_ERR_TIMEOUT at max_iterations, CELER_ERR_CAPACITY if the initializer
+ * buffer is full and no track can make progress, CELER_ERR_INVALID for an
+ * unknown mode or one the sort policy does not allow; the state stays
+ * usable after each of these. */
 celer_status celer_run_events(celer_ctx* ctx, int mode);
 
 /* Profile of the persistent loop since creation, in SM cycles, n <= 10
@@ -259,7 +274,12 @@ celer_status celer_run_iterations(celer_ctx* ctx, int mode, uint64_t budget, uin
 celer_status celer_set_split_actions(celer_ctx* ctx, int split);
 
 /* Copy the energy-deposit tally of one event (n bins, n = the problem's bin
- * count) and its escaped energy into host memory. Synchronises the stream. */
+ * count) and its escaped energy into host memory: the detector hits that
+ * Sec. 3.4 moves from device to host with a stream-ordered copy, per event
+ * as in the mixed-event mode of Sec. 5.1. host_out: caller-owned, n doubles
+ * (pageable or pinned); escaped: nullable. The copy is stream ordered and
+ * the call then synchronises the context's stream only. n other than the
+ * bin count: CELER_ERR_INVALID. */
 celer_status celer_read_tallies(celer_ctx* ctx, uint32_t event, double* host_out, uint64_t n, double* escaped);
 
 /* Zero the tally row, escaped energy and live-track count of an event so
@@ -270,7 +290,12 @@ celer_status celer_reset_event(celer_ctx* ctx, uint32_t event);
 celer_status celer_event_live(celer_ctx* ctx, uint32_t event, uint64_t* live);
 
 /* Per-primary records [first, first + count) in the order primaries were
- * added; edep_out (nullable) receives count x n_bins deposits. */
+ * added (history_capacity > 0): steps, secondaries, escaped and deposited
+ * energy of each primary and all its descendants, the per-event results of
+ * Sec. 5.1 resolved by primary, read out as in Sec. 3.4 (stream-ordered copy,
+ * then the context's stream is synchronised). host_out: caller-owned, count
+ * records; edep_out (nullable): count x n_bins deposits, row-major. A range
+ * beyond the recorded primaries: CELER_ERR_INVALID. */
 celer_status celer_read_history(celer_ctx* ctx, uint64_t first, uint64_t count, celer_history* host_out,
                                 double* edep_out);
 
@@ -318,7 +343,9 @@ celer_status celer_set_parent_reuse(celer_ctx* ctx, int on);
  * of step (particle type and next action) from its block's queues in shared
  * memory, steps them, and queues the survivors again by their next kind. A
  * track then moves on as soon as its own step is done instead of waiting for
- * its block's slowest group. A block holds at most 1024 live tracks in this
+ * its block's slowest group. Charged tracks are taken before photons (their
+ * steps form a shower's longest chains), and all but the first two warps of
+ * a block take only full pieces of 32. A block holds at most 1024 live tracks in this
  * mode; a block that starts a run with more runs block passes. Histories do
  * not change. On by default. Takes effect at the next run. on outside
  * {0, 1}: CELER_ERR_INVALID. */
@@ -344,13 +371,19 @@ celer_status celer_kernel_timing(celer_ctx* ctx, const char** names, double* tot
  * host loop that cannot pay for cudaMalloc/cudaFree (cudaFree synchronises
  * the whole device).
  *
- * d_keys: n keys in device memory; keys not below n_keys are ignored.
- * d_perm: device output; the slots of every key except skip_key (-1: none)
- * in partition order. d_offsets: device output of n_keys + 1 entries, the
- * first position of each key and n_keys' total at the end (the counts
- * include skip_key's slots, which occupy the last positions if skip_key is
- * the largest key). Work is queued on cuda_stream (a cudaStream_t; NULL: the
- * legacy default stream); the call does not synchronise.
+ * d_keys: n keys in device memory; keys not below n_keys are ignored (they
+ * get no position). d_perm: device output; the slots of every key except
+ * skip_key (-1: none) in partition order; positions of skip_key's slots and
+ * positions from d_offsets[n_keys] on are left untouched. d_offsets: device
+ * output of n_keys + 1 entries: d_offsets[k] is the first position of key k
+ * and d_offsets[n_keys] the number of slots whose key is below n_keys (n
+ * when every key is in range). The counts include skip_key's slots, which
+ * occupy the last positions if skip_key is the largest key. n = 0 writes
+ * zeros to d_offsets and nothing else (d_keys and d_perm may then be NULL).
+ * Work is queued on cuda_stream (a cudaStream_t; NULL: the legacy default
+ * stream); the call does not synchronise. If a CUDA error from earlier work
+ * is pending on the calling thread, the call launches nothing, leaves that
+ * error pending and returns CELER_ERR_CUDA.
  *
  * Working memory is one fixed array inside the library (256 KiB per device
  * that loads it, held until the process exits): n <= 2^20, n_keys <= 16,
@@ -358,7 +391,8 @@ celer_status celer_kernel_timing(celer_ctx* ctx, const char** names, double* tot
  * calls whose work overlaps on the GPU (other streams, other host threads)
  * race and must be serialised by the caller. The first call on each device
  * looks up the array's device address with that device current; make that
- * first call before any stream capture. */
+ * first call before any stream capture. The address is kept for the life of
+ * the process, so do not call this after cudaDeviceReset on that device. */
 celer_status celer_partition_keys_noalloc(const uint8_t* d_keys, uint64_t n, int n_keys, int skip_key, uint32_t* d_perm,
                                           uint32_t* d_offsets, void* cuda_stream);
 
@@ -450,6 +484,26 @@ celer_status celer_autotune(const celer_problem* base, const celer_primary* prim
 celer_status celer_debug_partition(celer_ctx* ctx, uint8_t* keys_out, uint32_t* perm_out, uint32_t* offsets_out,
                                    int* n_keys, int* n_blocks);
 
+/* Active-lane counters of the diagnostic build (compiled with
+ * -DCELER_LANE_COUNTERS; the product build returns CELER_ERR_STATE). Sec. 3.1
+ * judges reordering by the thread divergence it removes; these counters
+ * measure it without a profiler. For each of the first min(n_max, 20) sites,
+ * host_out receives three values: warp-level visits, the lanes active at
+ * them summed (mean active lanes = lanes / visits), and the SM cycles spent
+ * there summed where the site is timed (0 elsewhere). Sites: 0-7 the
+ * per-warp pieces of the asynchronous loop by key (particle type and next
+ * action, in the order photon boundary, electron boundary, electron range,
+ * Compton, photoelectric, pair, Moller, brems; lanes = tracks claimed;
+ * timed from the claim to the survivors' requeue), 8 its fills (timed), 9
+ * the step limit, 10 the along-step, 11-15 the Compton, photoelectric, pair,
+ * Moller and brems interactions, 16 and 17 one rejection attempt of the
+ * Compton and Moller samplers, 18 the side-plane distance along the helix,
+ * 19 the per-warp loop's rounds that found nothing to do (timed).
+ * The counters cover every kernel launched since the last read on the
+ * current device and are cleared by the read. *n_out receives the sites
+ * written. Null pointers or n_max < 0: CELER_ERR_INVALID. */
+celer_status celer_debug_lane_counts(uint64_t* host_out, int n_max, int* n_out);  /* 3 x n_max values */
+
 /* Per-slot status (0 vacant, 1 alive, 2 waiting for buffer space) and
  * particle type (0 photon, 1 electron) into host arrays of n_slots bytes, and
  * the number of GPU blocks B of the block-pass policies (LOCAL, DATA): block b
@@ -512,6 +566,17 @@ celer_status celer_debug_curand_philox(uint64_t seed, uint64_t subsequence, uint
  * step kernels' elementary functions against the library's (accuracy about
  * 1 ulp). fn outside 0-11 or null pointers give CELER_ERR_INVALID. */
 celer_status celer_debug_math(int fn, const double* host_x, uint64_t n, double* host_out);
+
+/* Measure the device's FP64 throughput, the ceiling of the step kernels'
+ * arithmetic: blocks_per_sm x (SM count) blocks of 256 threads each run 8
+ * independent FP64 fused multiply-add chains for iters iterations, timed
+ * with CUDA events after one shorter warm-up launch on the legacy default
+ * stream. *tflops_out receives 2 x 8 x iters x threads / time in TFLOP/s,
+ * *ms_out (nullable) the timed launch's duration. No counterpart in the
+ * paper: it gives the measured peak beside the derived one. blocks_per_sm
+ * outside 1-8, iters 0 or above 2^32, or a null tflops_out:
+ * CELER_ERR_INVALID. Allocates and frees a small output buffer. */
+celer_status celer_debug_fp64_rate(int blocks_per_sm, uint64_t iters, double* tflops_out, double* ms_out);
 
 /* Draw one rejection sample per record on the device: which 0 the Compton
  * (Klein-Nishina, Butcher-Messel) sampler of the step kernels, which decides

@@ -116,7 +116,7 @@ EXPORTS = [
     "celer_run_iterations", "celer_read_event_live", "celer_serve", "celer_autotune", "celer_get_problem",
     "celer_debug_sample", "celer_debug_slots", "celer_set_hit_readout", "celer_set_grid_blocks",
     "celer_set_parent_reuse", "celer_set_async_warps", "celer_debug_barrier_timeout", "celer_debug_queue_wait",
-    "celer_debug_tracks",
+    "celer_debug_tracks", "celer_debug_fp64_rate", "celer_debug_lane_counts",
 ]
 
 _lib = None
@@ -167,6 +167,8 @@ def load(path: Optional[str] = None):
         "celer_debug_queue_wait": ([i32, u64, C.POINTER(u32), C.POINTER(u32)], i32),
         "celer_debug_tracks": ([vp, vp, vp, vp, vp], i32),
         "celer_partition_keys_noalloc": ([vp, u64, i32, i32, vp, vp, vp], i32),
+        "celer_debug_fp64_rate": ([i32, u64, C.POINTER(C.c_double), C.POINTER(C.c_double)], i32),
+        "celer_debug_lane_counts": ([vp, i32, C.POINTER(C.c_int)], i32),
         "celer_run_iterations": ([vp, i32, u64, C.POINTER(u64)], i32),
         "celer_read_event_live": ([vp, u32, u32, vp], i32),
         "celer_serve": ([vp, vp, u64, C.POINTER(celer_serve_options), vp, C.POINTER(celer_serve_summary)], i32),
@@ -488,6 +490,30 @@ def partition_keys_noalloc(d_keys: int, n: int, n_keys: int, skip_key: int, d_pe
     addresses (e.g. tensor.data_ptr())."""
     _check(load().celer_partition_keys_noalloc(C.c_void_p(d_keys), n, n_keys, skip_key, C.c_void_p(d_perm),
                                                C.c_void_p(d_offsets), C.c_void_p(stream) if stream else None))
+
+
+def debug_fp64_rate(blocks_per_sm: int = 4, iters: int = 40000):
+    """Measured FP64 fused multiply-add throughput of the device (TFLOP/s)
+    and the timed launch's milliseconds."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(load().celer_debug_fp64_rate(blocks_per_sm, iters, C.byref(tf), C.byref(ms)))
+    return tf.value, ms.value
+
+
+LANE_SITES = ["piece g_geom", "piece e_geom", "piece e_range", "piece compton", "piece pe", "piece pair",
+              "piece moller", "piece brems", "fill", "step_limit", "along", "compton", "photoelectric", "pair",
+              "moller", "brems", "compton_attempt", "moller_attempt", "helix_side", "idle"]
+
+
+def debug_lane_counts():
+    """Visits, summed active lanes and summed SM cycles (timed sites) per
+    instrumented site since the last read (the diagnostic build only):
+    {site: (visits, lanes, cycles)}."""
+    out = np.zeros(3 * 20, dtype=np.uint64)
+    n = C.c_int()
+    _check(load().celer_debug_lane_counts(out.ctypes.data, 20, C.byref(n)))
+    return {name: (int(out[3 * k]), int(out[3 * k + 1]), int(out[3 * k + 2]))
+            for k, name in enumerate(LANE_SITES[:n.value])}
 
 
 def autotune(prob: wl.Problem, primaries: np.ndarray, slot_counts, block_sizes, policies, modes, stream=None):

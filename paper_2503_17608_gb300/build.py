@@ -17,6 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libceler_gb.so")
+# diagnostic variant: the same library with the active-lane counters compiled in
+LANES_BUILD = os.path.join(HERE, "_build_lanes")
+LANES_LIB = os.path.join(HERE, "libceler_gb_lanes.so")
 SOURCES = ["step.cu", "tables.cu", "driver.cu", "debug.cu", "noalloc.cu", "serve.cu"]
 HEADERS = ["common.cuh", "physics.cuh", "fastmath.cuh", "launch.h", "tables.h", "block_pass.cuh", "async_loop.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -36,8 +39,13 @@ def _stale(out: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=None, lanes: bool = False) -> str:
+    """Compile the library (lanes=True: the diagnostic variant with the
+    active-lane counters, libceler_gb_lanes.so); returns its path."""
+    build_dir, lib = (LANES_BUILD, LANES_LIB) if lanes else (BUILD, LIB)
+    if lanes:
+        extra_flags = list(extra_flags or []) + ["-DCELER_LANE_COUNTERS"]
+    os.makedirs(build_dir, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "celer_gb.h")]
     common = [nvcc(), "-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
               "-Xptxas", "-warn-spills"] + list(extra_flags or [])
@@ -45,7 +53,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     objs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(build_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
             jobs.append(common + ["-c", s, "-o", o])
@@ -62,11 +70,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        run([nvcc(), "-shared", *ARCH, "-o", LIB + ".tmp", *objs, "-lcudart_static", "-lrt", "-lpthread", "-ldl"])
-        os.replace(LIB + ".tmp", LIB)
-    return LIB
+    if force or jobs or _stale(lib, objs):
+        run([nvcc(), "-shared", *ARCH, "-o", lib + ".tmp", *objs, "-lcudart_static", "-lrt", "-lpthread", "-ldl"])
+        os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, lanes="--lanes" in sys.argv))

@@ -66,6 +66,10 @@ constexpr unsigned kAsyncFill = 32;
 // with more runs block passes instead.
 constexpr unsigned kWarpLive = 1024;  // live tracks per block in this mode: capacity of each queue
 constexpr int kLiveKeys = 8;          // the (particle type, action) keys of live tracks, K_G_GEOM..K_E_BREMS
+// Warps of a block that take pieces of any size; the others take full pieces
+// only (2 measured fastest on the 4 T calorimeter; 3 is 1 % slower there and
+// 2 % faster on the 1 GeV one; 4 is 7 % slower there).
+constexpr int kAnyPieceWarps = 2;
 
 // Shared-memory queues: entry t of a queue (at t mod kWarpLive) holds a
 // 16-bit state in its high half (2 lap: free for its writer; 2 lap + 1:
@@ -227,6 +231,8 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
     flags = __shfl_sync(0xffffffffu, flags, 0);
     if (flags & 1u) break;
     const bool drain = (flags & 2u) != 0u;
+    const long long t_round = CELER_LANE_CLOCK();  // diagnostic build only
+    (void)t_round;
     // the kind with the most tracks waiting (lanes 0..7 look at one each)
     unsigned waiting = 0;
     if (lane < kLiveKeys) {
@@ -242,12 +248,36 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
         best_k = ok;
       }
     }
-    {
-      // keep the kind this warp ran last while at least half as many of it
-      // wait: its code is still in the sub-partition's instruction cache
-      const unsigned w_last = __shfl_sync(0xffffffffu, waiting, last_k & 31u);
-      if (last_k < (unsigned)kLiveKeys && w_last > 0 && 2u * w_last >= best) best_k = last_k;
+    // Charged tracks first: their steps carry a shower's longest chains of
+    // dependent steps (the primary crossing layer after layer and radiating),
+    // so the job ends sooner when they wait least; the photons' chains are
+    // shorter. The first kAnyPieceWarps warps take a piece of any size, the
+    // others only full ones, so that with few tracks alive a block's work is
+    // concentrated in full warps instead of spread over many part-filled
+    // ones. A warp keeps the kind it ran last while at least half as many of
+    // it wait, so that its code is still in the instruction cache.
+    unsigned eb = (lane == K_E_GEOM || lane == K_E_RANGE || lane == K_E_MOLLER || lane == K_E_BREMS) ? waiting : 0u;
+    unsigned ek = (unsigned)lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned ob = __shfl_xor_sync(0xffffffffu, eb, o), ok = __shfl_xor_sync(0xffffffffu, ek, o);
+      if (ob > eb || (ob == eb && ok < ek)) {
+        eb = ob;
+        ek = ok;
+      }
     }
+    const unsigned w_last = __shfl_sync(0xffffffffu, waiting, last_k & 31u);
+    const bool keep_last = last_k < (unsigned)kLiveKeys && w_last > 0 && 2u * w_last >= best;
+    // (while draining any warp takes any piece: a warp that leaves the loop
+    // may have been the last one allowed to take a small piece)
+    const unsigned min_piece = (drain || warp < kAnyPieceWarps) ? 1u : 32u;
+    unsigned pick_k = 0xFFu;
+    if (eb >= min_piece) {
+      pick_k = ek;
+    } else if (best >= min_piece) {
+      pick_k = (keep_last && w_last >= min_piece) ? last_k : best_k;
+    }
+    if (eb > 0) best = eb;  // fills count the charged tracks waiting first
     // fill (one warp at a time) when nothing waits, or when no full piece
     // waits and the block holds fewer than half its share of the tracks,
     // alive and queued, over all blocks (at least kAsyncFill): few tracks
@@ -276,6 +306,7 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
         const long long old = (long long)atomicAdd(&c->avail, 0ull - want);
         if (old >= (long long)want) {
           take = (unsigned)want;
+          CELER_LANES_N(LS_FILL, take);
           first = atomicAdd(&c->head, want);
           f0 = atomicAdd(&s_head[kFreeQueue], take);  // only the filler claims free slots
           atomicAdd(&s_live, take);
@@ -306,26 +337,27 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
           fresh = true;
         }
       }
-    } else if (best > 0) {
-      // claim up to 32 tracks of kind best_k
+    } else if (pick_k != 0xFFu) {
+      // claim up to 32 tracks of kind pick_k
       unsigned h = 0;
       if (lane == 0) {
         for (int a = 0; a < 8; ++a) {
-          h = *reinterpret_cast<volatile unsigned*>(&s_head[best_k]);
-          const unsigned q = *reinterpret_cast<volatile unsigned*>(&s_tail[best_k]) - h;
+          h = *reinterpret_cast<volatile unsigned*>(&s_head[pick_k]);
+          const unsigned q = *reinterpret_cast<volatile unsigned*>(&s_tail[pick_k]) - h;
           if (q == 0) break;
           const unsigned want = q < 32u ? q : 32u;
-          if (atomicCAS(&s_head[best_k], h, h + want) == h) {
+          if (atomicCAS(&s_head[pick_k], h, h + want) == h) {
             n = want;
+            CELER_LANES_N(LS_PIECE + (int)pick_k, n);
             break;
           }
         }
       }
       n = __shfl_sync(0xffffffffu, n, 0);
       if (n == 0) continue;
-      last_k = best_k;
+      last_k = pick_k;
       h = __shfl_sync(0xffffffffu, h, 0);
-      if ((unsigned)lane < n) my_li = wq_read(p, w, (int)best_k, h + (unsigned)lane);
+      if ((unsigned)lane < n) my_li = wq_read(p, w, (int)pick_k, h + (unsigned)lane);
     }
     if (take > 0 || n > 0) {
       unsigned long long n_def = 0;
@@ -339,6 +371,7 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
           wq_requeue(p, w, ss, slot, my_li, steps);
         }
       }
+      if (lane == 0) CELER_LANE_CYCLES(take > 0 ? LS_FILL : LS_PIECE + (int)pick_k, CELER_LANE_CLOCK() - t_round);
       if (take > 0) continue;
       if ((++pieces & 15u) == 0) {  // the device counters every 16 pieces, and whenever the warp idles
         wq_flush_counts(p, steps, killed, fill);
@@ -377,6 +410,8 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
         atomicExch(&s_exit, 1u);
       }
       __nanosleep(500);
+      CELER_LANES_N(LS_IDLE, 0u);
+      CELER_LANE_CYCLES(LS_IDLE, CELER_LANE_CLOCK() - t_round);
     }
     __syncwarp();
   }

@@ -215,4 +215,54 @@ struct Params {
   TraceRow* trace;
 };
 
+// ---- active-lane counters (diagnostic build only)
+// Built with -DCELER_LANE_COUNTERS, every site below counts its warp-level
+// visits and the lanes active at each visit (for the per-warp piece sites,
+// the tracks the piece holds), so that the mean active lanes per site show
+// how much each sort policy cuts divergence. The counters are spread over 16
+// copies by block to keep the atomics apart. The product build compiles every
+// site to nothing.
+enum LaneSite : int {
+  LS_PIECE = 0,        // + K_* key: per-warp pieces of the asynchronous loop (tracks claimed)
+  LS_FILL = 8,         // per-warp fills of the asynchronous loop (initializers taken)
+  LS_STEP_LIMIT = 9,   // step limit of a live track
+  LS_ALONG = 10,       // along-step
+  LS_COMPTON = 11, LS_PE = 12, LS_PAIR = 13, LS_MOLLER = 14, LS_BREMS = 15,
+  LS_COMPTON_TRY = 16, // one rejection attempt of the Compton sampler
+  LS_MOLLER_TRY = 17,  // one rejection attempt of the Moller sampler
+  LS_HELIX_SIDE = 18,  // side-plane distance along the helix
+  LS_IDLE = 19,        // per-warp loop rounds of the asynchronous loop that found nothing to do
+  kLaneSites = 20
+};
+constexpr int kLaneCopies = 16;
+constexpr int kLaneValues = 3;  // per site: visits, lanes, SM cycles (where timed)
+#ifdef CELER_LANE_COUNTERS
+static __device__ unsigned long long g_lane_counts[kLaneCopies][kLaneSites][kLaneValues];
+__device__ __forceinline__ void lane_site(int site) {
+  const unsigned m = __activemask();
+  if ((int)(threadIdx.x & 31u) == __ffs(m) - 1) {
+    unsigned long long* c = g_lane_counts[blockIdx.x % kLaneCopies][site];
+    atomicAdd(c, 1ull);
+    atomicAdd(c + 1, (unsigned long long)__popc(m));
+  }
+}
+__device__ __forceinline__ void lane_site_n(int site, unsigned n) {  // one thread, n lanes of work
+  unsigned long long* c = g_lane_counts[blockIdx.x % kLaneCopies][site];
+  atomicAdd(c, 1ull);
+  atomicAdd(c + 1, (unsigned long long)n);
+}
+__device__ __forceinline__ void lane_cycles(int site, long long cycles) {  // one thread
+  atomicAdd(&g_lane_counts[blockIdx.x % kLaneCopies][site][2], (unsigned long long)cycles);
+}
+#define CELER_LANES(site) ::celer::lane_site(site)
+#define CELER_LANES_N(site, n) ::celer::lane_site_n((site), (n))
+#define CELER_LANE_CLOCK() clock64()
+#define CELER_LANE_CYCLES(site, c) ::celer::lane_cycles((site), (c))
+#else
+#define CELER_LANES(site) ((void)0)
+#define CELER_LANES_N(site, n) ((void)0)
+#define CELER_LANE_CLOCK() 0ll
+#define CELER_LANE_CYCLES(site, c) ((void)0)
+#endif
+
 }  // namespace celer

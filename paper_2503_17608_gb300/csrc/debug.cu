@@ -82,6 +82,24 @@ __global__ void k_sample(int which, uint32_t seed, uint32_t event, const double*
   }
 }
 
+// FP64 throughput probe: every thread runs 8 independent fused multiply-add
+// chains, so the FP64 pipes never wait on a result. The sum is written only
+// if it equals an impossible value, which keeps the work alive.
+__global__ void __launch_bounds__(256) k_fp64_rate(uint64_t iters, double seed, double* out) {
+  double a[8];
+  const double b = 1.0 - 1e-9 * (double)(threadIdx.x & 7), c = 1e-12 * (double)threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = seed + j;
+  for (uint64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = fma(a[j], b, c);
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) sum += a[j];
+  if (sum == -1.0) out[blockIdx.x] = sum;
+}
+
 }  // namespace
 
 extern "C" {
@@ -192,6 +210,41 @@ celer_status celer_debug_sample(int which, uint32_t seed, uint32_t event, const 
   cudaFree(d_ctr);
   cudaFree(d_ctr_out);
   cudaFree(d_ok);
+  return st;
+}
+
+celer_status celer_debug_fp64_rate(int blocks_per_sm, uint64_t iters, double* tflops_out, double* ms_out) {
+  if (blocks_per_sm < 1 || blocks_per_sm > 8 || iters == 0 || iters > (1ull << 32) || !tflops_out)
+    return CELER_ERR_INVALID;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return CELER_ERR_CUDA;
+  const int grid = sms * blocks_per_sm;
+  double* d_out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  celer_status st = CELER_OK;
+  if (cudaMalloc(&d_out, sizeof(double) * grid) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess)
+    st = CELER_ERR_CUDA;
+  float ms = 0.0f;
+  if (st == CELER_OK) {
+    k_fp64_rate<<<grid, 256>>>(iters / 8 + 1, 1.0, d_out);  // warm-up
+    cudaEventRecord(e0);
+    k_fp64_rate<<<grid, 256>>>(iters, 1.0, d_out);
+    cudaEventRecord(e1);
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || ms <= 0.0f)
+      st = CELER_ERR_CUDA;
+  }
+  if (st == CELER_OK) {
+    const double flop = 2.0 * 8.0 * (double)iters * (double)grid * 256.0;
+    *tflops_out = flop / (ms * 1e-3) / 1e12;
+    if (ms_out) *ms_out = ms;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(d_out);
   return st;
 }
 

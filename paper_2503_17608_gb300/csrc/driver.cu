@@ -999,6 +999,19 @@ celer_status celer_debug_partition(celer_ctx* ctx, uint8_t* keys_out, uint32_t* 
   return CELER_OK;
 }
 
+celer_status celer_debug_lane_counts(uint64_t* host_out, int n_max, int* n_out) {
+  if (!host_out || !n_out || n_max < 0) return CELER_ERR_INVALID;
+  *n_out = 0;
+  const int n = n_max < celer::kLaneSites ? n_max : celer::kLaneSites;
+  std::vector<unsigned long long> v((size_t)celer::kLaneValues * celer::kLaneSites, 0ull);
+  const cudaError_t e = celer::read_lane_counts(v.data(), celer::kLaneSites);
+  if (e == cudaErrorNotSupported) return CELER_ERR_STATE;
+  if (e != cudaSuccess) return CELER_ERR_CUDA;
+  for (int k = 0; k < celer::kLaneValues * n; ++k) host_out[k] = v[k];
+  *n_out = n;
+  return CELER_OK;
+}
+
 celer_status celer_debug_slots(celer_ctx* ctx, uint8_t* status_out, uint8_t* ptype_out, int* n_blocks) {
   if (!ctx || !status_out || !ptype_out || !n_blocks) return CELER_ERR_INVALID;
   const uint32_t N = ctx->p.n_slots;

@@ -65,6 +65,11 @@ struct DevicePrimary {
 void launch_push_device_primaries(const Params& p, const DevicePrimary* src, uint32_t n, uint32_t event,
                                   unsigned long long tid0, uint32_t prim0, cudaStream_t s);
 
+// Active-lane counters of the instrumented build (-DCELER_LANE_COUNTERS):
+// 3 x n_sites values (visits, lanes, cycles) summed over the copies, then
+// cleared; cudaErrorNotSupported in the product build.
+cudaError_t read_lane_counts(unsigned long long* host_out, int n_sites);
+
 const char* kernel_name(int id);
 enum KernelId : int {
   KID_FILL_STEP = 0, KID_SCATTER, KID_STEP, KID_FILL, KID_PRE_STEP, KID_ALONG_NEUTRAL, KID_ALONG_CHARGED,

@@ -178,6 +178,7 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
                                               const int32_t* lmat) {
   const Tracks& t = p.trk;
   const double E = t.E[slot];
+  CELER_LANES(LS_STEP_LIMIT);
   const uint8_t pt = t.ptype[slot];
   const int layer = t.layer[slot];
   double nmfp = t.nmfp[slot];
@@ -185,8 +186,8 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
   if (nmfp < 0.0) nmfp = -fast_log(rng.uniform(), p.mtab);
 
   const double2* mt = tab + lmat[layer] * (kCols * kGrid);
-  const GridPos g = grid_pos(E, p.lnEmin, p.inv_dl, p.mtab);
   const bool charged = pt != GAMMA;
+  const GridPos g = grid_pos(E, p.lnEmin, p.inv_dl, p.mtab);
   double mu0, mu1, mu2 = 0.0;
   if (!charged) {
     mu0 = interp(mt + COL_COMPTON * kGrid, g);
@@ -778,6 +779,7 @@ __device__ void phase_scatter(const Params& p, int bid, int nb) {
 // or escape through a z-plane, escape through a side plane, tracking cut.
 // Returns true if the track ended.
 __device__ __forceinline__ bool along_one(const Params& p, uint32_t slot, uint8_t pt, const SharedStatic& ss) {
+  CELER_LANES(LS_ALONG);
   const Tracks& t = p.trk;
   const bool charged = pt != GAMMA;
   const uint8_t act = t.action[slot];
@@ -856,6 +858,7 @@ __device__ __forceinline__ bool along_one(const Params& p, uint32_t slot, uint8_
 // Compton scattering: Klein-Nishina sampling, the recoil energy deposited
 // locally, the photon rotated; below the tracking cut it is absorbed.
 __device__ __forceinline__ bool compton_one(const Params& p, uint32_t slot) {
+  CELER_LANES(LS_COMPTON);
   const Tracks& t = p.trk;
   const double E = t.E[slot];
   const uint32_t ev = t.event[slot], prim = t.primary[slot];
@@ -892,6 +895,7 @@ __device__ __forceinline__ bool compton_one(const Params& p, uint32_t slot) {
 
 // Photoelectric absorption: all energy deposited locally.
 __device__ __forceinline__ bool photoelectric_one(const Params& p, uint32_t slot) {
+  CELER_LANES(LS_PE);
   const Tracks& t = p.trk;
   const uint32_t ev = t.event[slot];
   deposit(p, ev, t.primary[slot], t.layer[slot], t.z[slot], t.E[slot]);
@@ -978,6 +982,7 @@ __device__ __forceinline__ void defer_track(const Params& p, uint32_t slot, uint
 // two photons of m_e c^2 back to back in an isotropic direction.
 __device__ __forceinline__ bool pair_one(const Params& p, uint32_t slot, uint8_t st, bool tight,
                                          unsigned long long& n_def) {
+  CELER_LANES(LS_PAIR);
   const Tracks& t = p.trk;
   const bool keep = kMe >= p.cut_track;
   const bool reuse = keep && p.reuse_parent != 0;  // the first photon takes the parent's slot
@@ -1035,6 +1040,7 @@ __device__ __forceinline__ bool pair_one(const Params& p, uint32_t slot, uint8_t
 // energy-momentum conservation, primary from momentum conservation).
 __device__ __forceinline__ bool moller_one(const Params& p, uint32_t slot, uint8_t st, bool tight,
                                            unsigned long long& n_def) {
+  CELER_LANES(LS_MOLLER);
   const Tracks& t = p.trk;
   const double T = t.E[slot];
   if (T <= 2.0 * p.cut_moller) {  // kinematically closed at the post-step energy: null collision
@@ -1103,6 +1109,7 @@ __device__ __forceinline__ bool moller_one(const Params& p, uint32_t slot, uint8
 // along the parent direction; the parent keeps its direction.
 __device__ __forceinline__ bool brems_one(const Params& p, uint32_t slot, uint8_t st, bool tight,
                                           unsigned long long& n_def) {
+  CELER_LANES(LS_BREMS);
   const Tracks& t = p.trk;
   const double T = t.E[slot];
   if (T <= p.cut_brems) {  // null collision
@@ -1781,6 +1788,30 @@ const char* kernel_name(int id) {
                                          "along_charged", "compton", "photoelectric", "pair", "moller", "brems",
                                          "loop_ctl", "loop", "local"};
   return (id >= 0 && id < KID_COUNT) ? names[id] : "?";
+}
+
+// Active-lane counters of the instrumented build: per site, visits and lanes
+// summed over the copies, then cleared. Without the instrumentation there
+// is nothing to read.
+cudaError_t read_lane_counts(unsigned long long* host_out, int n_sites) {
+#ifdef CELER_LANE_COUNTERS
+  unsigned long long all[kLaneCopies][kLaneSites][kLaneValues];
+  cudaError_t e = cudaMemcpyFromSymbol(all, g_lane_counts, sizeof(all));
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < n_sites && k < kLaneSites; ++k) {
+    for (int j = 0; j < kLaneValues; ++j) {
+      unsigned long long v = 0;
+      for (int c = 0; c < kLaneCopies; ++c) v += all[c][k][j];
+      host_out[kLaneValues * k + j] = v;
+    }
+  }
+  static const unsigned long long zeros[kLaneCopies][kLaneSites][kLaneValues] = {};
+  return cudaMemcpyToSymbol(g_lane_counts, zeros, sizeof(zeros));
+#else
+  (void)host_out;
+  (void)n_sites;
+  return cudaErrorNotSupported;
+#endif
 }
 
 }  // namespace celer

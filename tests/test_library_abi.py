@@ -18,7 +18,7 @@ def declared_symbols():
         if fn.endswith(".h"):
             text = open(os.path.join(inc, fn)).read()
             text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-            names.update(re.findall(r"\b(celer_[a-z_]+)\s*\(", text))
+            names.update(re.findall(r"\b(celer_[a-z0-9_]+)\s*\(", text))
     return names
 
 
