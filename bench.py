@@ -801,11 +801,11 @@ def load_peaks():
 # Per track-step figures of the whole step loop (all phases of an iteration):
 # algorithmic state bytes (state read and written back once per step, without
 # secondaries or scratch) and thread-level FP64 operations
-# (2 x DFMA + DADD + DMUL) counted by ncu on the persistent loop kernel
-# (the ncu summaries committed beside this script, one per kernel and workload);
-# DRAM bytes per launch of that kernel from the same captures, for the
-# workloads that were captured whole. Keys: (workload, policy), and
-# (workload, policy, "async") for the asynchronous loop kernel.
+# (2 x DFMA + DADD + DMUL) counted by ncu on the loop kernels (the ncu
+# summaries under profiles/, one per kernel and workload). DRAM bytes per
+# launch come from a one-pass full-size capture of the current headline
+# kernel only; other kernels report no traffic. Keys: (workload, policy), and
+# (workload, policy, loop) for the asynchronous loop kernel.
 BYTES_PER_STEP = 160.0
 FP64_FLOP_PER_STEP = {("calorimeter-1gev", "none"): 131.0, ("calorimeter-1gev", "action"): 131.0,
                       ("calorimeter-1gev", "action_type"): 131.0, ("calorimeter-1gev", "data"): 119.5,
@@ -816,18 +816,12 @@ FP64_FLOP_PER_STEP = {("calorimeter-1gev", "none"): 131.0, ("calorimeter-1gev", 
                       ("calorimeter-1gev", "local", "async"): 119.5, ("calorimeter-1gev", "data", "async"): 119.5,
                       ("calorimeter-1gev", "local", "async-warps"): 119.6,
                       ("water-cube-10mev", None): 119.5}
-DRAM_BYTES_PER_LAUNCH = {("calorimeter-1gev", "none"): 0.79e6, ("calorimeter-1gev", "action_type"): 0.94e6,
-                         ("calorimeter-1gev", "data"): 1.64e6, ("calorimeter-1gev", "local"): 1.42e6,
-                         ("calorimeter-field-10gev", "none"): 28.26e6, ("calorimeter-field-10gev", "action_type"): 28.53e6,
-                         ("calorimeter-field-10gev", "data"): 26.94e6, ("calorimeter-field-10gev", "local"): 24.50e6,
-                         ("calorimeter-1gev", "local", "async"): 1.374e6, ("calorimeter-1gev", "data", "async"): 1.712e6,
-                         ("calorimeter-1gev", "local", "async-warps"): 4.401e6}
+DRAM_BYTES_PER_LAUNCH = {("calorimeter-field-10gev", "local", "async-warps"): 41.96e6}
 # FP64 warp instructions per track-step (sm__inst_executed_pipe_fp64 / track-steps)
 # of the loop kernel's one-launch ncu captures: an FP64 warp instruction holds
 # its sub-partition's FP64 pipe for 64 cycles whatever its active lanes, so
 # these set how busy the FP64 pipe is at a measured track-step rate.
-FP64_WARP_INSTR_PER_STEP = {("calorimeter-1gev", "local", "async-warps"): 21.3,
-                            ("calorimeter-field-10gev", "local", "async-warps"): 6.29}
+FP64_WARP_INSTR_PER_STEP = {("calorimeter-field-10gev", "local", "async-warps"): 5.04}
 FP64_PIPE_CYCLES_PER_WARP_INSTR = 64.0
 # FP64 peak of GB300 derived from its unit counts: 2 DFMA per SM-cycle
 # (ncu peak_sustained) x 152 SMs x 2.07 GHz x 2 flop

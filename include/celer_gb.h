@@ -344,8 +344,10 @@ celer_status celer_set_parent_reuse(celer_ctx* ctx, int on);
  * memory, steps them, and queues the survivors again by their next kind. A
  * track then moves on as soon as its own step is done instead of waiting for
  * its block's slowest group. Charged tracks are taken before photons (their
- * steps form a shower's longest chains), and all but the first two warps of
- * a block take only full pieces of 32. A block holds at most 1024 live tracks in this
+ * steps form a shower's longest chains), and in runs without an iteration
+ * budget all but the first two warps of a block take only full pieces of 32
+ * (budgeted runs, such as a serving loop's chunks, let every warp take any
+ * piece). A block holds at most 1024 live tracks in this
  * mode; a block that starts a run with more runs block passes. Histories do
  * not change. On by default. Takes effect at the next run. on outside
  * {0, 1}: CELER_ERR_INVALID. */
@@ -487,7 +489,7 @@ celer_status celer_debug_partition(celer_ctx* ctx, uint8_t* keys_out, uint32_t* 
 /* Active-lane counters of the diagnostic build (compiled with
  * -DCELER_LANE_COUNTERS; the product build returns CELER_ERR_STATE). Sec. 3.1
  * judges reordering by the thread divergence it removes; these counters
- * measure it without a profiler. For each of the first min(n_max, 20) sites,
+ * measure it without a profiler. For each of the first min(n_max, 26) sites,
  * host_out receives three values: warp-level visits, the lanes active at
  * them summed (mean active lanes = lanes / visits), and the SM cycles spent
  * there summed where the site is timed (0 elsewhere). Sites: 0-7 the
@@ -498,7 +500,9 @@ celer_status celer_debug_partition(celer_ctx* ctx, uint8_t* keys_out, uint32_t* 
  * the step limit, 10 the along-step, 11-15 the Compton, photoelectric, pair,
  * Moller and brems interactions, 16 and 17 one rejection attempt of the
  * Compton and Moller samplers, 18 the side-plane distance along the helix,
- * 19 the per-warp loop's rounds that found nothing to do (timed).
+ * 19 the per-warp loop's rounds that found nothing to do (timed), 20-22 the
+ * photon crossing pieces timed in three parts (choice and claim, the step,
+ * the next step limit and requeue), 23-25 the same for electron crossings.
  * The counters cover every kernel launched since the last read on the
  * current device and are cleared by the read. *n_out receives the sites
  * written. Null pointers or n_max < 0: CELER_ERR_INVALID. */

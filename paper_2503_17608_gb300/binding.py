@@ -502,16 +502,18 @@ def debug_fp64_rate(blocks_per_sm: int = 4, iters: int = 40000):
 
 LANE_SITES = ["piece g_geom", "piece e_geom", "piece e_range", "piece compton", "piece pe", "piece pair",
               "piece moller", "piece brems", "fill", "step_limit", "along", "compton", "photoelectric", "pair",
-              "moller", "brems", "compton_attempt", "moller_attempt", "helix_side", "idle"]
+              "moller", "brems", "compton_attempt", "moller_attempt", "helix_side", "idle",
+              "photon_crossing: claim", "photon_crossing: step", "photon_crossing: next limit",
+              "electron_crossing: claim", "electron_crossing: step", "electron_crossing: next limit"]
 
 
 def debug_lane_counts():
     """Visits, summed active lanes and summed SM cycles (timed sites) per
     instrumented site since the last read (the diagnostic build only):
     {site: (visits, lanes, cycles)}."""
-    out = np.zeros(3 * 20, dtype=np.uint64)
+    out = np.zeros(3 * len(LANE_SITES), dtype=np.uint64)
     n = C.c_int()
-    _check(load().celer_debug_lane_counts(out.ctypes.data, 20, C.byref(n)))
+    _check(load().celer_debug_lane_counts(out.ctypes.data, len(LANE_SITES), C.byref(n)))
     return {name: (int(out[3 * k]), int(out[3 * k + 1]), int(out[3 * k + 2]))
             for k, name in enumerate(LANE_SITES[:n.value])}
 

@@ -232,7 +232,10 @@ enum LaneSite : int {
   LS_MOLLER_TRY = 17,  // one rejection attempt of the Moller sampler
   LS_HELIX_SIDE = 18,  // side-plane distance along the helix
   LS_IDLE = 19,        // per-warp loop rounds of the asynchronous loop that found nothing to do
-  kLaneSites = 20
+  LS_T_PHOTON = 20,    // photon crossing pieces timed in three parts: choice and claim, the
+                       // step, the next step limit and requeue (20, 21, 22)
+  LS_T_ELECTRON = 23,  // the same for electron crossing pieces (23, 24, 25)
+  kLaneSites = 26
 };
 constexpr int kLaneCopies = 16;
 constexpr int kLaneValues = 3;  // per site: visits, lanes, SM cycles (where timed)

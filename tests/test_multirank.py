@@ -116,11 +116,20 @@ def test_bench_roofline_names_the_timed_kernel():
     sys.path.insert(0, ROOT)
     import bench
 
-    r = bench.roofline_loop("calorimeter-1gev", "local", "async-warps", 454824.0, 2.0)
+    key = ("calorimeter-field-10gev", "local", "async-warps")
+    r = bench.roofline_loop(*key, 7959709.0, 5.0, fp64_measured=1.25, sm_mhz=2070.0)
     assert r["kernel"] == "k_loop_async" and r["bound"] == "alu"
-    assert r["traffic"] == bench.DRAM_BYTES_PER_LAUNCH[("calorimeter-1gev", "local", "async-warps")]
-    assert r["frac"] == r["achieved"] / r["peak"]
-    assert abs(r["achieved"] - 119.6 * 454824.0 / 2e-3 / 1e12) < 1e-12
+    assert r["traffic"] == bench.DRAM_BYTES_PER_LAUNCH[key]
+    assert r["peak"] == 1.25 and r["frac"] == r["achieved"] / r["peak"]
+    fp = bench.FP64_FLOP_PER_STEP.get(key, bench.FP64_FLOP_PER_STEP[key[:2]])
+    assert abs(r["achieved"] - fp * 7959709.0 / 5e-3 / 1e12) < 1e-12
+    # FP64 pipe: warp instructions x 64 cycles over 4 sub-partitions x 152 SMs x the clock
+    wi = bench.FP64_WARP_INSTR_PER_STEP[key]
+    assert abs(r["fp64_pipe"]["busy_frac"] - wi * 7959709.0 * 64 / (5e-3 * 4 * 152 * 2.07e9)) < 1e-12
+    # without a measured peak the derived one is used
+    assert bench.roofline_loop(*key, 1.0, 1.0)["peak"] == bench.FP64_PEAK_TFLOPS
+    # other kernels were not captured whole: no traffic figure
+    assert bench.roofline_loop("calorimeter-1gev", "local", "async-warps", 1.0, 1.0)["traffic"] is None
     assert bench.roofline_loop("calorimeter-1gev", "local", "persistent", 1.0, 1.0)["kernel"] == "k_loop_local"
     assert bench.roofline_loop("calorimeter-1gev", "none", "persistent", 1.0, 1.0)["kernel"] == "k_loop"
     # a reduced workload carries no traffic figure (the captures were of the full one)
