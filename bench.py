@@ -815,6 +815,9 @@ FP64_FLOP_PER_STEP = {("calorimeter-1gev", "none"): 131.0, ("calorimeter-1gev", 
                       ("calorimeter-field-10gev", "local"): 129.5,
                       ("calorimeter-1gev", "local", "async"): 119.5, ("calorimeter-1gev", "data", "async"): 119.5,
                       ("calorimeter-1gev", "local", "async-warps"): 119.6,
+                      # current per-warp kernel, smaller case of the workload (2,500
+                      # primaries, 2^18 slots; the op counters take 3 passes)
+                      ("calorimeter-field-10gev", "local", "async-warps"): 128.8,
                       ("water-cube-10mev", None): 119.5}
 DRAM_BYTES_PER_LAUNCH = {("calorimeter-field-10gev", "local", "async-warps"): 41.96e6}
 # FP64 warp instructions per track-step (sm__inst_executed_pipe_fp64 / track-steps)

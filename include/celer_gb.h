@@ -196,7 +196,10 @@ void celer_destroy(celer_ctx* ctx);
  * its random stream together with (seed, event). Validation happens on the
  * host before any device work: CELER_ERR_INVALID for a bad record,
  * CELER_ERR_CAPACITY if the initializer buffer or history cannot hold them.
- * Synchronises the stream once to read the buffer fill level. */
+ * Reads the buffer fill level from the device (one stream synchronisation)
+ * only if step work has run since it was last read; consecutive calls between
+ * two runs (a serving loop admitting several events) synchronise at most
+ * once. */
 celer_status celer_add_primaries(celer_ctx* ctx, uint32_t event, const celer_primary* host_ptr, uint64_t n);
 
 /* Same as celer_add_primaries for n records already in device memory

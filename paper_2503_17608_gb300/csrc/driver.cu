@@ -34,6 +34,7 @@ uint64_t next_pow2(uint64_t v) {
 
 struct celer_ctx {
   celer_problem prob{};
+  bool ctl_fresh = false;  // h_ctl equals the device control block (no head/tail-moving work since)
   cudaStream_t stream = nullptr;
   cudaStream_t capture_stream = nullptr;
   Params p{};
@@ -279,6 +280,7 @@ celer_status build_graph(celer_ctx* ctx) {
 celer_status read_ctl(celer_ctx* ctx) {
   CELER_CUDA(ctx, cudaMemcpyAsync(ctx->h_ctl, ctx->p.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
   CELER_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->ctl_fresh = true;
   return CELER_OK;
 }
 
@@ -625,8 +627,14 @@ celer_status celer_add_primaries(celer_ctx* ctx, uint32_t event, const celer_pri
   }
   if (ctx->p.hist_cap > 0 && ctx->next_history + n > ctx->p.hist_cap)
     return fail(ctx, CELER_ERR_CAPACITY, "history capacity exceeded");
-  celer_status st = read_ctl(ctx);
-  if (st != CELER_OK) return st;
+  // The buffer's fill level: the host copy of the control block is current
+  // if no kernel that moves the buffer's head or tail ran since it was read
+  // (only this call's own pushes, which it accounts for), so a run of
+  // admissions between two step runs synchronises the stream once.
+  if (!ctx->ctl_fresh) {
+    celer_status st = read_ctl(ctx);
+    if (st != CELER_OK) return st;
+  }
   const uint64_t queued = ctx->h_ctl->tail - ctx->h_ctl->head;
   if (queued + n > ctx->p.ring_capacity) return fail(ctx, CELER_ERR_CAPACITY, "initializer buffer full");
 
@@ -655,6 +663,7 @@ celer_status celer_add_primaries(celer_ctx* ctx, uint32_t event, const celer_pri
     launch_push_primaries(ctx->p, ctx->d_stage, (uint32_t)m, ctx->stream);
     CELER_CUDA(ctx, cudaGetLastError());
     CELER_CUDA(ctx, cudaEventRecord(ctx->stage_done, ctx->stream));
+    ctx->h_ctl->tail += m;  // the push appends exactly m entries
     done += m;
   }
   return CELER_OK;
@@ -662,6 +671,7 @@ celer_status celer_add_primaries(celer_ctx* ctx, uint32_t event, const celer_pri
 
 celer_status celer_add_primaries_device(celer_ctx* ctx, uint32_t event, const celer_primary* dev, uint64_t n) {
   if (!ctx) return CELER_ERR_INVALID;
+  ctx->ctl_fresh = false;  // the device decides whether the batch is taken
   if (n == 0) return CELER_OK;
   if (!dev) return fail(ctx, CELER_ERR_INVALID, "null primaries");
   if (n > 0xFFFFFFFFull) return fail(ctx, CELER_ERR_INVALID, "too many primaries in one call");
@@ -680,6 +690,7 @@ celer_status celer_add_primaries_device(celer_ctx* ctx, uint32_t event, const ce
 
 celer_status celer_step(celer_ctx* ctx, celer_step_stats* stats) {
   if (!ctx) return CELER_ERR_INVALID;
+  ctx->ctl_fresh = false;
   begin_policy_run(ctx);
   launch_iteration(ctx, ctx->stream, 0, 0);
   CELER_CUDA(ctx, cudaGetLastError());
@@ -696,6 +707,7 @@ celer_status celer_run_events(celer_ctx* ctx, int mode) { return celer_run_itera
 
 celer_status celer_run_iterations(celer_ctx* ctx, int mode, uint64_t budget, uint64_t* done) {
   if (!ctx) return CELER_ERR_INVALID;
+  ctx->ctl_fresh = false;
   if (mode < CELER_LOOP_HOST || mode > CELER_LOOP_ASYNC) return fail(ctx, CELER_ERR_INVALID, "unknown loop mode");
   if (mode == CELER_LOOP_ASYNC) {
     if (!fused_local(ctx))

@@ -99,3 +99,28 @@ def test_autotuner_tries_both_schedules_of_the_asynchronous_loop():
         runnable = not (t["mode"] == A and t["sort_policy"] == wl.SORT_NONE)
         assert (t["track_steps_per_s"] > 0) == runnable
     assert best["track_steps_per_s"] == max(t["track_steps_per_s"] for t in trials)
+
+
+def test_consecutive_admissions_track_the_buffer_fill_level():
+    """celer_add_primaries reads the buffer's fill level from the device only
+    after step work; between two runs it counts its own pushes. A second
+    batch that would overflow the buffer is refused without a run in between,
+    and after a run the space is back."""
+    prob = wl.calorimeter_problem(1 << 10, init_capacity=64, max_events=4)
+    a = wl.electron_beam(40, 50.0, event=0)
+    b = wl.electron_beam(30, 50.0, event=1)
+    c = wl.electron_beam(20, 50.0, event=2)
+    with binding.Context(prob) as ctx:
+        ctx.add_primaries(0, a)
+        with pytest.raises(binding.CelerError) as ei:
+            ctx.add_primaries(1, b)  # 40 + 30 > 64
+        assert ei.value.status == 2
+        ctx.add_primaries(2, c)  # 40 + 20 fits
+        assert ctx.stats()["queued"] == 60
+        ctx.run_events(binding.LOOP_PERSISTENT)
+        ctx.add_primaries(1, b)  # the buffer drained
+        ctx.run_events(binding.LOOP_ASYNC if prob.sort_policy in (wl.SORT_LOCAL, wl.SORT_DATA)
+                       else binding.LOOP_PERSISTENT)
+        for e, ev in ((0, a), (1, b), (2, c)):
+            tally, esc = ctx.read_tallies(e)
+            assert tally.sum() + esc == pytest.approx(ev["E"].sum(), rel=1e-12)
