@@ -259,8 +259,8 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
     // shorter. In whole-job runs the first kAnyPieceWarps warps take a piece
     // of any size, the others only full ones, so that with few tracks alive a
     // block's work is concentrated in full warps instead of spread over many
-    // part-filled ones. A warp keeps the kind it ran last while at least half as many of
-    // it wait, so that its code is still in the instruction cache.
+    // part-filled ones. A warp keeps the kind it ran last while at least half
+    // as many of it wait, so that its code is still in the instruction cache.
     unsigned eb = (lane == K_E_GEOM || lane == K_E_RANGE || lane == K_E_MOLLER || lane == K_E_BREMS) ? waiting : 0u;
     unsigned ek = (unsigned)lane;
 #pragma unroll

@@ -128,3 +128,28 @@ def test_fast_sincos_outside_range_follows_cuda():
         np.testing.assert_array_equal(np.isnan(fast), np.isnan(cuda))
         ok = ~np.isnan(cuda)
         np.testing.assert_array_equal(fast[ok], cuda[ok])
+
+
+def test_fp64_rate_probe():
+    """The FP64 throughput probe behind the bench's ALU roofline: at most the
+    derived peak (2 FP64 FMA per SM-cycle at the maximum clock), and well
+    above a fraction of it; bad arguments are refused."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    derived = 2 * 2 * sms * 2.07e9 / 1e12
+    tflops, ms = binding.debug_fp64_rate(4, 20000)
+    assert ms > 0.0
+    assert 0.3 * derived < tflops <= 1.05 * derived, (tflops, derived)
+    for bad in ((0, 100), (9, 100), (4, 0)):
+        with pytest.raises(binding.CelerError) as ei:
+            binding.debug_fp64_rate(*bad)
+        assert ei.value.status == 1
+
+
+def test_lane_counters_are_absent_from_the_product_build():
+    """The active-lane counters exist only in the diagnostic build; the
+    product library answers CELER_ERR_STATE."""
+    with pytest.raises(binding.CelerError) as ei:
+        binding.debug_lane_counts()
+    assert ei.value.status == 5
