@@ -504,7 +504,9 @@ LANE_SITES = ["piece g_geom", "piece e_geom", "piece e_range", "piece compton", 
               "piece moller", "piece brems", "fill", "step_limit", "along", "compton", "photoelectric", "pair",
               "moller", "brems", "compton_attempt", "moller_attempt", "helix_side", "idle",
               "photon_crossing: claim", "photon_crossing: step", "photon_crossing: next limit",
-              "electron_crossing: claim", "electron_crossing: step", "electron_crossing: next limit"]
+              "electron_crossing: claim", "electron_crossing: step", "electron_crossing: next limit",
+              "photon limit: loads", "photon limit: grid (log)", "photon limit: cross sections",
+              "photon limit: planes", "photon limit: rest and stores", "queue push"]
 
 
 def debug_lane_counts():

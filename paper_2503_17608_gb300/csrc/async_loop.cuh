@@ -144,7 +144,11 @@ __device__ __forceinline__ void wq_requeue(const Params& p, const WarpQueues& w,
   } else {
     act = t.action[slot];
   }
+#ifdef CELER_LANE_COUNTERS
+  long long t_push = clock64();
+#endif
   wq_push(p, w, key_of(POLICY_ACTION_TYPE, t.ptype[slot], act), li);
+  CELER_LANE_MARK(LS_T_PUSH, t_push);
 }
 
 // Warp-level sums of the per-lane counts of one piece, added to the device

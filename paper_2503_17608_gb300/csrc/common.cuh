@@ -235,7 +235,11 @@ enum LaneSite : int {
   LS_T_PHOTON = 20,    // photon crossing pieces timed in three parts: choice and claim, the
                        // step, the next step limit and requeue (20, 21, 22)
   LS_T_ELECTRON = 23,  // the same for electron crossing pieces (23, 24, 25)
-  kLaneSites = 26
+  LS_T_LIMIT = 26,     // the step limit of a photon timed in five parts: the state loads, the
+                       // grid position (logarithm), the cross sections, the distances to the
+                       // planes, the rest with the stores (26-30)
+  LS_T_PUSH = 31,      // queueing a track by its next kind (per-warp loop)
+  kLaneSites = 32
 };
 constexpr int kLaneCopies = 16;
 constexpr int kLaneValues = 3;  // per site: visits, lanes, SM cycles (where timed)
@@ -261,11 +265,24 @@ __device__ __forceinline__ void lane_cycles(int site, long long cycles) {  // on
 #define CELER_LANES_N(site, n) ::celer::lane_site_n((site), (n))
 #define CELER_LANE_CLOCK() clock64()
 #define CELER_LANE_CYCLES(site, c) ::celer::lane_cycles((site), (c))
+// the lanes here gathered, the time since mark t recorded at site, t reset
+#define CELER_LANE_MARK(site, t)                                     \
+  do {                                                               \
+    const unsigned m_ = __activemask();                              \
+    __syncwarp(m_);                                                  \
+    const long long n_ = clock64();                                  \
+    if ((int)(threadIdx.x & 31u) == __ffs(m_) - 1) {                 \
+      ::celer::lane_site_n((site), (unsigned)__popc(m_));            \
+      ::celer::lane_cycles((site), n_ - (t));                        \
+    }                                                                \
+    (t) = n_;                                                        \
+  } while (0)
 #else
 #define CELER_LANES(site) ((void)0)
 #define CELER_LANES_N(site, n) ((void)0)
 #define CELER_LANE_CLOCK() 0ll
 #define CELER_LANE_CYCLES(site, c) ((void)0)
+#define CELER_LANE_MARK(site, t) ((void)0)
 #endif
 
 }  // namespace celer

@@ -177,17 +177,25 @@ __device__ __forceinline__ uint8_t key_of(int policy, uint8_t ptype, uint8_t act
 __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, const double2* tab, const double* zb,
                                               const int32_t* lmat) {
   const Tracks& t = p.trk;
+  long long t_mark = CELER_LANE_CLOCK();  // diagnostic build only
+  (void)t_mark;
   const double E = t.E[slot];
   CELER_LANES(LS_STEP_LIMIT);
   const uint8_t pt = t.ptype[slot];
   const int layer = t.layer[slot];
   double nmfp = t.nmfp[slot];
   TrackRng rng(p.seed, t.event[slot], t.tid[slot], t.ctr[slot]);
+  // every field of the state in one round of loads, before the calls below
+  // (the compiler keeps loads behind a call it cannot see into): +1-2 %
+  const double x = t.x[slot], y = t.y[slot], z = t.z[slot];
+  const double ux = t.ux[slot], uy = t.uy[slot], uz = t.uz[slot];
   if (nmfp < 0.0) nmfp = -fast_log(rng.uniform(), p.mtab);
 
   const double2* mt = tab + lmat[layer] * (kCols * kGrid);
   const bool charged = pt != GAMMA;
+  if (!charged) CELER_LANE_MARK(LS_T_LIMIT, t_mark);
   const GridPos g = grid_pos(E, p.lnEmin, p.inv_dl, p.mtab);
+  if (!charged) CELER_LANE_MARK(LS_T_LIMIT + 1, t_mark);
   double mu0, mu1, mu2 = 0.0;
   if (!charged) {
     mu0 = interp(mt + COL_COMPTON * kGrid, g);
@@ -200,6 +208,7 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
   const double mu = (mu0 + mu1) + mu2;
   const bool eloss = charged && (p.processes & PROC_ELOSS);
   const double R = eloss ? interp(mt + COL_RANGE * kGrid, g) : 0.0;
+  if (!charged) CELER_LANE_MARK(LS_T_LIMIT + 2, t_mark);
 
   // The limits are compared in the order z-planes, side planes, range,
   // interaction, each candidate replacing the current one only if strictly
@@ -208,8 +217,6 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
   // limit s, i.e. unless |d| > s |u| (1 + 2^-50): beyond that margin the
   // rounded quotient is >= s too, so skipping its division changes no choice
   // (the divisions dominate the FP64 cost of the step limit).
-  const double x = t.x[slot], y = t.y[slot], z = t.z[slot];
-  const double ux = t.ux[slot], uy = t.uy[slot], uz = t.uz[slot];
   double s_geo = kInf;
   uint8_t act = A_NONE;
   const long long uzb = __double_as_longlong(uz);
@@ -241,6 +248,7 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
     act = A_SIDE;
   }
   if (s_geo < 0.0) s_geo = 0.0;
+  if (!charged) CELER_LANE_MARK(LS_T_LIMIT + 3, t_mark);
 
   double s = s_geo;
   if (eloss) {
@@ -304,6 +312,7 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
   t.step[slot] = s;
   if (eloss) t.rpost[slot] = R - s;
   t.action[slot] = act;
+  if (!charged) CELER_LANE_MARK(LS_T_LIMIT + 4, t_mark);
   return act;
 }
 
@@ -787,6 +796,11 @@ __device__ __forceinline__ bool along_one(const Params& p, uint32_t slot, uint8_
   int layer = t.layer[slot];
   double E = t.E[slot];
   double z = t.z[slot];
+  // the rest of the state in the same round of loads, ahead of the atomic
+  const double s = t.step[slot];
+  double x = t.x[slot], y = t.y[slot];
+  double ux = t.ux[slot], uy = t.uy[slot];
+  const double uz = t.uz[slot];
   if (prim < p.hist_cap) atomicAdd(&p.hist_steps[prim], 1ull);
   if (act == A_TRAPPED) {
     deposit(p, ev, prim, layer, z, E);
@@ -795,10 +809,6 @@ __device__ __forceinline__ bool along_one(const Params& p, uint32_t slot, uint8_
   }
   const bool eloss = charged && (p.processes & PROC_ELOSS);
   const bool helix = charged && p.Bz != 0.0;
-  const double s = t.step[slot];
-  double x = t.x[slot], y = t.y[slot];
-  double ux = t.ux[slot], uy = t.uy[slot];
-  const double uz = t.uz[slot];
   if (helix) {
     const Curvature cv = curvature(pt, E, p.Bz);
     if (p.field_cap > 0)
