@@ -492,7 +492,7 @@ celer_status celer_debug_partition(celer_ctx* ctx, uint8_t* keys_out, uint32_t* 
 /* Active-lane counters of the diagnostic build (compiled with
  * -DCELER_LANE_COUNTERS; the product build returns CELER_ERR_STATE). Sec. 3.1
  * judges reordering by the thread divergence it removes; these counters
- * measure it without a profiler. For each of the first min(n_max, 32) sites,
+ * measure it without a profiler. For each of the first min(n_max, 35) sites,
  * host_out receives three values: warp-level visits, the lanes active at
  * them summed (mean active lanes = lanes / visits), and the SM cycles spent
  * there summed where the site is timed (0 elsewhere). Sites: 0-7 the
@@ -508,7 +508,8 @@ celer_status celer_debug_partition(celer_ctx* ctx, uint8_t* keys_out, uint32_t* 
  * the next step limit and requeue), 23-25 the same for electron crossings,
  * 26-30 a photon's step limit timed in five parts (state loads, grid position,
  * cross sections, distances to the planes, the rest with the stores), 31 the
- * per-warp loop's queueing of a track by its next kind.
+ * per-warp loop's queueing of a track by its next kind, 32-34 the Compton
+ * pieces timed in three parts as the crossings.
  * The counters cover every kernel launched since the last read on the
  * current device and are cleared by the read. *n_out receives the sites
  * written. Null pointers or n_max < 0: CELER_ERR_INVALID. */

@@ -506,7 +506,8 @@ LANE_SITES = ["piece g_geom", "piece e_geom", "piece e_range", "piece compton", 
               "photon_crossing: claim", "photon_crossing: step", "photon_crossing: next limit",
               "electron_crossing: claim", "electron_crossing: step", "electron_crossing: next limit",
               "photon limit: loads", "photon limit: grid (log)", "photon limit: cross sections",
-              "photon limit: planes", "photon limit: rest and stores", "queue push"]
+              "photon limit: planes", "photon limit: rest and stores", "queue push",
+              "compton: claim", "compton: step", "compton: next limit"]
 
 
 def debug_lane_counts():

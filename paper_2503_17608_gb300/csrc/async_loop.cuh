@@ -405,8 +405,8 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
         }
       }
       __syncwarp();
-      if (lane == 0 && take == 0 && (pick_k == K_G_GEOM || pick_k == K_E_GEOM)) {
-        const int base = pick_k == K_G_GEOM ? LS_T_PHOTON : LS_T_ELECTRON;
+      if (lane == 0 && take == 0 && (pick_k == K_G_GEOM || pick_k == K_E_GEOM || pick_k == K_G_COMPTON)) {
+        const int base = pick_k == K_G_GEOM ? LS_T_PHOTON : (pick_k == K_E_GEOM ? LS_T_ELECTRON : LS_T_COMPTON);
         CELER_LANES_N(base, n);
         CELER_LANE_CYCLES(base, t_read - t_round);
         CELER_LANES_N(base + 1, n);

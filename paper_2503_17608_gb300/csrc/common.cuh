@@ -239,7 +239,8 @@ enum LaneSite : int {
                        // grid position (logarithm), the cross sections, the distances to the
                        // planes, the rest with the stores (26-30)
   LS_T_PUSH = 31,      // queueing a track by its next kind (per-warp loop)
-  kLaneSites = 32
+  LS_T_COMPTON = 32,   // Compton pieces timed in three parts as the crossings (32, 33, 34)
+  kLaneSites = 35
 };
 constexpr int kLaneCopies = 16;
 constexpr int kLaneValues = 3;  // per site: visits, lanes, SM cycles (where timed)
