@@ -248,15 +248,11 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
       const unsigned hd = *reinterpret_cast<volatile unsigned*>(&s_head[lane]);  // before the tail: hd <= tail
       waiting = *reinterpret_cast<volatile unsigned*>(&s_tail[lane]) - hd;
     }
-    unsigned best = waiting, best_k = (unsigned)lane;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned ob = __shfl_xor_sync(0xffffffffu, best, o), ok = __shfl_xor_sync(0xffffffffu, best_k, o);
-      if (ob > best || (ob == best && ok < best_k)) {
-        best = ob;
-        best_k = ok;
-      }
-    }
+    // (one warp-wide maximum of waiting << 8 | (255 - lane): the most
+    // waiting, the lowest kind among equals)
+    const unsigned kb = __reduce_max_sync(0xffffffffu, (waiting << 8) | (255u - (unsigned)lane));
+    unsigned best = kb >> 8;
+    const unsigned best_k = 255u - (kb & 0xFFu);
     // Charged tracks first: their steps carry a shower's longest chains of
     // dependent steps (the primary crossing layer after layer and radiating),
     // so the job ends sooner when they wait least; the photons' chains are
@@ -265,16 +261,9 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
     // block's work is concentrated in full warps instead of spread over many
     // part-filled ones. A warp keeps the kind it ran last while at least half
     // as many of it wait, so that its code is still in the instruction cache.
-    unsigned eb = (lane == K_E_GEOM || lane == K_E_RANGE || lane == K_E_MOLLER || lane == K_E_BREMS) ? waiting : 0u;
-    unsigned ek = (unsigned)lane;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned ob = __shfl_xor_sync(0xffffffffu, eb, o), ok = __shfl_xor_sync(0xffffffffu, ek, o);
-      if (ob > eb || (ob == eb && ok < ek)) {
-        eb = ob;
-        ek = ok;
-      }
-    }
+    const unsigned ew = (lane == K_E_GEOM || lane == K_E_RANGE || lane == K_E_MOLLER || lane == K_E_BREMS) ? waiting : 0u;
+    const unsigned ke = __reduce_max_sync(0xffffffffu, (ew << 8) | (255u - (unsigned)lane));
+    const unsigned eb = ke >> 8, ek = 255u - (ke & 0xFFu);
     const unsigned w_last = __shfl_sync(0xffffffffu, waiting, last_k & 31u);
     const bool keep_last = last_k < (unsigned)kLiveKeys && w_last > 0 && 2u * w_last >= best;
     // (while draining any warp takes any piece: a warp that leaves the loop
