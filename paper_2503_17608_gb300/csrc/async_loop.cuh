@@ -102,26 +102,38 @@ __device__ __forceinline__ bool wq_wait(const Params& p, volatile unsigned* e, u
   }
 }
 
-// Append v to queue k (one thread). The caller's global-memory writes of the
-// track are ordered before the entry (block scope: the reader is a warp of
-// the same block).
+// Block-scope release store and acquire load of a shared-memory word.
+__device__ __forceinline__ void st_release_cta(volatile unsigned* a, unsigned v) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared((const void*)a);
+  asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(s), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_cta(volatile unsigned* a) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared((const void*)a);
+  unsigned v;
+  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(s) : "memory");
+  return v;
+}
+
+// Append v to queue k (one thread). The entry is written with a release
+// store, so the caller's global-memory writes of the track are visible to
+// the warp that reads it (block scope: a warp of the same block).
 __device__ __forceinline__ void wq_push(const Params& p, const WarpQueues& w, int k, unsigned v) {
   const unsigned t = atomicAdd(&w.tail[k], 1u);
   volatile unsigned* e = w.q + (size_t)k * kWarpLive + (t % kWarpLive);
   const unsigned lap2 = (2u * (t / kWarpLive)) & 0xFFFFu;
   if (!wq_wait(p, e, lap2)) return;
-  __threadfence_block();
-  *e = (((lap2 + 1u) & 0xFFFFu) << 16) | (v & 0xFFFFu);
+  st_release_cta(e, (((lap2 + 1u) & 0xFFFFu) << 16) | (v & 0xFFFFu));
 }
 
-// Read entry t of queue k (one thread; t claimed by its warp) and free it for
-// the next lap. Returns 0xFFFFFFFF if the wait gave up.
+// Read entry t of queue k (one thread; t claimed by its warp) with an
+// acquire load (the pusher's writes of the track come before the reader's
+// reads of it) and free it for the next lap. Returns 0xFFFFFFFF if the wait
+// gave up.
 __device__ __forceinline__ unsigned wq_read(const Params& p, const WarpQueues& w, int k, unsigned t) {
   volatile unsigned* e = w.q + (size_t)k * kWarpLive + (t % kWarpLive);
   const unsigned lap2 = (2u * (t / kWarpLive)) & 0xFFFFu;
   if (!wq_wait(p, e, (lap2 + 1u) & 0xFFFFu)) return 0xFFFFFFFFu;
-  const unsigned v = *e & 0xFFFFu;
-  __threadfence_block();
+  const unsigned v = ld_acquire_cta(e) & 0xFFFFu;
   *e = ((lap2 + 2u) & 0xFFFFu) << 16;
   return v;
 }
