@@ -147,7 +147,7 @@ __device__ __forceinline__ uint32_t local_slot(unsigned li, int bid, int nb) {
 // is alive (counted as a step), or its pending interaction if it is deferred;
 // then it is queued by its kind.
 __device__ __forceinline__ void wq_requeue(const Params& p, const WarpQueues& w, const SharedStatic& ss, uint32_t slot,
-                                           unsigned li, unsigned long long& steps) {
+                                           unsigned li, unsigned& steps) {
   const Tracks& t = p.trk;
   uint8_t act;
   if (t.status[slot] == ALIVE) {
@@ -163,25 +163,22 @@ __device__ __forceinline__ void wq_requeue(const Params& p, const WarpQueues& w,
   CELER_LANE_MARK(LS_T_PUSH, t_push);
 }
 
-// Warp-level sums of the per-lane counts of one piece, added to the device
+// Warp sums of the per-lane counts since the last flush (at most 16 pieces
+// or fills, a few per lane each, so 32-bit sums), added to the device
 // counters by lane 0. Ended tracks are counted after a fence, behind the
 // tail reservations of their interactions (the run's end condition).
-__device__ __forceinline__ void wq_flush_counts(const Params& p, unsigned long long steps, unsigned long long killed,
-                                                unsigned long long fill) {
+__device__ __forceinline__ void wq_flush_counts(const Params& p, unsigned steps, unsigned killed, unsigned fill) {
   Ctl* c = p.ctl;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    steps += __shfl_xor_sync(0xffffffffu, steps, o);
-    killed += __shfl_xor_sync(0xffffffffu, killed, o);
-    fill += __shfl_xor_sync(0xffffffffu, fill, o);
-  }
+  steps = __reduce_add_sync(0xffffffffu, steps);
+  killed = __reduce_add_sync(0xffffffffu, killed);
+  fill = __reduce_add_sync(0xffffffffu, fill);
   if ((threadIdx.x & 31) == 0) {
-    if (steps) atomicAdd(&c->steps_total, steps);
+    if (steps) atomicAdd(&c->steps_total, (unsigned long long)steps);
     const long long dalive = (long long)fill - (long long)killed;
     if (dalive != 0) atomicAdd(&c->alive, (unsigned long long)dalive);
     if (killed) {
       __threadfence();
-      atomicAdd(&c->finished, killed);
+      atomicAdd(&c->finished, (unsigned long long)killed);
     }
   }
 }
@@ -214,7 +211,8 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
   }
   __syncthreads();
   // the block's live tracks to their queues, vacant slots to the free queue
-  unsigned long long steps = 0, killed = 0, fill = 0, pieces = 0;
+  unsigned steps = 0, killed = 0, fill = 0, events = 0;
+  unsigned long long pieces = 0;
   const unsigned n_own = (owned + 31u) / 32u;
   for (unsigned m = (unsigned)warp; m < n_own; m += (unsigned)nwarps) {
     const unsigned li = m * 32u + (unsigned)lane;
@@ -417,11 +415,12 @@ __device__ unsigned long long warp_queue_loop(const Params& p, int bid, int nb, 
       }
 #endif
       if (lane == 0) CELER_LANE_CYCLES(take > 0 ? LS_FILL : LS_PIECE + (int)pick_k, CELER_LANE_CLOCK() - t_round);
-      if (take > 0) continue;
-      if ((++pieces & 15u) == 0) {  // the device counters every 16 pieces, and whenever the warp idles
+      if ((++events & 15u) == 0) {  // the device counters every 16 pieces or fills, and whenever the warp idles
         wq_flush_counts(p, steps, killed, fill);
         steps = killed = fill = 0;
       }
+      if (take > 0) continue;
+      ++pieces;
       if (pieces >= budget && lane == 0) atomicExch(&s_drain, 1u);
       if (pieces >= max_pieces && lane == 0) {
         atomicOr(&c->error, ERR_ITERATIONS);
