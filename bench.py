@@ -819,12 +819,12 @@ FP64_FLOP_PER_STEP = {("calorimeter-1gev", "none"): 131.0, ("calorimeter-1gev", 
                       # primaries, 2^18 slots; the op counters take 3 passes)
                       ("calorimeter-field-10gev", "local", "async-warps"): 128.8,
                       ("water-cube-10mev", None): 119.5}
-DRAM_BYTES_PER_LAUNCH = {("calorimeter-field-10gev", "local", "async-warps"): 41.00e6}
+DRAM_BYTES_PER_LAUNCH = {("calorimeter-field-10gev", "local", "async-warps"): 40.77e6}
 # FP64 warp instructions per track-step (sm__inst_executed_pipe_fp64 / track-steps)
 # of the loop kernel's one-launch ncu captures: an FP64 warp instruction holds
 # its sub-partition's FP64 pipe for 64 cycles whatever its active lanes, so
 # these set how busy the FP64 pipe is at a measured track-step rate.
-FP64_WARP_INSTR_PER_STEP = {("calorimeter-field-10gev", "local", "async-warps"): 5.05}
+FP64_WARP_INSTR_PER_STEP = {("calorimeter-field-10gev", "local", "async-warps"): 5.04}
 FP64_PIPE_CYCLES_PER_WARP_INSTR = 64.0
 # FP64 peak of GB300 derived from its unit counts: 2 DFMA per SM-cycle
 # (ncu peak_sustained) x 152 SMs x 2.07 GHz x 2 flop
