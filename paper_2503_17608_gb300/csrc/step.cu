@@ -722,7 +722,7 @@ __device__ void phase_fill_step(const Params& p, int bid, int nb, const SharedSt
 // live keys in that order, one per warp, and places each live slot at: the
 // block's first position for the key (from the scan) + the block's same-key
 // slots placed so far (a running cursor) + same-key slots of earlier warps in
-// this round + same-key lanes below. The order within a key is thus by owning
+// this pass of the loop + same-key lanes below. The order within a key is thus by owning
 // block, then chunk, then lane: deterministic, and no scan over all tiles.
 __device__ void phase_scatter(const Params& p, int bid, int nb) {
   __shared__ unsigned s_cnt[kTile / 32][kMaxKeys];
@@ -736,7 +736,7 @@ __device__ void phase_scatter(const Params& p, int bid, int nb) {
   if ((int)threadIdx.x < live_keys) s_cursor[threadIdx.x] = p.block_offsets[threadIdx.x * nb + bid];
   const uint32_t n_own = (uint32_t)bid < p.n_chunks ? (p.n_chunks - (uint32_t)bid + nb - 1) / nb : 0u;
   for (uint32_t m0 = 0; m0 < n_own; m0 += blockDim.x) {
-    // this round's live chunks of the block, compacted in order
+    // this pass's live chunks of the block, compacted in order
     const uint32_t m = m0 + threadIdx.x;
     const uint32_t gm = (uint32_t)bid + (uint32_t)nb * m;
     const bool live = m < n_own && p.chunk_dirty[gm] != 0;
