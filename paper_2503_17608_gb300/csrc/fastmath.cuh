@@ -138,7 +138,8 @@ static __device__ __noinline__ double fast_log(double x, const double* __restric
 // |r| <= ln2/128; 2^(n/64) = 2^(n >> 6) T_(n & 63), the power of two added
 // to the exponent field (|x| < 708 keeps the result normal).
 static __device__ __noinline__ double fast_exp(double x, const double* __restrict__ mt) {
-  if (!(fabs(x) < 708.0)) return exp(x);
+  // |x| < 708 on the bit pattern (NaN and inf fail it, as in FP64)
+  if ((unsigned long long)(__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll) >= 0x4086200000000000ull) return exp(x);
   constexpr double kShift = 0x1.8p52;
   const double t = fma(x, __ldg(mt + kMtInvC), kShift);
   const int n = (int)(uint32_t)__double_as_longlong(t);

@@ -94,6 +94,13 @@ struct TrackRng {
   __device__ __forceinline__ double uniform() { return unit_from_bits(raw()); }
 };
 
+// Comparisons of doubles on their bit patterns (integer instructions instead
+// of the FP64 pipe): for x >= +0 and y >= +0 (either may be +inf or NaN)
+// x < y iff bits(x) < bits(y), except that a NaN x compares above every
+// number. Each use states why its operands qualify and why a NaN operand
+// gives the same outcome as the FP64 comparison.
+__device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
+
 // ------------------------------------------------------------------ tables
 struct GridPos {
   int bin;
@@ -103,7 +110,7 @@ struct GridPos {
 // Grid coordinate (ln E - ln E_min) / dl, bin clamped to [0, n - 2].
 __device__ __forceinline__ GridPos grid_pos(double E, double lnEmin, double inv_dl, const double* mt) {
   const double x = (fast_log(E, mt) - lnEmin) * inv_dl;
-  int b = (int)floor(x);
+  int b = __double2int_rd(x);  // (int)floor(x), one conversion
   b = b < 0 ? 0 : (b > kGrid - 2 ? kGrid - 2 : b);
   return GridPos{b, x - (double)b};
 }

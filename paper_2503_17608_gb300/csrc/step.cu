@@ -189,7 +189,9 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
   // (the compiler keeps loads behind a call it cannot see into): +1-2 %
   const double x = t.x[slot], y = t.y[slot], z = t.z[slot];
   const double ux = t.ux[slot], uy = t.uy[slot], uz = t.uz[slot];
-  if (nmfp < 0.0) nmfp = -fast_log(rng.uniform(), p.mtab);
+  // nmfp < 0 on the bits: -1 marks it unset; otherwise it is >= +0 (a
+  // zero difference rounds to +0)
+  if (dbits(nmfp) < 0) nmfp = -fast_log(rng.uniform(), p.mtab);
 
   const double2* mt = tab + lmat[layer] * (kCols * kGrid);
   const bool charged = pt != GAMMA;
@@ -200,7 +202,8 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
   if (!charged) {
     mu0 = interp(mt + COL_COMPTON * kGrid, g);
     mu1 = interp(mt + COL_PE * kGrid, g);
-    mu2 = E > kPairThreshold ? interp(mt + COL_PAIR * kGrid, g) : 0.0;
+    // E > threshold on the bits (E >= +0; a NaN E makes mu NaN either way)
+    mu2 = dbits(E) > dbits(kPairThreshold) ? interp(mt + COL_PAIR * kGrid, g) : 0.0;
   } else {
     mu0 = interp(mt + COL_MOLLER * kGrid, g);
     mu1 = interp(mt + COL_BREMS * kGrid, g);
@@ -233,14 +236,17 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
     cv = curvature(pt, E, p.Bz);
     s_side = helix_side_distance(cv, x, y, ux, uy, p.hx, p.hy);
   } else {
+    // the signs of ux, uy on their bits: nonzero (NaN included) and
+    // positive; for a positive NaN the distance test fails either way
     const double reach = s_geo * kLimitMargin;
-    if (ux != 0.0) {
-      const double d = ux > 0.0 ? p.hx - x : -p.hx - x;
-      if ((ux > 0.0 ? d : -d) <= reach * fabs(ux)) s_side = d / ux;
+    const long long bx = dbits(ux), by = dbits(uy);
+    if (((unsigned long long)bx << 1) != 0ull) {
+      const double d = bx > 0 ? p.hx - x : -p.hx - x;
+      if ((bx > 0 ? d : -d) <= reach * fabs(ux)) s_side = d / ux;
     }
-    if (uy != 0.0) {
-      const double d = uy > 0.0 ? p.hy - y : -p.hy - y;
-      if ((uy > 0.0 ? d : -d) <= reach * fabs(uy)) s_side = fmin(s_side, d / uy);
+    if (((unsigned long long)by << 1) != 0ull) {
+      const double d = by > 0 ? p.hy - y : -p.hy - y;
+      if ((by > 0 ? d : -d) <= reach * fabs(uy)) s_side = fmin(s_side, d / uy);
     }
   }
   if (s_side < s_geo) {
@@ -265,14 +271,16 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
     }
   }
   bool interact = false;
-  if (mu > 0.0 && nmfp <= s * mu * kLimitMargin) {
+  // mu > 0 on the bits (mu >= +0: a sum of interpolated non-negative
+  // tables; for a NaN mu the second test fails either way)
+  if (dbits(mu) > 0 && nmfp <= s * mu * kLimitMargin) {
     const double s_int = nmfp / mu;
     if (s_int < s) {
       s = s_int;
       interact = true;
     }
   }
-  if (s == kInf) {
+  if (dbits(s) == dbits(kInf)) {
     act = A_TRAPPED;
     s = 0.0;
   } else {
@@ -287,22 +295,24 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
     nmfp -= s * mu;
   }
   if (interact) {
+    // an interaction means a finite mu, so every operand below is finite
+    // and >= +0: the comparisons on the bits are exact
     const double target = rng.uniform() * mu;
     int last = -1;
-    if (mu0 > 0.0) last = 0;
-    if (mu1 > 0.0) last = 1;
-    if (mu2 > 0.0) last = 2;
+    if (dbits(mu0) > 0) last = 0;
+    if (dbits(mu1) > 0) last = 1;
+    if (dbits(mu2) > 0) last = 2;
     int sel;
     double acc = mu0;
-    if (target < acc) {
+    if (dbits(target) < dbits(acc)) {
       sel = 0;
     } else {
       acc += mu1;
-      if (target < acc) {
+      if (dbits(target) < dbits(acc)) {
         sel = 1;
       } else {
         acc += mu2;
-        sel = (!charged && target < acc) ? 2 : last;
+        sel = (!charged && dbits(target) < dbits(acc)) ? 2 : last;
       }
     }
     act = charged ? (sel == 0 ? A_MOLLER : A_BREMS) : (uint8_t)(A_COMPTON + sel);
@@ -846,7 +856,8 @@ __device__ __forceinline__ bool along_one(const Params& p, uint32_t slot, uint8_
     release(p, slot, ev);
     return true;
   }
-  if (E < p.cut_track) {
+  // E < cut on the bits (E >= +0; a NaN E fails it, as in FP64)
+  if (dbits(E) < dbits(p.cut_track)) {
     deposit(p, ev, prim, layer, z, E);
     release(p, slot, ev);
     return true;
