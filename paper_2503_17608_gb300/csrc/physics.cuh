@@ -95,10 +95,11 @@ struct TrackRng {
 };
 
 // Comparisons of doubles on their bit patterns (integer instructions instead
-// of the FP64 pipe): for x >= +0 and y >= +0 (either may be +inf or NaN)
-// x < y iff bits(x) < bits(y), except that a NaN x compares above every
-// number. Each use states why its operands qualify and why a NaN operand
-// gives the same outcome as the FP64 comparison.
+// of the FP64 pipe). For x, y >= +0 (+inf included) x < y iff bits(x) <
+// bits(y) as signed integers; a negative x (-0 included) has negative bits,
+// below every y >= +0, and a positive NaN has bits above +inf. Each use
+// states why its operands qualify and why a NaN gives the outcome of the
+// FP64 comparison.
 __device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
 
 // ------------------------------------------------------------------ tables
@@ -127,8 +128,8 @@ __device__ __forceinline__ double interp(const double2* col, GridPos g) {
 // integers (same order as the values) and keeps the FP64 pipe free.
 __device__ __forceinline__ double inverse_range(const double2* R, double r, double lnEmin, double dl,
                                                 const double* mt) {
-  if (r <= R[0].x) return 0.0;
   const long long rb = __double_as_longlong(r);
+  if (rb <= __double_as_longlong(R[0].x)) return 0.0;  // r <= R_0 > 0 on the bits (r may be negative)
   int lo = 0;
 #pragma unroll
   for (int step = 128; step > 0; step >>= 1) {
@@ -156,7 +157,7 @@ __device__ __forceinline__ void rotate_dir(double& ux, double& uy, double& uz, d
   double sp, cp;
   fast_sincos_2pi(u_phi, mt, &sp, &cp);
   double e1x, e1y, e1z, e2x, e2y, e2z;
-  if (fabs(uz) < 1.0 - 1e-10) {
+  if ((dbits(uz) & 0x7FFFFFFFFFFFFFFFll) < dbits(1.0 - 1e-10)) {  // |uz| < 1 - 1e-10 on the bits
     const double q = ux * ux + uy * uy;
     const double inv_n = rsqrt(q);
     e1x = uy * inv_n;
@@ -275,7 +276,7 @@ static __device__ __noinline__ double helix_side_distance(Curvature c, double x,
                                                           double hx, double hy) {
   CELER_LANES(LS_HELIX_SIDE);
   const double A2 = ux * ux + uy * uy;
-  if (A2 == 0.0) return kInf;
+  if (dbits(A2) == 0ll) return kInf;  // A2 >= +0
   const double inv_A = rsqrt(A2);
   const double A = A2 * inv_A;
   const double kappa = c.kappa;
@@ -292,13 +293,13 @@ static __device__ __noinline__ double helix_side_distance(Curvature c, double x,
   for (int i = 0; i < 2; ++i) {
     const double X = i == 0 ? hx : -hx;
     const double d = kappa * (X - xc) * inv_A;
-    if (fabs(d) <= 1.0) tmin = fmin(tmin, first_turn(d, bx, sigma));
+    if ((dbits(d) & 0x7FFFFFFFFFFFFFFFll) <= dbits(1.0)) tmin = fmin(tmin, first_turn(d, bx, sigma));
   }
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
     const double Y = i == 0 ? hy : -hy;
     const double d = kappa * (Y - yc) * inv_A;
-    if (fabs(d) <= 1.0) tmin = fmin(tmin, first_turn(d, by, sigma));
+    if ((dbits(d) & 0x7FFFFFFFFFFFFFFFll) <= dbits(1.0)) tmin = fmin(tmin, first_turn(d, by, sigma));
   }
   return tmin == kInf ? kInf : tmin * inv_K;
 }
@@ -402,7 +403,9 @@ static __device__ __noinline__ double sample_compton_fp64(double E, TrackRng& rn
 static __device__ __noinline__ double sample_compton(double E, TrackRng& rng, double& cost, bool& ok,
                                                      const double* mt) {
   const double k = E / kMe;
-  if (!(k >= 1e-4 && k <= 1e6)) return sample_compton_fp64(E, rng, cost, ok, mt);
+  // 1e-4 <= k <= 1e6 on the bits (negative and NaN k fall outside)
+  if ((unsigned long long)(dbits(k) - dbits(1e-4)) > (unsigned long long)(dbits(1e6) - dbits(1e-4)))
+    return sample_compton_fp64(E, rng, cost, ok, mt);
   const double eps0 = 1.0 / (1.0 + 2.0 * k);
   const double eps0sq = eps0 * eps0;
   const double a1 = -fast_log(eps0, mt);
@@ -516,7 +519,9 @@ static __device__ __noinline__ double sample_moller_fp64(double T, double Tcut, 
 // attempt; the accepted attempt's eps is computed once, after the loop.
 static __device__ __noinline__ double sample_moller(double T, double Tcut, TrackRng& rng, bool& ok) {
   const double x = Tcut / T;
-  if (!(x >= 1e-8 && x < 0.5)) return sample_moller_fp64(T, Tcut, rng, ok);
+  // 1e-8 <= x < 1/2 on the bits (negative and NaN x fall outside)
+  if ((unsigned long long)(dbits(x) - dbits(1e-8)) >= (unsigned long long)(dbits(0.5) - dbits(1e-8)))
+    return sample_moller_fp64(T, Tcut, rng, ok);
   const double y = 1.0 - 2.0 * x;
   const float tmf = f32_trunc(T) * (float)(1.0 / kMe);  // g - 1
   const float gf = tmf + 1.0f;

@@ -25,12 +25,12 @@ __device__ __forceinline__ uint32_t row_of(const Params& p, uint32_t ev) { retur
 
 __device__ __forceinline__ int tally_bin(const Params& p, int layer, double z) {
   if (p.tally_mode == 1) return layer;
-  int b = (int)floor((z - p.z0) * p.zscale);
+  int b = __double2int_rd((z - p.z0) * p.zscale);  // (int)floor, one conversion
   return b < 0 ? 0 : (b > p.n_bins - 1 ? p.n_bins - 1 : b);
 }
 
 __device__ __forceinline__ void deposit(const Params& p, uint32_t ev, uint32_t prim, int layer, double z, double e) {
-  if (e == 0.0) return;
+  if ((__double_as_longlong(e) << 1) == 0ll) return;  // e == +-0 on the bits
   const int b = tally_bin(p, layer, z);
   atomicAdd(&p.tally[(size_t)row_of(p, ev) * p.n_bins + b], e);
   if (prim < p.hist_cap) atomicAdd(&p.hist_edep[(size_t)prim * p.n_bins + b], e);
@@ -230,7 +230,7 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
     act = up ? A_ZUP : A_ZDOWN;
   }
   double s_side = kInf;
-  const bool helix = charged && p.Bz != 0.0;
+  const bool helix = charged && (dbits(p.Bz) << 1) != 0ll;  // Bz != 0 on the bits
   Curvature cv{0.0, 0.0};
   if (helix) {
     cv = curvature(pt, E, p.Bz);
@@ -260,12 +260,13 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
   if (eloss) {
     // s_rng = R (R <= f) or a R + f (1 - a)(2 - f / R) >= a R + f (1 - a)
     double s_rng = kInf;
-    if (R <= kFinalR) {
+    // R, s and the bound are >= +0 (a NaN fails both tests, as in FP64)
+    if (dbits(R) <= dbits(kFinalR)) {
       s_rng = R;
-    } else if (kAlphaR * R + kFinalR * (1.0 - kAlphaR) <= s * kRangeMargin) {
+    } else if (dbits(kAlphaR * R + kFinalR * (1.0 - kAlphaR)) <= dbits(s * kRangeMargin)) {
       s_rng = kAlphaR * R + kFinalR * (1.0 - kAlphaR) * (2.0 - kFinalR / R);
     }
-    if (s_rng < s) {
+    if (dbits(s_rng) < dbits(s)) {  // s_rng >= +0; s >= +0 or -0 (then false either way)
       s = s_rng;
       act = A_RANGE;
     }
@@ -275,7 +276,7 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
   // tables; for a NaN mu the second test fails either way)
   if (dbits(mu) > 0 && nmfp <= s * mu * kLimitMargin) {
     const double s_int = nmfp / mu;
-    if (s_int < s) {
+    if (dbits(s_int) < dbits(s)) {  // s_int >= +0; s >= +0 or -0 (then false either way)
       s = s_int;
       interact = true;
     }
@@ -818,7 +819,7 @@ __device__ __forceinline__ bool along_one(const Params& p, uint32_t slot, uint8_
     return true;
   }
   const bool eloss = charged && (p.processes & PROC_ELOSS);
-  const bool helix = charged && p.Bz != 0.0;
+  const bool helix = charged && (dbits(p.Bz) << 1) != 0ll;  // Bz != 0 on the bits
   if (helix) {
     const Curvature cv = curvature(pt, E, p.Bz);
     if (p.field_cap > 0)
@@ -898,7 +899,7 @@ __device__ __forceinline__ bool compton_one(const Params& p, uint32_t slot) {
   const double u_phi = rng.uniform();
   const double E1 = eps * E;
   deposit(p, ev, prim, layer, z, E - E1);
-  if (E1 < p.cut_track) {
+  if (dbits(E1) < dbits(p.cut_track)) {  // on the bits: a negative E1 passes, a positive NaN fails, as in FP64
     deposit(p, ev, prim, layer, z, E1);
     release(p, slot, ev);
     return true;
@@ -1111,7 +1112,7 @@ __device__ __forceinline__ bool moller_one(const Params& p, uint32_t slot, uint8
   } else {
     deposit(p, ev, prim, layer, z, Td);
   }
-  if (E1 < p.cut_track) {
+  if (dbits(E1) < dbits(p.cut_track)) {  // on the bits: a negative E1 passes, a positive NaN fails, as in FP64
     deposit(p, ev, prim, layer, z, E1);
     release(p, slot, ev);
     return true;
@@ -1159,7 +1160,7 @@ __device__ __forceinline__ bool brems_one(const Params& p, uint32_t slot, uint8_
   } else {
     deposit(p, ev, prim, layer, z, k);
   }
-  if (E1 < p.cut_track) {
+  if (dbits(E1) < dbits(p.cut_track)) {  // on the bits: a negative E1 passes, a positive NaN fails, as in FP64
     deposit(p, ev, prim, layer, z, E1);
     release(p, slot, ev);
     return true;
