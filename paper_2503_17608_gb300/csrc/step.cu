@@ -249,11 +249,13 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
       if ((by > 0 ? d : -d) <= reach * fabs(uy)) s_side = fmin(s_side, d / uy);
     }
   }
-  if (s_side < s_geo) {
+  // most steps reach no side plane (s_side = inf): those skip the FP64
+  // comparison; s_geo < 0 on the bits (negative, not -0, which stays)
+  if (dbits(s_side) != dbits(kInf) && s_side < s_geo) {
     s_geo = s_side;
     act = A_SIDE;
   }
-  if (s_geo < 0.0) s_geo = 0.0;
+  if (dbits(s_geo) < 0 && dbits(s_geo) != dbits(-0.0)) s_geo = 0.0;
   if (!charged) CELER_LANE_MARK(LS_T_LIMIT + 3, t_mark);
 
   double s = s_geo;
