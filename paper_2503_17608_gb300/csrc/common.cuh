@@ -85,6 +85,8 @@ enum ErrorBits : uint32_t { ERR_RING_OVERFLOW = 1u, ERR_NO_PROGRESS = 2u, ERR_IT
 
 struct Tracks {
   double *x, *y, *z, *ux, *uy, *uz, *E, *nmfp, *step, *rpost;
+  double* gfrac;   // a photon's grid position in ln E (bin, fraction), kept
+  int32_t* gbin;   // from the step that sampled its n_mfp (same energy since)
   unsigned long long* tid;
   uint32_t *ctr, *event, *primary;
   int32_t* layer;

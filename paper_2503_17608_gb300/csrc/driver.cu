@@ -475,6 +475,8 @@ celer_status celer_create(const celer_problem* pb, celer_ctx** out) {
   CREATE_CUDA(dalloc(ctx, &t.nmfp, N));
   CREATE_CUDA(dalloc(ctx, &t.step, N));
   CREATE_CUDA(dalloc(ctx, &t.rpost, N));
+  CREATE_CUDA(dalloc(ctx, &t.gfrac, N));
+  CREATE_CUDA(dalloc(ctx, &t.gbin, N));
   CREATE_CUDA(dalloc(ctx, &t.tid, N));
   CREATE_CUDA(dalloc(ctx, &t.ctr, N));
   CREATE_CUDA(dalloc(ctx, &t.event, N));

@@ -189,14 +189,29 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
   // (the compiler keeps loads behind a call it cannot see into): +1-2 %
   const double x = t.x[slot], y = t.y[slot], z = t.z[slot];
   const double ux = t.ux[slot], uy = t.uy[slot], uz = t.uz[slot];
+  const double gfrac = t.gfrac[slot];
+  const int gbin = t.gbin[slot];
   // nmfp < 0 on the bits: -1 marks it unset; otherwise it is >= +0 (a
   // zero difference rounds to +0)
-  if (dbits(nmfp) < 0) nmfp = -fast_log(rng.uniform(), p.mtab);
+  const bool fresh = dbits(nmfp) < 0;
+  if (fresh) nmfp = -fast_log(rng.uniform(), p.mtab);
 
   const double2* mt = tab + lmat[layer] * (kCols * kGrid);
   const bool charged = pt != GAMMA;
   if (!charged) CELER_LANE_MARK(LS_T_LIMIT, t_mark);
-  const GridPos g = grid_pos(E, p.lnEmin, p.inv_dl, p.mtab);
+  // A photon's energy changes only where its n_mfp is reset (creation, an
+  // interaction), so the grid position computed at the step that samples
+  // n_mfp holds until the next such step: later steps reload it.
+  GridPos g;
+  if (charged || fresh) {
+    g = grid_pos(E, p.lnEmin, p.inv_dl, p.mtab);
+    if (!charged) {
+      t.gbin[slot] = g.bin;
+      t.gfrac[slot] = g.frac;
+    }
+  } else {
+    g = GridPos{gbin, gfrac};
+  }
   if (!charged) CELER_LANE_MARK(LS_T_LIMIT + 1, t_mark);
   double mu0, mu1, mu2 = 0.0;
   if (!charged) {
