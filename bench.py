@@ -807,24 +807,22 @@ def load_peaks():
 # kernel only; other kernels report no traffic. Keys: (workload, policy), and
 # (workload, policy, loop) for the asynchronous loop kernel.
 BYTES_PER_STEP = 160.0
-FP64_FLOP_PER_STEP = {("calorimeter-1gev", "none"): 131.0, ("calorimeter-1gev", "action"): 131.0,
-                      ("calorimeter-1gev", "action_type"): 131.0, ("calorimeter-1gev", "data"): 119.5,
-                      ("calorimeter-1gev", "local"): 119.5,
-                      ("calorimeter-field-10gev", "none"): 138.4, ("calorimeter-field-10gev", "action"): 138.4,
-                      ("calorimeter-field-10gev", "action_type"): 138.4, ("calorimeter-field-10gev", "data"): 129.5,
-                      ("calorimeter-field-10gev", "local"): 129.5,
-                      ("calorimeter-1gev", "local", "async"): 119.5, ("calorimeter-1gev", "data", "async"): 119.5,
-                      ("calorimeter-1gev", "local", "async-warps"): 119.6,
-                      # current per-warp kernel, smaller case of the workload (2,500
+FP64_FLOP_PER_STEP = {("calorimeter-1gev", "none"): 114.5, ("calorimeter-1gev", "action"): 114.5,
+                      ("calorimeter-1gev", "action_type"): 114.5, ("calorimeter-1gev", "data"): 103.0,
+                      ("calorimeter-1gev", "local"): 103.0,
+                      ("calorimeter-field-10gev", "none"): 116.4, ("calorimeter-field-10gev", "action"): 116.4,
+                      ("calorimeter-field-10gev", "action_type"): 116.4, ("calorimeter-field-10gev", "data"): 112.2,
+                      ("calorimeter-field-10gev", "local"): 112.2,
+                      # the 4 T workload's counts come from its smaller case (2,500
                       # primaries, 2^18 slots; the op counters take 3 passes)
-                      ("calorimeter-field-10gev", "local", "async-warps"): 128.8,
+                      ("calorimeter-field-10gev", "local", "async-warps"): 112.2,
                       ("water-cube-10mev", None): 119.5}
-DRAM_BYTES_PER_LAUNCH = {("calorimeter-field-10gev", "local", "async-warps"): 40.77e6}
+DRAM_BYTES_PER_LAUNCH = {("calorimeter-field-10gev", "local", "async-warps"): 49.54e6}
 # FP64 warp instructions per track-step (sm__inst_executed_pipe_fp64 / track-steps)
 # of the loop kernel's one-launch ncu captures: an FP64 warp instruction holds
 # its sub-partition's FP64 pipe for 64 cycles whatever its active lanes, so
 # these set how busy the FP64 pipe is at a measured track-step rate.
-FP64_WARP_INSTR_PER_STEP = {("calorimeter-field-10gev", "local", "async-warps"): 5.04}
+FP64_WARP_INSTR_PER_STEP = {("calorimeter-field-10gev", "local", "async-warps"): 4.05}
 FP64_PIPE_CYCLES_PER_WARP_INSTR = 64.0
 # FP64 peak of GB300 derived from its unit counts: 2 DFMA per SM-cycle
 # (ncu peak_sustained) x 152 SMs x 2.07 GHz x 2 flop
