@@ -816,7 +816,10 @@ FP64_FLOP_PER_STEP = {("calorimeter-1gev", "none"): 114.5, ("calorimeter-1gev", 
                       # the 4 T workload's counts come from its smaller case (2,500
                       # primaries, 2^18 slots; the op counters take 3 passes)
                       ("calorimeter-field-10gev", "local", "async-warps"): 112.2,
-                      ("water-cube-10mev", None): 119.5}
+                      # water cube: k_loop (none; action and action_type run the same
+                      # kernel and counted the same on the calorimeters) and the others
+                      ("water-cube-10mev", "none"): 292.2, ("water-cube-10mev", "action"): 292.2,
+                      ("water-cube-10mev", "action_type"): 292.2, ("water-cube-10mev", None): 288.2}
 DRAM_BYTES_PER_LAUNCH = {("calorimeter-field-10gev", "local", "async-warps"): 49.54e6}
 # FP64 warp instructions per track-step (sm__inst_executed_pipe_fp64 / track-steps)
 # of the loop kernel's one-launch ncu captures: an FP64 warp instruction holds
