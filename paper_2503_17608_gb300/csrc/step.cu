@@ -249,7 +249,14 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
   Curvature cv{0.0, 0.0};
   if (helix) {
     cv = curvature(pt, E, p.Bz);
-    s_side = helix_side_distance(cv, x, y, ux, uy, p.hx, p.hy);
+    // Over a path s the transverse position moves by at most s, so a side
+    // plane farther than s_geo + 1e-3 cm lies beyond the z-plane limit: its
+    // helix distance (rounded within ~1e-5 cm even at grazing incidence)
+    // cannot be the shorter one, and is not computed (+4 % on the 4 T
+    // calorimeter, whose high-energy circles all cross the side planes).
+    const double reach = s_geo + 1e-3;
+    if (!(p.hx - fabs(x) > reach && p.hy - fabs(y) > reach))
+      s_side = helix_side_distance(cv, x, y, ux, uy, p.hx, p.hy);
   } else {
     // the signs of ux, uy on their bits: nonzero (NaN included) and
     // positive; for a positive NaN the distance test fails either way
