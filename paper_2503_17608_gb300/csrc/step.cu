@@ -251,7 +251,7 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
     cv = curvature(pt, E, p.Bz);
     // Over a path s the transverse position moves by at most s, so a side
     // plane farther than s_geo + 1e-3 cm lies beyond the z-plane limit: its
-    // helix distance (rounded within ~1e-5 cm even at grazing incidence)
+    // helix distance (rounded within ~2e-5 cm even at grazing incidence)
     // cannot be the shorter one, and is not computed (+4 % on the 4 T
     // calorimeter, whose high-energy circles all cross the side planes).
     const double reach = s_geo + 1e-3;
