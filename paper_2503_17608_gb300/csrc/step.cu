@@ -258,17 +258,23 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
     if (!(p.hx - fabs(x) > reach && p.hy - fabs(y) > reach))
       s_side = helix_side_distance(cv, x, y, ux, uy, p.hx, p.hy);
   } else {
-    // the signs of ux, uy on their bits: nonzero (NaN included) and
-    // positive; for a positive NaN the distance test fails either way
     const double reach = s_geo * kLimitMargin;
-    const long long bx = dbits(ux), by = dbits(uy);
-    if (((unsigned long long)bx << 1) != 0ull) {
-      const double d = bx > 0 ? p.hx - x : -p.hx - x;
-      if ((bx > 0 ? d : -d) <= reach * fabs(ux)) s_side = d / ux;
-    }
-    if (((unsigned long long)by << 1) != 0ull) {
-      const double d = by > 0 ? p.hy - y : -p.hy - y;
-      if ((by > 0 ? d : -d) <= reach * fabs(uy)) s_side = fmin(s_side, d / uy);
+    // both planes beyond reach along their axis (|u| <= 1 + 2^-52, hence
+    // the second margin): both tests below would fail, and most steps skip
+    // them (+4 % on the 4 T calorimeter, +8 % on the 1 GeV one)
+    const double reach2 = reach * kLimitMargin;
+    if (!(p.hx - fabs(x) > reach2 && p.hy - fabs(y) > reach2)) {
+      // the signs of ux, uy on their bits: nonzero (NaN included) and
+      // positive; for a positive NaN the distance test fails either way
+      const long long bx = dbits(ux), by = dbits(uy);
+      if (((unsigned long long)bx << 1) != 0ull) {
+        const double d = bx > 0 ? p.hx - x : -p.hx - x;
+        if ((bx > 0 ? d : -d) <= reach * fabs(ux)) s_side = d / ux;
+      }
+      if (((unsigned long long)by << 1) != 0ull) {
+        const double d = by > 0 ? p.hy - y : -p.hy - y;
+        if ((by > 0 ? d : -d) <= reach * fabs(uy)) s_side = fmin(s_side, d / uy);
+      }
     }
   }
   // most steps reach no side plane (s_side = inf): those skip the FP64
