@@ -246,9 +246,7 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
   }
   double s_side = kInf;
   const bool helix = charged && (dbits(p.Bz) << 1) != 0ll;  // Bz != 0 on the bits
-  Curvature cv{0.0, 0.0};
   if (helix) {
-    cv = curvature(pt, E, p.Bz);
     // Over a path s the transverse position moves by at most s, so a side
     // plane farther than s_geo + 1e-3 cm lies beyond the z-plane limit: its
     // helix distance (rounded within ~2e-5 cm even at grazing incidence)
@@ -256,7 +254,7 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
     // calorimeter, whose high-energy circles all cross the side planes).
     const double reach = s_geo + 1e-3;
     if (!(p.hx - fabs(x) > reach && p.hy - fabs(y) > reach))
-      s_side = helix_side_distance(cv, x, y, ux, uy, p.hx, p.hy);
+      s_side = helix_side_distance(curvature(pt, E, p.Bz), x, y, ux, uy, p.hx, p.hy);
   } else {
     const double reach = s_geo * kLimitMargin;
     // both planes beyond reach along their axis (|u| <= 1 + 2^-52, hence
@@ -318,10 +316,13 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
     // Runge-Kutta field propagation with a substep cap (Sec. 3.3): a step
     // needing more than `cap` substeps of 0.1 rad of turn is cut there and
     // ends without a crossing or an interaction, to go on next iteration
-    if (helix && p.field_cap > 0 && s * fabs(cv.kappa) > kRkTurn * p.field_cap) {
-      s = kRkTurn * p.field_cap / fabs(cv.kappa);
-      act = A_FIELD;
-      interact = false;
+    if (helix && p.field_cap > 0) {
+      const double kappa = curvature(pt, E, p.Bz).kappa;
+      if (s * fabs(kappa) > kRkTurn * p.field_cap) {
+        s = kRkTurn * p.field_cap / fabs(kappa);
+        act = A_FIELD;
+        interact = false;
+      }
     }
     nmfp -= s * mu;
   }
