@@ -807,25 +807,25 @@ def load_peaks():
 # kernel only; other kernels report no traffic. Keys: (workload, policy), and
 # (workload, policy, loop) for the asynchronous loop kernel.
 BYTES_PER_STEP = 160.0
-FP64_FLOP_PER_STEP = {("calorimeter-1gev", "none"): 114.5, ("calorimeter-1gev", "action"): 114.5,
-                      ("calorimeter-1gev", "action_type"): 114.5, ("calorimeter-1gev", "data"): 103.0,
-                      ("calorimeter-1gev", "local"): 103.0,
-                      ("calorimeter-field-10gev", "none"): 116.4, ("calorimeter-field-10gev", "action"): 116.4,
-                      ("calorimeter-field-10gev", "action_type"): 116.4, ("calorimeter-field-10gev", "data"): 112.2,
-                      ("calorimeter-field-10gev", "local"): 112.2,
+FP64_FLOP_PER_STEP = {("calorimeter-1gev", "none"): 97.0, ("calorimeter-1gev", "action"): 97.0,
+                      ("calorimeter-1gev", "action_type"): 97.0, ("calorimeter-1gev", "data"): 86.4,
+                      ("calorimeter-1gev", "local"): 86.4, ("calorimeter-1gev", "local", "async-warps"): 86.5,
+                      ("calorimeter-field-10gev", "none"): 95.7, ("calorimeter-field-10gev", "action"): 95.7,
+                      ("calorimeter-field-10gev", "action_type"): 95.7, ("calorimeter-field-10gev", "data"): 92.5,
+                      ("calorimeter-field-10gev", "local"): 92.5,
                       # the 4 T workload's counts come from its smaller case (2,500
                       # primaries, 2^18 slots; the op counters take 3 passes)
-                      ("calorimeter-field-10gev", "local", "async-warps"): 112.2,
+                      ("calorimeter-field-10gev", "local", "async-warps"): 92.5,
                       # water cube: k_loop (none; action and action_type run the same
                       # kernel and counted the same on the calorimeters) and the others
-                      ("water-cube-10mev", "none"): 292.2, ("water-cube-10mev", "action"): 292.2,
-                      ("water-cube-10mev", "action_type"): 292.2, ("water-cube-10mev", None): 288.2}
-DRAM_BYTES_PER_LAUNCH = {("calorimeter-field-10gev", "local", "async-warps"): 49.54e6}
+                      ("water-cube-10mev", "none"): 290.5, ("water-cube-10mev", "action"): 290.5,
+                      ("water-cube-10mev", "action_type"): 290.5, ("water-cube-10mev", None): 286.7}
+DRAM_BYTES_PER_LAUNCH = {("calorimeter-field-10gev", "local", "async-warps"): 49.74e6}
 # FP64 warp instructions per track-step (sm__inst_executed_pipe_fp64 / track-steps)
 # of the loop kernel's one-launch ncu captures: an FP64 warp instruction holds
 # its sub-partition's FP64 pipe for 64 cycles whatever its active lanes, so
 # these set how busy the FP64 pipe is at a measured track-step rate.
-FP64_WARP_INSTR_PER_STEP = {("calorimeter-field-10gev", "local", "async-warps"): 4.05}
+FP64_WARP_INSTR_PER_STEP = {("calorimeter-field-10gev", "local", "async-warps"): 3.36}
 FP64_PIPE_CYCLES_PER_WARP_INSTR = 64.0
 # FP64 peak of GB300 derived from its unit counts: 2 DFMA per SM-cycle
 # (ncu peak_sustained) x 152 SMs x 2.07 GHz x 2 flop
