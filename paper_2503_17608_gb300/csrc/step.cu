@@ -30,7 +30,7 @@ __device__ __forceinline__ int tally_bin(const Params& p, int layer, double z) {
 }
 
 __device__ __forceinline__ void deposit(const Params& p, uint32_t ev, uint32_t prim, int layer, double z, double e) {
-  if ((__double_as_longlong(e) << 1) == 0ll) return;  // e == +-0 on the bits
+  if (((unsigned long long)__double_as_longlong(e) << 1) == 0ull) return;  // e == +-0 on the bits
   const int b = tally_bin(p, layer, z);
   atomicAdd(&p.tally[(size_t)row_of(p, ev) * p.n_bins + b], e);
   if (prim < p.hist_cap) atomicAdd(&p.hist_edep[(size_t)prim * p.n_bins + b], e);
@@ -245,7 +245,7 @@ __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, co
     act = up ? A_ZUP : A_ZDOWN;
   }
   double s_side = kInf;
-  const bool helix = charged && (dbits(p.Bz) << 1) != 0ll;  // Bz != 0 on the bits
+  const bool helix = charged && ((unsigned long long)dbits(p.Bz) << 1) != 0ull;  // Bz != 0 on the bits
   if (helix) {
     // Over a path s the transverse position moves by at most s, so a side
     // plane farther than s_geo + 1e-3 cm lies beyond the z-plane limit: its
@@ -850,7 +850,7 @@ __device__ __forceinline__ bool along_one(const Params& p, uint32_t slot, uint8_
     return true;
   }
   const bool eloss = charged && (p.processes & PROC_ELOSS);
-  const bool helix = charged && (dbits(p.Bz) << 1) != 0ll;  // Bz != 0 on the bits
+  const bool helix = charged && ((unsigned long long)dbits(p.Bz) << 1) != 0ull;  // Bz != 0 on the bits
   if (helix) {
     const Curvature cv = curvature(pt, E, p.Bz);
     if (p.field_cap > 0)
