@@ -803,8 +803,8 @@ def load_peaks():
 # secondaries or scratch) and thread-level FP64 operations
 # (2 x DFMA + DADD + DMUL) counted by ncu on the loop kernels (the ncu
 # summaries under profiles/, one per kernel and workload). DRAM bytes per
-# launch come from a one-pass full-size capture of the current headline
-# kernel only; other kernels report no traffic. Keys: (workload, policy), and
+# launch come from one-pass full-size captures of the per-warp kernel on the
+# two calorimeters; other kernels report no traffic. Keys: (workload, policy), and
 # (workload, policy, loop) for the asynchronous loop kernel.
 BYTES_PER_STEP = 160.0
 FP64_FLOP_PER_STEP = {("calorimeter-1gev", "none"): 97.0, ("calorimeter-1gev", "action"): 97.0,
@@ -820,12 +820,14 @@ FP64_FLOP_PER_STEP = {("calorimeter-1gev", "none"): 97.0, ("calorimeter-1gev", "
                       # kernel and counted the same on the calorimeters) and the others
                       ("water-cube-10mev", "none"): 290.5, ("water-cube-10mev", "action"): 290.5,
                       ("water-cube-10mev", "action_type"): 290.5, ("water-cube-10mev", None): 286.7}
-DRAM_BYTES_PER_LAUNCH = {("calorimeter-field-10gev", "local", "async-warps"): 49.74e6}
+DRAM_BYTES_PER_LAUNCH = {("calorimeter-field-10gev", "local", "async-warps"): 49.74e6,
+                         ("calorimeter-1gev", "local", "async-warps"): 3.39e6}
 # FP64 warp instructions per track-step (sm__inst_executed_pipe_fp64 / track-steps)
 # of the loop kernel's one-launch ncu captures: an FP64 warp instruction holds
 # its sub-partition's FP64 pipe for 64 cycles whatever its active lanes, so
 # these set how busy the FP64 pipe is at a measured track-step rate.
-FP64_WARP_INSTR_PER_STEP = {("calorimeter-field-10gev", "local", "async-warps"): 3.36}
+FP64_WARP_INSTR_PER_STEP = {("calorimeter-field-10gev", "local", "async-warps"): 3.36,
+                            ("calorimeter-1gev", "local", "async-warps"): 8.04}
 FP64_PIPE_CYCLES_PER_WARP_INSTR = 64.0
 # FP64 peak of GB300 derived from its unit counts: 2 DFMA per SM-cycle
 # (ncu peak_sustained) x 152 SMs x 2.07 GHz x 2 flop
