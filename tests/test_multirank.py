@@ -128,8 +128,12 @@ def test_bench_roofline_names_the_timed_kernel():
     assert abs(r["fp64_pipe"]["busy_frac"] - wi * 7959709.0 * 64 / (5e-3 * 4 * 152 * 2.07e9)) < 1e-12
     # without a measured peak the derived one is used
     assert bench.roofline_loop(*key, 1.0, 1.0)["peak"] == bench.FP64_PEAK_TFLOPS
-    # other kernels were not captured whole: no traffic figure
-    assert bench.roofline_loop("calorimeter-1gev", "local", "async-warps", 1.0, 1.0)["traffic"] is None
+    # the per-warp kernel was captured whole on both calorimeters; other kernels
+    # were not: no traffic figure
+    k1 = ("calorimeter-1gev", "local", "async-warps")
+    assert bench.roofline_loop(*k1, 1.0, 1.0)["traffic"] == bench.DRAM_BYTES_PER_LAUNCH[k1]
+    assert bench.roofline_loop("calorimeter-1gev", "local", "persistent", 1.0, 1.0)["traffic"] is None
+    assert bench.roofline_loop("calorimeter-1gev", "local", "async", 1.0, 1.0)["traffic"] is None
     assert bench.roofline_loop("calorimeter-1gev", "local", "persistent", 1.0, 1.0)["kernel"] == "k_loop_local"
     assert bench.roofline_loop("calorimeter-1gev", "none", "persistent", 1.0, 1.0)["kernel"] == "k_loop"
     # a reduced workload carries no traffic figure (the captures were of the full one)
