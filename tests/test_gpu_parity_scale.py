@@ -127,3 +127,21 @@ def test_narrow_world_field_histories(policy, mode, warps):
     el = prim["ptype"] == wl.ELECTRON
     assert np.mean(o0["hist"]["steps"][el] != o["hist"]["steps"][el]) > 0.4
     assert o["hist"]["escaped"].sum() > 0.05 * prim["E"].sum()
+
+
+@pytest.mark.parametrize("policy,mode,warps", [(wl.SORT_LOCAL, binding.LOOP_ASYNC, True),
+                                               (wl.SORT_NONE, binding.LOOP_PERSISTENT, False)])
+def test_narrow_world_line_histories(policy, mode, warps):
+    # the same narrow world without the field: straight tracks leave through
+    # the side planes, so the step limit's straight-line side tests (both
+    # planes tested together against the z-plane limit first) decide often
+    prob = wl.calorimeter_problem(1 << 16, Bz=0.0, half_x=2.0, half_y=2.0)
+    prim = narrow_primaries(seed=6)
+    g = run_headline(prob, prim, policy=policy, mode=mode, warps=warps)
+    o = run_oracle(prob, prim)
+    frac, mask = match_fraction(g, o)
+    assert frac >= NARROW_MIN, frac
+    np.testing.assert_allclose(g["hist"]["escaped"][mask], o["hist"]["escaped"][mask], rtol=1e-9, atol=1e-9)
+    assert_history_conservation(prim, g["hist"])
+    assert_conservation(prim, g["tally"])
+    assert o["hist"]["escaped"].sum() > 0.05 * prim["E"].sum()
