@@ -177,8 +177,7 @@ __device__ __forceinline__ uint8_t key_of(int policy, uint8_t ptype, uint8_t act
 __device__ __forceinline__ uint8_t step_limit(const Params& p, uint32_t slot, const double2* tab, const double* zb,
                                               const int32_t* lmat) {
   const Tracks& t = p.trk;
-  long long t_mark = CELER_LANE_CLOCK();  // diagnostic build only
-  (void)t_mark;
+  [[maybe_unused]] long long t_mark = CELER_LANE_CLOCK();  // diagnostic build only
   const double E = t.E[slot];
   CELER_LANES(LS_STEP_LIMIT);
   const uint8_t pt = t.ptype[slot];
